@@ -1,0 +1,221 @@
+"""Seeded synthetic inputs for the MoA generalized inner / outer product.
+
+This module is shared by the CPU oracle (``oracle/``), the tests and
+``bench.py``.  It holds no arithmetic of the method itself: it only draws
+numbers, rounds them to the storage type an operand is given in, and packs
+Boolean arrays into the bit layout of the C ABI.
+
+Generator
+---------
+SplitMix64 (Steele, Lea & Flood, "Fast splittable pseudorandom number
+generators", OOPSLA 2014) is counter based: its i-th output is
+``mix(key + (i + 1) * GAMMA)``.  That lets numpy draw any slice of a stream
+in one vectorised pass, and gives the same bytes on x86-64 and aarch64
+(integer arithmetic plus IEEE float ops only, no libm transcendental).
+Each (seed, stream) pair selects an independent key.
+
+Workload recipes follow the five benchmark configurations of the method's
+inner product (Eq. 2) and outer product (Eq. 1); the shapes, value
+distributions and structure are stated beside each function.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def _mix(z: np.ndarray) -> np.ndarray:
+    """SplitMix64 finaliser (variant 13 of Stafford's mixers)."""
+    z = np.asarray(z, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+def _key(seed: int, stream: int) -> np.uint64:
+    with np.errstate(over="ignore"):
+        k = _mix(np.uint64(seed & 0xFFFFFFFFFFFFFFFF) * GAMMA + np.uint64(stream & 0xFFFFFFFF) + np.uint64(1))
+        return np.uint64(_mix(k ^ np.uint64(0xD1B54A32D192ED03)))
+
+
+def u64(seed: int, stream: int, n: int, offset: int = 0) -> np.ndarray:
+    """Outputs ``offset .. offset+n-1`` of the SplitMix64 stream (seed, stream)."""
+    key = _key(seed, stream)
+    idx = np.arange(offset + 1, offset + n + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        return _mix(key + idx * GAMMA)
+
+
+def uniform01(seed: int, stream: int, n: int) -> np.ndarray:
+    """Doubles in [0, 1) from the top 53 bits of each output."""
+    return (u64(seed, stream, n) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def uniform(seed: int, stream: int, shape, lo: float, hi: float) -> np.ndarray:
+    n = int(np.prod(shape, dtype=np.int64))
+    return (lo + (hi - lo) * uniform01(seed, stream, n)).reshape(shape)
+
+
+def int_uniform(seed: int, stream: int, shape, lo: int, hi: int) -> np.ndarray:
+    """Integers uniform in [lo, hi] (inclusive) as int32; modulo bias < 2^-40."""
+    n = int(np.prod(shape, dtype=np.int64))
+    span = np.uint64(hi - lo + 1)
+    v = (u64(seed, stream, n) % span).astype(np.int64) + lo
+    return v.astype(np.int32).reshape(shape)
+
+
+def bernoulli(seed: int, stream: int, shape, p: float) -> np.ndarray:
+    return uniform01(seed, stream, int(np.prod(shape, dtype=np.int64))).reshape(shape) < p
+
+
+def log_uniform_signed(seed: int, stream: int, shape, lo_exp2: int = -13, hi_exp2: int = 13) -> np.ndarray:
+    """Random sign times a magnitude spread evenly over octaves.
+
+    Stand-in for ``sign * 10**U(-4, 4)``: the binary exponent is uniform over
+    the integers in [lo_exp2, hi_exp2) and the significand uniform in [1, 2),
+    so magnitudes cover 2^-13 .. 2^13 (1.2e-4 .. 8.2e3), every octave equally
+    likely.  Built with ``ldexp`` only, so it is bit-identical across hosts.
+    """
+    n = int(np.prod(shape, dtype=np.int64))
+    r = u64(seed, stream, n)
+    e = (r % np.uint64(hi_exp2 - lo_exp2)).astype(np.int64) + lo_exp2
+    f = 1.0 + ((r >> np.uint64(11)) & np.uint64((1 << 52) - 1)).astype(np.float64) * (2.0 ** -52)
+    s = np.where((r >> np.uint64(10)) & np.uint64(1), -1.0, 1.0)
+    return (s * np.ldexp(f, e)).reshape(shape)
+
+
+# ---------------------------------------------------------------- rounding
+def to_f32(x: np.ndarray) -> np.ndarray:
+    """Round to FP32 (IEEE round-to-nearest-even, numpy's cast)."""
+    return np.asarray(x, dtype=np.float64).astype(np.float32)
+
+
+def f32_to_bf16_bits(x: np.ndarray) -> np.ndarray:
+    """FP32 -> bfloat16 bit patterns, round-to-nearest-even (finite inputs and inf)."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    nan = (u & np.uint64(0x7FFFFFFF)) > np.uint64(0x7F800000)
+    r = (u + np.uint64(0x7FFF) + ((u >> np.uint64(16)) & np.uint64(1))) >> np.uint64(16)
+    r = np.where(nan, (u >> np.uint64(16)) | np.uint64(0x40), r)
+    return r.astype(np.uint16)
+
+
+def bf16_bits_to_f64(b: np.ndarray) -> np.ndarray:
+    return (np.asarray(b, dtype=np.uint16).astype(np.uint32) << np.uint32(16)).view(np.float32).astype(np.float64)
+
+
+def to_bf16(x: np.ndarray):
+    """Round to bfloat16 via FP32 (f64 -> f32 RNE -> bf16 RNE).
+
+    Returns (bits as uint16, the exact values as float64)."""
+    b = f32_to_bf16_bits(to_f32(x))
+    return b, bf16_bits_to_f64(b)
+
+
+# ---------------------------------------------------------------- bit packing
+def pack_bits(x: np.ndarray) -> np.ndarray:
+    """Row-major ravel packed as a bit stream: element e -> word e//32, bit e%32
+    (LSB first); the last word is zero-padded.  Matches the MOA_B1_U32 layout."""
+    flat = np.ascontiguousarray(x, dtype=bool).ravel()
+    nw = (flat.size + 31) // 32
+    pad = np.zeros(nw * 32, dtype=np.uint64)
+    pad[: flat.size] = flat
+    w = pad.reshape(nw, 32) << np.arange(32, dtype=np.uint64)
+    return w.sum(axis=1).astype(np.uint32)
+
+
+def unpack_bits(words: np.ndarray, n: int) -> np.ndarray:
+    w = np.asarray(words, dtype=np.uint32).astype(np.uint64)
+    bits = (w[:, None] >> np.arange(32, dtype=np.uint64)) & np.uint64(1)
+    return bits.ravel()[:n].astype(bool)
+
+
+# ---------------------------------------------------------------- workloads
+# Inner product (Eq. 2), FP64, rank 4 x rank 3.
+C1_SHAPE_A = (16, 12, 8, 64)
+C1_SHAPE_B = (64, 24, 20)
+C1_SHAPE_B_OUTER = (4, 5)
+# Semirings, rank 3 x rank 3.
+C3_SHAPE_A = (32, 128, 512)
+C3_SHAPE_B = (512, 64, 64)
+# Memory-bound outer product (Eq. 1): 128*64*32 x 32*64 = 536,870,912 outputs.
+C4_SHAPE_A = (128, 64, 32)
+C4_SHAPE_B = (32, 64)
+C2_SIZES = (256, 512, 1024, 2048, 4096, 8192)
+
+
+def rank4x3_f64(seed: int = 1, shape_a=C1_SHAPE_A, shape_b=C1_SHAPE_B):
+    """Plain-method inner product inputs: U(-1, 1) FP64, A <16,12,8,64>, B <64,24,20>."""
+    return uniform(seed, 0, shape_a, -1.0, 1.0), uniform(seed, 1, shape_b, -1.0, 1.0)
+
+
+def outer_second_f64(seed: int = 1, shape=C1_SHAPE_B_OUTER):
+    """Second outer-product operand for the plain method: U(-1, 1), shape <4,5>."""
+    return uniform(seed, 2, shape, -1.0, 1.0)
+
+
+def square(n: int, dist: str = "uniform", seed: int = 2, m: int | None = None, k: int | None = None):
+    """Square (or m x k . k x n) matrix-multiply operands as FP64.
+
+    dist = "uniform": U(-1, 1); dist = "loguniform": random sign times an
+    octave-uniform magnitude over 2^-13 .. 2^13 (see ``log_uniform_signed``)."""
+    m = n if m is None else m
+    k = n if k is None else k
+    tag = 0 if dist == "uniform" else 10
+    if dist == "uniform":
+        return uniform(seed, tag, (m, k), -1.0, 1.0), uniform(seed, tag + 1, (k, n), -1.0, 1.0)
+    if dist == "loguniform":
+        return log_uniform_signed(seed, tag, (m, k)), log_uniform_signed(seed, tag + 1, (k, n))
+    raise ValueError(dist)
+
+
+def semiring_inputs(kind: str, seed: int = 3, shape_a=C3_SHAPE_A, shape_b=C3_SHAPE_B):
+    """Operands of the semiring workloads.
+
+    kind: "tropical" ((min,+) and (max,+)): U(0, 100) FP32 with 5% +inf;
+          "tropical_finite": U(0, 100) FP32, no inf;
+          "maxmul": U(0, 1) FP32;
+          "int32": integers uniform in [-128, 127];
+          "bool": Bernoulli(0.05) (returned unpacked, as bool arrays).
+    """
+    if kind == "tropical":
+        a = to_f32(uniform(seed, 20, shape_a, 0.0, 100.0))
+        b = to_f32(uniform(seed, 21, shape_b, 0.0, 100.0))
+        a[bernoulli(seed, 22, shape_a, 0.05)] = np.inf
+        b[bernoulli(seed, 23, shape_b, 0.05)] = np.inf
+        return a, b
+    if kind == "tropical_finite":
+        return to_f32(uniform(seed, 24, shape_a, 0.0, 100.0)), to_f32(uniform(seed, 25, shape_b, 0.0, 100.0))
+    if kind == "maxmul":
+        return to_f32(uniform(seed, 26, shape_a, 0.0, 1.0)), to_f32(uniform(seed, 27, shape_b, 0.0, 1.0))
+    if kind == "int32":
+        return int_uniform(seed, 28, shape_a, -128, 127), int_uniform(seed, 29, shape_b, -128, 127)
+    if kind == "bool":
+        return bernoulli(seed, 30, shape_a, 0.05), bernoulli(seed, 31, shape_b, 0.05)
+    raise ValueError(kind)
+
+
+def outer_inputs(op: str, dtype: str, seed: int = 4, shape_a=C4_SHAPE_A, shape_b=C4_SHAPE_B):
+    """Outer-product operands: U(-1, 1); for "/" the divisor is U(-1, 1)
+    conditioned on |b| >= 0.1 (drawn directly as sign * U(0.1, 1)).
+    dtype "f32" -> float32 arrays; "bf16" -> (uint16 bits, float64 values)
+    pairs; "i32" -> integers uniform in [-1000, 1000]; "f64" -> float64."""
+    if dtype == "i32":
+        return int_uniform(seed, 40, shape_a, -1000, 1000), int_uniform(seed, 41, shape_b, -1000, 1000)
+    a = uniform(seed, 42, shape_a, -1.0, 1.0)
+    if op == "div":
+        mag = uniform(seed, 43, shape_b, 0.1, 1.0)
+        sgn = np.where(bernoulli(seed, 44, shape_b, 0.5), -1.0, 1.0)
+        b = sgn * mag
+    else:
+        b = uniform(seed, 43, shape_b, -1.0, 1.0)
+    if dtype == "f64":
+        return a, b
+    if dtype == "f32":
+        return to_f32(a), to_f32(b)
+    if dtype == "bf16":
+        return to_bf16(a), to_bf16(b)
+    raise ValueError(dtype)

@@ -1,0 +1,61 @@
+"""The seeded input generators: published test vectors, determinism, the
+stated distributions, the bf16 rounding and the bit-packing layout."""
+import numpy as np
+import pytest
+
+import synth
+
+
+def test_splitmix64_published_vector():
+    # SplitMix64 with state 1234567: the first five outputs of the reference C
+    # implementation (Vigna, splitmix64.c).
+    want = [6457827717110365317, 3203168211198807973, 9817491932198370423, 4593380528125082431,
+            16408922859458223821]
+    with np.errstate(over="ignore"):
+        got = [int(synth._mix(np.uint64(1234567) + np.uint64(i + 1) * synth.GAMMA)) for i in range(5)]
+    assert got == want
+
+
+def test_streams_are_deterministic_and_sliceable():
+    a = synth.u64(5, 3, 1000)
+    assert np.array_equal(a, synth.u64(5, 3, 1000))
+    assert np.array_equal(a[400:700], synth.u64(5, 3, 300, offset=400))
+    assert not np.array_equal(a, synth.u64(5, 4, 1000))
+    assert not np.array_equal(a, synth.u64(6, 3, 1000))
+
+
+def test_distributions():
+    u = synth.uniform(1, 0, (200000,), -1, 1)
+    assert u.min() >= -1 and u.max() < 1 and abs(u.mean()) < 0.01
+    t, _ = synth.semiring_inputs("tropical", shape_a=(64, 512), shape_b=(512, 8))
+    frac = np.isinf(t).mean()
+    assert 0.04 < frac < 0.06 and np.nanmin(t) >= 0 and t[np.isfinite(t)].max() < 100
+    i, _ = synth.semiring_inputs("int32", shape_a=(64, 512), shape_b=(512, 8))
+    assert i.min() == -128 and i.max() == 127
+    lg = synth.log_uniform_signed(2, 0, (100000,))
+    m = np.abs(lg)
+    assert m.min() >= 2.0 ** -13 and m.max() < 2.0 ** 13
+    assert 0.45 < (lg < 0).mean() < 0.55
+    _, b = synth.outer_inputs("div", "f32")
+    assert np.abs(b).min() >= np.float32(0.1)
+    bb, _ = synth.semiring_inputs("bool", shape_a=(64, 512), shape_b=(512, 8))
+    assert 0.04 < bb.mean() < 0.06
+
+
+def test_bf16_rounding_matches_torch():
+    torch = pytest.importorskip("torch")
+    x = np.concatenate([synth.uniform(3, 0, (5000,), -1, 1), synth.log_uniform_signed(3, 1, (5000,), -120, 120),
+                        np.array([0.0, -0.0, np.inf, -np.inf, 1.00390625, 1.01171875])]).astype(np.float32)
+    ours = synth.f32_to_bf16_bits(x).view(np.int16)
+    ref = torch.from_numpy(x).to(torch.bfloat16).view(torch.int16).numpy()
+    assert np.array_equal(ours, ref)
+
+
+def test_bit_packing_layout():
+    x = np.zeros((3, 40), dtype=bool)
+    x[0, 0] = x[0, 33] = x[2, 39] = True  # elements 0, 33, 119
+    w = synth.pack_bits(x)
+    assert w.dtype == np.uint32 and w.size == 4
+    assert w[0] == 1 and w[1] == 2 and w[2] == 0 and w[3] == (1 << (119 - 96))
+    y = synth.semiring_inputs("bool", shape_a=(7, 96), shape_b=(96, 3))[0]
+    assert np.array_equal(synth.unpack_bits(synth.pack_bits(y), y.size).reshape(y.shape), y)
