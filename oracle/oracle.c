@@ -292,7 +292,8 @@ static int outer_shape(int rankA, const int64_t *shA, int rankB, const int64_t *
 }
 
 /*
- * Eq. (1) with a general binary operator (the paper names + - * /).
+ * Eq. (1) with a general binary operator (the paper names + - * / and
+ * allows any binary operation; min and max are provided as well).
  * Operands are given exactly as doubles.  out_kind 0: the op in binary64;
  * 1: the op correctly rounded to FP32; 2: the FP32 result rounded again to
  * bfloat16 (RNE), stored as bit patterns.
@@ -303,7 +304,7 @@ int oracle_outer_f(int op, int rankA, const int64_t *shA, const double *A, int r
     int64_t shC[MAXRANK], ic[MAXRANK];
     int st = outer_shape(rankA, shA, rankB, shB, &rC, shC);
     if (st) return st;
-    if (op < OP_ADD || op > OP_DIV) return ORC_ERR_OP;
+    if (op < OP_ADD || op > OP_MAX) return ORC_ERR_OP;
     const int64_t nC = tau(rC, shC);
     for (int64_t k = 0; k < n_out; ++k) {
         int64_t o = out_idx ? out_idx[k] : k;
@@ -311,7 +312,15 @@ int oracle_outer_f(int op, int rankA, const int64_t *shA, const double *A, int r
         psi_index(o, rC, shC, ic);
         double a = A[psi_offset(rankA, shA, ic)];
         double b = B[psi_offset(rankB, shB, ic + rankA)];
-        double c = op == OP_ADD ? a + b : op == OP_SUB ? a - b : op == OP_MUL ? a * b : a / b;
+        double c;
+        switch (op) {
+        case OP_ADD: c = a + b; break;
+        case OP_SUB: c = a - b; break;
+        case OP_MUL: c = a * b; break;
+        case OP_DIV: c = a / b; break;
+        case OP_MIN: c = fmin(a, b); break;
+        default: c = fmax(a, b); break;
+        }
         if (out_kind == 0) ((double *)out)[k] = c;
         else if (out_kind == 1) ((float *)out)[k] = (float)c;
         else ((uint16_t *)out)[k] = f32_to_bf16_rne((float)c);

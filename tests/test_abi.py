@@ -1,0 +1,97 @@
+"""The C ABI library without a GPU: it loads, exports every function that
+include/moa.h declares, and its host-side validation rejects bad calls
+before any launch (these calls never reach CUDA)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+import paper_0907_0792_gb300 as moa
+from paper_0907_0792_gb300 import _build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    _build.build()
+    return moa.lib()
+
+
+def _declared():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"^[A-Za-z_][\w\s\*]*?\b(moa_\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol(L):
+    names = _declared()
+    assert "moa_inner" in names and "moa_outer" in names and len(names) >= 10
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_inner_shape_fig1_example(L):
+    assert moa.moa_inner_shape((2, 3), (3, 4)) == (2, 4)
+    assert moa.moa_inner_shape((16, 12, 8, 64), (64, 24, 20)) == (16, 12, 8, 24, 20)
+    assert moa.moa_outer_shape((16, 12, 8, 64), (4, 5)) == (16, 12, 8, 64, 4, 5)
+    assert moa.moa_outer_shape((), (3,)) == (3,)
+    with pytest.raises(moa.MoaError) as e:
+        moa.moa_inner_shape((2, 3), (4, 3))
+    assert e.value.status == 3
+
+
+def _inner_status(reduce, combine, dtype, form, sa, sb, out_dtype, A=0x1000, B=0x2000, out=0x3000):
+    return moa.moa_inner(reduce, combine, dtype, form, sa, A, sb, B, out, out_dtype, stream=0, check=False)
+
+
+def test_validation_before_launch(L):
+    # shape mismatch (Eq. 2 needs rho A[-1] == rho B[0])
+    assert _inner_status("add", "mul", "f64", "native", (4, 5), (6, 7), "f64") == 3
+    # ranks
+    assert _inner_status("add", "mul", "f64", "native", (), (6, 7), "f64") == 2
+    assert _inner_status("add", "mul", "f64", "native", (1,) * 9, (1, 2), "f64") == 2
+    # unsupported tuples
+    assert _inner_status("add", "mul", "f64", "bf16x3", (4, 5), (5, 7), "f64") == 5
+    assert _inner_status("min", "add", "f64", "native", (4, 5), (5, 7), "f64") == 5
+    assert _inner_status("or", "and", "f32", "native", (4, 5), (5, 7), "f32") == 5
+    assert _inner_status("add", "mul", "i32", "native", (4, 5), (5, 7), "f32") == 5
+    # negative extent, overflow
+    assert _inner_status("add", "mul", "f32", "native", (-1, 5), (5, 7), "f32") == 4
+    assert _inner_status("add", "mul", "f32", "native", (2 ** 40, 5), (5, 2 ** 40), "f32") == 4
+    # null pointers
+    assert _inner_status("add", "mul", "f32", "native", (4, 5), (5, 7), "f32", out=0) == 1
+    assert _inner_status("add", "mul", "f32", "native", (4, 5), (5, 7), "f32", A=0) == 1
+    # misaligned
+    assert _inner_status("add", "mul", "f64", "native", (4, 5), (5, 7), "f64", A=0x1004) == 10
+    # bad enum
+    assert _inner_status(99, "mul", "f32", "native", (4, 5), (5, 7), "f32") == 11
+    # empty result: a no-op that succeeds without touching the device
+    assert _inner_status("add", "mul", "f32", "native", (0, 5), (5, 7), "f32", A=0, out=0) == 0
+
+
+def test_outer_validation(L):
+    def st(op, dt, sa, sb, odt, A=0x1000, B=0x2000, out=0x3000):
+        return moa.moa_outer(op, dt, sa, A, sb, B, out, odt, stream=0, check=False)
+    assert st("mul", "f32", (1,) * 9, (2,), "f32") == 2
+    assert st("div", "i32", (3,), (2,), "i32") == 5
+    assert st("mul", "f32", (3,), (2,), "f64") == 5
+    assert st("mul", "f32", (2 ** 32,), (2 ** 32,), "f32") == 4
+    assert st("mul", "f32", (3,), (2,), "f32", out=0) == 1
+    assert st("mul", "f32", (0,), (2,), "f32", A=0, out=0) == 0
+
+
+def test_status_strings(L):
+    assert moa.moa_status_string(0) == "ok"
+    assert "shape" in moa.moa_status_string(3)
+    assert moa.moa_version() >= 0x000100
+
+
+def test_header_cites_the_paper():
+    txt = open(os.path.join(ROOT, "include", "moa.h")).read()
+    assert "Eq. (1)" in txt and "Eq. (2)" in txt

@@ -228,7 +228,8 @@ def test_sampled_outputs_match_full():
 
 
 # ------------------------------------------------------------------ outer
-@pytest.mark.parametrize("op,uf", [("mul", np.multiply), ("add", np.add), ("sub", np.subtract), ("div", np.divide)])
+@pytest.mark.parametrize("op,uf", [("mul", np.multiply), ("add", np.add), ("sub", np.subtract), ("div", np.divide),
+                                   ("min", np.minimum), ("max", np.maximum)])
 def test_outer_matches_numpy_ufunc_outer(op, uf):
     A, B = synth.outer_inputs(op, "f64", shape_a=(3, 4, 5), shape_b=(2, 7))
     assert np.array_equal(oracle.outer_f(op, A, B), uf.outer(A, B))
@@ -240,7 +241,8 @@ def test_outer_matches_numpy_ufunc_outer(op, uf):
     gb = oracle.outer_f(op, av, bv, out="bf16")
     ta = torch.from_numpy(av.astype(np.float32))
     tb = torch.from_numpy(bv.astype(np.float32))
-    t = {"mul": torch.mul, "add": torch.add, "sub": torch.sub, "div": torch.div}[op]
+    t = {"mul": torch.mul, "add": torch.add, "sub": torch.sub, "div": torch.div, "min": torch.minimum,
+         "max": torch.maximum}[op]
     ref = t(ta.reshape(3, 4, 5, 1, 1), tb.reshape(1, 1, 1, 2, 7)).to(torch.bfloat16).view(torch.int16).numpy()
     assert np.array_equal(gb.view(np.int16), ref)
 
