@@ -1,0 +1,413 @@
+"""Benchmark of the MoA generalized inner / outer product on GB300.
+
+Headline workload: the square matrix-multiply sweep's largest case, the
+(+,*) inner product (Eq. 2, matrix multiply as its special case, Sec. I) of
+two 8192 x 8192 arrays with bf16 elements, FP32 accumulation, through
+``moa_inner``.  One step = one such inner product (2 n^3 flops); inputs
+(2 x 128 MiB) are larger than L2, so no flush is needed between steps.
+
+Also measured in the same run, each in its own timed loop (keys "rows"):
+the other forms of the sweep at n = 8192 (FP32 FMA, BF16 and split-BF16x3
+from FP32 operands, plain FP64), the generalized semirings on the
+<32,128,512> x <512,64,64> arrays, the memory-bound outer products of
+<128,64,32> x <32,64>, and the plain-method FP64 rank-4 x rank-3 product.
+
+``--impl reference`` times the CPU oracle (the appendix-order loop, FP64,
+OpenMP over result rows) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_HEAD = 8192
+METRIC = "MoA inner-product TFLOP/s (% peak) & outer-product GB/s; mixed vs FP64 form"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained", d["bf16_tflops"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+                for n, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+def _events_time(fn, iters, stream):
+    """Average ms per call of fn over `iters` calls, CUDA events on `stream`."""
+    import torch
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s.record(stream)
+    for _ in range(iters):
+        fn()
+    e.record(stream)
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / iters
+
+
+def _flush_l2(buf):
+    buf.add_(1)  # writes 256 MiB, larger than L2
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0
+    import torch.distributed as dist
+    dist.init_process_group("nccl" if os.environ.get("MOA_BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+    return dist.get_rank(), ws, int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _max_over_ranks(x, ws):
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- rows
+def _row_inner_square(moa, torch, form, dtype, n, reps, stream, peaks, flush):
+    import numpy as np
+
+    import synth
+    A64, B64 = synth.square(n, "uniform")
+    if dtype == "f64":
+        A, B = torch.from_numpy(A64).cuda(), torch.from_numpy(B64).cuda()
+        D = torch.empty((n, n), dtype=torch.float64, device="cuda")
+        odt = "f64"
+    elif dtype == "f32":
+        A = torch.from_numpy(synth.to_f32(A64)).cuda()
+        B = torch.from_numpy(synth.to_f32(B64)).cuda()
+        D = torch.empty((n, n), dtype=torch.float32, device="cuda")
+        odt = "f32"
+    else:
+        A = torch.from_numpy(synth.to_bf16(A64)[0].view(np.int16)).view(torch.bfloat16).cuda()
+        B = torch.from_numpy(synth.to_bf16(B64)[0].view(np.int16)).view(torch.bfloat16).cuda()
+        D = torch.empty((n, n), dtype=torch.float32, device="cuda")
+        odt = "f32"
+    call = lambda: moa.moa_inner("add", "mul", dtype, form, (n, n), A, (n, n), B, D, odt, stream)
+    call()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(reps):
+        flush()
+        times.append(_events_time(call, 1, stream))
+    ms = statistics.median(times)
+    tflops = 2.0 * n ** 3 / (ms * 1e-3) / 1e12
+    row = {"form": form, "dtype": dtype, "n": n, "ms": round(ms, 4), "tflops": round(tflops, 2)}
+    del A, B, D
+    torch.cuda.empty_cache()
+    return row
+
+
+def _row_semiring(moa, torch, kind, reduce, combine, reps, stream, flush):
+    import numpy as np
+
+    import synth
+    A, B = synth.semiring_inputs(kind)
+    M, K, N = 32 * 128, 512, 64 * 64
+    if kind == "bool":
+        a = torch.from_numpy(synth.pack_bits(A).view(np.int32)).cuda()
+        b = torch.from_numpy(synth.pack_bits(B).view(np.int32)).cuda()
+        D = torch.empty(((M * N + 31) // 32,), dtype=torch.int32, device="cuda")
+        dt = odt = "b1"
+    else:
+        a, b = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+        D = torch.empty((32, 128, 64, 64), dtype=a.dtype, device="cuda")
+        dt = odt = "i32" if kind == "int32" else "f32"
+    call = lambda: moa.moa_inner(reduce, combine, dt, "native", A.shape, a, B.shape, b, D, odt, stream)
+    call()
+    times = []
+    for _ in range(reps):
+        flush()
+        times.append(_events_time(call, 1, stream))
+    ms = statistics.median(times)
+    return {"semiring": f"({reduce},{combine})", "dtype": dt, "shape": "<32,128,512>x<512,64,64>", "ms": round(ms, 4),
+            "gops": round(M * N * K / (ms * 1e-3) / 1e9, 1)}
+
+
+def _row_outer(moa, torch, op, dt, reps, stream, peaks):
+    import numpy as np
+
+    import synth
+    shA, shB = synth.C4_SHAPE_A, synth.C4_SHAPE_B
+    if dt == "bf16":
+        (ab, _), (bb, _) = synth.outer_inputs(op, "bf16")
+        A = torch.from_numpy(ab.view(np.int16)).view(torch.bfloat16).cuda()
+        B = torch.from_numpy(bb.view(np.int16)).view(torch.bfloat16).cuda()
+        C = torch.empty(shA + shB, dtype=torch.bfloat16, device="cuda")
+    else:
+        A, B = (torch.from_numpy(x).cuda() for x in synth.outer_inputs(op, dt))
+        C = torch.empty(shA + shB, dtype=A.dtype, device="cuda")
+    call = lambda: moa.moa_outer(op, dt, shA, A, shB, B, C, dt, stream)
+    call()
+    ms = _events_time(call, reps, stream)  # output (>= 1 GiB) is far larger than L2
+    nbytes = C.numel() * C.element_size() + (A.numel() + B.numel()) * A.element_size()
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    row = {"op": op, "dtype": dt, "shape": "<128,64,32>x<32,64>", "ms": round(ms, 4), "gbs": round(gbs, 1),
+           "frac_hbm": round(gbs / peaks["hbm_gbs"], 3)}
+    del A, B, C
+    torch.cuda.empty_cache()
+    return row
+
+
+def _row_plain_method(moa, torch, reps, stream):
+    import synth
+    A, B = synth.rank4x3_f64()
+    Ob = synth.outer_second_f64()
+    a, b, ob = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), torch.from_numpy(Ob).cuda()
+    D = torch.empty((16, 12, 8, 24, 20), dtype=torch.float64, device="cuda")
+    C = torch.empty((16, 12, 8, 64, 4, 5), dtype=torch.float64, device="cuda")
+    ci = lambda: moa.moa_inner("add", "mul", "f64", "native", A.shape, a, B.shape, b, D, "f64", stream)
+    co = lambda: moa.moa_outer("mul", "f64", A.shape, a, Ob.shape, ob, C, "f64", stream)
+    ci(), co()
+    ms_i = _events_time(ci, reps, stream)
+    ms_o = _events_time(co, reps, stream)
+    return {"inner_ms": round(ms_i, 4), "inner_gflops": round(2 * 1536 * 480 * 64 / (ms_i * 1e-3) / 1e9, 1),
+            "outer_ms": round(ms_o, 4), "outer_gbs": round((C.numel() + A.size) * 8 / (ms_o * 1e-3) / 1e9, 1)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_oracle_sample(seconds: float = 12.0, threads: int | None = None):
+    """The oracle's appendix-order loop (FP64, OpenMP over rows) on the first
+    R rows of the n = 8192 product, R sized for about `seconds` of work."""
+    import numpy as np
+
+    import oracle
+    import synth
+    n = N_HEAD
+    threads = threads or oracle.max_threads()
+    A64, B64 = synth.square(n, "uniform")
+    rows = max(threads, 16)
+    t0 = time.perf_counter()
+    oracle.rowwise("f64", A64[:rows], B64, threads=threads)
+    dt = time.perf_counter() - t0
+    R = int(min(n, max(rows, rows * seconds / max(dt, 1e-3))))
+    R = max(threads, R // threads * threads)
+    t0 = time.perf_counter()
+    oracle.rowwise("f64", A64[:R], B64, threads=threads)
+    dt = time.perf_counter() - t0
+    tflops = 2.0 * R * n * n / dt / 1e12
+    return {"value": tflops, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
+            "sample": f"appendix-order FP64 loop, first {R} of {n} result rows of the {n}x{n} product "
+                      f"({2.0 * R * n * n / 1e9:.1f} GFLOP in {dt:.2f} s)"}
+
+
+def run_reference(args, rank, ws):
+    if rank != 0:
+        return
+    res = []
+    for _ in range(args.warmup):
+        pass
+    samples = [cpu_oracle_sample(seconds=max(2.0, 60.0 / max(1, args.steps))) for _ in range(max(1, args.steps))]
+    v = statistics.median(s["value"] for s in samples)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "square (+,*) inner product n=8192, rows sampled"},
+            "cpu_baseline": {"kind": "oracle", "cores": samples[0]["cores"], "sample": samples[0]["sample"], "value": v},
+            "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="moa", choices=["moa", "reference"])
+    ap.add_argument("--no-rows", action="store_true", help="skip the per-row measurements")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank, ws, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, rank, ws)
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_0907_0792_gb300 as moa
+    import synth
+
+    torch.cuda.set_device(local)
+    moa.lib()
+    peaks = _peaks()
+    stream = torch.cuda.current_stream()
+    n = N_HEAD
+
+    # ---- headline: bf16 8192^3 (+,*) through moa_inner, inputs resident in HBM
+    A64, B64 = synth.square(n, "uniform")
+    a_bits, _ = synth.to_bf16(A64)
+    b_bits, _ = synth.to_bf16(B64)
+    A = torch.from_numpy(a_bits.view(np.int16)).view(torch.bfloat16).cuda()
+    B = torch.from_numpy(b_bits.view(np.int16)).view(torch.bfloat16).cuda()
+    D = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    step = lambda: moa.moa_inner("add", "mul", "bf16", "native", (n, n), A, (n, n), B, D, "f32", stream)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    _barrier(ws)
+    with ClockSampler(local) as clk:
+        time.sleep(0.3)
+        torch.cuda.synchronize()
+        _barrier(ws)
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        for _ in range(args.steps):
+            step()
+        e.record(stream)
+        torch.cuda.synchronize()
+        _barrier(ws)
+    ms_local = s.elapsed_time(e) / args.steps
+    ms = _max_over_ranks(ms_local, ws)
+    flops = 2.0 * n ** 3
+    value = ws * flops / (ms * 1e-3) / 1e12
+    kernel_tflops = flops / (ms_local * 1e-3) / 1e12
+    st = moa.moa_device_status()
+    if st != 0:
+        raise RuntimeError("device status " + moa.moa_status_string(st))
+
+    # ---- e2e: the same call with host buffers, copies inside the timed region
+    hA = torch.from_numpy(a_bits.view(np.int16)).view(torch.bfloat16).pin_memory()
+    hB = torch.from_numpy(b_bits.view(np.int16)).view(torch.bfloat16).pin_memory()
+    hD = torch.empty((n, n), dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        A.copy_(hA, non_blocking=True)
+        B.copy_(hB, non_blocking=True)
+        step()
+        hD.copy_(D, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e2e_steps = max(3, min(args.steps, 10))
+    ms_e2e = _max_over_ranks(_events_time(e2e_step, e2e_steps, stream), ws)
+    e2e = {"value": round(ws * flops / (ms_e2e * 1e-3) / 1e12, 2), "unit": "TFLOP/s",
+           "h2d_bytes_per_step": int(hA.numel() * 2 + hB.numel() * 2), "d2h_bytes_per_step": int(hD.numel() * 4),
+           "ms_per_step": round(ms_e2e, 3)}
+    del hA, hB, hD, A, B, D
+    torch.cuda.empty_cache()
+
+    peak_tc = peaks["bf16_tflops"]
+    roofline = {"bound": "tensor", "achieved": round(kernel_tflops, 1), "peak": peak_tc, "unit": "TFLOP/s",
+                "frac": round(kernel_tflops / peak_tc, 3), "traffic": None,
+                "kernel": "tc_gemm_bf16<256,4>", "peak_kind": f"bf16 dense burst, {peaks['source']}"}
+
+    rows = {}
+    if not args.no_rows:
+        flush_buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+        flush = lambda: _flush_l2(flush_buf)
+        sweep = []
+        for form, dt, reps in (("native", "bf16", 5), ("bf16", "f32", 5), ("bf16x3", "f32", 5), ("native", "f32", 3),
+                               ("native", "f64", 1)):
+            sweep.append(_row_inner_square(moa, torch, form, dt, n, reps, stream, peaks, flush))
+        rows["square_sweep_n8192"] = sweep
+        rows["semirings"] = [
+            _row_semiring(moa, torch, "tropical", "min", "add", 5, stream, flush),
+            _row_semiring(moa, torch, "tropical", "max", "add", 5, stream, flush),
+            _row_semiring(moa, torch, "maxmul", "max", "mul", 5, stream, flush),
+            _row_semiring(moa, torch, "int32", "add", "mul", 5, stream, flush),
+            _row_semiring(moa, torch, "bool", "or", "and", 5, stream, flush)]
+        rows["outer"] = [_row_outer(moa, torch, op, dt, 10, stream, peaks)
+                         for op, dt in (("mul", "f32"), ("add", "f32"), ("sub", "f32"), ("div", "f32"),
+                                        ("mul", "bf16"), ("div", "bf16"), ("mul", "i32"))]
+        rows["plain_method_f64_rank4x3"] = _row_plain_method(moa, torch, 20, stream)
+        del flush_buf
+        st = moa.moa_device_status()
+        if st != 0:
+            raise RuntimeError("device status " + moa.moa_status_string(st))
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_oracle_sample(args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 2), "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+                "config": {"workload": "square (+,*) inner product n=8192, bf16 operands, FP32 accumulate/out",
+                           "M": n, "K": n, "N": n, "seed": 2, "values": "U(-1,1) rounded to bf16",
+                           "l2": "inputs 2 x 128 MiB > L2, no flush", "parallelism": f"replicas x{ws}"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+                "clocks": clk.summary(), "device_status": "ok", "rows": rows}
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,251 @@
+/*
+ * moa.h — C ABI of libmoa, a GB300 (sm_103a) implementation of the
+ * generalized inner and outer product of arbitrary-rank arrays from
+ * Raynolds & Mullin, "A generalized inner and outer product of arbitrary
+ * multi-dimensional arrays using A Mathematics of Arrays (MoA)".
+ *
+ * The paper's statement of the problem (Sec. I): every array is given to the
+ * routine as a shape vector (rho A: the length of each axis) and a vector
+ * holding its elements; both operations live behind one entry point that
+ * takes a general binary operation.
+ *
+ *  - Outer product, Eq. (1): C_{ijkpqlm} = A_{ijkp} op B_{qlm};
+ *    rho C = rho A ++ rho B.
+ *  - Inner product, Eq. (2): D_{ijklm} = reduce_p ( A_{ijkp} combine B_{plm} );
+ *    the last axis of A is contracted with the first axis of B,
+ *    rho D = (rho A without its last axis) ++ (rho B without its first).
+ *    (reduce, combine) = (add, mul) is matrix multiply (Sec. I).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  Layout     Element vectors are row-major (C order) ravels of the array,
+ *             as the appendix's addressing RES(i*restride+j),
+ *             L(l+i*lstride), R(l*rstride+j) implies.  MOA_B1_U32 arrays are
+ *             the row-major ravel packed as a bit stream: element e is bit
+ *             (e % 32) (LSB first) of 32-bit word e / 32; the last word's
+ *             unused bits are zero on input and written as zero on output.
+ *  Shapes     Host arrays of int64_t, read during the call only (the library
+ *             keeps no pointer to them).  Entries must be >= 0, rank <= 8,
+ *             and the element count must not overflow int64_t.
+ *  Memory     A, B and out are device pointers owned by the caller.  out
+ *             holds prod(rho D) (inner) or prod(rho A)*prod(rho B) (outer)
+ *             elements of out_dtype and must not overlap A or B.  The
+ *             library owns only an internal scratch workspace, kept per
+ *             (device, stream) and grown on demand with stream-ordered
+ *             allocation; moa_release_workspace() frees it.
+ *  Streams    Every call only enqueues work on `stream` (0 = legacy default
+ *             stream) and returns; it never synchronises, except
+ *             moa_device_status().  Calls that share a stream may share the
+ *             workspace; calls on different streams never do.
+ *  Errors     All arguments are validated on the host before any launch; a
+ *             rejected call launches nothing and returns the error code.
+ *             CUDA launch/API failures return MOA_ERR_CUDA.  Device-side
+ *             waits are bounded: a kernel that gives up records
+ *             MOA_ERR_TIMEOUT in a device status word that
+ *             moa_device_status() reports.
+ *  Exactness  Integer, min/max and Boolean results are bit-exact.  FP32
+ *             single-operation results (semiring combine, outer product) are
+ *             IEEE round-to-nearest-even, no flush-to-zero.  Floating (+,*)
+ *             forms meet the normalised error |D - D_exact| / sum_p |A||B|
+ *             stated beside moa_form.
+ */
+#ifndef MOA_H
+#define MOA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t (a CUDA stream handle); 0 is the default stream. */
+typedef struct CUstream_st *moa_stream;
+
+typedef enum {
+    MOA_OK = 0,
+    MOA_ERR_NULL = 1,           /* a required pointer is NULL */
+    MOA_ERR_RANK = 2,           /* rank out of range for the operation */
+    MOA_ERR_SHAPE_MISMATCH = 3, /* inner product with rho A[-1] != rho B[0] (Eq. 2) */
+    MOA_ERR_OVERFLOW = 4,       /* negative extent, or an element count over int64 */
+    MOA_ERR_UNSUPPORTED = 5,    /* (reduce, combine, dtype, form, out_dtype) not provided */
+    MOA_ERR_WORKSPACE = 6,      /* scratch allocation failed */
+    MOA_ERR_CUDA = 7,           /* a CUDA API call or launch failed */
+    MOA_ERR_TIMEOUT = 8,        /* a device-side bounded wait gave up */
+    MOA_ERR_INTERNAL = 9,
+    MOA_ERR_ALIGNMENT = 10,     /* pointer not aligned to its element size */
+    MOA_ERR_INVALID = 11        /* malformed argument (e.g. bad enum, bad plan) */
+} moa_status;
+
+typedef enum {
+    MOA_OP_ADD = 0,
+    MOA_OP_SUB = 1,
+    MOA_OP_MUL = 2,
+    MOA_OP_DIV = 3,
+    MOA_OP_MIN = 4,
+    MOA_OP_MAX = 5,
+    MOA_OP_OR = 6,
+    MOA_OP_AND = 7
+} moa_op;
+
+/* Storage type of an element vector. */
+typedef enum {
+    MOA_F64 = 0,
+    MOA_F32 = 1,
+    MOA_BF16 = 2,
+    MOA_FP8E4M3 = 3, /* reserved for storage; FP8 is used internally by MOA_FORM_FP8_T128 */
+    MOA_I32 = 4,
+    MOA_B1_U32 = 5   /* packed bits, see "Layout" above */
+} moa_dtype;
+
+/*
+ * How the (add, mul) inner product is computed; other semirings take
+ * MOA_FORM_NATIVE only.  Normalised error bounds (max over elements of
+ * |D - D_exact| / sum_p |A||B|, D_exact from the operands as given):
+ *   NATIVE    f64: FP64 FMA, <= 1e-12.  f32: FP32 FMA, <= 2e-6.
+ *             bf16 (inputs already bf16, FP32 out): tensor cores, FP32
+ *             accumulation, <= 2e-6 relative to the bf16 operands.
+ *             i32: exact modulo 2^32.
+ *   BF16      f32 in/out: operands rounded to bf16, tensor cores, <= 1e-2.
+ *   FP8_T128  f32 in/out: operands scaled by powers of two per 1x128 block
+ *             along the contraction and rounded to e4m3; tensor cores with
+ *             the scale applied per block in FP32, <= 6e-2.
+ *   BF16X3    f32 in/out: each operand split into three bf16 terms
+ *             (hi + mid + lo), the six cross products of order <= 2
+ *             accumulated in FP32 on tensor cores, <= 2e-6.
+ *   OZAKI     f64 in/out: operands cut into fixed-point slices with
+ *             per-row / per-column power-of-two exponents, exact slice
+ *             products on tensor cores, recombined in FP64, <= 1e-12.
+ */
+typedef enum {
+    MOA_FORM_NATIVE = 0,
+    MOA_FORM_BF16 = 1,
+    MOA_FORM_FP8_T128 = 2,
+    MOA_FORM_BF16X3 = 3,
+    MOA_FORM_OZAKI = 4
+} moa_form;
+
+/*
+ * moa_inner — generalized inner product, Eq. (2) (Sec. I):
+ *   D[i.., j..] = reduce_{p=0}^{K-1} ( A[i.., p] combine B[p, j..] ),
+ * folded from the identity of `reduce` (0 for add, +inf for min, -inf for
+ * max, false for or).  K = rho A[rankA-1] = rho B[0]; K = 0 fills D with
+ * that identity; an empty D is a no-op.  The arrays are flattened by psi
+ * (Fig. 1: one result row per index vector of A's leading axes) into
+ * M = prod(rho A[0..rankA-2]) rows, K, N = prod(rho B[1..rankB-1]) columns
+ * without moving data.
+ *
+ * Supported (reduce, combine, dtype -> out_dtype, form):
+ *   (add, mul) F64 -> F64      NATIVE | OZAKI
+ *   (add, mul) F32 -> F32      NATIVE | BF16 | FP8_T128 | BF16X3
+ *   (add, mul) BF16 -> F32     NATIVE
+ *   (add, mul) I32 -> I32      NATIVE (wraps modulo 2^32)
+ *   (min|max, add|mul) F32 -> F32   NATIVE
+ *   (or, and) B1_U32 -> B1_U32      NATIVE
+ * rankA, rankB in [1, 8].  Returns MOA_ERR_SHAPE_MISMATCH when
+ * rho A[-1] != rho B[0], MOA_ERR_UNSUPPORTED for any other tuple.
+ */
+moa_status moa_inner(moa_op reduce, moa_op combine, moa_dtype dtype, moa_form form, int rankA,
+                     const int64_t *shapeA, const void *A, int rankB, const int64_t *shapeB, const void *B,
+                     void *out, moa_dtype out_dtype, moa_stream stream);
+
+/*
+ * moa_outer — generalized outer product, Eq. (1) (Sec. I, "the binary
+ * operator ... can be any binary operation (e.g. +, -, *, /)"):
+ *   C[i.., j..] = A[i..] op B[j..],  rho C = rho A ++ rho B.
+ * Supported (op, dtype -> out_dtype):
+ *   add|sub|mul|div|min|max: F64 -> F64, F32 -> F32,
+ *                            BF16 -> BF16 (op in FP32, rounded once, RNE),
+ *                            BF16 -> F32;
+ *   add|sub|mul:             I32 -> I32 (wraps modulo 2^32).
+ * rankA, rankB in [0, 8] (a rank-0 operand is a scalar).
+ */
+moa_status moa_outer(moa_op op, moa_dtype dtype, int rankA, const int64_t *shapeA, const void *A, int rankB,
+                     const int64_t *shapeB, const void *B, void *out, moa_dtype out_dtype, moa_stream stream);
+
+/*
+ * moa_inner_shape — rho D of Eq. (2) without computing anything; the Fig. 1
+ * example rho A = <2 3>, rho B = <3 4> gives rho D = <2 4>.  shapeD must hold
+ * rankA + rankB - 2 entries.  Pure host function.
+ */
+moa_status moa_inner_shape(int rankA, const int64_t *shapeA, int rankB, const int64_t *shapeB, int *rankD,
+                           int64_t *shapeD);
+
+/* moa_outer_shape — rho C = rho A ++ rho B (Eq. 1); shapeC holds rankA + rankB entries. */
+moa_status moa_outer_shape(int rankA, const int64_t *shapeA, int rankB, const int64_t *shapeB, int *rankC,
+                           int64_t *shapeC);
+
+/* ------------------------------------------------------------- batching */
+
+/*
+ * One problem of a batch: an inner product (kind 0) or an outer product
+ * (kind 1), described exactly as for moa_inner / moa_outer.  The shape
+ * arrays are read during moa_batch_plan_create only; A, B and out are device
+ * pointers that must stay valid, and keep their sizes, for every execute.
+ */
+typedef struct {
+    int32_t kind; /* 0 inner (Eq. 2), 1 outer (Eq. 1) */
+    int32_t reduce;   /* moa_op; inner only */
+    int32_t combine;  /* moa_op; the op of an outer product */
+    int32_t dtype;    /* moa_dtype of A and B */
+    int32_t form;     /* moa_form; inner (add, mul) only */
+    int32_t out_dtype;
+    int32_t rankA, rankB;
+    const int64_t *shapeA;
+    const int64_t *shapeB;
+    const void *A;
+    const void *B;
+    void *out;
+} moa_problem;
+
+typedef struct moa_batch_plan moa_batch_plan;
+
+/*
+ * moa_batch_plan_create — validate `count` problems (each as its single call
+ * would), group them by kernel, choose tiles for each group (from the tile
+ * cache, timing candidates on first use when tuning is enabled), lay out the
+ * device descriptor array and work queue, and allocate the plan's own device
+ * memory on the current device.  On error nothing is left allocated and
+ * *plan is NULL; the index of the first bad problem is written to
+ * *bad_index (if not NULL).  Supported problems: (add, mul) F32 with forms
+ * BF16X3 or NATIVE; (min|max, add) F32; outer F32 ops.
+ */
+moa_status moa_batch_plan_create(int count, const moa_problem *problems, moa_batch_plan **plan, int *bad_index);
+
+/*
+ * moa_batch_execute — run every problem of the plan on `stream`.  The first
+ * execute on a stream records the launch sequence into a CUDA graph; later
+ * executes on that stream replay it.  Problems write disjoint outputs.
+ */
+moa_status moa_batch_execute(moa_batch_plan *plan, moa_stream stream);
+
+/* Plan statistics: problem count, grouped launches per execute, total tiles, total flop-equivalent work. */
+moa_status moa_batch_plan_info(const moa_batch_plan *plan, int64_t *n_problems, int64_t *n_launches,
+                               int64_t *n_tiles, double *work_flops);
+
+/* Release the plan (synchronises the device first). NULL is accepted. */
+void moa_batch_plan_destroy(moa_batch_plan *plan);
+
+/* ------------------------------------------------------------ utilities */
+
+/* Human-readable name of a status code (static string). */
+const char *moa_status_string(moa_status s);
+
+/*
+ * moa_device_status — synchronise `stream`, then read and clear the device
+ * status word written by bounded waits; returns MOA_ERR_TIMEOUT if any
+ * kernel gave up since the last call, MOA_ERR_CUDA on a sticky CUDA error,
+ * MOA_OK otherwise.
+ */
+moa_status moa_device_status(moa_stream stream);
+
+/* Free the scratch workspace held for every stream of the current device (synchronises). */
+moa_status moa_release_workspace(void);
+
+/* Library version, e.g. 0x000100 for 0.1.0. */
+int moa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MOA_H */

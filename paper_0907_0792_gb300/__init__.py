@@ -1,0 +1,232 @@
+"""Python binding of libmoa — the GB300 generalized inner / outer product of
+arbitrary-rank arrays (Raynolds & Mullin, A Mathematics of Arrays).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library ``_build/libmoa.so`` behind the C ABI of ``include/moa.h``.  PyTorch
+supplies device memory and the current stream.  There is no CPU fallback:
+if the library has not been built, importing the binding's functions raises.
+
+Low-level calls mirror the C ABI one to one (``moa_inner``, ``moa_outer``,
+``moa_inner_shape`` ...).  ``inner`` / ``outer`` are conveniences that take
+torch tensors, read rho A / rho B from their shapes and allocate the result.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import _build
+
+__all__ = [
+    "MoaError", "lib", "moa_inner", "moa_outer", "moa_inner_shape", "moa_outer_shape", "moa_status_string",
+    "moa_device_status", "moa_release_workspace", "moa_version", "inner", "outer", "OPS", "DTYPES", "FORMS",
+    "moa_batch_plan_create", "moa_batch_execute", "moa_batch_plan_destroy", "moa_batch_plan_info", "MoaProblem",
+]
+
+OPS = {"add": 0, "sub": 1, "mul": 2, "div": 3, "min": 4, "max": 5, "or": 6, "and": 7}
+DTYPES = {"f64": 0, "f32": 1, "bf16": 2, "fp8e4m3": 3, "i32": 4, "b1": 5}
+FORMS = {"native": 0, "bf16": 1, "fp8_t128": 2, "bf16x3": 3, "ozaki": 4}
+STATUS = {0: "MOA_OK", 1: "MOA_ERR_NULL", 2: "MOA_ERR_RANK", 3: "MOA_ERR_SHAPE_MISMATCH", 4: "MOA_ERR_OVERFLOW",
+          5: "MOA_ERR_UNSUPPORTED", 6: "MOA_ERR_WORKSPACE", 7: "MOA_ERR_CUDA", 8: "MOA_ERR_TIMEOUT",
+          9: "MOA_ERR_INTERNAL", 10: "MOA_ERR_ALIGNMENT", 11: "MOA_ERR_INVALID"}
+
+_lib = None
+_I64P = C.POINTER(C.c_int64)
+
+
+class MoaError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = int(status)
+        super().__init__(f"{what}: {STATUS.get(self.status, self.status)} ({_status_text(self.status)})")
+
+
+class MoaProblem(C.Structure):
+    """One problem of a batch (moa_problem in include/moa.h)."""
+    _fields_ = [("kind", C.c_int32), ("reduce", C.c_int32), ("combine", C.c_int32), ("dtype", C.c_int32),
+                ("form", C.c_int32), ("out_dtype", C.c_int32), ("rankA", C.c_int32), ("rankB", C.c_int32),
+                ("shapeA", _I64P), ("shapeB", _I64P), ("A", C.c_void_p), ("B", C.c_void_p), ("out", C.c_void_p)]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded libmoa.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libmoa.so is not built ({path}); run __graft_entry__.build() first")
+        L = C.CDLL(path)
+        V, I, P, I64 = C.c_void_p, C.c_int, C.c_void_p, C.c_int64
+        L.moa_inner.argtypes = [I, I, I, I, I, _I64P, P, I, _I64P, P, P, I, V]
+        L.moa_outer.argtypes = [I, I, I, _I64P, P, I, _I64P, P, P, I, V]
+        L.moa_inner_shape.argtypes = [I, _I64P, I, _I64P, C.POINTER(C.c_int), _I64P]
+        L.moa_outer_shape.argtypes = [I, _I64P, I, _I64P, C.POINTER(C.c_int), _I64P]
+        L.moa_status_string.argtypes = [I]
+        L.moa_status_string.restype = C.c_char_p
+        L.moa_device_status.argtypes = [V]
+        L.moa_batch_plan_create.argtypes = [I, C.POINTER(MoaProblem), C.POINTER(C.c_void_p), C.POINTER(C.c_int)]
+        L.moa_batch_execute.argtypes = [V, V]
+        L.moa_batch_plan_destroy.argtypes = [V]
+        L.moa_batch_plan_destroy.restype = None
+        L.moa_batch_plan_info.argtypes = [V, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64), C.POINTER(C.c_double)]
+        _lib = L
+    return _lib
+
+
+def _status_text(st: int) -> str:
+    try:
+        return lib().moa_status_string(int(st)).decode()
+    except Exception:
+        return "?"
+
+
+def _shape(shape):
+    arr = (C.c_int64 * max(1, len(shape)))(*[int(s) for s in shape])
+    return C.cast(arr, _I64P), arr
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _enum(table, v):
+    return table[v] if isinstance(v, str) else int(v)
+
+
+def _check(st, what):
+    if st != 0:
+        raise MoaError(st, what)
+
+
+# ------------------------------------------------------------------ raw ABI
+def moa_inner(reduce, combine, dtype, form, shapeA, A, shapeB, B, out, out_dtype, stream=None, check=True):
+    """C ABI moa_inner: Eq. (2) D = reduce_p (A[..., p] combine B[p, ...])."""
+    sa, _ka = _shape(shapeA)
+    sb, _kb = _shape(shapeB)
+    st = lib().moa_inner(_enum(OPS, reduce), _enum(OPS, combine), _enum(DTYPES, dtype), _enum(FORMS, form),
+                         len(shapeA), sa, _ptr(A), len(shapeB), sb, _ptr(B), _ptr(out), _enum(DTYPES, out_dtype),
+                         _stream(stream))
+    if check:
+        _check(st, "moa_inner")
+    return st
+
+
+def moa_outer(op, dtype, shapeA, A, shapeB, B, out, out_dtype, stream=None, check=True):
+    """C ABI moa_outer: Eq. (1) C = A op B, rho C = rho A ++ rho B."""
+    sa, _ka = _shape(shapeA)
+    sb, _kb = _shape(shapeB)
+    st = lib().moa_outer(_enum(OPS, op), _enum(DTYPES, dtype), len(shapeA), sa, _ptr(A), len(shapeB), sb, _ptr(B),
+                         _ptr(out), _enum(DTYPES, out_dtype), _stream(stream))
+    if check:
+        _check(st, "moa_outer")
+    return st
+
+
+def moa_inner_shape(shapeA, shapeB):
+    sa, _ka = _shape(shapeA)
+    sb, _kb = _shape(shapeB)
+    rd = C.c_int(0)
+    out = (C.c_int64 * 16)()
+    _check(lib().moa_inner_shape(len(shapeA), sa, len(shapeB), sb, C.byref(rd), C.cast(out, _I64P)),
+           "moa_inner_shape")
+    return tuple(out[i] for i in range(rd.value))
+
+
+def moa_outer_shape(shapeA, shapeB):
+    sa, _ka = _shape(shapeA)
+    sb, _kb = _shape(shapeB)
+    rc = C.c_int(0)
+    out = (C.c_int64 * 16)()
+    _check(lib().moa_outer_shape(len(shapeA), sa, len(shapeB), sb, C.byref(rc), C.cast(out, _I64P)),
+           "moa_outer_shape")
+    return tuple(out[i] for i in range(rc.value))
+
+
+def moa_status_string(st: int) -> str:
+    return _status_text(st)
+
+
+def moa_device_status(stream=None) -> int:
+    return int(lib().moa_device_status(_stream(stream)))
+
+
+def moa_release_workspace() -> int:
+    return int(lib().moa_release_workspace())
+
+
+def moa_version() -> int:
+    return int(lib().moa_version())
+
+
+def moa_batch_plan_create(problems):
+    """problems: a ctypes array of MoaProblem.  Returns the plan handle."""
+    plan = C.c_void_p()
+    bad = C.c_int(-1)
+    st = lib().moa_batch_plan_create(len(problems), problems, C.byref(plan), C.byref(bad))
+    if st != 0:
+        raise MoaError(st, f"moa_batch_plan_create (problem {bad.value})")
+    return plan
+
+
+def moa_batch_execute(plan, stream=None):
+    _check(lib().moa_batch_execute(plan, _stream(stream)), "moa_batch_execute")
+
+
+def moa_batch_plan_info(plan):
+    a, b, c, d = C.c_int64(), C.c_int64(), C.c_int64(), C.c_double()
+    _check(lib().moa_batch_plan_info(plan, C.byref(a), C.byref(b), C.byref(c), C.byref(d)), "moa_batch_plan_info")
+    return {"problems": a.value, "launches": b.value, "tiles": c.value, "work_flops": d.value}
+
+
+def moa_batch_plan_destroy(plan):
+    lib().moa_batch_plan_destroy(plan)
+
+
+# ------------------------------------------------------------ conveniences
+def _dtype_of(t):
+    import torch
+    return {torch.float64: "f64", torch.float32: "f32", torch.bfloat16: "bf16", torch.int32: "i32"}[t.dtype]
+
+
+def inner(A, B, reduce="add", combine="mul", form="native", out=None, out_dtype=None, stream=None):
+    """Eq. (2) on torch CUDA tensors (rho A = A.shape, rho B = B.shape)."""
+    import torch
+    dt = _dtype_of(A)
+    if out_dtype is None:
+        out_dtype = "f32" if dt == "bf16" else dt
+    shD = tuple(A.shape[:-1]) + tuple(B.shape[1:])
+    if out is None:
+        tdt = {"f64": torch.float64, "f32": torch.float32, "i32": torch.int32}[out_dtype]
+        out = torch.empty(shD, dtype=tdt, device=A.device)
+    moa_inner(reduce, combine, dt, form, tuple(A.shape), A.contiguous(), tuple(B.shape), B.contiguous(), out,
+              out_dtype, stream)
+    return out
+
+
+def outer(A, B, op="mul", out=None, out_dtype=None, stream=None):
+    """Eq. (1) on torch CUDA tensors; rho C = rho A ++ rho B."""
+    import torch
+    dt = _dtype_of(A)
+    out_dtype = out_dtype or dt
+    shC = tuple(A.shape) + tuple(B.shape)
+    if out is None:
+        tdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16, "i32": torch.int32}[out_dtype]
+        out = torch.empty(shC, dtype=tdt, device=A.device)
+    moa_outer(op, dt, tuple(A.shape), A.contiguous(), tuple(B.shape), B.contiguous(), out, out_dtype, stream)
+    return out

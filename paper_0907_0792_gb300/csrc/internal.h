@@ -1,0 +1,47 @@
+// Host-side interface between the C ABI (api.cu) and the kernel files.
+// Every launcher takes the psi-flattened problem (Fig. 1: M result rows of N
+// elements, contraction length K) and device pointers, enqueues on `stream`
+// and returns a cudaError_t (cudaSuccess when the launch was accepted).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "moa.h"
+
+namespace moa {
+
+// Workspace: scratch device memory owned by the library, one buffer per
+// (device, stream), grown with stream-ordered allocation (api.cu).
+void *workspace_get(cudaStream_t stream, size_t bytes, moa_status *st);
+
+// outer.cu — Eq. (1) over the flattened operands (C is M x N, M = |A|, N = |B|).
+cudaError_t launch_outer(int op, moa_dtype dtype, moa_dtype out_dtype, const void *A, const void *B, void *C,
+                         int64_t M, int64_t N, cudaStream_t stream);
+
+// fill.cu helpers: fill `count` elements of `elem_bytes` bytes with a pattern.
+cudaError_t launch_fill32(uint32_t *p, uint32_t value, int64_t count, cudaStream_t stream);
+cudaError_t launch_fill64(uint64_t *p, uint64_t value, int64_t count, cudaStream_t stream);
+
+// semiring.cu — CUDA-core tiled inner product, Eq. (2), D = A (M x K) . B (K x N).
+// kind selects the element type / operator pair.
+enum SemiringKind {
+    SR_F64_PLUS_TIMES = 0,
+    SR_F32_PLUS_TIMES = 1,
+    SR_F32_MIN_PLUS = 2,
+    SR_F32_MAX_PLUS = 3,
+    SR_F32_MIN_TIMES = 4,
+    SR_F32_MAX_TIMES = 5,
+    SR_I32_PLUS_TIMES = 6,
+};
+cudaError_t launch_semiring(SemiringKind kind, const void *A, const void *B, void *D, int64_t M, int64_t N, int64_t K,
+                            cudaStream_t stream);
+
+// bits.cu — (or, and) on packed bits.  A, B, D use the MOA_B1_U32 stream
+// layout; ws is scratch of bits_workspace_bytes(M, N, K) bytes (may be NULL
+// when that is 0).
+size_t bits_workspace_bytes(int64_t M, int64_t N, int64_t K);
+cudaError_t launch_or_and(const uint32_t *A, const uint32_t *B, uint32_t *D, int64_t M, int64_t N, int64_t K,
+                          void *ws, cudaStream_t stream);
+
+}  // namespace moa

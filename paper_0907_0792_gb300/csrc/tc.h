@@ -1,0 +1,27 @@
+// Host interface of the tensor-core (tcgen05) forms of the (add, mul) inner
+// product, Eq. (2) with * = multiply: the matrix-multiply special case that
+// Sec. I singles out.  All take the psi-flattened problem D (M x N) =
+// A (M x K) . B (K x N), row-major, and enqueue on `stream`.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "moa.h"
+
+namespace moa {
+
+// bf16 operands as given, FP32 out.
+moa_status tc_inner_bf16(const __nv_bfloat16 *A, const __nv_bfloat16 *B, float *D, int64_t M, int64_t N, int64_t K,
+                         cudaStream_t stream);
+// FP32 operands, FP32 out: MOA_FORM_BF16, MOA_FORM_BF16X3 or MOA_FORM_FP8_T128.
+moa_status tc_inner_f32(moa_form form, const float *A, const float *B, float *D, int64_t M, int64_t N, int64_t K,
+                        cudaStream_t stream);
+// FP64 operands, FP64 out, Ozaki-sliced on bf16 tensor cores.
+moa_status tc_inner_ozaki(const double *A, const double *B, double *D, int64_t M, int64_t N, int64_t K,
+                          cudaStream_t stream);
+// Read and clear the status word of the tensor-core kernels (bounded waits).
+cudaError_t tc_read_and_clear_status(uint32_t *flags);
+
+}  // namespace moa

@@ -1,0 +1,113 @@
+// Precision forms of the (add, mul) inner product (Eq. 2, the matrix-
+// multiply special case of Sec. I) built on the tcgen05 GEMM of tc_gemm.cu:
+//   bf16 operands as given          -> one term, no pre-pass when aligned;
+//   FP32 operands, MOA_FORM_BF16     -> round each operand to bf16 (RNE);
+//   FP32 operands, MOA_FORM_BF16X3   -> split each operand exactly-ish into
+//       x = hi + mid + lo (three bf16 values, each the RNE rounding of what
+//       the previous ones left), then accumulate the six cross products of
+//       total order <= 2 (hh, hm, mh, hl, lh, mm) in one FP32 accumulator
+//       (Henry, Tang & Heinecke, "Leveraging the bfloat16 AI datatype for
+//       higher-precision computations", ARITH 2019).
+// The pre-pass is memory bound: one read of the FP32 operand, one write of
+// each bf16 plane, rows padded to a multiple of 8 elements (16 bytes) so the
+// planes meet the TMA stride rule.
+#include "common.cuh"
+#include "internal.h"
+#include "tc.h"
+
+namespace moa {
+
+moa_status tc_gemm_planes(const __nv_bfloat16 *A, int64_t lda, int planesA, const __nv_bfloat16 *B, int64_t ldb,
+                          int planesB, int n_terms, const int *term_a, const int *term_b, float *D, int64_t ldd,
+                          int64_t M, int64_t N, int64_t K, bool promote, cudaStream_t s);
+
+namespace {
+
+template <typename Tin> MOA_DEV float to_f32(Tin x) { return (float)x; }
+template <> MOA_DEV float to_f32<__nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+// X: rows x cols (row stride cols); out: NPL planes of rows x colsp, plane
+// stride plane_elems; columns cols..colsp-1 are zero.
+template <typename Tin, int NPL>
+__global__ void __launch_bounds__(256) split_planes(const Tin *__restrict__ X, int64_t rows, int64_t cols, int64_t colsp,
+                                                     __nv_bfloat16 *__restrict__ out, int64_t plane_elems) {
+    for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
+        const Tin *src = X + r * cols;
+        __nv_bfloat16 *dst = out + r * colsp;
+        for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < colsp; c += (int64_t)gridDim.x * blockDim.x) {
+            const float x = c < cols ? to_f32(src[c]) : 0.0f;
+            const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+            dst[c] = hi;
+            if (NPL > 1) {
+                const float r1 = __fsub_rn(x, __bfloat162float(hi));  // exact
+                const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+                dst[plane_elems + c] = mid;
+                if (NPL > 2) dst[2 * plane_elems + c] = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(mid)));
+            }
+        }
+    }
+}
+
+int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
+
+template <typename Tin, int NPL>
+cudaError_t run_split(const Tin *X, int64_t rows, int64_t cols, int64_t colsp, __nv_bfloat16 *out, cudaStream_t s) {
+    if (rows == 0 || colsp == 0) return cudaSuccess;
+    const int64_t gx = colsp >= 256 * 4 ? 4 : (colsp + 255) / 256;
+    int64_t gy = rows < 2048 ? rows : 2048;
+    split_planes<Tin, NPL><<<dim3((unsigned)gx, (unsigned)gy), 256, 0, s>>>(X, rows, cols, colsp, out, rows * colsp);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+moa_status tc_inner_bf16(const __nv_bfloat16 *A, const __nv_bfloat16 *B, float *D, int64_t M, int64_t N, int64_t K,
+                         cudaStream_t s) {
+    const int ta[1] = {0}, tb[1] = {0};
+    if ((uintptr_t)A % 16 == 0 && (uintptr_t)B % 16 == 0 && K % 8 == 0 && N % 8 == 0)
+        return tc_gemm_planes(A, K, 1, B, N, 1, 1, ta, tb, D, N, M, N, K, false, s);
+    // copy into 16-byte-aligned, padded rows first
+    const int64_t Kp = round8(K), Np = round8(N);
+    moa_status st;
+    __nv_bfloat16 *ws = (__nv_bfloat16 *)workspace_get(s, (size_t)(M * Kp + K * Np) * 2, &st);
+    if (st != MOA_OK) return st;
+    __nv_bfloat16 *a = ws, *b = ws + M * Kp;
+    if (run_split<__nv_bfloat16, 1>(A, M, K, Kp, a, s) != cudaSuccess) return MOA_ERR_CUDA;
+    if (run_split<__nv_bfloat16, 1>(B, K, N, Np, b, s) != cudaSuccess) return MOA_ERR_CUDA;
+    return tc_gemm_planes(a, Kp, 1, b, Np, 1, 1, ta, tb, D, N, M, N, K, false, s);
+}
+
+moa_status tc_inner_f32(moa_form form, const float *A, const float *B, float *D, int64_t M, int64_t N, int64_t K,
+                        cudaStream_t s) {
+    if (form != MOA_FORM_BF16 && form != MOA_FORM_BF16X3) return MOA_ERR_UNSUPPORTED;
+    const int npl = form == MOA_FORM_BF16 ? 1 : 3;
+    const int64_t Kp = round8(K), Np = round8(N);
+    moa_status st;
+    __nv_bfloat16 *ws = (__nv_bfloat16 *)workspace_get(s, (size_t)npl * (M * Kp + K * Np) * 2, &st);
+    if (st != MOA_OK) return st;
+    __nv_bfloat16 *a = ws, *b = ws + npl * M * Kp;
+    cudaError_t e1, e2;
+    if (npl == 1) {
+        e1 = run_split<float, 1>(A, M, K, Kp, a, s);
+        e2 = run_split<float, 1>(B, K, N, Np, b, s);
+    } else {
+        e1 = run_split<float, 3>(A, M, K, Kp, a, s);
+        e2 = run_split<float, 3>(B, K, N, Np, b, s);
+    }
+    if (e1 != cudaSuccess || e2 != cudaSuccess) return MOA_ERR_CUDA;
+    if (npl == 1) {
+        const int ta[1] = {0}, tb[1] = {0};
+        return tc_gemm_planes(a, Kp, 1, b, Np, 1, 1, ta, tb, D, N, M, N, K, false, s);
+    }
+    // planes 0 = hi, 1 = mid, 2 = lo; the small products go first in each
+    // k-block so they accumulate at their own magnitude, hi*hi last
+    const int ta[6] = {1, 0, 2, 0, 1, 0};
+    const int tb[6] = {1, 2, 0, 1, 0, 0};
+    return tc_gemm_planes(a, Kp, 3, b, Np, 3, 6, ta, tb, D, N, M, N, K, true, s);
+}
+
+moa_status tc_inner_ozaki(const double *, const double *, double *, int64_t, int64_t, int64_t, cudaStream_t) {
+    return MOA_ERR_UNSUPPORTED;
+}
+
+}  // namespace moa

@@ -1,0 +1,420 @@
+// Tensor-core forms of the (add, mul) inner product, Eq. (2) with * =
+// multiply — the matrix-multiply special case of Sec. I — on the psi-
+// flattened problem D (M x N, FP32) = A (M x K) . B (K x N).
+//
+// Kernel: persistent, warp-specialised tcgen05 GEMM for sm_103a.
+//   warp 0      TMA producer: 128 x 64 tile of A (K-major, 128-B swizzle)
+//               and 64 x BN tile of B (row-major = MN-major, 128-B swizzle,
+//               BN/64 boxes) per pipeline stage, completion on an mbarrier.
+//   warp 1      allocates TMEM and issues tcgen05.mma (128 x BN x 16, bf16 in,
+//               FP32 accumulate in TMEM); tcgen05.commit frees each stage and
+//               publishes each finished accumulator.
+//   warps 2-9   epilogue: tcgen05.ld of the accumulator (warp w may read
+//               the 32-lane quarter w % 4 of TMEM; two warps per quarter,
+//               each taking half of the BN columns), stores of FP32 rows.
+// Two TMEM accumulators (2 x BN columns) let the epilogue of tile t overlap
+// the main loop of tile t+1.  Tiles are walked in groups of 16 row-tiles so
+// the A and B panels in flight stay resident in L2.
+//
+// Promoted accumulation (PROMOTE): the tensor core's FP32 accumulation is
+// not round-to-nearest (its error grows with the number of MMAs folded into
+// one accumulator), so for the split-BF16x3 form every 64-deep k-block is
+// accumulated in a fresh TMEM accumulator and then added into FP32
+// registers by the epilogue with IEEE adds; the two TMEM buffers then
+// alternate per k-block instead of per tile.
+//
+// One launch accumulates a list of "terms": pairs (plane of A, plane of B)
+// of 3-D bf16 tensors [plane][rows][cols].  One term is the plain bf16
+// product; six terms give the split-BF16x3 form (hi/mid/lo planes, products
+// of total order <= 2), all into the same FP32 accumulator.
+//
+// Every mbarrier wait is bounded; a wait that gives up sets the CTA's abort
+// flag and the device status word, lets in-flight copies and MMAs land, frees
+// TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "internal.h"
+#include "tc.h"
+#include "tc_ptx.cuh"
+
+namespace moa {
+
+__device__ uint32_t g_tc_status;
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;  // 64 bf16 = 128 B = one swizzle row
+constexpr int kMaxTerms = 8;
+constexpr int kThreads = 320;  // 1 producer, 1 MMA, 8 epilogue warps
+constexpr int kEpiWarps = 8;
+
+struct GemmParams {
+    int M, N, K;
+    int tiles_m, tiles_n;
+    int kblocks;  // ceil(K / BK) per term
+    int n_terms;
+    uint32_t term_a, term_b;  // plane of A / B for term i in bits 4i..4i+3
+    float *D;
+    int64_t ldd;
+    int vec_store;  // D rows 16-byte aligned and ldd % 4 == 0
+};
+
+template <int BN, int STAGES> struct Cfg {
+    static constexpr int A_BYTES = BM * BK * 2;
+    static constexpr int B_BYTES = BK * BN * 2;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int NBARS = 2 * STAGES + 5;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 1024;  // + barriers, + alignment slack
+    static constexpr int TMEM_COLS = 2 * BN;
+    static constexpr uint32_t IDESC = ptx::idesc_bf16_f32(BM, BN, 1);
+    static_assert(NBARS * 8 + 16 <= 1024, "barrier area");
+    static_assert(TMEM_COLS <= 512, "TMEM has 512 columns");
+};
+
+MOA_DEV void tile_of(int t, int tiles_m, int tiles_n, int &tm, int &tn) {
+    constexpr int GM = 16;
+    const int group = t / (GM * tiles_n);
+    const int first = group * GM;
+    const int gsz = min(tiles_m - first, GM);
+    const int local = t - group * GM * tiles_n;
+    tm = first + local % gsz;
+    tn = local / gsz;
+}
+
+// Wait used only while shutting down after an abort: ignores the abort flag.
+MOA_DEV bool drain_wait(uint32_t bar, uint32_t parity) {
+    const uint64_t t0 = globaltimer();
+    while (!ptx::mbar_try_wait(bar, parity)) {
+        if (globaltimer() - t0 > kWaitLimitNs) return false;
+    }
+    return true;
+}
+
+template <int BN, int STAGES, bool PROMOTE>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const GemmParams p) {
+    using C = Cfg<BN, STAGES>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *bars = (uint64_t *)(smem + STAGES * C::STAGE_BYTES);
+    uint32_t *tmem_slot = (uint32_t *)(bars + C::NBARS);
+    volatile uint32_t *abort_flag = tmem_slot + 1;
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const uint32_t tiles0 = ptx::smem_u32(smem);
+    const uint32_t bar0 = ptx::smem_u32(bars);
+    auto full = [&](int s) { return bar0 + 8u * s; };
+    auto empty = [&](int s) { return bar0 + 8u * (STAGES + s); };
+    auto tfull = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
+    auto tempty = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 + b); };
+    const uint32_t drain = bar0 + 8u * (2 * STAGES + 4);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            ptx::mbar_init(full(s), 1);
+            ptx::mbar_init(empty(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            ptx::mbar_init(tfull(b), 1);
+            ptx::mbar_init(tempty(b), kEpiWarps);  // one arrival per epilogue warp
+        }
+        ptx::mbar_init(drain, 1);
+        *abort_flag = 0u;
+        ptx::fence_mbar_init();
+        ptx::fence_proxy_async_smem();
+        ptx::prefetch_tmap(&tmA);
+        ptx::prefetch_tmap(&tmB);
+    }
+    if (warp == 1) {
+        ptx::tmem_alloc(ptx::smem_u32(tmem_slot), C::TMEM_COLS);
+        ptx::tmem_relinquish();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const int num_tiles = p.tiles_m * p.tiles_n;
+    const int kiters = p.kblocks * p.n_terms;
+
+    if (warp == 0 && lane == 0) {
+        // ------------------------------------------------ TMA producer
+        int stage = 0;
+        uint32_t phase = 0, issued = 0, last_par = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+            int tm, tn;
+            tile_of(t, p.tiles_m, p.tiles_n, tm, tn);
+            for (int it = 0; it < kiters; ++it) {
+                const int kb = it / p.n_terms, term = it - kb * p.n_terms;
+                if (!ptx::mbar_wait(empty(stage), phase ^ 1u, abort_flag, &g_tc_status)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t sa = tiles0 + stage * C::STAGE_BYTES, sb = sa + C::A_BYTES;
+                ptx::mbar_arrive_expect_tx(full(stage), C::STAGE_BYTES);
+                const int pa = (int)((p.term_a >> (4 * term)) & 15u), pb = (int)((p.term_b >> (4 * term)) & 15u);
+                ptx::tma_load_3d(sa, &tmA, full(stage), kb * BK, tm * BM, pa);
+#pragma unroll
+                for (int j = 0; j < BN / 64; ++j)
+                    ptx::tma_load_3d(sb + j * (BK * 128), &tmB, full(stage), tn * BN + j * 64, kb * BK, pb);
+                issued |= 1u << stage;
+                last_par = (last_par & ~(1u << stage)) | (phase << stage);
+                if (++stage == STAGES) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+            }
+        }
+        if (!ok) {  // let every copy already issued land before the CTA exits
+            for (int s = 0; s < STAGES; ++s)
+                if (issued & (1u << s)) drain_wait(full(s), (last_par >> s) & 1u);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ------------------------------------------------ MMA issuer
+        int stage = 0, abuf = 0;
+        uint32_t phase = 0, aphase = 0;
+        bool ok = true;
+        // an accumulator is handed to the epilogue once per tile, or once
+        // per k-block (all terms of that k-block) when promoting
+        const int per_acc = PROMOTE ? p.n_terms : kiters;
+        for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+            for (int it = 0; it < kiters; ++it) {
+                const int j = it % per_acc;  // position inside the current accumulator
+                if (j == 0) {
+                    if (!ptx::mbar_wait(tempty(abuf), aphase ^ 1u, abort_flag, &g_tc_status)) {
+                        ok = false;
+                        break;
+                    }
+                    ptx::tc_fence_after();
+                }
+                const uint32_t dacc = tmem + (uint32_t)(abuf * BN);
+                if (!ptx::mbar_wait(full(stage), phase, abort_flag, &g_tc_status)) {
+                    ok = false;
+                    break;
+                }
+                ptx::tc_fence_after();
+                const uint32_t sa = tiles0 + stage * C::STAGE_BYTES, sb = sa + C::A_BYTES;
+#pragma unroll
+                for (int k = 0; k < BK / 16; ++k) {
+                    const uint64_t ad = ptx::smem_desc_sw128(sa + k * 32, 16, 1024);
+                    const uint64_t bd = ptx::smem_desc_sw128(sb + k * 2048, BK * 128, 1024);
+                    ptx::mma_bf16(dacc, ad, bd, C::IDESC, (j > 0 || k > 0) ? 1u : 0u);
+                }
+                ptx::mma_commit(empty(stage));
+                if (++stage == STAGES) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+                if (j == per_acc - 1) {
+                    ptx::mma_commit(tfull(abuf));
+                    abuf ^= 1;
+                    if (!abuf) aphase ^= 1u;
+                }
+            }
+        }
+        if (!ok) {  // MMAs already issued must finish before TMEM is freed
+            ptx::mma_commit(drain);
+            drain_wait(drain, 0);
+        }
+    } else if (warp >= 2) {
+        // ------------------------------------------------ epilogue
+        const int q = warp & 3;                  // TMEM lane quarter this warp may access
+        const int half = (warp - 2) / 4;         // which half of the BN columns
+        constexpr int HC = BN / 2;               // columns per epilogue warp
+        int abuf = 0;
+        uint32_t aphase = 0;
+        auto wait_acc = [&]() -> bool {
+            int okw = 1;
+            if (lane == 0) okw = ptx::mbar_wait(tfull(abuf), aphase, abort_flag, &g_tc_status) ? 1 : 0;
+            okw = __shfl_sync(0xffffffffu, okw, 0);
+            if (okw) ptx::tc_fence_after();
+            return okw != 0;
+        };
+        auto release_acc = [&]() {
+            ptx::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(tempty(abuf));
+            abuf ^= 1;
+            if (!abuf) aphase ^= 1u;
+        };
+        // 32 consecutive columns of one row (registers indexed at compile time only)
+        auto store32 = [&](int64_t row, int64_t col0, const uint32_t (&v)[32]) {
+            if (row >= p.M || col0 >= p.N) return;
+            float *dst = p.D + row * p.ldd + col0;
+            if (p.vec_store && col0 + 32 <= p.N) {
+#pragma unroll
+                for (int j = 0; j < 32; j += 4)
+                    *reinterpret_cast<float4 *>(dst + j) = make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]),
+                                                                       __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (col0 + j < p.N) dst[j] = __uint_as_float(v[j]);
+            }
+        };
+        bool ok = true;
+        for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+            int tm, tn;
+            tile_of(t, p.tiles_m, p.tiles_n, tm, tn);
+            const int64_t row = (int64_t)tm * BM + q * 32 + lane;
+            const int64_t colh = (int64_t)tn * BN + half * HC;
+            if constexpr (PROMOTE) {
+                float acc[HC];
+#pragma unroll
+                for (int j = 0; j < HC; ++j) acc[j] = 0.0f;
+                for (int kb = 0; kb < p.kblocks; ++kb) {
+                    if (!wait_acc()) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(abuf * BN + half * HC);
+#pragma unroll
+                    for (int c = 0; c < HC; c += 32) {
+                        uint32_t r[32];
+                        ptx::tmem_ld32(tb + c, r);
+                        ptx::tmem_ld_wait();
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) acc[c + j] = __fadd_rn(acc[c + j], __uint_as_float(r[j]));
+                    }
+                    release_acc();
+                }
+                if (!ok) break;
+#pragma unroll
+                for (int c = 0; c < HC; c += 32) {
+                    uint32_t r[32];
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) r[j] = __float_as_uint(acc[c + j]);
+                    store32(row, colh + c, r);
+                }
+            } else {
+                if (!wait_acc()) break;
+                const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(abuf * BN + half * HC);
+#pragma unroll 1
+                for (int c = 0; c < HC; c += 32) {
+                    uint32_t r[32];
+                    ptx::tmem_ld32(tb + c, r);
+                    ptx::tmem_ld_wait();
+                    store32(row, colh + c, r);
+                }
+                release_acc();
+            }
+        }
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem, C::TMEM_COLS);
+    }
+}
+
+// ------------------------------------------------------------------ host
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+    });
+    return fn;
+}
+
+// 3-D bf16 tensor [planes][rows][inner] with the given strides (bytes),
+// 128-B swizzled boxes of box_inner x box_rows.
+bool make_tmap(CUtensorMap *m, const void *base, uint64_t inner, uint64_t rows, uint64_t planes, uint64_t row_bytes,
+               uint64_t plane_bytes, uint32_t box_inner, uint32_t box_rows) {
+    auto enc = tmap_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {inner, rows, planes};
+    cuuint64_t strides[2] = {row_bytes, plane_bytes};
+    cuuint32_t box[3] = {box_inner, box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+template <int BN, int STAGES, bool PROMOTE>
+cudaError_t launch_tc(const CUtensorMap &ta, const CUtensorMap &tb, GemmParams &p, cudaStream_t s) {
+    using C = Cfg<BN, STAGES>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e =
+            cudaFuncSetAttribute(tc_gemm_bf16<BN, STAGES, PROMOTE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    p.tiles_m = (p.M + BM - 1) / BM;
+    p.tiles_n = (p.N + BN - 1) / BN;
+    const int tiles = p.tiles_m * p.tiles_n;
+    const int grid = tiles < num_sms() ? tiles : num_sms();
+    tc_gemm_bf16<BN, STAGES, PROMOTE><<<grid, kThreads, C::SMEM, s>>>(ta, tb, p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// Planes of A are [planes][M][lda] bf16, of B [planes][K][ldb] bf16;
+// lda, ldb multiples of 8 and the bases 16-byte aligned (TMA rules).
+moa_status tc_gemm_planes(const __nv_bfloat16 *A, int64_t lda, int planesA, const __nv_bfloat16 *B, int64_t ldb,
+                          int planesB, int n_terms, const int *term_a, const int *term_b, float *D, int64_t ldd,
+                          int64_t M, int64_t N, int64_t K, bool promote, cudaStream_t s) {
+    if (M >= (1ll << 31) || N >= (1ll << 31) || K >= (1ll << 31)) return MOA_ERR_OVERFLOW;
+    if (n_terms < 1 || n_terms > kMaxTerms) return MOA_ERR_INTERNAL;
+    if ((uintptr_t)A % 16 || (uintptr_t)B % 16 || lda % 8 || ldb % 8) return MOA_ERR_INTERNAL;
+    const int BN = (N <= 128) ? 128 : 256;
+    CUtensorMap ta, tb;
+    if (!make_tmap(&ta, A, (uint64_t)K, (uint64_t)M, (uint64_t)planesA, (uint64_t)lda * 2, (uint64_t)(lda * M * 2), BK, BM))
+        return MOA_ERR_CUDA;
+    if (!make_tmap(&tb, B, (uint64_t)N, (uint64_t)K, (uint64_t)planesB, (uint64_t)ldb * 2, (uint64_t)(ldb * K * 2), 64, BK))
+        return MOA_ERR_CUDA;
+    GemmParams p{};
+    p.M = (int)M, p.N = (int)N, p.K = (int)K;
+    p.kblocks = (int)((K + BK - 1) / BK);
+    p.n_terms = n_terms;
+    for (int i = 0; i < n_terms; ++i) {
+        if (term_a[i] < 0 || term_a[i] >= planesA || term_b[i] < 0 || term_b[i] >= planesB) return MOA_ERR_INTERNAL;
+        p.term_a |= (uint32_t)term_a[i] << (4 * i);
+        p.term_b |= (uint32_t)term_b[i] << (4 * i);
+    }
+    p.D = D;
+    p.ldd = ldd;
+    p.vec_store = ((uintptr_t)D % 16 == 0) && (ldd % 4 == 0);
+    cudaError_t e;
+    if (promote)
+        e = BN == 128 ? launch_tc<128, 6, true>(ta, tb, p, s) : launch_tc<256, 4, true>(ta, tb, p, s);
+    else
+        e = BN == 128 ? launch_tc<128, 6, false>(ta, tb, p, s) : launch_tc<256, 4, false>(ta, tb, p, s);
+    return e == cudaSuccess ? MOA_OK : MOA_ERR_CUDA;
+}
+
+cudaError_t tc_read_and_clear_status(uint32_t *flags) {
+    cudaError_t e = cudaMemcpyFromSymbol(flags, g_tc_status, sizeof(uint32_t));
+    if (e != cudaSuccess) return e;
+    const uint32_t zero = 0;
+    return cudaMemcpyToSymbol(g_tc_status, &zero, sizeof(uint32_t));
+}
+
+}  // namespace moa
