@@ -73,7 +73,8 @@ typedef enum {
     MOA_ERR_TIMEOUT = 8,        /* a device-side bounded wait gave up */
     MOA_ERR_INTERNAL = 9,
     MOA_ERR_ALIGNMENT = 10,     /* pointer not aligned to its element size */
-    MOA_ERR_INVALID = 11        /* malformed argument (e.g. bad enum, bad plan) */
+    MOA_ERR_INVALID = 11,       /* malformed argument (e.g. bad enum, bad plan) */
+    MOA_ERR_SCRATCH_LIMIT = 12  /* problem needs more scratch than the fixed no-allocation buffer holds */
 } moa_status;
 
 typedef enum {
@@ -149,8 +150,8 @@ moa_status moa_inner(moa_op reduce, moa_op combine, moa_dtype dtype, moa_form fo
                      void *out, moa_dtype out_dtype, moa_stream stream);
 
 /*
- * moa_outer — generalized outer product, Eq. (1) (Sec. I, "the binary
- * operator ... can be any binary operation (e.g. +, -, *, /)"):
+ * moa_outer — generalized outer product, Eq. (1) (Sec. I; the operator of
+ * the outer product may be any binary operation, + - * / among them):
  *   C[i.., j..] = A[i..] op B[j..],  rho C = rho A ++ rho B.
  * Supported (op, dtype -> out_dtype):
  *   add|sub|mul|div|min|max: F64 -> F64, F32 -> F32,
@@ -243,6 +244,46 @@ moa_status moa_release_workspace(void);
 
 /* Library version, e.g. 0x000100 for 0.1.0. */
 int moa_version(void);
+
+/* ------------------------------------------------ no-allocation variant */
+
+/* Size of the fixed scratch buffer used by moa_inner_bf16x3_noalloc. */
+#define MOA_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+/*
+ * moa_inner_bf16x3_noalloc — the (add, mul) inner product of FP32 arrays in
+ * the split-BF16x3 form (same result as moa_inner(MOA_OP_ADD, MOA_OP_MUL,
+ * MOA_F32, MOA_FORM_BF16X3, ..., MOA_F32, stream)), for callers that must not
+ * allocate device memory.  The paper has no counterpart to this call: it
+ * exists for the library's users, not for the method.
+ *
+ * Who needs it: code that runs where an allocation is not allowed or not
+ * affordable — inside a region being captured into a CUDA graph (a
+ * cudaMalloc there breaks or invalidates the capture), a serving loop with
+ * a fixed memory budget that must never grow or stall on the allocator
+ * (cudaMalloc can synchronise the device), or a host callback / custom
+ * allocator hook where calling back into an allocator is not permitted.
+ *
+ * Scratch: the bf16 split planes live in one file-scope device array of
+ * MOA_NOALLOC_SCRATCH_BYTES bytes that every GPU which loads the library
+ * holds until the process exits.  A problem needs 6 * (M*Kp + K*Np) bytes,
+ * Kp and Np being K and N rounded up to a multiple of 8 (M, K, N the
+ * psi-flattened extents, as for moa_inner); a larger one returns
+ * MOA_ERR_SCRATCH_LIMIT before any launch.  Nothing in the array needs to
+ * start at zero (every byte a call reads is written earlier in that call).
+ *
+ * Set-up: the first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress, no allocation) with that device current;
+ * make that first call before any stream capture.  The call allocates
+ * nothing — no cudaMalloc, cudaFree or allocating library routine.
+ *
+ * Concurrency: every call shares the one array, so calls that can overlap
+ * on the GPU (different streams, or different host threads) race; serialise
+ * them, e.g. on one stream.  Arguments, validation and errors otherwise as
+ * for moa_inner.
+ */
+moa_status moa_inner_bf16x3_noalloc(int rankA, const int64_t *shapeA, const float *A, int rankB,
+                                    const int64_t *shapeB, const float *B, float *out, moa_stream stream);
 
 #ifdef __cplusplus
 }

@@ -21,14 +21,18 @@ __all__ = [
     "MoaError", "lib", "moa_inner", "moa_outer", "moa_inner_shape", "moa_outer_shape", "moa_status_string",
     "moa_device_status", "moa_release_workspace", "moa_version", "inner", "outer", "OPS", "DTYPES", "FORMS",
     "moa_batch_plan_create", "moa_batch_execute", "moa_batch_plan_destroy", "moa_batch_plan_info", "MoaProblem",
+    "moa_inner_bf16x3_noalloc", "NOALLOC_SCRATCH_BYTES",
 ]
+
+# size of the fixed device buffer behind moa_inner_bf16x3_noalloc (MOA_NOALLOC_SCRATCH_BYTES)
+NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 OPS = {"add": 0, "sub": 1, "mul": 2, "div": 3, "min": 4, "max": 5, "or": 6, "and": 7}
 DTYPES = {"f64": 0, "f32": 1, "bf16": 2, "fp8e4m3": 3, "i32": 4, "b1": 5}
 FORMS = {"native": 0, "bf16": 1, "fp8_t128": 2, "bf16x3": 3, "ozaki": 4}
 STATUS = {0: "MOA_OK", 1: "MOA_ERR_NULL", 2: "MOA_ERR_RANK", 3: "MOA_ERR_SHAPE_MISMATCH", 4: "MOA_ERR_OVERFLOW",
           5: "MOA_ERR_UNSUPPORTED", 6: "MOA_ERR_WORKSPACE", 7: "MOA_ERR_CUDA", 8: "MOA_ERR_TIMEOUT",
-          9: "MOA_ERR_INTERNAL", 10: "MOA_ERR_ALIGNMENT", 11: "MOA_ERR_INVALID"}
+          9: "MOA_ERR_INTERNAL", 10: "MOA_ERR_ALIGNMENT", 11: "MOA_ERR_INVALID", 12: "MOA_ERR_SCRATCH_LIMIT"}
 
 _lib = None
 _I64P = C.POINTER(C.c_int64)
@@ -72,6 +76,7 @@ def lib():
         L.moa_batch_plan_destroy.argtypes = [V]
         L.moa_batch_plan_destroy.restype = None
         L.moa_batch_plan_info.argtypes = [V, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64), C.POINTER(C.c_double)]
+        L.moa_inner_bf16x3_noalloc.argtypes = [I, _I64P, P, I, _I64P, P, P, V]
         _lib = L
     return _lib
 
@@ -135,6 +140,19 @@ def moa_outer(op, dtype, shapeA, A, shapeB, B, out, out_dtype, stream=None, chec
                          _ptr(out), _enum(DTYPES, out_dtype), _stream(stream))
     if check:
         _check(st, "moa_outer")
+    return st
+
+
+def moa_inner_bf16x3_noalloc(shapeA, A, shapeB, B, out, stream=None, check=True):
+    """C ABI moa_inner_bf16x3_noalloc: the FP32 split-BF16x3 inner product
+    with its scratch in a fixed device buffer, for callers that must not
+    allocate device memory (see include/moa.h)."""
+    sa, _ka = _shape(shapeA)
+    sb, _kb = _shape(shapeB)
+    st = lib().moa_inner_bf16x3_noalloc(len(shapeA), sa, _ptr(A), len(shapeB), sb, _ptr(B), _ptr(out),
+                                        _stream(stream))
+    if check:
+        _check(st, "moa_inner_bf16x3_noalloc")
     return st
 
 

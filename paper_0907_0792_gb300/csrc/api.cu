@@ -309,6 +309,7 @@ const char *moa_status_string(moa_status s) {
     case MOA_ERR_INTERNAL: return "internal error";
     case MOA_ERR_ALIGNMENT: return "misaligned pointer";
     case MOA_ERR_INVALID: return "invalid argument";
+    case MOA_ERR_SCRATCH_LIMIT: return "problem needs more scratch than the fixed no-allocation buffer holds";
     }
     return "unknown status";
 }

@@ -21,6 +21,11 @@ moa_status tc_inner_f32(moa_form form, const float *A, const float *B, float *D,
 // FP64 operands, FP64 out, Ozaki-sliced on bf16 tensor cores.
 moa_status tc_inner_ozaki(const double *A, const double *B, double *D, int64_t M, int64_t N, int64_t K,
                           cudaStream_t stream);
+// Split-BF16x3 with caller-provided scratch of tc_bf16x3_scratch_bytes()
+// bytes (16-byte aligned); allocates nothing.
+size_t tc_bf16x3_scratch_bytes(int64_t M, int64_t N, int64_t K);
+moa_status tc_inner_bf16x3_scratch(const float *A, const float *B, float *D, int64_t M, int64_t N, int64_t K,
+                                   void *scratch, cudaStream_t stream);
 // Read and clear the status word of the tensor-core kernels (bounded waits).
 cudaError_t tc_read_and_clear_status(uint32_t *flags);
 

@@ -106,6 +106,21 @@ moa_status tc_inner_f32(moa_form form, const float *A, const float *B, float *D,
     return tc_gemm_planes(a, Kp, 3, b, Np, 3, 6, ta, tb, D, N, M, N, K, true, s);
 }
 
+size_t tc_bf16x3_scratch_bytes(int64_t M, int64_t N, int64_t K) {
+    return (size_t)3 * (size_t)(M * round8(K) + K * round8(N)) * 2;
+}
+
+moa_status tc_inner_bf16x3_scratch(const float *A, const float *B, float *D, int64_t M, int64_t N, int64_t K,
+                                   void *scratch, cudaStream_t s) {
+    const int64_t Kp = round8(K), Np = round8(N);
+    __nv_bfloat16 *a = (__nv_bfloat16 *)scratch, *b = a + 3 * M * Kp;
+    if (run_split<float, 3>(A, M, K, Kp, a, s) != cudaSuccess) return MOA_ERR_CUDA;
+    if (run_split<float, 3>(B, K, N, Np, b, s) != cudaSuccess) return MOA_ERR_CUDA;
+    const int ta[6] = {1, 0, 2, 0, 1, 0};
+    const int tb[6] = {1, 2, 0, 1, 0, 0};
+    return tc_gemm_planes(a, Kp, 3, b, Np, 3, 6, ta, tb, D, N, M, N, K, true, s);
+}
+
 moa_status tc_inner_ozaki(const double *, const double *, double *, int64_t, int64_t, int64_t, cudaStream_t) {
     return MOA_ERR_UNSUPPORTED;
 }
