@@ -7,8 +7,8 @@ two 8192 x 8192 arrays with bf16 elements, FP32 accumulation, through
 (2 x 128 MiB) are larger than L2, so no flush is needed between steps.
 
 Also measured in the same run, each in its own timed loop (keys "rows"):
-the other forms of the sweep at n = 8192 (FP32 FMA, BF16 and split-BF16x3
-from FP32 operands, plain FP64), the generalized semirings on the
+the other forms of the sweep at n = 8192 (FP32 FMA; BF16, FP8 and split-BF16x3
+from FP32 operands; Ozaki-sliced and plain FP64), the generalized semirings on the
 <32,128,512> x <512,64,64> arrays, the memory-bound outer products of
 <128,64,32> x <32,64>, and the plain-method FP64 rank-4 x rank-3 product.
 
@@ -44,7 +44,9 @@ def _peaks():
 
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms; each line
+    is stamped with the host time it arrived so only samples inside the timed
+    window are summarised."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
@@ -54,29 +56,39 @@ class ClockSampler:
         self.proc = None
 
     def __enter__(self):
+        import threading
+        self.stamped = []
+        self.window = None
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
+        if self.proc is not None:
+            def reader():
+                for line in self.proc.stdout:
+                    if line.strip():
+                        self.stamped.append((time.time(), line))
+            self.thread = threading.Thread(target=reader, daemon=True)
+            self.thread.start()
         return self
 
     def __exit__(self, *a):
-        self.lines = []
         if self.proc is not None:
             self.proc.terminate()
             try:
-                out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
-                out = ""
-            self.lines = [l for l in out.splitlines() if l.strip()]
+            self.thread.join(timeout=5)
 
     def summary(self):
         sm, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in getattr(self, "lines", []):
+        t0, t1 = self.window if self.window else (0.0, float("inf"))
+        lines = [l for t, l in self.stamped if t0 <= t <= t1 + 0.06]
+        for l in lines:
             f = [x.strip() for x in l.split(",")]
             try:
                 sm.append(float(f[1]))
@@ -87,7 +99,7 @@ class ClockSampler:
             except (ValueError, IndexError):
                 continue
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "window_s": round(t1 - t0, 3) if self.window else None}
 
 
 # ---------------------------------------------------------------- helpers
@@ -282,10 +294,12 @@ def run_reference(args, rank, ws):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=1500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="moa", choices=["moa", "reference"])
-    ap.add_argument("--no-rows", action="store_true", help="skip the per-row measurements")
+    ap.add_argument("--rows", default="all",
+                    help="comma list of extra rows to measure: sweep,semirings,outer,plain (all / none)")
+    ap.add_argument("--no-rows", action="store_true", help="same as --rows none")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
@@ -325,11 +339,13 @@ def main():
         torch.cuda.synchronize()
         _barrier(ws)
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t_start = time.time()
         s.record(stream)
         for _ in range(args.steps):
             step()
         e.record(stream)
         torch.cuda.synchronize()
+        clk.window = (t_start, time.time())
         _barrier(ws)
     ms_local = s.elapsed_time(e) / args.steps
     ms = _max_over_ranks(ms_local, ws)
@@ -367,24 +383,31 @@ def main():
                 "kernel": "tc_gemm_bf16<256,4>", "peak_kind": f"bf16 dense burst, {peaks['source']}"}
 
     rows = {}
-    if not args.no_rows:
+    want = set() if args.no_rows or args.rows == "none" else (
+        {"sweep", "semirings", "outer", "plain"} if args.rows == "all" else set(args.rows.split(",")))
+    if want:
         flush_buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
         flush = lambda: _flush_l2(flush_buf)
-        sweep = []
-        for form, dt, reps in (("native", "bf16", 5), ("bf16", "f32", 5), ("bf16x3", "f32", 5), ("native", "f32", 3),
-                               ("native", "f64", 1)):
-            sweep.append(_row_inner_square(moa, torch, form, dt, n, reps, stream, peaks, flush))
-        rows["square_sweep_n8192"] = sweep
-        rows["semirings"] = [
-            _row_semiring(moa, torch, "tropical", "min", "add", 5, stream, flush),
-            _row_semiring(moa, torch, "tropical", "max", "add", 5, stream, flush),
-            _row_semiring(moa, torch, "maxmul", "max", "mul", 5, stream, flush),
-            _row_semiring(moa, torch, "int32", "add", "mul", 5, stream, flush),
-            _row_semiring(moa, torch, "bool", "or", "and", 5, stream, flush)]
-        rows["outer"] = [_row_outer(moa, torch, op, dt, 10, stream, peaks)
-                         for op, dt in (("mul", "f32"), ("add", "f32"), ("sub", "f32"), ("div", "f32"),
-                                        ("mul", "bf16"), ("div", "bf16"), ("mul", "i32"))]
-        rows["plain_method_f64_rank4x3"] = _row_plain_method(moa, torch, 20, stream)
+        if "sweep" in want:
+            sweep = []
+            for form, dt, reps in (("native", "bf16", 5), ("bf16", "f32", 5), ("fp8_t128", "f32", 5),
+                                   ("bf16x3", "f32", 5), ("native", "f32", 3), ("ozaki", "f64", 3),
+                                   ("native", "f64", 1)):
+                sweep.append(_row_inner_square(moa, torch, form, dt, n, reps, stream, peaks, flush))
+            rows["square_sweep_n8192"] = sweep
+        if "semirings" in want:
+            rows["semirings"] = [
+                _row_semiring(moa, torch, "tropical", "min", "add", 5, stream, flush),
+                _row_semiring(moa, torch, "tropical", "max", "add", 5, stream, flush),
+                _row_semiring(moa, torch, "maxmul", "max", "mul", 5, stream, flush),
+                _row_semiring(moa, torch, "int32", "add", "mul", 5, stream, flush),
+                _row_semiring(moa, torch, "bool", "or", "and", 5, stream, flush)]
+        if "outer" in want:
+            rows["outer"] = [_row_outer(moa, torch, op, dt, 10, stream, peaks)
+                             for op, dt in (("mul", "f32"), ("add", "f32"), ("sub", "f32"), ("div", "f32"),
+                                            ("mul", "bf16"), ("div", "bf16"), ("mul", "i32"))]
+        if "plain" in want:
+            rows["plain_method_f64_rank4x3"] = _row_plain_method(moa, torch, 20, stream)
         del flush_buf
         st = moa.moa_device_status()
         if st != 0:

@@ -1,0 +1,119 @@
+// FP8 (e4m3) form of the (add, mul) inner product (Eq. 2, matrix-multiply
+// case): quantisation pre-pass.  A is scaled per 1 x 128 block along the
+// contraction (row i, k-block kb), B per 128 x 128 tile (k-block kb, column
+// block nb), each by a power of two s = 2^(E - 8) where max|x| = m 2^E,
+// m in [1/2, 1): the block maximum maps into [128, 256), inside e4m3's range
+// (largest finite 448), and x / s is one exact scaling followed by one
+// round-to-nearest-even conversion to e4m3 (saturating).  The tcgen05 kernel
+// (tc_gemm.cu, MODE_FP8) multiplies each k-block's exact FP32 partial sum by
+// sA * sB, also exact.
+#include <cuda_fp8.h>
+
+#include "common.cuh"
+#include "internal.h"
+#include "tc.h"
+
+namespace moa {
+
+moa_status tc_gemm_fp8(const uint8_t *A, int64_t lda, const uint8_t *B, int64_t ldb, const float *scale_a,
+                       const float *scale_b, float *D, int64_t ldd, int64_t M, int64_t N, int64_t K, cudaStream_t s);
+
+namespace {
+
+MOA_DEV float block_scale(float amax, float *inv) {
+    if (!(amax > 0.0f)) {
+        *inv = 1.0f;
+        return 1.0f;
+    }
+    int E;
+    frexpf(amax, &E);
+    *inv = ldexpf(1.0f, 8 - E);
+    return ldexpf(1.0f, E - 8);
+}
+
+MOA_DEV uint8_t to_e4m3(float x) { return (uint8_t)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3); }
+
+// One warp per (row, k-block) of A: 128 elements, 4 per lane.
+__global__ void quant_a_kernel(const float *__restrict__ A, int64_t M, int64_t K, int64_t Kp, int64_t KB,
+                               uint8_t *__restrict__ A8, float *__restrict__ sA) {
+    const int64_t nw = (int64_t)gridDim.x * blockDim.x / 32;
+    const int lane = threadIdx.x % 32;
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; w < M * KB; w += nw) {
+        const int64_t row = w / KB, kb = w - row * KB;
+        const int64_t k0 = kb * 128 + lane * 4;
+        float x[4];
+        float amax = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            x[i] = (k0 + i < K) ? __ldg(A + row * K + k0 + i) : 0.0f;
+            amax = fmaxf(amax, fabsf(x[i]));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        float inv;
+        const float sc = block_scale(amax, &inv);
+        if (k0 < Kp) {
+            uint32_t packed = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) packed |= (uint32_t)to_e4m3(__fmul_rn(x[i], inv)) << (8 * i);
+            *reinterpret_cast<uint32_t *>(A8 + row * Kp + k0) = packed;
+        }
+        if (lane == 0) sA[row * KB + kb] = sc;
+    }
+}
+
+// One block per 128 x 128 tile of B.
+__global__ void __launch_bounds__(256) quant_b_kernel(const float *__restrict__ B, int64_t K, int64_t N, int64_t Np,
+                                                      int64_t NB, uint8_t *__restrict__ B8, float *__restrict__ sB) {
+    __shared__ float red[8];
+    const int64_t kb = blockIdx.y, nb = blockIdx.x;
+    const int t = threadIdx.x;
+    float amax = 0.0f;
+    for (int e = t; e < 128 * 128; e += 256) {
+        const int64_t k = kb * 128 + e / 128, n = nb * 128 + e % 128;
+        if (k < K && n < N) amax = fmaxf(amax, fabsf(__ldg(B + k * N + n)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if (t % 32 == 0) red[t / 32] = amax;
+    __syncthreads();
+    amax = red[0];
+#pragma unroll
+    for (int i = 1; i < 8; ++i) amax = fmaxf(amax, red[i]);
+    float inv;
+    const float sc = block_scale(amax, &inv);
+    for (int e = t; e < 128 * 128; e += 256) {
+        const int64_t k = kb * 128 + e / 128, n = nb * 128 + e % 128;
+        if (k < K && n < Np) B8[k * Np + n] = n < N ? to_e4m3(__fmul_rn(__ldg(B + k * N + n), inv)) : (uint8_t)0;
+    }
+    if (t == 0) sB[kb * NB + nb] = sc;
+}
+
+}  // namespace
+
+size_t fp8_workspace_bytes(int64_t M, int64_t N, int64_t K) {
+    const int64_t Kp = (K + 15) / 16 * 16, Np = (N + 15) / 16 * 16, KB = (K + 127) / 128, NB = (N + 127) / 128;
+    return (size_t)(M * Kp + K * Np) + (size_t)(M * KB + KB * NB) * 4 + 64;
+}
+
+moa_status tc_inner_fp8(const float *A, const float *B, float *D, int64_t M, int64_t N, int64_t K, cudaStream_t s) {
+    const int64_t Kp = (K + 15) / 16 * 16, Np = (N + 15) / 16 * 16, KB = (K + 127) / 128, NB = (N + 127) / 128;
+    moa_status st;
+    uint8_t *ws = (uint8_t *)workspace_get(s, fp8_workspace_bytes(M, N, K), &st);
+    if (st != MOA_OK) return st;
+    uint8_t *a8 = ws, *b8 = ws + M * Kp;
+    float *sa = (float *)(((uintptr_t)(b8 + K * Np) + 15) & ~(uintptr_t)15);
+    float *sb = sa + M * KB;
+    {
+        int64_t warps = M * KB;
+        int64_t blocks = (warps * 32 + 255) / 256;
+        if (blocks > 152 * 16) blocks = 152 * 16;
+        quant_a_kernel<<<(unsigned)blocks, 256, 0, s>>>(A, M, K, Kp, KB, a8, sa);
+        if (KB > 65535) return MOA_ERR_OVERFLOW;
+        quant_b_kernel<<<dim3((unsigned)NB, (unsigned)KB), 256, 0, s>>>(B, K, N, Np, NB, b8, sb);
+        if (cudaGetLastError() != cudaSuccess) return MOA_ERR_CUDA;
+    }
+    return tc_gemm_fp8(a8, Kp, b8, Np, sa, sb, D, N, M, N, K, s);
+}
+
+}  // namespace moa

@@ -18,6 +18,8 @@ moa_status tc_inner_bf16(const __nv_bfloat16 *A, const __nv_bfloat16 *B, float *
 // FP32 operands, FP32 out: MOA_FORM_BF16, MOA_FORM_BF16X3 or MOA_FORM_FP8_T128.
 moa_status tc_inner_f32(moa_form form, const float *A, const float *B, float *D, int64_t M, int64_t N, int64_t K,
                         cudaStream_t stream);
+// FP32 operands, FP32 out, e4m3 with per-128 power-of-two block scales.
+moa_status tc_inner_fp8(const float *A, const float *B, float *D, int64_t M, int64_t N, int64_t K, cudaStream_t stream);
 // FP64 operands, FP64 out, Ozaki-sliced on bf16 tensor cores.
 moa_status tc_inner_ozaki(const double *A, const double *B, double *D, int64_t M, int64_t N, int64_t K,
                           cudaStream_t stream);

@@ -79,6 +79,7 @@ moa_status tc_inner_bf16(const __nv_bfloat16 *A, const __nv_bfloat16 *B, float *
 
 moa_status tc_inner_f32(moa_form form, const float *A, const float *B, float *D, int64_t M, int64_t N, int64_t K,
                         cudaStream_t s) {
+    if (form == MOA_FORM_FP8_T128) return tc_inner_fp8(A, B, D, M, N, K, s);
     if (form != MOA_FORM_BF16 && form != MOA_FORM_BF16X3) return MOA_ERR_UNSUPPORTED;
     const int npl = form == MOA_FORM_BF16 ? 1 : 3;
     const int64_t Kp = round8(K), Np = round8(N);
@@ -119,10 +120,6 @@ moa_status tc_inner_bf16x3_scratch(const float *A, const float *B, float *D, int
     const int ta[6] = {1, 0, 2, 0, 1, 0};
     const int tb[6] = {1, 2, 0, 1, 0, 0};
     return tc_gemm_planes(a, Kp, 3, b, Np, 3, 6, ta, tb, D, N, M, N, K, true, s);
-}
-
-moa_status tc_inner_ozaki(const double *, const double *, double *, int64_t, int64_t, int64_t, cudaStream_t) {
-    return MOA_ERR_UNSUPPORTED;
 }
 
 }  // namespace moa

@@ -28,6 +28,23 @@
 // product; six terms give the split-BF16x3 form (hi/mid/lo planes, products
 // of total order <= 2), all into the same FP32 accumulator.
 //
+// FP8 mode (MODE_FP8): e4m3 operands (1-byte elements, 128-deep k-blocks,
+// kind::f8f6f4 MMAs of depth 32) with a power-of-two scale per 1 x 128 block
+// of A (row, k-block) and per 128 x 128 tile of B (k-block, column block).
+// Every k-block is accumulated in a fresh TMEM accumulator and the epilogue
+// adds it into FP32 registers times sA * sB (exact: both are powers of two).
+//
+// Ozaki mode (MODE_OZAKI): the planes hold fixed-point digit slices (small
+// integers, exact in bf16) and the terms are the slice pairs (s, u) with
+// s + u < S.  Each term's contraction is cut into chunks short enough that
+// the FP32 accumulator holds the exact integer sum; the epilogue adds each
+// chunk, scaled exactly by the pair's power-of-two weight, to a double-float
+// (hi + lo FP32 pair, TwoSum) accumulator per output element: FP32 ALU
+// only, ~48 bits relative to the running sum.  The hi / lo sums live in the
+// upper half of TMEM (columns 2*BN .. 4*BN), next to the two accumulators.  FP64 arithmetic (scarce on
+// this part) is used once per output: hi + lo in FP64 and the power-of-two
+// scaling by the row / column exponents.
+//
 // Every mbarrier wait is bounded; a wait that gives up sets the CTA's abort
 // flag and the device status word, lets in-flight copies and MMAs land, frees
 // TMEM and returns.
@@ -48,30 +65,71 @@ __device__ uint32_t g_tc_status;
 namespace {
 
 constexpr int BM = 128;
-constexpr int BK = 64;  // 64 bf16 = 128 B = one swizzle row
+constexpr int BK = 64;  // bf16 elements per k-block: 64 x 2 B = 128 B = one swizzle row
 constexpr int kMaxTerms = 8;
 constexpr int kThreads = 320;  // 1 producer, 1 MMA, 8 epilogue warps
 constexpr int kEpiWarps = 8;
+
+enum Mode { MODE_STORE = 0, MODE_PROMOTE = 1, MODE_OZAKI = 2, MODE_FP8 = 3 };
 
 struct GemmParams {
     int M, N, K;
     int tiles_m, tiles_n;
     int kblocks;  // ceil(K / BK) per term
     int n_terms;
-    uint32_t term_a, term_b;  // plane of A / B for term i in bits 4i..4i+3
+    uint32_t term_a, term_b;  // plane of A / B for term i in bits 4i..4i+3 (store / promote modes)
     float *D;
     int64_t ldd;
     int vec_store;  // D rows 16-byte aligned and ldd % 4 == 0
+    // Ozaki mode
+    int slices;      // S: digit planes per operand
+    int beta;        // bits per digit
+    int lsb;         // the accumulator counts units of 2^-lsb of 2^(e_row + e_col)
+    int chunk;       // k-blocks per exact FP32 chunk
+    double *D64;
+    const uint64_t *row_max;  // |A| row maxima as FP64 bit patterns
+    const uint64_t *col_max;  // |B| column maxima as FP64 bit patterns
+    // FP8 mode
+    const float *scale_a;  // [M][kblocks]: power-of-two scale of A's 1 x 128 blocks
+    const float *scale_b;  // [kblocks][ceil(N / 128)]: scale of B's 128 x 128 tiles
+    int nblk_b;            // ceil(N / 128)
 };
 
-template <int BN, int STAGES> struct Cfg {
-    static constexpr int A_BYTES = BM * BK * 2;
-    static constexpr int B_BYTES = BK * BN * 2;
+// Ozaki term -> slice pair (s, u): weight classes g = s + u from S-1
+// (lightest) down to 0, heaviest digit of A first within a class.
+MOA_DEV void ozaki_pair(int term, int S, int &s, int &u) {
+    for (int g = S - 1; g >= 0; --g) {
+        if (term <= g) {
+            s = term;
+            u = g - term;
+            return;
+        }
+        term -= g + 1;
+    }
+    s = u = 0;
+}
+
+// Exponent e with |x| < 2^e for the largest |x| of a row / column, from its
+// FP64 bit pattern (0 for an all-zero row).
+MOA_DEV int scale_exponent(uint64_t maxbits) {
+    const int be = (int)((maxbits >> 52) & 0x7FF);
+    if (be == 0) return maxbits == 0 ? 0 : -1022;
+    return be - 1022;
+}
+
+template <int BN, int STAGES, int MODE = 0> struct Cfg {
+    static constexpr int ESZ = MODE == 3 ? 1 : 2;  // element bytes (e4m3 / bf16)
+    static constexpr int BKE = 128 / ESZ;          // elements per k-block (one 128-B swizzle row)
+    static constexpr int UK = 32 / ESZ;            // contraction depth of one MMA
+    static constexpr int BOXN = 128 / ESZ;         // N elements per B box
+    static constexpr int BOX_BYTES = BKE * 128;    // one B box: BKE rows of 128 B
+    static constexpr int A_BYTES = BM * 128;
+    static constexpr int B_BYTES = BKE * BN * ESZ;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int NBARS = 2 * STAGES + 5;
     static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 1024;  // + barriers, + alignment slack
-    static constexpr int TMEM_COLS = 2 * BN;
-    static constexpr uint32_t IDESC = ptx::idesc_bf16_f32(BM, BN, 1);
+    static constexpr int TMEM_COLS = (MODE == 2 ? 4 : 2) * BN;  // Ozaki: + hi / lo running sums
+    static constexpr uint32_t IDESC = MODE == 3 ? ptx::idesc_e4m3_f32(BM, BN, 1) : ptx::idesc_bf16_f32(BM, BN, 1);
     static_assert(NBARS * 8 + 16 <= 1024, "barrier area");
     static_assert(TMEM_COLS <= 512, "TMEM has 512 columns");
 };
@@ -95,10 +153,10 @@ MOA_DEV bool drain_wait(uint32_t bar, uint32_t parity) {
     return true;
 }
 
-template <int BN, int STAGES, bool PROMOTE>
+template <int BN, int STAGES, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const GemmParams p) {
-    using C = Cfg<BN, STAGES>;
+    using C = Cfg<BN, STAGES, MODE>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *bars = (uint64_t *)(smem + STAGES * C::STAGE_BYTES);
@@ -151,18 +209,27 @@ __global__ void __launch_bounds__(kThreads, 1)
             int tm, tn;
             tile_of(t, p.tiles_m, p.tiles_n, tm, tn);
             for (int it = 0; it < kiters; ++it) {
-                const int kb = it / p.n_terms, term = it - kb * p.n_terms;
+                int kb, pa, pb;
+                if constexpr (MODE == MODE_OZAKI) {  // term-major: all k-blocks of one slice pair
+                    const int term = it / p.kblocks;
+                    kb = it - term * p.kblocks;
+                    ozaki_pair(term, p.slices, pa, pb);
+                } else {  // k-block-major: every term of one k-block
+                    kb = it / p.n_terms;
+                    const int term = it - kb * p.n_terms;
+                    pa = (int)((p.term_a >> (4 * term)) & 15u);
+                    pb = (int)((p.term_b >> (4 * term)) & 15u);
+                }
                 if (!ptx::mbar_wait(empty(stage), phase ^ 1u, abort_flag, &g_tc_status)) {
                     ok = false;
                     break;
                 }
                 const uint32_t sa = tiles0 + stage * C::STAGE_BYTES, sb = sa + C::A_BYTES;
                 ptx::mbar_arrive_expect_tx(full(stage), C::STAGE_BYTES);
-                const int pa = (int)((p.term_a >> (4 * term)) & 15u), pb = (int)((p.term_b >> (4 * term)) & 15u);
-                ptx::tma_load_3d(sa, &tmA, full(stage), kb * BK, tm * BM, pa);
+                ptx::tma_load_3d(sa, &tmA, full(stage), kb * C::BKE, tm * BM, pa);
 #pragma unroll
-                for (int j = 0; j < BN / 64; ++j)
-                    ptx::tma_load_3d(sb + j * (BK * 128), &tmB, full(stage), tn * BN + j * 64, kb * BK, pb);
+                for (int j = 0; j < BN / C::BOXN; ++j)
+                    ptx::tma_load_3d(sb + j * C::BOX_BYTES, &tmB, full(stage), tn * BN + j * C::BOXN, kb * C::BKE, pb);
                 issued |= 1u << stage;
                 last_par = (last_par & ~(1u << stage)) | (phase << stage);
                 if (++stage == STAGES) {
@@ -180,12 +247,23 @@ __global__ void __launch_bounds__(kThreads, 1)
         int stage = 0, abuf = 0;
         uint32_t phase = 0, aphase = 0;
         bool ok = true;
-        // an accumulator is handed to the epilogue once per tile, or once
-        // per k-block (all terms of that k-block) when promoting
-        const int per_acc = PROMOTE ? p.n_terms : kiters;
+        // an accumulator is handed to the epilogue once per tile (store),
+        // once per k-block with all its terms (promote), or once per chunk of
+        // a slice pair (Ozaki)
         for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
             for (int it = 0; it < kiters; ++it) {
-                const int j = it % per_acc;  // position inside the current accumulator
+                int j, last;  // position inside the current accumulator; whether it is its last step
+                if constexpr (MODE == MODE_STORE) {
+                    j = it;
+                    last = it == kiters - 1;
+                } else if constexpr (MODE == MODE_PROMOTE || MODE == MODE_FP8) {
+                    j = it % p.n_terms;
+                    last = j == p.n_terms - 1;
+                } else {
+                    const int kb = it % p.kblocks;
+                    j = kb % p.chunk;
+                    last = (j == p.chunk - 1) || (kb == p.kblocks - 1);
+                }
                 if (j == 0) {
                     if (!ptx::mbar_wait(tempty(abuf), aphase ^ 1u, abort_flag, &g_tc_status)) {
                         ok = false;
@@ -201,17 +279,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                 ptx::tc_fence_after();
                 const uint32_t sa = tiles0 + stage * C::STAGE_BYTES, sb = sa + C::A_BYTES;
 #pragma unroll
-                for (int k = 0; k < BK / 16; ++k) {
+                for (int k = 0; k < C::BKE / C::UK; ++k) {
+                    // A: +32 B along the swizzled K row; B: +UK rows of 128 B
                     const uint64_t ad = ptx::smem_desc_sw128(sa + k * 32, 16, 1024);
-                    const uint64_t bd = ptx::smem_desc_sw128(sb + k * 2048, BK * 128, 1024);
-                    ptx::mma_bf16(dacc, ad, bd, C::IDESC, (j > 0 || k > 0) ? 1u : 0u);
+                    const uint64_t bd = ptx::smem_desc_sw128(sb + k * C::UK * 128, C::BOX_BYTES, 1024);
+                    if constexpr (MODE == MODE_FP8)
+                        ptx::mma_e4m3(dacc, ad, bd, C::IDESC, (j > 0 || k > 0) ? 1u : 0u);
+                    else
+                        ptx::mma_bf16(dacc, ad, bd, C::IDESC, (j > 0 || k > 0) ? 1u : 0u);
                 }
                 ptx::mma_commit(empty(stage));
                 if (++stage == STAGES) {
                     stage = 0;
                     phase ^= 1u;
                 }
-                if (j == per_acc - 1) {
+                if (last) {
                     ptx::mma_commit(tfull(abuf));
                     abuf ^= 1;
                     if (!abuf) aphase ^= 1u;
@@ -264,7 +346,113 @@ __global__ void __launch_bounds__(kThreads, 1)
             tile_of(t, p.tiles_m, p.tiles_n, tm, tn);
             const int64_t row = (int64_t)tm * BM + q * 32 + lane;
             const int64_t colh = (int64_t)tn * BN + half * HC;
-            if constexpr (PROMOTE) {
+            if constexpr (MODE == MODE_OZAKI) {
+                // double-float accumulator (hi + lo) in TMEM, units of 2^-lsb of 2^(e_row + e_col)
+                const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+                const uint32_t thi = lane_base + (uint32_t)(2 * BN + half * HC);
+                const uint32_t tlo = lane_base + (uint32_t)(3 * BN + half * HC);
+                {
+                    uint32_t z[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) z[j] = 0u;
+#pragma unroll
+                    for (int c0 = 0; c0 < HC; c0 += 16) {
+                        ptx::tmem_st16(thi + c0, z);
+                        ptx::tmem_st16(tlo + c0, z);
+                    }
+                    ptx::tmem_st_wait();
+                }
+                const int chunks = (p.kblocks + p.chunk - 1) / p.chunk;
+                for (int term = 0; term < p.n_terms && ok; ++term) {
+                    int sa_, sb_;
+                    ozaki_pair(term, p.slices, sa_, sb_);
+                    // weight of this pair, 2^k with 0 <= k < 128: exact in FP32
+                    const float w = __int_as_float((127 + p.lsb - (sa_ + sb_ + 2) * p.beta) << 23);
+                    for (int c = 0; c < chunks; ++c) {
+                        if (!wait_acc()) {
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t tb = lane_base + (uint32_t)(abuf * BN + half * HC);
+#pragma unroll 1
+                        for (int c0 = 0; c0 < HC; c0 += 16) {
+                            uint32_t r[16], h[16], l[16];
+                            ptx::tmem_ld16(tb + c0, r);
+                            ptx::tmem_ld16(thi + c0, h);
+                            ptx::tmem_ld16(tlo + c0, l);
+                            ptx::tmem_ld_wait();
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                // the chunk sum is an exact integer below 2^24; scaling by w is exact
+                                const float x = __fmul_rn(__uint_as_float(r[j]), w);
+                                const float hv = __uint_as_float(h[j]);
+                                const float sum = __fadd_rn(hv, x);  // TwoSum (Knuth)
+                                const float bv = __fsub_rn(sum, hv);
+                                const float err = __fadd_rn(__fsub_rn(hv, __fsub_rn(sum, bv)), __fsub_rn(x, bv));
+                                h[j] = __float_as_uint(sum);
+                                l[j] = __float_as_uint(__fadd_rn(__uint_as_float(l[j]), err));
+                            }
+                            ptx::tmem_st16(thi + c0, h);
+                            ptx::tmem_st16(tlo + c0, l);
+                        }
+                        ptx::tmem_st_wait();
+                        release_acc();
+                    }
+                }
+                if (!ok) break;
+#pragma unroll 1
+                for (int c0 = 0; c0 < HC; c0 += 16) {
+                    uint32_t h[16], l[16];
+                    ptx::tmem_ld16(thi + c0, h);
+                    ptx::tmem_ld16(tlo + c0, l);
+                    ptx::tmem_ld_wait();
+                    if (row < p.M) {
+                        const int er = scale_exponent(p.row_max[row]);
+                        double *dst = p.D64 + row * p.ldd;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const int64_t col = colh + c0 + j;
+                            if (col < p.N) {
+                                const int ec = scale_exponent(p.col_max[col]);
+                                dst[col] = ldexp((double)__uint_as_float(h[j]) + (double)__uint_as_float(l[j]),
+                                                 er + ec - p.lsb);
+                            }
+                        }
+                    }
+                }
+            } else if constexpr (MODE == MODE_FP8) {
+                float acc[HC];
+#pragma unroll
+                for (int j = 0; j < HC; ++j) acc[j] = 0.0f;
+                const int colblk = (int)(colh / 128);  // HC <= 128 columns, all in one B scale block
+                const bool row_ok = row < p.M;
+                for (int kb = 0; kb < p.kblocks; ++kb) {
+                    if (!wait_acc()) {
+                        ok = false;
+                        break;
+                    }
+                    const float sa = row_ok ? p.scale_a[row * p.kblocks + kb] : 0.0f;
+                    const float f = __fmul_rn(sa, colh < p.N ? p.scale_b[(int64_t)kb * p.nblk_b + colblk] : 0.0f);
+                    const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(abuf * BN + half * HC);
+#pragma unroll
+                    for (int c = 0; c < HC; c += 32) {
+                        uint32_t r[32];
+                        ptx::tmem_ld32(tb + c, r);
+                        ptx::tmem_ld_wait();
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) acc[c + j] = fmaf(__uint_as_float(r[j]), f, acc[c + j]);
+                    }
+                    release_acc();
+                }
+                if (!ok) break;
+#pragma unroll
+                for (int c = 0; c < HC; c += 32) {
+                    uint32_t r[32];
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) r[j] = __float_as_uint(acc[c + j]);
+                    store32(row, colh + c, r);
+                }
+            } else if constexpr (MODE == MODE_PROMOTE) {
                 float acc[HC];
 #pragma unroll
                 for (int j = 0; j < HC; ++j) acc[j] = 0.0f;
@@ -333,14 +521,15 @@ PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
 // 3-D bf16 tensor [planes][rows][inner] with the given strides (bytes),
 // 128-B swizzled boxes of box_inner x box_rows.
 bool make_tmap(CUtensorMap *m, const void *base, uint64_t inner, uint64_t rows, uint64_t planes, uint64_t row_bytes,
-               uint64_t plane_bytes, uint32_t box_inner, uint32_t box_rows) {
+               uint64_t plane_bytes, uint32_t box_inner, uint32_t box_rows,
+               CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16) {
     auto enc = tmap_encoder();
     if (!enc) return false;
     cuuint64_t dims[3] = {inner, rows, planes};
     cuuint64_t strides[2] = {row_bytes, plane_bytes};
     cuuint32_t box[3] = {box_inner, box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
+    return enc(m, dt, 3, const_cast<void *>(base), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -356,13 +545,13 @@ int num_sms() {
     return n;
 }
 
-template <int BN, int STAGES, bool PROMOTE>
+template <int BN, int STAGES, int MODE>
 cudaError_t launch_tc(const CUtensorMap &ta, const CUtensorMap &tb, GemmParams &p, cudaStream_t s) {
-    using C = Cfg<BN, STAGES>;
+    using C = Cfg<BN, STAGES, MODE>;
     static bool attr = false;
     if (!attr) {
         cudaError_t e =
-            cudaFuncSetAttribute(tc_gemm_bf16<BN, STAGES, PROMOTE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+            cudaFuncSetAttribute(tc_gemm_bf16<BN, STAGES, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -370,7 +559,7 @@ cudaError_t launch_tc(const CUtensorMap &ta, const CUtensorMap &tb, GemmParams &
     p.tiles_n = (p.N + BN - 1) / BN;
     const int tiles = p.tiles_m * p.tiles_n;
     const int grid = tiles < num_sms() ? tiles : num_sms();
-    tc_gemm_bf16<BN, STAGES, PROMOTE><<<grid, kThreads, C::SMEM, s>>>(ta, tb, p);
+    tc_gemm_bf16<BN, STAGES, MODE><<<grid, kThreads, C::SMEM, s>>>(ta, tb, p);
     return cudaGetLastError();
 }
 
@@ -404,9 +593,60 @@ moa_status tc_gemm_planes(const __nv_bfloat16 *A, int64_t lda, int planesA, cons
     p.vec_store = ((uintptr_t)D % 16 == 0) && (ldd % 4 == 0);
     cudaError_t e;
     if (promote)
-        e = BN == 128 ? launch_tc<128, 6, true>(ta, tb, p, s) : launch_tc<256, 4, true>(ta, tb, p, s);
+        e = BN == 128 ? launch_tc<128, 6, MODE_PROMOTE>(ta, tb, p, s) : launch_tc<256, 4, MODE_PROMOTE>(ta, tb, p, s);
     else
-        e = BN == 128 ? launch_tc<128, 6, false>(ta, tb, p, s) : launch_tc<256, 4, false>(ta, tb, p, s);
+        e = BN == 128 ? launch_tc<128, 6, MODE_STORE>(ta, tb, p, s) : launch_tc<256, 4, MODE_STORE>(ta, tb, p, s);
+    return e == cudaSuccess ? MOA_OK : MOA_ERR_CUDA;
+}
+
+// FP8 GEMM: A8 [M][lda] and B8 [K][ldb] e4m3 bytes (lda, ldb multiples of 16),
+// scale_a [M][ceil(K/128)], scale_b [ceil(K/128)][ceil(N/128)] powers of two;
+// D (M x N, FP32, row stride ldd) = sum over k-blocks of sA * sB * (A8 . B8).
+moa_status tc_gemm_fp8(const uint8_t *A, int64_t lda, const uint8_t *B, int64_t ldb, const float *scale_a,
+                       const float *scale_b, float *D, int64_t ldd, int64_t M, int64_t N, int64_t K, cudaStream_t s) {
+    if (M >= (1ll << 31) || N >= (1ll << 31) || K >= (1ll << 31)) return MOA_ERR_OVERFLOW;
+    if ((uintptr_t)A % 16 || (uintptr_t)B % 16 || lda % 16 || ldb % 16) return MOA_ERR_INTERNAL;
+    CUtensorMap ta, tb;
+    if (!make_tmap(&ta, A, (uint64_t)K, (uint64_t)M, 1, (uint64_t)lda, (uint64_t)(lda * M), 128, BM,
+                   CU_TENSOR_MAP_DATA_TYPE_UINT8))
+        return MOA_ERR_CUDA;
+    if (!make_tmap(&tb, B, (uint64_t)N, (uint64_t)K, 1, (uint64_t)ldb, (uint64_t)(ldb * K), 128, 128,
+                   CU_TENSOR_MAP_DATA_TYPE_UINT8))
+        return MOA_ERR_CUDA;
+    GemmParams p{};
+    p.M = (int)M, p.N = (int)N, p.K = (int)K;
+    p.kblocks = (int)((K + 127) / 128);
+    p.n_terms = 1;
+    p.D = D, p.ldd = ldd;
+    p.vec_store = ((uintptr_t)D % 16 == 0) && (ldd % 4 == 0);
+    p.scale_a = scale_a, p.scale_b = scale_b, p.nblk_b = (int)((N + 127) / 128);
+    cudaError_t e = launch_tc<256, 4, MODE_FP8>(ta, tb, p, s);
+    return e == cudaSuccess ? MOA_OK : MOA_ERR_CUDA;
+}
+
+// Ozaki slice-pair GEMM: planes [S][M][lda] and [S][K][ldb] of bf16 digits,
+// D64 (M x N, FP64, row stride ldd) = sum over pairs s + u < S of
+// 2^(e_row + e_col - (s + u + 2) * beta) * (A_s . B_u); lsb is chosen so
+// every pair weight 2^(lsb - (s + u + 2) beta) is within FP32's range.
+moa_status tc_gemm_ozaki(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb, int S, int beta,
+                         int lsb, int chunk_kblocks, const uint64_t *row_max, const uint64_t *col_max, double *D,
+                         int64_t ldd, int64_t M, int64_t N, int64_t K, cudaStream_t s) {
+    if (M >= (1ll << 31) || N >= (1ll << 31) || K >= (1ll << 31)) return MOA_ERR_OVERFLOW;
+    if (S < 1 || S > 10 || chunk_kblocks < 1 || lsb - 2 * beta > 100 || lsb - (S + 1) * beta < 0)
+        return MOA_ERR_INTERNAL;
+    if ((uintptr_t)A % 16 || (uintptr_t)B % 16 || lda % 8 || ldb % 8) return MOA_ERR_INTERNAL;
+    CUtensorMap ta, tb;
+    if (!make_tmap(&ta, A, (uint64_t)K, (uint64_t)M, (uint64_t)S, (uint64_t)lda * 2, (uint64_t)(lda * M * 2), BK, BM))
+        return MOA_ERR_CUDA;
+    if (!make_tmap(&tb, B, (uint64_t)N, (uint64_t)K, (uint64_t)S, (uint64_t)ldb * 2, (uint64_t)(ldb * K * 2), 64, BK))
+        return MOA_ERR_CUDA;
+    GemmParams p{};
+    p.M = (int)M, p.N = (int)N, p.K = (int)K;
+    p.kblocks = (int)((K + BK - 1) / BK);
+    p.n_terms = S * (S + 1) / 2;
+    p.slices = S, p.beta = beta, p.lsb = lsb, p.chunk = chunk_kblocks;
+    p.D64 = D, p.ldd = ldd, p.row_max = row_max, p.col_max = col_max;
+    cudaError_t e = launch_tc<128, 6, MODE_OZAKI>(ta, tb, p, s);
     return e == cudaSuccess ? MOA_OK : MOA_ERR_CUDA;
 }
 

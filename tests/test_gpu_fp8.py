@@ -1,0 +1,55 @@
+"""GPU parity of the FP8 (e4m3, per-128 power-of-two scales) form of the
+(+,*) inner product against the oracle's Dot2 reference of the FP32
+operands.  Tolerance: 6e-2 for contractions of 256 or more; below that the
+bound comes from the arithmetic alone — each product carries at most two
+e4m3 roundings (unit roundoff u = 2^-4), so |error| <= (2u + u^2) sum|a||b|,
+i.e. 0.129."""
+import numpy as np
+import pytest
+
+import paper_0907_0792_gb300 as moa
+import synth
+from gpu_helpers import assert_norm_err, check_status, empty, sample_idx, to_dev
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -4
+SMALL_K_TOL = 2 * U + U * U
+SHAPES = [((300, 136), (136, 200)), ((2, 64, 72), (72, 5, 80)), ((129, 8), (8, 257)), ((37, 61), (61, 45)),
+          ((520, 1000), (1000, 700)), ((130, 300), (300, 131)), ((1, 1), (1, 1))]
+
+
+def _fp8(A, B):
+    import torch
+    D = empty(A.shape[:-1] + B.shape[1:], torch.float32)
+    moa.moa_inner("add", "mul", "f32", "fp8_t128", A.shape, to_dev(A), B.shape, to_dev(B), D, "f32")
+    return D
+
+
+@pytest.mark.parametrize("shA,shB", SHAPES)
+@pytest.mark.parametrize("dist", ["uniform", "loguniform"])
+def test_fp8_small(shA, shB, dist):
+    if dist == "uniform":
+        A = synth.to_f32(synth.uniform(51, 0, shA, -1, 1))
+        B = synth.to_f32(synth.uniform(51, 1, shB, -1, 1))
+    else:
+        A = synth.to_f32(synth.log_uniform_signed(51, 0, shA))
+        B = synth.to_f32(synth.log_uniform_signed(51, 1, shB))
+    tol = 6e-2 if shA[-1] >= 256 else SMALL_K_TOL
+    assert_norm_err(_fp8(A, B).cpu().numpy(), A, B, tol)
+    check_status()
+
+
+@pytest.mark.parametrize("n", [512, 4096, 8192])
+def test_fp8_square(n):
+    import torch
+    idx = sample_idx(n * n, 2000)
+    for dist in ("uniform", "loguniform"):
+        A64, B64 = synth.square(n, dist)
+        A, B = synth.to_f32(A64), synth.to_f32(B64)
+        D = _fp8(A, B)
+        got = D.view(-1)[torch.from_numpy(idx).to(D.device)].cpu().numpy()
+        assert_norm_err(got, A, B, 6e-2, out_idx=idx)
+        del D
+    check_status()
+    torch.cuda.empty_cache()

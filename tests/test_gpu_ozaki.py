@@ -1,0 +1,69 @@
+"""GPU parity of the Ozaki-sliced FP64 (+,*) inner product (tensor cores,
+FP64-accurate) against the oracle's Dot2 reference: normalised error
+<= 1e-12, the bound the plain FP64 form is held to."""
+import numpy as np
+import pytest
+
+import paper_0907_0792_gb300 as moa
+import synth
+from gpu_helpers import assert_norm_err, check_status, empty, sample_idx, to_dev
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+SHAPES = [((300, 136), (136, 200)), ((2, 64, 72), (72, 5, 80)), ((129, 8), (8, 257)), ((1, 1), (1, 1)),
+          ((37, 61), (61, 45)), ((130, 1500), (1500, 131)), ((16, 12, 8, 64), (64, 24, 20))]
+
+
+def _ozaki(A, B):
+    import torch
+    D = empty(A.shape[:-1] + B.shape[1:], torch.float64)
+    moa.moa_inner("add", "mul", "f64", "ozaki", A.shape, to_dev(A), B.shape, to_dev(B), D, "f64")
+    return D
+
+
+@pytest.mark.parametrize("shA,shB", SHAPES)
+@pytest.mark.parametrize("dist", ["uniform", "loguniform"])
+def test_ozaki_small(shA, shB, dist):
+    if dist == "uniform":
+        A, B = synth.uniform(41, 0, shA, -1, 1), synth.uniform(41, 1, shB, -1, 1)
+    else:
+        A, B = synth.log_uniform_signed(41, 0, shA), synth.log_uniform_signed(41, 1, shB)
+    D = _ozaki(A, B)
+    assert_norm_err(D.cpu().numpy(), A, B, TOL)
+    check_status()
+
+
+def test_ozaki_zero_rows_columns_and_wide_range():
+    A = synth.uniform(42, 0, (70, 90), -1, 1)
+    B = synth.uniform(42, 1, (90, 50), -1, 1)
+    A[3] = 0.0
+    B[:, 7] = 0.0
+    A[5] *= 1e200
+    B[:, 9] *= 1e-200
+    A[6, 4] = 5e-310  # subnormal entry
+    D = _ozaki(A, B).cpu().numpy()
+    assert np.all(D[3] == 0) and np.all(D[:, 7] == 0)
+    assert_norm_err(D, A, B, TOL)
+
+
+@pytest.mark.parametrize("n", [512])
+def test_ozaki_square_whole(n):
+    for dist in ("uniform", "loguniform"):
+        A, B = synth.square(n, dist)
+        assert_norm_err(_ozaki(A, B).cpu().numpy(), A, B, TOL)
+    check_status()
+
+
+@pytest.mark.parametrize("n", [4096, 8192])
+def test_ozaki_square_large_sampled(n):
+    import torch
+    idx = sample_idx(n * n, 1000)
+    for dist in ("uniform", "loguniform"):
+        A, B = synth.square(n, dist)
+        D = _ozaki(A, B)
+        got = D.view(-1)[torch.from_numpy(idx).to(D.device)].cpu().numpy()
+        assert_norm_err(got, A, B, TOL, out_idx=idx)
+        del D
+    check_status()
+    torch.cuda.empty_cache()
