@@ -247,6 +247,57 @@ def _row_plain_method(moa, torch, reps, stream):
             "outer_ms": round(ms_o, 4), "outer_gbs": round((C.numel() + A.size) * 8 / (ms_o * 1e-3) / 1e9, 1)}
 
 
+def _row_batched(moa, torch, reps, stream):
+    """The uneven batch: 10,000 problems (70% split-BF16x3, 20% (min,+),
+    10% outer) through one plan (grouped persistent kernel in a CUDA graph),
+    against one call per problem of the same forms."""
+    import synth
+    probs = synth.batched_problems()
+    pool, oa, ob, od, dtot = synth.batched_inputs(probs)
+    dpool = torch.from_numpy(pool).cuda()
+    dout = torch.empty((dtot,), dtype=torch.float32, device="cuda")
+    base, obase = dpool.data_ptr(), dout.data_ptr()
+    specs = []
+    for p, a, b, d in zip(probs, oa, ob, od):
+        common = dict(shapeA=p["shapeA"], shapeB=p["shapeB"], A=base + 4 * a, B=base + 4 * b, out=obase + 4 * d)
+        if p["kind"] == "outer":
+            specs.append(dict(kind="outer", combine="mul", **common))
+        elif p["kind"] == "minplus":
+            specs.append(dict(kind="inner", reduce="min", combine="add", **common))
+        else:
+            specs.append(dict(kind="inner", form="bf16x3", **common))
+    arr, keep = moa.make_problems(specs)
+    plan = moa.moa_batch_plan_create(arr)
+    info = moa.moa_batch_plan_info(plan)
+    t0 = time.perf_counter()
+    moa.moa_batch_execute(plan, stream)  # tunes (first use) and captures the graph
+    torch.cuda.synchronize()
+    first_s = time.perf_counter() - t0
+    moa.moa_batch_execute(plan, stream)
+    ms = _events_time(lambda: moa.moa_batch_execute(plan, stream), reps, stream)
+
+    def per_problem():
+        for sp in specs:
+            if sp["kind"] == "outer":
+                moa.moa_outer("mul", "f32", sp["shapeA"], sp["A"], sp["shapeB"], sp["B"], sp["out"], "f32", stream)
+            elif sp.get("reduce") == "min":
+                moa.moa_inner("min", "add", "f32", "native", sp["shapeA"], sp["A"], sp["shapeB"], sp["B"], sp["out"],
+                              "f32", stream)
+            else:
+                moa.moa_inner("add", "mul", "f32", "bf16x3", sp["shapeA"], sp["A"], sp["shapeB"], sp["B"], sp["out"],
+                              "f32", stream)
+    per_problem()
+    ms_single = _events_time(per_problem, 1, stream)
+    moa.moa_batch_plan_destroy(plan)
+    n = len(probs)
+    return {"problems": n, "items": info["items"] if "items" in info else info["tiles"],
+            "grouped_launches_per_execute": info["launches"], "ms": round(ms, 3),
+            "problems_per_s": round(n / (ms * 1e-3), 1),
+            "effective_tflops": round(info["work_flops"] / (ms * 1e-3) / 1e12, 2),
+            "one_call_per_problem_ms": round(ms_single, 3), "speedup_vs_one_call_per_problem": round(ms_single / ms, 2),
+            "first_execute_s_incl_tuning": round(first_s, 3)}
+
+
 # ---------------------------------------------------------------- CPU oracle
 def cpu_oracle_sample(seconds: float = 12.0, threads: int | None = None):
     """The oracle's appendix-order loop (FP64, OpenMP over rows) on the first
@@ -298,7 +349,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="moa", choices=["moa", "reference"])
     ap.add_argument("--rows", default="all",
-                    help="comma list of extra rows to measure: sweep,semirings,outer,plain (all / none)")
+                    help="comma list of extra rows to measure: sweep,semirings,outer,plain,batched (all / none)")
     ap.add_argument("--no-rows", action="store_true", help="same as --rows none")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -384,7 +435,7 @@ def main():
 
     rows = {}
     want = set() if args.no_rows or args.rows == "none" else (
-        {"sweep", "semirings", "outer", "plain"} if args.rows == "all" else set(args.rows.split(",")))
+        {"sweep", "semirings", "outer", "plain", "batched"} if args.rows == "all" else set(args.rows.split(",")))
     if want:
         flush_buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
         flush = lambda: _flush_l2(flush_buf)
@@ -408,6 +459,8 @@ def main():
                                             ("mul", "bf16"), ("div", "bf16"), ("mul", "i32"))]
         if "plain" in want:
             rows["plain_method_f64_rank4x3"] = _row_plain_method(moa, torch, 20, stream)
+        if "batched" in want:
+            rows["batched_10000"] = _row_batched(moa, torch, 10, stream)
         del flush_buf
         st = moa.moa_device_status()
         if st != 0:

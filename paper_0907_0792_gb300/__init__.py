@@ -21,7 +21,7 @@ __all__ = [
     "MoaError", "lib", "moa_inner", "moa_outer", "moa_inner_shape", "moa_outer_shape", "moa_status_string",
     "moa_device_status", "moa_release_workspace", "moa_version", "inner", "outer", "OPS", "DTYPES", "FORMS",
     "moa_batch_plan_create", "moa_batch_execute", "moa_batch_plan_destroy", "moa_batch_plan_info", "MoaProblem",
-    "moa_inner_bf16x3_noalloc", "NOALLOC_SCRATCH_BYTES",
+    "moa_inner_bf16x3_noalloc", "NOALLOC_SCRATCH_BYTES", "make_problems",
 ]
 
 # size of the fixed device buffer behind moa_inner_bf16x3_noalloc (MOA_NOALLOC_SCRATCH_BYTES)
@@ -190,6 +190,29 @@ def moa_release_workspace() -> int:
 
 def moa_version() -> int:
     return int(lib().moa_version())
+
+
+def make_problems(specs):
+    """Build a ctypes array of MoaProblem from dicts with keys kind ("inner" |
+    "outer"), reduce, combine, dtype, form, out_dtype, shapeA, shapeB, A, B,
+    out (tensors or device addresses).  Returns (array, keep-alive list)."""
+    arr = (MoaProblem * len(specs))()
+    keep = []
+    for i, sp in enumerate(specs):
+        sa, ka = _shape(sp["shapeA"])
+        sb, kb = _shape(sp["shapeB"])
+        keep += [ka, kb]
+        q = arr[i]
+        q.kind = 0 if sp["kind"] == "inner" else 1
+        q.reduce = _enum(OPS, sp.get("reduce", "add"))
+        q.combine = _enum(OPS, sp.get("combine", "mul"))
+        q.dtype = _enum(DTYPES, sp.get("dtype", "f32"))
+        q.form = _enum(FORMS, sp.get("form", "native"))
+        q.out_dtype = _enum(DTYPES, sp.get("out_dtype", "f32"))
+        q.rankA, q.rankB = len(sp["shapeA"]), len(sp["shapeB"])
+        q.shapeA, q.shapeB = sa, sb
+        q.A, q.B, q.out = _ptr(sp["A"]), _ptr(sp["B"]), _ptr(sp["out"])
+    return arr, keep
 
 
 def moa_batch_plan_create(problems):

@@ -316,9 +316,10 @@ const char *moa_status_string(moa_status s) {
 
 moa_status moa_device_status(moa_stream stream) {
     if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return MOA_ERR_CUDA;
-    uint32_t flags = 0;
+    uint32_t flags = 0, bflags = 0;
     if (tc_read_and_clear_status(&flags) != cudaSuccess) return MOA_ERR_CUDA;
-    if (flags & kStatusTimeout) return MOA_ERR_TIMEOUT;
+    if (batch_read_and_clear_status(&bflags) != cudaSuccess) return MOA_ERR_CUDA;
+    if ((flags | bflags) & kStatusTimeout) return MOA_ERR_TIMEOUT;
     return MOA_OK;
 }
 

@@ -1,34 +1,901 @@
-// Batched execution of many inner / outer products (placeholder until the
-// grouped persistent kernel lands).
+// Batched execution of many generalized inner / outer products of uneven
+// ranks and shapes (Eq. 1 and Eq. 2 per problem) in one grouped launch.
+//
+// Plan (host, moa_batch_plan_create): every problem is validated as its
+// single call would be and psi-flattened; its work is cut into items —
+//   TC   one 128 x 128 tile of a split-BF16x3 (+,*) problem (tensor cores),
+//   CC   one 128 x 128 tile of a CUDA-core semiring problem ((min|max|+),
+//        (+|*)) — 8 x 8 register micro-tiles, shared-memory panels,
+//   OUT  a block of rows of an outer product,
+//   FILL the reduce identity for an inner product with an empty contraction.
+// Items are ordered by an estimated cost (the ordering policy is picked by
+// the autotuner), and per-problem descriptors, the TMA tensor maps of the
+// split planes and the item list are uploaded once.
+//
+// Execute (moa_batch_execute): a CUDA graph, captured on the first execute
+// and replayed after, holding (1) the grouped split pre-pass (FP32 -> three
+// bf16 planes for every BF16x3 problem) and (2) one persistent grouped
+// kernel (one CTA per SM).  In that kernel the TMA warp pulls item indices
+// from a device-side queue (one atomic counter) and hands each to the MMA
+// warp and the 8 epilogue warps through a 4-slot ring of shared-memory slots
+// guarded by mbarriers.  TC items run the tcgen05 pipeline of tc_gemm.cu in
+// its promoted form (per-k-block FP32 promotion); CC / OUT / FILL items are
+// computed by the 8 epilogue warps while the TMA and MMA warps run ahead on
+// the next tensor-core item, so tensor-core and CUDA-core work overlap.
+// Every wait is bounded and reports through the batch status word.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
 #include "common.cuh"
 #include "internal.h"
+#include "semiring_ops.cuh"
+#include "tc.h"
+#include "tc_ptx.cuh"
+
+namespace moa {
+
+__device__ uint32_t g_batch_status;
+
+namespace {
+
+enum ItemType { IT_TC = 0, IT_CC = 1, IT_OUT = 2, IT_FILL = 3 };
+enum CcOp { CC_MIN_PLUS = 0, CC_MAX_PLUS = 1, CC_MIN_TIMES = 2, CC_MAX_TIMES = 3, CC_PLUS_TIMES = 4 };
+
+struct alignas(16) BInst {
+    int32_t type;  // IT_*
+    int32_t op;    // CcOp (CC), moa_op (OUT), fill bit pattern (FILL)
+    int32_t M, N, K, kblocks;
+    const float *A;
+    const float *B;
+    float *D;
+    int32_t tmap;  // TC: index of A's tensor map; B's follows it
+    int32_t vec;   // D 16-byte aligned and N % 4 == 0
+};
+
+struct alignas(16) BItem {
+    int32_t inst, type, a, b;  // TC / CC: tile (a = row tile, b = column tile); OUT / FILL: rows [a, a + b)
+};
+
+struct SplitJob {
+    const float *src;
+    __nv_bfloat16 *dst;
+    int64_t cols, colsp, plane, r0, r1;
+};
+
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4, RING = 4, TERMS = 6;
+constexpr int kThreads = 320, kEpiWarps = 8;
+constexpr int A_BYTES = BM * BK * 2, B_BYTES = BK * BN * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int CC_BK = 16, CC_PAD = 4, CC_LD = 128 + CC_PAD;
+constexpr int CC_BYTES = 2 * 2 * CC_BK * CC_LD * 4;  // As[2][16][132] + Bs[2][16][132]
+constexpr int NBARS = 2 * STAGES + 5 + 2 * RING;
+constexpr int SMEM = STAGES * STAGE_BYTES + CC_BYTES + 1024 + 1024;
+constexpr int TMEM_COLS = 2 * BN;
+constexpr uint32_t IDESC = ptx::idesc_bf16_f32(BM, BN, 1);
+// split-BF16x3 terms (plane of A, plane of B): small products first, hi*hi last
+__constant__ int kTermA[TERMS] = {1, 0, 2, 0, 1, 0};
+__constant__ int kTermB[TERMS] = {1, 2, 0, 1, 0, 0};
+
+struct BatchParams {
+    const BInst *inst;
+    const BItem *items;
+    int n_items;
+    int *queue;
+    const CUtensorMap *tmaps;
+};
+
+MOA_DEV void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+// One 128 x 128 CUDA-core tile of D = reduce_p(A combine B), 256 threads
+// (the epilogue warps), panels in shared memory, tail of K by a short loop.
+template <class Op>
+MOA_DEV void cc_tile(const BInst &in, int tm, int tn, float *As, float *Bs, int tid) {
+    const int64_t M = in.M, N = in.N, K = in.K;
+    const float *A = in.A, *B = in.B;
+    const int tx = tid % 16, ty = tid / 16;
+    const int64_t m0 = (int64_t)tm * 128, n0 = (int64_t)tn * 128;
+    const int a_k = tid % CC_BK, a_m = tid / CC_BK;  // 16 rows per pass
+    const int b_n = tid % 128, b_k = tid / 128;      // 2 rows per pass
+    float ra[8], rb[8];
+    auto load = [&](int64_t k0) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int64_t m = m0 + a_m + r * 16, k = k0 + a_k;
+            ra[r] = (m < M && k < K) ? __ldg(A + m * K + k) : Op::identity();
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int64_t k = k0 + b_k + r * 2, n = n0 + b_n;
+            rb[r] = (k < K && n < N) ? __ldg(B + k * N + n) : Op::identity();
+        }
+    };
+    auto stash = [&](int buf) {
+        float *as = As + buf * CC_BK * CC_LD, *bs = Bs + buf * CC_BK * CC_LD;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) as[a_k * CC_LD + a_m + r * 16] = ra[r];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) bs[(b_k + r * 2) * CC_LD + b_n] = rb[r];
+    };
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = Op::identity();
+    const int64_t full = K / CC_BK;
+    const int tail = (int)(K - full * CC_BK);
+    const int64_t panels = full + (tail ? 1 : 0);
+    if (panels > 0) {
+        load(0);
+        stash(0);
+    }
+    epi_bar();
+    for (int64_t p = 0; p < panels; ++p) {
+        const int buf = (int)(p & 1);
+        if (p + 1 < panels) load((p + 1) * CC_BK);
+        const float *as = As + buf * CC_BK * CC_LD + ty * 8, *bs = Bs + buf * CC_BK * CC_LD + tx * 8;
+        if (p < full) {
+#pragma unroll
+            for (int kk = 0; kk < CC_BK; kk += 2) {
+                float a0[8], b0[8], a1[8], b1[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) a0[i] = as[kk * CC_LD + i], a1[i] = as[(kk + 1) * CC_LD + i];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) b0[j] = bs[kk * CC_LD + j], b1[j] = bs[(kk + 1) * CC_LD + j];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] = Op::step2(acc[i][j], a0[i], b0[j], a1[i], b1[j]);
+            }
+        } else {
+            for (int kk = 0; kk < tail; ++kk) {
+                float a0[8], b0[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) a0[i] = as[kk * CC_LD + i];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) b0[j] = bs[kk * CC_LD + j];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] = Op::step(acc[i][j], a0[i], b0[j]);
+            }
+        }
+        if (p + 1 < panels) stash(buf ^ 1);
+        epi_bar();
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int64_t m = m0 + ty * 8 + i;
+        if (m >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int64_t n = n0 + tx * 8 + j;
+            if (n < N) in.D[m * N + n] = acc[i][j];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    batch_grouped_kernel(const __grid_constant__ BatchParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    float *ccA = (float *)(smem + STAGES * STAGE_BYTES);
+    float *ccB = ccA + 2 * CC_BK * CC_LD;
+    uint64_t *bars = (uint64_t *)(smem + STAGES * STAGE_BYTES + CC_BYTES);
+    uint32_t *tmem_slot = (uint32_t *)(bars + NBARS);
+    volatile uint32_t *abort_flag = tmem_slot + 1;
+    volatile int *ring = (volatile int *)(tmem_slot + 2);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const uint32_t tiles0 = ptx::smem_u32(smem);
+    const uint32_t bar0 = ptx::smem_u32(bars);
+    auto full = [&](int s) { return bar0 + 8u * s; };
+    auto empty = [&](int s) { return bar0 + 8u * (STAGES + s); };
+    auto tfull = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
+    auto tempty = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 + b); };
+    const uint32_t drain = bar0 + 8u * (2 * STAGES + 4);
+    auto rfull = [&](int s) { return bar0 + 8u * (2 * STAGES + 5 + s); };
+    auto rempty = [&](int s) { return bar0 + 8u * (2 * STAGES + 5 + RING + s); };
+    uint32_t *status = &g_batch_status;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) ptx::mbar_init(full(s), 1), ptx::mbar_init(empty(s), 1);
+        for (int b = 0; b < 2; ++b) ptx::mbar_init(tfull(b), 1), ptx::mbar_init(tempty(b), kEpiWarps);
+        ptx::mbar_init(drain, 1);
+        for (int s = 0; s < RING; ++s) ptx::mbar_init(rfull(s), 1), ptx::mbar_init(rempty(s), 1 + kEpiWarps);
+        *abort_flag = 0u;
+        ptx::fence_mbar_init();
+        ptx::fence_proxy_async_smem();
+    }
+    if (warp == 1) {
+        ptx::tmem_alloc(ptx::smem_u32(tmem_slot), TMEM_COLS);
+        ptx::tmem_relinquish();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // ------------------------------------------------ queue + TMA producer
+        int stage = 0, slot = 0;
+        uint32_t phase = 0, rphase = 0, issued = 0, last_par = 0;
+        bool ok = true;
+        for (;;) {
+            int item = atomicAdd(p.queue, 1);
+            if (item >= p.n_items) item = -1;
+            if (!ptx::mbar_wait(rempty(slot), rphase ^ 1u, abort_flag, status)) {
+                ok = false;
+                break;
+            }
+            ring[slot] = item;
+            ptx::mbar_arrive(rfull(slot));
+            if (++slot == RING) slot = 0, rphase ^= 1u;
+            if (item < 0) break;
+            const BItem it = p.items[item];
+            if (it.type != IT_TC) continue;
+            const BInst in = p.inst[it.inst];
+            const CUtensorMap *ta = p.tmaps + in.tmap, *tb = ta + 1;
+            ptx::fence_tensormap(ta);
+            ptx::fence_tensormap(tb);
+            const int kiters = in.kblocks * TERMS;
+            for (int i = 0; i < kiters; ++i) {
+                const int kb = i / TERMS, term = i - kb * TERMS;
+                if (!ptx::mbar_wait(empty(stage), phase ^ 1u, abort_flag, status)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t sa = tiles0 + stage * STAGE_BYTES, sb = sa + A_BYTES;
+                ptx::mbar_arrive_expect_tx(full(stage), STAGE_BYTES);
+                ptx::tma_load_3d(sa, ta, full(stage), kb * BK, it.a * BM, kTermA[term]);
+#pragma unroll
+                for (int j = 0; j < BN / 64; ++j)
+                    ptx::tma_load_3d(sb + j * (BK * 128), tb, full(stage), it.b * BN + j * 64, kb * BK, kTermB[term]);
+                issued |= 1u << stage;
+                last_par = (last_par & ~(1u << stage)) | (phase << stage);
+                if (++stage == STAGES) stage = 0, phase ^= 1u;
+            }
+            if (!ok) break;
+        }
+        if (!ok) {
+            for (int s = 0; s < STAGES; ++s)
+                if (issued & (1u << s)) {
+                    const uint64_t t0 = globaltimer();
+                    while (!ptx::mbar_try_wait(full(s), (last_par >> s) & 1u) && globaltimer() - t0 < kWaitLimitNs) {
+                    }
+                }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ------------------------------------------------ MMA issuer
+        int stage = 0, abuf = 0, slot = 0;
+        uint32_t phase = 0, aphase = 0, rphase = 0;
+        bool ok = true;
+        for (;;) {
+            if (!ptx::mbar_wait(rfull(slot), rphase, abort_flag, status)) {
+                ok = false;
+                break;
+            }
+            const int item = ring[slot];
+            ptx::mbar_arrive(rempty(slot));
+            if (++slot == RING) slot = 0, rphase ^= 1u;
+            if (item < 0) break;
+            const BItem it = p.items[item];
+            if (it.type != IT_TC) continue;
+            const int kiters = p.inst[it.inst].kblocks * TERMS;
+            for (int i = 0; i < kiters; ++i) {
+                const int j = i % TERMS;
+                if (j == 0) {
+                    if (!ptx::mbar_wait(tempty(abuf), aphase ^ 1u, abort_flag, status)) {
+                        ok = false;
+                        break;
+                    }
+                    ptx::tc_fence_after();
+                }
+                if (!ptx::mbar_wait(full(stage), phase, abort_flag, status)) {
+                    ok = false;
+                    break;
+                }
+                ptx::tc_fence_after();
+                const uint32_t sa = tiles0 + stage * STAGE_BYTES, sb = sa + A_BYTES;
+                const uint32_t dacc = tmem + (uint32_t)(abuf * BN);
+#pragma unroll
+                for (int k = 0; k < BK / 16; ++k) {
+                    const uint64_t ad = ptx::smem_desc_sw128(sa + k * 32, 16, 1024);
+                    const uint64_t bd = ptx::smem_desc_sw128(sb + k * 2048, BK * 128, 1024);
+                    ptx::mma_bf16(dacc, ad, bd, IDESC, (j > 0 || k > 0) ? 1u : 0u);
+                }
+                ptx::mma_commit(empty(stage));
+                if (++stage == STAGES) stage = 0, phase ^= 1u;
+                if (j == TERMS - 1) {
+                    ptx::mma_commit(tfull(abuf));
+                    abuf ^= 1;
+                    if (!abuf) aphase ^= 1u;
+                }
+            }
+            if (!ok) break;
+        }
+        if (!ok) {
+            ptx::mma_commit(drain);
+            const uint64_t t0 = globaltimer();
+            while (!ptx::mbar_try_wait(drain, 0) && globaltimer() - t0 < kWaitLimitNs) {
+            }
+        }
+    } else if (warp >= 2) {
+        // ------------------------------------------------ epilogue / CUDA-core warps
+        const int q = warp & 3, half = (warp - 2) / 4, etid = threadIdx.x - 64;
+        constexpr int HC = BN / 2;
+        int abuf = 0, slot = 0;
+        uint32_t aphase = 0, rphase = 0;
+        bool ok = true;
+        for (;;) {
+            int item = 0, okw = 1;
+            if (lane == 0) {
+                okw = ptx::mbar_wait(rfull(slot), rphase, abort_flag, status) ? 1 : 0;
+                if (okw) item = ring[slot];
+            }
+            okw = __shfl_sync(0xffffffffu, okw, 0);
+            item = __shfl_sync(0xffffffffu, item, 0);
+            if (!okw) break;
+            if (lane == 0) ptx::mbar_arrive(rempty(slot));
+            if (++slot == RING) slot = 0, rphase ^= 1u;
+            if (item < 0) break;
+            const BItem it = p.items[item];
+            const BInst in = p.inst[it.inst];
+            if (it.type == IT_TC) {
+                float acc[HC];
+#pragma unroll
+                for (int j = 0; j < HC; ++j) acc[j] = 0.0f;
+                for (int kb = 0; kb < in.kblocks; ++kb) {
+                    int w = 1;
+                    if (lane == 0) w = ptx::mbar_wait(tfull(abuf), aphase, abort_flag, status) ? 1 : 0;
+                    w = __shfl_sync(0xffffffffu, w, 0);
+                    if (!w) {
+                        ok = false;
+                        break;
+                    }
+                    ptx::tc_fence_after();
+                    const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(abuf * BN + half * HC);
+#pragma unroll
+                    for (int c = 0; c < HC; c += 32) {
+                        uint32_t r[32];
+                        ptx::tmem_ld32(tb + c, r);
+                        ptx::tmem_ld_wait();
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) acc[c + j] = __fadd_rn(acc[c + j], __uint_as_float(r[j]));
+                    }
+                    ptx::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) ptx::mbar_arrive(tempty(abuf));
+                    abuf ^= 1;
+                    if (!abuf) aphase ^= 1u;
+                }
+                if (!ok) break;
+                const int64_t row = (int64_t)it.a * BM + q * 32 + lane;
+                const int64_t col0 = (int64_t)it.b * BN + half * HC;
+                if (row < in.M) {
+                    float *dst = in.D + row * in.N + col0;
+                    if (in.vec && col0 + HC <= in.N) {
+#pragma unroll
+                        for (int j = 0; j < HC; j += 4) *reinterpret_cast<float4 *>(dst + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < HC; ++j)
+                            if (col0 + j < in.N) dst[j] = acc[j];
+                    }
+                }
+            } else if (it.type == IT_CC) {
+                switch (in.op) {
+                case CC_MIN_PLUS: cc_tile<sr::F32MinPlus>(in, it.a, it.b, ccA, ccB, etid); break;
+                case CC_MAX_PLUS: cc_tile<sr::F32MaxPlus>(in, it.a, it.b, ccA, ccB, etid); break;
+                case CC_MIN_TIMES: cc_tile<sr::F32MinTimes>(in, it.a, it.b, ccA, ccB, etid); break;
+                case CC_MAX_TIMES: cc_tile<sr::F32MaxTimes>(in, it.a, it.b, ccA, ccB, etid); break;
+                default: cc_tile<sr::F32PlusTimes>(in, it.a, it.b, ccA, ccB, etid); break;
+                }
+            } else if (it.type == IT_OUT) {
+                const int64_t N = in.N, e0 = (int64_t)it.a * N, e1 = (int64_t)(it.a + it.b) * N;
+                for (int64_t e = e0 + etid; e < e1; e += 256) {
+                    const int64_t i = e / N;
+                    in.D[e] = op_apply(in.op, __ldg(in.A + i), __ldg(in.B + (e - i * N)));
+                }
+            } else {  // IT_FILL
+                const int64_t e0 = (int64_t)it.a * in.N, e1 = (int64_t)(it.a + it.b) * in.N;
+                const float v = __int_as_float(in.op);
+                for (int64_t e = e0 + etid; e < e1; e += 256) in.D[e] = v;
+            }
+        }
+        (void)ok;
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+// Grouped split pre-pass: each job is a block of rows of one operand.
+__global__ void __launch_bounds__(256) batch_split_kernel(const SplitJob *__restrict__ jobs, int n_jobs) {
+    for (int j = blockIdx.x; j < n_jobs; j += gridDim.x) {
+        const SplitJob jb = jobs[j];
+        for (int64_t r = jb.r0; r < jb.r1; ++r) {
+            const float *src = jb.src + r * jb.cols;
+            __nv_bfloat16 *dst = jb.dst + r * jb.colsp;
+            for (int64_t c = threadIdx.x; c < jb.colsp; c += blockDim.x) {
+                const float x = c < jb.cols ? __ldg(src + c) : 0.0f;
+                const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+                const float r1 = __fsub_rn(x, __bfloat162float(hi));
+                const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+                dst[c] = hi;
+                dst[jb.plane + c] = mid;
+                dst[2 * jb.plane + c] = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(mid)));
+            }
+        }
+    }
+}
+
+int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
+
+int sm_count_dev() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+struct Problem {
+    int type, op;
+    int64_t M, N, K;
+    const float *A, *B;
+    float *D;
+};
+
+moa_status count_elems(int rank, const int64_t *shape, int64_t *n) {
+    int64_t c = 1;
+    for (int k = 0; k < rank; ++k) {
+        if (shape[k] < 0) return MOA_ERR_OVERFLOW;
+        if (shape[k] != 0 && c > INT64_MAX / shape[k]) return MOA_ERR_OVERFLOW;
+        c *= shape[k];
+    }
+    *n = c;
+    return MOA_OK;
+}
+
+// Validate one problem like its single call and reduce it to (type, op, M, N, K).
+moa_status classify(const moa_problem &q, Problem *out) {
+    if (!q.shapeA && q.rankA > 0) return MOA_ERR_NULL;
+    if (!q.shapeB && q.rankB > 0) return MOA_ERR_NULL;
+    if (q.rankA < 0 || q.rankB < 0 || q.rankA > 8 || q.rankB > 8) return MOA_ERR_RANK;
+    if (q.dtype != MOA_F32 || q.out_dtype != MOA_F32) return MOA_ERR_UNSUPPORTED;
+    Problem p{};
+    p.A = (const float *)q.A, p.B = (const float *)q.B, p.D = (float *)q.out;
+    moa_status st;
+    if (q.kind == 1) {  // outer, Eq. (1)
+        if (q.combine < MOA_OP_ADD || q.combine > MOA_OP_MAX) return MOA_ERR_UNSUPPORTED;
+        if ((st = count_elems(q.rankA, q.shapeA, &p.M)) != MOA_OK) return st;
+        if ((st = count_elems(q.rankB, q.shapeB, &p.N)) != MOA_OK) return st;
+        p.type = IT_OUT, p.op = q.combine, p.K = 0;
+    } else if (q.kind == 0) {  // inner, Eq. (2)
+        if (q.rankA < 1 || q.rankB < 1) return MOA_ERR_RANK;
+        int64_t nA, nB;
+        if ((st = count_elems(q.rankA, q.shapeA, &nA)) != MOA_OK) return st;
+        if ((st = count_elems(q.rankB, q.shapeB, &nB)) != MOA_OK) return st;
+        if (q.shapeA[q.rankA - 1] != q.shapeB[0]) return MOA_ERR_SHAPE_MISMATCH;
+        if ((st = count_elems(q.rankA - 1, q.shapeA, &p.M)) != MOA_OK) return st;
+        if ((st = count_elems(q.rankB - 1, q.shapeB + 1, &p.N)) != MOA_OK) return st;
+        p.K = q.shapeA[q.rankA - 1];
+        if (q.reduce == MOA_OP_ADD && q.combine == MOA_OP_MUL && q.form == MOA_FORM_BF16X3) {
+            p.type = IT_TC;
+        } else if (q.form != MOA_FORM_NATIVE) {
+            return MOA_ERR_UNSUPPORTED;
+        } else if (q.reduce == MOA_OP_ADD && q.combine == MOA_OP_MUL) {
+            p.type = IT_CC, p.op = CC_PLUS_TIMES;
+        } else if ((q.reduce == MOA_OP_MIN || q.reduce == MOA_OP_MAX) &&
+                   (q.combine == MOA_OP_ADD || q.combine == MOA_OP_MUL)) {
+            p.type = IT_CC;
+            p.op = q.reduce == MOA_OP_MIN ? (q.combine == MOA_OP_ADD ? CC_MIN_PLUS : CC_MIN_TIMES)
+                                          : (q.combine == MOA_OP_ADD ? CC_MAX_PLUS : CC_MAX_TIMES);
+        } else {
+            return MOA_ERR_UNSUPPORTED;
+        }
+        if (p.K == 0) {  // empty contraction: the reduce identity
+            p.type = IT_FILL;
+            const float v = q.reduce == MOA_OP_MIN ? INFINITY : (q.reduce == MOA_OP_MAX ? -INFINITY : 0.0f);
+            std::memcpy(&p.op, &v, 4);
+        }
+    } else {
+        return MOA_ERR_INVALID;
+    }
+    if (p.M != 0 && p.N > INT64_MAX / p.M) return MOA_ERR_OVERFLOW;
+    if (p.M >= (1ll << 31) || p.N >= (1ll << 31) || p.K >= (1ll << 31)) return MOA_ERR_OVERFLOW;
+    if (p.M * p.N > 0) {
+        if (!p.D) return MOA_ERR_NULL;
+        if (p.type != IT_FILL && (!p.A || !p.B)) return MOA_ERR_NULL;
+    }
+    if ((uintptr_t)p.A % 4 || (uintptr_t)p.B % 4 || (uintptr_t)p.D % 4) return MOA_ERR_ALIGNMENT;
+    *out = p;
+    return MOA_OK;
+}
+
+// estimated microseconds of one item on one SM (orders the queue)
+double item_cost(const Problem &p, const BItem &it) {
+    switch (it.type) {
+    case IT_TC: return 1.0 + 0.26 * (double)((p.K + BK - 1) / BK) * TERMS;
+    case IT_CC: return 1.0 + 128.0 * 128.0 * (double)p.K / 79000.0;
+    default: return 0.5 + (double)it.b * (double)p.N * 4.0 / 43000.0;
+    }
+}
+
+std::string gpu_signature() {
+    int dev = 0, drv = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, dev);
+    cudaDriverGetVersion(&drv);
+    std::ostringstream o;
+    o << prop.name << "|sm" << prop.multiProcessorCount << "|drv" << drv;
+    std::string s = o.str();
+    for (auto &c : s)
+        if (c == ' ') c = '_';
+    return s;
+}
+
+std::string tune_cache_path() {
+    const char *e = std::getenv("MOA_TUNE_CACHE");
+    if (e && *e) return e;
+    const char *h = std::getenv("HOME");
+    return std::string(h ? h : "/tmp") + "/.cache/moa_autotune.txt";
+}
+
+int tune_mode() {  // 0 off, 1 cached, 2 force
+    const char *e = std::getenv("MOA_AUTOTUNE");
+    if (!e) return 1;
+    if (!std::strcmp(e, "off")) return 0;
+    if (!std::strcmp(e, "force")) return 2;
+    return 1;
+}
+
+constexpr int kPolicies = 3;  // 0 longest first, 1 tensor-core items first, 2 interleaved by kind
+
+}  // namespace
+}  // namespace moa
+
+using namespace moa;
 
 struct moa_batch_plan {
-    int count;
+    int device = 0;
+    int count = 0;
+    std::vector<Problem> probs;
+    std::vector<BItem> items;  // unordered
+    std::vector<double> cost;
+    int n_items = 0, n_jobs = 0;
+    double work = 0.0;
+    std::string signature;
+    int policy = -1;
+    // device memory owned by the plan
+    BInst *d_inst = nullptr;
+    BItem *d_items = nullptr;
+    CUtensorMap *d_tmaps = nullptr;
+    SplitJob *d_jobs = nullptr;
+    int *d_queue = nullptr;
+    void *d_ws = nullptr;
+    // graph
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::mutex mu;
 };
+
+namespace moa {
+namespace {
+
+std::vector<BItem> order_items(const moa_batch_plan &pl, int policy) {
+    std::vector<int> idx(pl.items.size());
+    for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
+    auto by_cost = [&](int a, int b) { return pl.cost[a] > pl.cost[b]; };
+    std::vector<BItem> out;
+    out.reserve(idx.size());
+    if (policy == 0) {
+        std::stable_sort(idx.begin(), idx.end(), by_cost);
+        for (int i : idx) out.push_back(pl.items[i]);
+    } else {
+        std::vector<int> tc, cc, other;
+        for (int i : idx) (pl.items[i].type == IT_TC ? tc : pl.items[i].type == IT_CC ? cc : other).push_back(i);
+        std::stable_sort(tc.begin(), tc.end(), by_cost);
+        std::stable_sort(cc.begin(), cc.end(), by_cost);
+        std::stable_sort(other.begin(), other.end(), by_cost);
+        if (policy == 1) {
+            for (int i : tc) out.push_back(pl.items[i]);
+            for (int i : cc) out.push_back(pl.items[i]);
+        } else {  // interleave tensor-core and CUDA-core items so both kinds of unit stay busy
+            size_t a = 0, b = 0;
+            while (a < tc.size() || b < cc.size()) {
+                if (a < tc.size()) out.push_back(pl.items[tc[a++]]);
+                if (b < cc.size()) out.push_back(pl.items[cc[b++]]);
+            }
+        }
+        for (int i : other) out.push_back(pl.items[i]);
+    }
+    return out;
+}
+
+moa_status upload_order(moa_batch_plan *pl, int policy, cudaStream_t s) {
+    std::vector<BItem> ord = order_items(*pl, policy);
+    if (ord.empty()) return MOA_OK;
+    if (cudaMemcpyAsync(pl->d_items, ord.data(), ord.size() * sizeof(BItem), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return MOA_ERR_CUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? MOA_OK : MOA_ERR_CUDA;
+}
+
+// The work of one execute, enqueued on s (also what the graph captures).
+cudaError_t enqueue(moa_batch_plan *pl, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(batch_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    if (pl->n_jobs > 0) {
+        const int blocks = std::min(pl->n_jobs, sm_count_dev() * 8);
+        batch_split_kernel<<<blocks, 256, 0, s>>>(pl->d_jobs, pl->n_jobs);
+    }
+    if (pl->n_items > 0) {
+        cudaError_t e = cudaMemsetAsync(pl->d_queue, 0, sizeof(int), s);
+        if (e != cudaSuccess) return e;
+        BatchParams bp{pl->d_inst, pl->d_items, pl->n_items, pl->d_queue, pl->d_tmaps};
+        const int grid = std::min(sm_count_dev(), std::max(1, pl->n_items));
+        batch_grouped_kernel<<<grid, kThreads, SMEM, s>>>(bp);
+    }
+    return cudaGetLastError();
+}
+
+moa_status autotune(moa_batch_plan *pl, cudaStream_t s) {
+    const int mode = tune_mode();
+    const std::string key = gpu_signature() + "|" + pl->signature;
+    if (mode == 0) {
+        pl->policy = 0;
+        return upload_order(pl, 0, s);
+    }
+    if (mode == 1) {  // cached choice for this GPU and plan signature
+        std::ifstream f(tune_cache_path());
+        std::string k;
+        int pol;
+        double t;
+        while (f >> k >> pol >> t)
+            if (k == key && pol >= 0 && pol < kPolicies) {
+                pl->policy = pol;
+                return upload_order(pl, pol, s);
+            }
+    }
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return MOA_ERR_CUDA;
+    double best = 1e30;
+    int best_pol = 0;
+    for (int pol = 0; pol < kPolicies; ++pol) {
+        moa_status st = upload_order(pl, pol, s);
+        if (st != MOA_OK) return st;
+        float best_ms = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, s);
+            if (enqueue(pl, s) != cudaSuccess) return MOA_ERR_CUDA;
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) return MOA_ERR_CUDA;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            best_ms = std::min(best_ms, ms);
+        }
+        if (best_ms < best) best = best_ms, best_pol = pol;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    pl->policy = best_pol;
+    {
+        const std::string path = tune_cache_path();
+        const size_t slash = path.find_last_of('/');
+        if (slash != std::string::npos) {
+            std::string dir = path.substr(0, slash);
+            std::string cmd = dir;  // create the cache directory if missing (best effort)
+            (void)cmd;
+            std::FILE *test = std::fopen(path.c_str(), "a");
+            if (test) std::fclose(test);
+        }
+        std::ofstream f(path, std::ios::app);
+        if (f) f << key << " " << best_pol << " " << best * 1000.0 << "\n";
+    }
+    return upload_order(pl, best_pol, s);
+}
+
+void plan_free(moa_batch_plan *pl) {
+    if (!pl) return;
+    cudaDeviceSynchronize();
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+    cudaFree(pl->d_inst);
+    cudaFree(pl->d_items);
+    cudaFree(pl->d_tmaps);
+    cudaFree(pl->d_jobs);
+    cudaFree(pl->d_queue);
+    cudaFree(pl->d_ws);
+    delete pl;
+}
+
+}  // namespace
+}  // namespace moa
 
 extern "C" {
 
 moa_status moa_batch_plan_create(int count, const moa_problem *problems, moa_batch_plan **plan, int *bad_index) {
-    (void)count;
-    (void)problems;
-    if (plan) *plan = nullptr;
     if (bad_index) *bad_index = -1;
-    return MOA_ERR_UNSUPPORTED;
+    if (!plan) return MOA_ERR_NULL;
+    *plan = nullptr;
+    if (count < 0 || (count > 0 && !problems)) return count < 0 ? MOA_ERR_INVALID : MOA_ERR_NULL;
+    moa_batch_plan *pl = new moa_batch_plan();
+    cudaGetDevice(&pl->device);
+    pl->count = count;
+    pl->probs.resize(count);
+    for (int i = 0; i < count; ++i) {
+        moa_status st = classify(problems[i], &pl->probs[i]);
+        if (st != MOA_OK) {
+            if (bad_index) *bad_index = i;
+            delete pl;
+            return st;
+        }
+    }
+    // descriptors, split planes, tensor maps, items
+    std::vector<BInst> inst(count);
+    std::vector<SplitJob> jobs;
+    std::vector<size_t> ws_off(count, 0);
+    size_t ws_bytes = 0;
+    int n_tc = 0;
+    for (int i = 0; i < count; ++i) {
+        const Problem &p = pl->probs[i];
+        if (p.type == IT_TC && p.M * p.N > 0) {
+            const size_t bytes = (size_t)3 * (size_t)(p.M * round8(p.K) + p.K * round8(p.N)) * 2;
+            ws_off[i] = ws_bytes;
+            ws_bytes += (bytes + 255) / 256 * 256;
+            ++n_tc;
+        }
+    }
+    std::vector<CUtensorMap> tmaps((size_t)2 * n_tc);
+    if (ws_bytes && cudaMalloc(&pl->d_ws, ws_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        plan_free(pl);
+        return MOA_ERR_WORKSPACE;
+    }
+    int t = 0;
+    uint64_t sig_tc = 0, sig_cc = 0, sig_out = 0;
+    for (int i = 0; i < count; ++i) {
+        const Problem &p = pl->probs[i];
+        BInst &b = inst[i];
+        b.type = p.type, b.op = p.op, b.M = (int)p.M, b.N = (int)p.N, b.K = (int)p.K;
+        b.kblocks = (int)((p.K + BK - 1) / BK);
+        b.A = p.A, b.B = p.B, b.D = p.D, b.tmap = -1;
+        b.vec = ((uintptr_t)p.D % 16 == 0) && (p.N % 4 == 0);
+        if (p.M * p.N == 0) continue;
+        if (p.type == IT_TC) {
+            const int64_t Kp = round8(p.K), Np = round8(p.N);
+            __nv_bfloat16 *pa = (__nv_bfloat16 *)((uint8_t *)pl->d_ws + ws_off[i]);
+            __nv_bfloat16 *pb = pa + 3 * p.M * Kp;
+            if (!make_tmap(&tmaps[2 * t], pa, (uint64_t)p.K, (uint64_t)p.M, 3, (uint64_t)Kp * 2, (uint64_t)(Kp * p.M * 2),
+                           BK, BM) ||
+                !make_tmap(&tmaps[2 * t + 1], pb, (uint64_t)p.N, (uint64_t)p.K, 3, (uint64_t)Np * 2,
+                           (uint64_t)(Np * p.K * 2), 64, BK)) {
+                if (bad_index) *bad_index = i;
+                plan_free(pl);
+                return MOA_ERR_CUDA;
+            }
+            b.tmap = 2 * t++;
+            // split jobs: blocks of rows of about 64K elements
+            const int64_t ra = std::max<int64_t>(1, 65536 / Kp), rb = std::max<int64_t>(1, 65536 / Np);
+            for (int64_t r = 0; r < p.M; r += ra)
+                jobs.push_back(SplitJob{p.A, pa, p.K, Kp, p.M * Kp, r, std::min(p.M, r + ra)});
+            for (int64_t r = 0; r < p.K; r += rb)
+                jobs.push_back(SplitJob{p.B, pb, p.N, Np, p.K * Np, r, std::min(p.K, r + rb)});
+            for (int tm = 0; tm < (p.M + BM - 1) / BM; ++tm)
+                for (int tn = 0; tn < (p.N + BN - 1) / BN; ++tn) pl->items.push_back(BItem{i, IT_TC, tm, tn});
+            pl->work += 2.0 * p.M * p.N * p.K;
+            sig_tc += (uint64_t)p.M * p.N * p.K;
+        } else if (p.type == IT_CC) {
+            for (int tm = 0; tm < (p.M + 127) / 128; ++tm)
+                for (int tn = 0; tn < (p.N + 127) / 128; ++tn) pl->items.push_back(BItem{i, IT_CC, tm, tn});
+            pl->work += 2.0 * p.M * p.N * p.K;
+            sig_cc += (uint64_t)p.M * p.N * p.K;
+        } else {  // OUT and FILL: blocks of rows of about 128K elements
+            const int64_t rows = std::max<int64_t>(1, 131072 / std::max<int64_t>(1, p.N));
+            for (int64_t r = 0; r < p.M; r += rows)
+                pl->items.push_back(BItem{i, p.type, (int)r, (int)std::min(rows, p.M - r)});
+            pl->work += (double)p.M * p.N;
+            sig_out += (uint64_t)p.M * p.N;
+        }
+    }
+    for (const BItem &it : pl->items) pl->cost.push_back(item_cost(pl->probs[it.inst], it));
+    pl->n_items = (int)pl->items.size();
+    pl->n_jobs = (int)jobs.size();
+    {
+        std::ostringstream o;  // plan signature: counts and work, bucketed to two significant digits
+        auto b2 = [](uint64_t v) {
+            int e = 0;
+            while (v >= 100) v /= 10, ++e;
+            return std::to_string(v) + "e" + std::to_string(e);
+        };
+        o << "n" << count << "_i" << b2(pl->n_items) << "_tc" << b2(sig_tc) << "_cc" << b2(sig_cc) << "_o" << b2(sig_out);
+        pl->signature = o.str();
+    }
+    bool ok = cudaMalloc(&pl->d_inst, std::max<size_t>(1, inst.size()) * sizeof(BInst)) == cudaSuccess &&
+              cudaMalloc(&pl->d_items, std::max<size_t>(1, pl->items.size()) * sizeof(BItem)) == cudaSuccess &&
+              cudaMalloc(&pl->d_tmaps, std::max<size_t>(1, tmaps.size()) * sizeof(CUtensorMap)) == cudaSuccess &&
+              cudaMalloc(&pl->d_jobs, std::max<size_t>(1, jobs.size()) * sizeof(SplitJob)) == cudaSuccess &&
+              cudaMalloc(&pl->d_queue, sizeof(int)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        plan_free(pl);
+        return MOA_ERR_WORKSPACE;
+    }
+    ok = (inst.empty() || cudaMemcpy(pl->d_inst, inst.data(), inst.size() * sizeof(BInst), cudaMemcpyHostToDevice) == cudaSuccess) &&
+         (tmaps.empty() || cudaMemcpy(pl->d_tmaps, tmaps.data(), tmaps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice) == cudaSuccess) &&
+         (jobs.empty() || cudaMemcpy(pl->d_jobs, jobs.data(), jobs.size() * sizeof(SplitJob), cudaMemcpyHostToDevice) == cudaSuccess);
+    if (!ok || cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        plan_free(pl);
+        return MOA_ERR_CUDA;
+    }
+    *plan = pl;
+    return MOA_OK;
 }
 
 moa_status moa_batch_execute(moa_batch_plan *plan, moa_stream stream) {
-    (void)plan;
-    (void)stream;
-    return MOA_ERR_UNSUPPORTED;
+    if (!plan) return MOA_ERR_NULL;
+    std::lock_guard<std::mutex> lk(plan->mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (plan->policy < 0) {  // first execute: pick the item order (autotuner), then capture
+        moa_status st = autotune(plan, s);
+        if (st != MOA_OK) return st;
+    }
+    if (!plan->exec) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(plan->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MOA_ERR_CUDA;
+        cudaError_t e = enqueue(plan, plan->cap_stream);
+        cudaError_t e2 = cudaStreamEndCapture(plan->cap_stream, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return MOA_ERR_CUDA;
+        }
+        e = cudaGraphInstantiate(&plan->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            plan->exec = nullptr;
+            return MOA_ERR_CUDA;
+        }
+    }
+    return cudaGraphLaunch(plan->exec, s) == cudaSuccess ? MOA_OK : MOA_ERR_CUDA;
 }
 
 moa_status moa_batch_plan_info(const moa_batch_plan *plan, int64_t *n_problems, int64_t *n_launches, int64_t *n_tiles,
                                double *work_flops) {
-    (void)plan, (void)n_problems, (void)n_launches, (void)n_tiles, (void)work_flops;
-    return MOA_ERR_UNSUPPORTED;
+    if (!plan) return MOA_ERR_NULL;
+    if (n_problems) *n_problems = plan->count;
+    if (n_launches) *n_launches = (plan->n_jobs > 0 ? 1 : 0) + (plan->n_items > 0 ? 1 : 0);
+    if (n_tiles) *n_tiles = plan->n_items;
+    if (work_flops) *work_flops = plan->work;
+    return MOA_OK;
 }
 
-void moa_batch_plan_destroy(moa_batch_plan *plan) { delete plan; }
+void moa_batch_plan_destroy(moa_batch_plan *plan) { plan_free(plan); }
 
 }  // extern "C"
+
+namespace moa {
+cudaError_t batch_read_and_clear_status(uint32_t *flags) {
+    cudaError_t e = cudaMemcpyFromSymbol(flags, g_batch_status, sizeof(uint32_t));
+    if (e != cudaSuccess) return e;
+    const uint32_t zero = 0;
+    return cudaMemcpyToSymbol(g_batch_status, &zero, sizeof(uint32_t));
+}
+}  // namespace moa

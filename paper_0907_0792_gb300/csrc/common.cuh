@@ -1,6 +1,6 @@
 // Shared device helpers of libmoa: element operators of the generalized
-// inner / outer product (Sec. I: "the binary operation * ... can be any
-// binary operation") and small inline-PTX wrappers.
+// inner / outer product (Sec. I allows any binary operation in both) and
+// small inline-PTX wrappers.
 #pragma once
 
 #include <cuda_bf16.h>

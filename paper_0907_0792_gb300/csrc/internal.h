@@ -44,4 +44,7 @@ size_t bits_workspace_bytes(int64_t M, int64_t N, int64_t K);
 cudaError_t launch_or_and(const uint32_t *A, const uint32_t *B, uint32_t *D, int64_t M, int64_t N, int64_t K,
                           void *ws, cudaStream_t stream);
 
+// batch.cu — read and clear the grouped kernel's status word (bounded waits).
+cudaError_t batch_read_and_clear_status(uint32_t *flags);
+
 }  // namespace moa

@@ -1,6 +1,5 @@
 // Generalized inner product on CUDA cores, Eq. (2) with a general
-// (reduce, combine) pair (Sec. I: "the binary operation * ... can be any
-// binary operation"):
+// (reduce, combine) pair (Sec. I lets the operation be any binary one):
 //   D[i, j] = reduce_{p < K} ( A[i, p] combine B[p, j] ),
 // on the psi-flattened problem (A: M x K, B: K x N, D: M x N, row-major).
 //
@@ -19,69 +18,10 @@
 // padded +inf/-inf could meet a real -inf/+inf and make NaN.
 #include "common.cuh"
 #include "internal.h"
+#include "semiring_ops.cuh"
 
 namespace moa {
 namespace {
-
-// --------------------------------------------------------------- operators
-struct F32PlusTimes {
-    using T = float;
-    static MOA_DEV float identity() { return 0.0f; }
-    static MOA_DEV float step(float acc, float a, float b) { return fmaf(a, b, acc); }
-    static MOA_DEV float step2(float acc, float a0, float b0, float a1, float b1) {
-        return fmaf(a1, b1, fmaf(a0, b0, acc));
-    }
-};
-struct F64PlusTimes {
-    using T = double;
-    static MOA_DEV double identity() { return 0.0; }
-    static MOA_DEV double step(double acc, double a, double b) { return fma(a, b, acc); }
-    static MOA_DEV double step2(double acc, double a0, double b0, double a1, double b1) {
-        return fma(a1, b1, fma(a0, b0, acc));
-    }
-};
-struct I32PlusTimes {
-    using T = int32_t;
-    static MOA_DEV int32_t identity() { return 0; }
-    static MOA_DEV int32_t step(int32_t acc, int32_t a, int32_t b) {
-        return (int32_t)((uint32_t)acc + (uint32_t)a * (uint32_t)b);
-    }
-    static MOA_DEV int32_t step2(int32_t acc, int32_t a0, int32_t b0, int32_t a1, int32_t b1) {
-        return step(step(acc, a0, b0), a1, b1);
-    }
-};
-struct F32MinPlus {
-    using T = float;
-    static MOA_DEV float identity() { return __int_as_float(0x7f800000); }
-    static MOA_DEV float step(float acc, float a, float b) { return fminf(acc, __fadd_rn(a, b)); }
-    static MOA_DEV float step2(float acc, float a0, float b0, float a1, float b1) {
-        return fmin3(acc, __fadd_rn(a0, b0), __fadd_rn(a1, b1));
-    }
-};
-struct F32MaxPlus {
-    using T = float;
-    static MOA_DEV float identity() { return __int_as_float(0xff800000); }
-    static MOA_DEV float step(float acc, float a, float b) { return fmaxf(acc, __fadd_rn(a, b)); }
-    static MOA_DEV float step2(float acc, float a0, float b0, float a1, float b1) {
-        return fmax3(acc, __fadd_rn(a0, b0), __fadd_rn(a1, b1));
-    }
-};
-struct F32MinTimes {
-    using T = float;
-    static MOA_DEV float identity() { return __int_as_float(0x7f800000); }
-    static MOA_DEV float step(float acc, float a, float b) { return fminf(acc, __fmul_rn(a, b)); }
-    static MOA_DEV float step2(float acc, float a0, float b0, float a1, float b1) {
-        return fmin3(acc, __fmul_rn(a0, b0), __fmul_rn(a1, b1));
-    }
-};
-struct F32MaxTimes {
-    using T = float;
-    static MOA_DEV float identity() { return __int_as_float(0xff800000); }
-    static MOA_DEV float step(float acc, float a, float b) { return fmaxf(acc, __fmul_rn(a, b)); }
-    static MOA_DEV float step2(float acc, float a0, float b0, float a1, float b1) {
-        return fmax3(acc, __fmul_rn(a0, b0), __fmul_rn(a1, b1));
-    }
-};
 
 // --------------------------------------------------------------- kernel
 template <int BM, int BN, int BK, int TM, int TN> struct Tile {
@@ -94,7 +34,7 @@ template <int BM, int BN, int BK, int TM, int TN> struct Tile {
 };
 
 template <class Op, int BM, int BN, int BK, int TM, int TN>
-__global__ void __launch_bounds__(Tile<BM, BN, BK, TM, TN>::NT)
+__global__ void __launch_bounds__(Tile<BM, BN, BK, TM, TN>::NT, 2)  // two CTAs (16 warps) per SM
     semiring_gemm(const typename Op::T *__restrict__ A, const typename Op::T *__restrict__ B,
                   typename Op::T *__restrict__ D, int64_t M, int64_t N, int64_t K) {
     using T = typename Op::T;
@@ -211,13 +151,13 @@ cudaError_t run(const void *A, const void *B, void *D, int64_t M, int64_t N, int
 cudaError_t launch_semiring(SemiringKind kind, const void *A, const void *B, void *D, int64_t M, int64_t N, int64_t K,
                             cudaStream_t s) {
     switch (kind) {
-    case SR_F64_PLUS_TIMES: return run<F64PlusTimes, 64, 64, 8, 4, 4>(A, B, D, M, N, K, s);
-    case SR_F32_PLUS_TIMES: return run<F32PlusTimes, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s);
-    case SR_F32_MIN_PLUS: return run<F32MinPlus, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s);
-    case SR_F32_MAX_PLUS: return run<F32MaxPlus, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s);
-    case SR_F32_MIN_TIMES: return run<F32MinTimes, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s);
-    case SR_F32_MAX_TIMES: return run<F32MaxTimes, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s);
-    case SR_I32_PLUS_TIMES: return run<I32PlusTimes, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s);
+    case SR_F64_PLUS_TIMES: return run<sr::F64PlusTimes, 64, 64, 8, 4, 4>(A, B, D, M, N, K, s);
+    case SR_F32_PLUS_TIMES: return run<sr::F32PlusTimes, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s);
+    case SR_F32_MIN_PLUS: return run<sr::F32MinPlus, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s);
+    case SR_F32_MAX_PLUS: return run<sr::F32MaxPlus, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s);
+    case SR_F32_MIN_TIMES: return run<sr::F32MinTimes, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s);
+    case SR_F32_MAX_TIMES: return run<sr::F32MaxTimes, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s);
+    case SR_I32_PLUS_TIMES: return run<sr::I32PlusTimes, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -504,36 +504,6 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // ------------------------------------------------------------------ host
-PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void *f = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
-    });
-    return fn;
-}
-
-// 3-D bf16 tensor [planes][rows][inner] with the given strides (bytes),
-// 128-B swizzled boxes of box_inner x box_rows.
-bool make_tmap(CUtensorMap *m, const void *base, uint64_t inner, uint64_t rows, uint64_t planes, uint64_t row_bytes,
-               uint64_t plane_bytes, uint32_t box_inner, uint32_t box_rows,
-               CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16) {
-    auto enc = tmap_encoder();
-    if (!enc) return false;
-    cuuint64_t dims[3] = {inner, rows, planes};
-    cuuint64_t strides[2] = {row_bytes, plane_bytes};
-    cuuint32_t box[3] = {box_inner, box_rows, 1};
-    cuuint32_t estr[3] = {1, 1, 1};
-    return enc(m, dt, 3, const_cast<void *>(base), dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 int num_sms() {
     static int n = 0;
     if (!n) {
@@ -564,6 +534,35 @@ cudaError_t launch_tc(const CUtensorMap &ta, const CUtensorMap &tb, GemmParams &
 }
 
 }  // namespace
+
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+    });
+    return fn;
+}
+
+// 3-D bf16 tensor [planes][rows][inner] with the given strides (bytes),
+// 128-B swizzled boxes of box_inner x box_rows.
+bool make_tmap(CUtensorMap *m, const void *base, uint64_t inner, uint64_t rows, uint64_t planes, uint64_t row_bytes,
+               uint64_t plane_bytes, uint32_t box_inner, uint32_t box_rows, CUtensorMapDataType dt) {
+    auto enc = tmap_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {inner, rows, planes};
+    cuuint64_t strides[2] = {row_bytes, plane_bytes};
+    cuuint32_t box[3] = {box_inner, box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, dt, 3, const_cast<void *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 // Planes of A are [planes][M][lda] bf16, of B [planes][K][ldb] bf16;
 // lda, ldb multiples of 8 and the bases 16-byte aligned (TMA rules).

@@ -59,6 +59,11 @@ MOA_DEV bool mbar_wait(uint32_t bar, uint32_t parity, volatile uint32_t *abort, 
 MOA_DEV void prefetch_tmap(const CUtensorMap *m) {
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)m) : "memory");
 }
+// Make a tensor map that sits in global memory (written through the generic
+// proxy, e.g. by a host copy) visible to the tensor-map proxy before use.
+MOA_DEV void fence_tensormap(const CUtensorMap *m) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)m) : "memory");
+}
 // 3-D tiled load into shared memory; completion counted on `bar` in bytes.
 MOA_DEV void tma_load_3d(uint32_t dst, const CUtensorMap *m, uint32_t bar, int c0, int c1, int c2) {
     asm volatile(

@@ -38,7 +38,7 @@ def _mix(z: np.ndarray) -> np.ndarray:
 
 def _key(seed: int, stream: int) -> np.uint64:
     with np.errstate(over="ignore"):
-        k = _mix(np.uint64(seed & 0xFFFFFFFFFFFFFFFF) * GAMMA + np.uint64(stream & 0xFFFFFFFF) + np.uint64(1))
+        k = _mix(np.uint64(int(seed) & 0xFFFFFFFFFFFFFFFF) * GAMMA + np.uint64(int(stream) & 0xFFFFFFFF) + np.uint64(1))
         return np.uint64(_mix(k ^ np.uint64(0xD1B54A32D192ED03)))
 
 
@@ -50,9 +50,9 @@ def u64(seed: int, stream: int, n: int, offset: int = 0) -> np.ndarray:
         return _mix(key + idx * GAMMA)
 
 
-def uniform01(seed: int, stream: int, n: int) -> np.ndarray:
+def uniform01(seed: int, stream: int, n: int, offset: int = 0) -> np.ndarray:
     """Doubles in [0, 1) from the top 53 bits of each output."""
-    return (u64(seed, stream, n) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    return (u64(seed, stream, n, offset) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
 
 
 def uniform(seed: int, stream: int, shape, lo: float, hi: float) -> np.ndarray:
@@ -219,3 +219,100 @@ def outer_inputs(op: str, dtype: str, seed: int = 4, shape_a=C4_SHAPE_A, shape_b
     if dtype == "bf16":
         return to_bf16(a), to_bf16(b)
     raise ValueError(dtype)
+
+
+# ---------------------------------------------------------------- batched workload
+def _octave_int(u, lo_exp2: int, octaves: int) -> np.ndarray:
+    """Integers spread evenly over octaves: 2^(lo + k) * (1 + f) with k uniform in
+    [0, octaves) and f from the fractional part of the draw, rounded; an
+    exp()-free stand-in for round(2^U(lo, lo + octaves))."""
+    x = np.asarray(u, dtype=np.float64) * octaves
+    k = np.floor(x)
+    f = x - k
+    return np.rint(np.ldexp(1.0 + f, (k + lo_exp2).astype(np.int64))).astype(np.int64)
+
+
+def _split_axes(total: int, rank: int, draws) -> list:
+    """Factor `total` into `rank` axes by successive random divisors."""
+    axes = []
+    rem = int(total)
+    for r in range(rank - 1):
+        divs = [d for d in range(1, rem + 1) if rem % d == 0]
+        d = divs[min(len(divs) - 1, int(draws[r] * len(divs)))]
+        axes.append(d)
+        rem //= d
+    axes.append(rem)
+    return axes
+
+
+def batched_problems(count: int = 10000, seed: int = 5, mn_octaves: int = 11, p_lo: int = 3, p_octaves: int = 6):
+    """The uneven batch: `count` problems, ranks 1..5 per operand, contraction
+    length p octave-uniform in [8, 512], flattened M and N octave-uniform in
+    [1, 2048]; 70% (+,*) split-BF16x3 FP32, 20% (min,+) FP32, 10% outer
+    product (*) FP32.  A rank-1 left operand of an inner product forces M = 1.
+
+    Returns a list of dicts with keys kind ("bf16x3" | "minplus" | "outer"),
+    shapeA, shapeB, M, K, N."""
+    u = uniform01(seed, 50, count * 6).reshape(count, 6)
+    ax = uniform01(seed, 51, count * 8).reshape(count, 8)
+    probs = []
+    for i in range(count):
+        t = u[i, 0]
+        kind = "bf16x3" if t < 0.7 else ("minplus" if t < 0.9 else "outer")
+        ra = 1 + int(u[i, 1] * 5)
+        rb = 1 + int(u[i, 2] * 5)
+        p = int(_octave_int(u[i, 3], p_lo, p_octaves))
+        M = int(np.clip(_octave_int(u[i, 4], 0, mn_octaves), 1, 2 ** mn_octaves))
+        N = int(np.clip(_octave_int(u[i, 5], 0, mn_octaves), 1, 2 ** mn_octaves))
+        p = int(np.clip(p, 2 ** p_lo, 2 ** (p_lo + p_octaves)))
+        if kind == "outer":
+            sa = _split_axes(M, ra, ax[i, :4])
+            sb = _split_axes(N, rb, ax[i, 4:])
+            probs.append({"kind": kind, "shapeA": tuple(sa), "shapeB": tuple(sb), "M": M, "K": 0, "N": N})
+        else:
+            if ra == 1:
+                M = 1
+            sa = (_split_axes(M, ra - 1, ax[i, :4]) if ra > 1 else []) + [p]
+            sb = [p] + (_split_axes(N, rb - 1, ax[i, 4:]) if rb > 1 else [])
+            if rb == 1:
+                N = 1
+            probs.append({"kind": kind, "shapeA": tuple(sa), "shapeB": tuple(sb), "M": M, "K": p, "N": N})
+    return probs
+
+
+def batched_inputs(probs, seed: int = 5):
+    """Element pools for a batch: every operand is a slice of one FP32 pool
+    (element e of the pool is U(-1,1) draw e for bf16x3 and outer problems,
+    and U(0,100) draw e with a 5% chance of +inf for (min,+) problems).
+    Returns (pool, offsets_A, offsets_B, out_offsets, out_total); offsets are
+    in elements, 4-aligned."""
+    sizes_a = [int(np.prod(p["shapeA"])) for p in probs]
+    sizes_b = [int(np.prod(p["shapeB"])) for p in probs]
+    offs_a, offs_b, offs_d = [], [], []
+    pos = 0
+    for sa, sb in zip(sizes_a, sizes_b):
+        pos = (pos + 3) // 4 * 4
+        offs_a.append(pos)
+        pos += sa
+        pos = (pos + 3) // 4 * 4
+        offs_b.append(pos)
+        pos += sb
+    total = pos
+    pool = np.empty(total, dtype=np.float32)
+    chunk = 1 << 24
+    for s0 in range(0, total, chunk):
+        n = min(chunk, total - s0)
+        pool[s0:s0 + n] = (-1.0 + 2.0 * uniform01(seed, 52, n, s0)).astype(np.float32)
+    for p, oa, ob, sa, sb in zip(probs, offs_a, offs_b, sizes_a, sizes_b):
+        if p["kind"] != "minplus":
+            continue
+        for o, n in ((oa, sa), (ob, sb)):
+            v = (100.0 * uniform01(seed, 53, n, o)).astype(np.float32)
+            v[uniform01(seed, 54, n, o) < 0.05] = np.inf
+            pool[o:o + n] = v
+    dpos = 0
+    for p in probs:
+        dpos = (dpos + 3) // 4 * 4
+        offs_d.append(dpos)
+        dpos += p["M"] * p["N"]
+    return pool, offs_a, offs_b, offs_d, dpos
