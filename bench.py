@@ -129,14 +129,21 @@ def _dist():
     return dist.get_rank(), ws, int(os.environ.get("LOCAL_RANK", "0"))
 
 
-def _max_over_ranks(x, ws):
+def _max_over_ranks(x, ws, device="cuda"):
+    """The slowest rank's time (the job is done when the last rank is)."""
     if ws <= 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(work_per_rank, ms_max, ws):
+    """Whole-job throughput of `ws` replicas that each did `work_per_rank`,
+    timed by the slowest rank: units per second."""
+    return ws * work_per_rank / (ms_max * 1e-3)
 
 
 def _barrier(ws):
@@ -351,6 +358,8 @@ def main():
     ap.add_argument("--rows", default="all",
                     help="comma list of extra rows to measure: sweep,semirings,outer,plain,batched (all / none)")
     ap.add_argument("--no-rows", action="store_true", help="same as --rows none")
+    ap.add_argument("--sweep-forms", default="all",
+                    help="comma list of form:dtype pairs for the sweep row (e.g. ozaki:f64,fp8_t128:f32)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
@@ -401,7 +410,7 @@ def main():
     ms_local = s.elapsed_time(e) / args.steps
     ms = _max_over_ranks(ms_local, ws)
     flops = 2.0 * n ** 3
-    value = ws * flops / (ms * 1e-3) / 1e12
+    value = whole_job_rate(flops, ms, ws) / 1e12
     kernel_tflops = flops / (ms_local * 1e-3) / 1e12
     st = moa.moa_device_status()
     if st != 0:
@@ -441,9 +450,12 @@ def main():
         flush = lambda: _flush_l2(flush_buf)
         if "sweep" in want:
             sweep = []
-            for form, dt, reps in (("native", "bf16", 5), ("bf16", "f32", 5), ("fp8_t128", "f32", 5),
-                                   ("bf16x3", "f32", 5), ("native", "f32", 3), ("ozaki", "f64", 3),
-                                   ("native", "f64", 1)):
+            forms = (("native", "bf16", 5), ("bf16", "f32", 5), ("fp8_t128", "f32", 5), ("bf16x3", "f32", 5),
+                     ("native", "f32", 3), ("ozaki", "f64", 3), ("native", "f64", 1))
+            if args.sweep_forms != "all":
+                pick = set(args.sweep_forms.split(","))
+                forms = tuple(f for f in forms if f"{f[0]}:{f[1]}" in pick)
+            for form, dt, reps in forms:
                 sweep.append(_row_inner_square(moa, torch, form, dt, n, reps, stream, peaks, flush))
             rows["square_sweep_n8192"] = sweep
         if "semirings" in want:

@@ -239,6 +239,15 @@ const char *moa_status_string(moa_status s);
  */
 moa_status moa_device_status(moa_stream stream);
 
+/*
+ * moa_selftest_wait_timeout — exercise the bounded-wait machinery: launch one
+ * CTA that waits on a barrier nothing ever completes, for limit_us
+ * microseconds (1 .. 1,000,000), after which it gives up and records a
+ * time-out, so the next moa_device_status() returns MOA_ERR_TIMEOUT and the
+ * context stays usable.  Diagnostic only (no counterpart in the paper).
+ */
+moa_status moa_selftest_wait_timeout(uint32_t limit_us, moa_stream stream);
+
 /* Free the scratch workspace held for every stream of the current device (synchronises). */
 moa_status moa_release_workspace(void);
 

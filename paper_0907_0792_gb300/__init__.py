@@ -21,7 +21,7 @@ __all__ = [
     "MoaError", "lib", "moa_inner", "moa_outer", "moa_inner_shape", "moa_outer_shape", "moa_status_string",
     "moa_device_status", "moa_release_workspace", "moa_version", "inner", "outer", "OPS", "DTYPES", "FORMS",
     "moa_batch_plan_create", "moa_batch_execute", "moa_batch_plan_destroy", "moa_batch_plan_info", "MoaProblem",
-    "moa_inner_bf16x3_noalloc", "NOALLOC_SCRATCH_BYTES", "make_problems",
+    "moa_inner_bf16x3_noalloc", "NOALLOC_SCRATCH_BYTES", "make_problems", "moa_selftest_wait_timeout",
 ]
 
 # size of the fixed device buffer behind moa_inner_bf16x3_noalloc (MOA_NOALLOC_SCRATCH_BYTES)
@@ -77,6 +77,7 @@ def lib():
         L.moa_batch_plan_destroy.restype = None
         L.moa_batch_plan_info.argtypes = [V, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64), C.POINTER(C.c_double)]
         L.moa_inner_bf16x3_noalloc.argtypes = [I, _I64P, P, I, _I64P, P, P, V]
+        L.moa_selftest_wait_timeout.argtypes = [C.c_uint32, V]
         _lib = L
     return _lib
 
@@ -182,6 +183,10 @@ def moa_status_string(st: int) -> str:
 
 def moa_device_status(stream=None) -> int:
     return int(lib().moa_device_status(_stream(stream)))
+
+
+def moa_selftest_wait_timeout(limit_us: int, stream=None) -> int:
+    return int(lib().moa_selftest_wait_timeout(int(limit_us), _stream(stream)))
 
 
 def moa_release_workspace() -> int:

@@ -325,6 +325,11 @@ moa_status moa_device_status(moa_stream stream) {
 
 moa_status moa_release_workspace(void) { return workspace_release_all(); }
 
+moa_status moa_selftest_wait_timeout(uint32_t limit_us, moa_stream stream) {
+    if (limit_us == 0 || limit_us > 1000000u) return MOA_ERR_INVALID;
+    return from_cuda(tc_wait_probe((uint64_t)limit_us * 1000ull, (cudaStream_t)stream));
+}
+
 int moa_version(void) { return 0x000100; }
 
 }  // extern "C"

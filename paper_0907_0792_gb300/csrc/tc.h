@@ -37,6 +37,8 @@ moa_status tc_inner_ozaki(const double *A, const double *B, double *D, int64_t M
 size_t tc_bf16x3_scratch_bytes(int64_t M, int64_t N, int64_t K);
 moa_status tc_inner_bf16x3_scratch(const float *A, const float *B, float *D, int64_t M, int64_t N, int64_t K,
                                    void *scratch, cudaStream_t stream);
+// Launch the bounded-wait self-test (a wait that can only time out).
+cudaError_t tc_wait_probe(uint64_t limit_ns, cudaStream_t stream);
 // Read and clear the status word of the tensor-core kernels (bounded waits).
 cudaError_t tc_read_and_clear_status(uint32_t *flags);
 

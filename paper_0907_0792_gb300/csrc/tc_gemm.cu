@@ -649,6 +649,29 @@ moa_status tc_gemm_ozaki(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat1
     return e == cudaSuccess ? MOA_OK : MOA_ERR_CUDA;
 }
 
+// Self-test of the bounded waits: one CTA waits on an mbarrier that nothing
+// ever arrives on, gives up after limit_ns and records kStatusTimeout.
+__global__ void wait_probe_kernel(uint64_t limit_ns) {
+    __shared__ uint64_t bar;
+    const uint32_t b = ptx::smem_u32(&bar);
+    if (threadIdx.x == 0) {
+        ptx::mbar_init(b, 1);
+        ptx::fence_mbar_init();
+        const uint64_t t0 = globaltimer();
+        while (!ptx::mbar_try_wait(b, 0)) {
+            if (globaltimer() - t0 > limit_ns) {
+                atomicOr(&g_tc_status, kStatusTimeout);
+                break;
+            }
+        }
+    }
+}
+
+cudaError_t tc_wait_probe(uint64_t limit_ns, cudaStream_t s) {
+    wait_probe_kernel<<<1, 32, 0, s>>>(limit_ns);
+    return cudaGetLastError();
+}
+
 cudaError_t tc_read_and_clear_status(uint32_t *flags) {
     cudaError_t e = cudaMemcpyFromSymbol(flags, g_tc_status, sizeof(uint32_t));
     if (e != cudaSuccess) return e;
