@@ -254,12 +254,12 @@ def _row_plain_method(moa, torch, reps, stream):
             "outer_ms": round(ms_o, 4), "outer_gbs": round((C.numel() + A.size) * 8 / (ms_o * 1e-3) / 1e9, 1)}
 
 
-def _row_batched(moa, torch, reps, stream):
+def _row_batched(moa, torch, reps, stream, compare=True, count=10000):
     """The uneven batch: 10,000 problems (70% split-BF16x3, 20% (min,+),
     10% outer) through one plan (grouped persistent kernel in a CUDA graph),
     against one call per problem of the same forms."""
     import synth
-    probs = synth.batched_problems()
+    probs = synth.batched_problems(count)
     pool, oa, ob, od, dtot = synth.batched_inputs(probs)
     dpool = torch.from_numpy(pool).cuda()
     dout = torch.empty((dtot,), dtype=torch.float32, device="cuda")
@@ -293,15 +293,18 @@ def _row_batched(moa, torch, reps, stream):
             else:
                 moa.moa_inner("add", "mul", "f32", "bf16x3", sp["shapeA"], sp["A"], sp["shapeB"], sp["B"], sp["out"],
                               "f32", stream)
-    per_problem()
-    ms_single = _events_time(per_problem, 1, stream)
+    ms_single = None
+    if compare:
+        per_problem()
+        ms_single = _events_time(per_problem, 1, stream)
     moa.moa_batch_plan_destroy(plan)
     n = len(probs)
     return {"problems": n, "items": info["items"] if "items" in info else info["tiles"],
             "grouped_launches_per_execute": info["launches"], "ms": round(ms, 3),
             "problems_per_s": round(n / (ms * 1e-3), 1),
             "effective_tflops": round(info["work_flops"] / (ms * 1e-3) / 1e12, 2),
-            "one_call_per_problem_ms": round(ms_single, 3), "speedup_vs_one_call_per_problem": round(ms_single / ms, 2),
+            "one_call_per_problem_ms": round(ms_single, 3) if ms_single else None,
+            "speedup_vs_one_call_per_problem": round(ms_single / ms, 2) if ms_single else None,
             "first_execute_s_incl_tuning": round(first_s, 3)}
 
 
@@ -358,10 +361,14 @@ def main():
     ap.add_argument("--rows", default="all",
                     help="comma list of extra rows to measure: sweep,semirings,outer,plain,batched (all / none)")
     ap.add_argument("--no-rows", action="store_true", help="same as --rows none")
+    ap.add_argument("--sweep-n", type=int, default=N_HEAD, help="matrix size of the sweep row")
     ap.add_argument("--sweep-forms", default="all",
                     help="comma list of form:dtype pairs for the sweep row (e.g. ozaki:f64,fp8_t128:f32)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--batched-count", type=int, default=10000, help="problems in the batched row")
+    ap.add_argument("--batched-no-compare", action="store_true",
+                    help="skip the one-call-per-problem comparison of the batched row")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -456,8 +463,8 @@ def main():
                 pick = set(args.sweep_forms.split(","))
                 forms = tuple(f for f in forms if f"{f[0]}:{f[1]}" in pick)
             for form, dt, reps in forms:
-                sweep.append(_row_inner_square(moa, torch, form, dt, n, reps, stream, peaks, flush))
-            rows["square_sweep_n8192"] = sweep
+                sweep.append(_row_inner_square(moa, torch, form, dt, args.sweep_n, reps, stream, peaks, flush))
+            rows[f"square_sweep_n{args.sweep_n}"] = sweep
         if "semirings" in want:
             rows["semirings"] = [
                 _row_semiring(moa, torch, "tropical", "min", "add", 5, stream, flush),
@@ -472,7 +479,8 @@ def main():
         if "plain" in want:
             rows["plain_method_f64_rank4x3"] = _row_plain_method(moa, torch, 20, stream)
         if "batched" in want:
-            rows["batched_10000"] = _row_batched(moa, torch, 10, stream)
+            rows["batched_10000"] = _row_batched(moa, torch, 10, stream, compare=not args.batched_no_compare,
+                                                 count=args.batched_count)
         del flush_buf
         st = moa.moa_device_status()
         if st != 0:

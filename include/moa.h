@@ -116,6 +116,7 @@ typedef enum {
  *   OZAKI     f64 in/out: operands cut into fixed-point slices with
  *             per-row / per-column power-of-two exponents, exact slice
  *             products on tensor cores, recombined in FP64, <= 1e-12.
+ *             Contraction length K <= 16384 (MOA_ERR_UNSUPPORTED beyond).
  */
 typedef enum {
     MOA_FORM_NATIVE = 0,

@@ -97,8 +97,11 @@ MOA_DEV void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
 // One 128 x 128 CUDA-core tile of D = reduce_p(A combine B), 256 threads
 // (the epilogue warps), panels in shared memory, tail of K by a short loop.
-template <class Op>
-MOA_DEV void cc_tile(const BInst &in, int tm, int tn, float *As, float *Bs, int tid) {
+// RH / CH: whether the tile's second 64 rows / columns hold any output; the
+// halves a thread would compute outside the problem are skipped (the flags
+// are the same for every thread of the tile, so no warp diverges).
+template <class Op, bool RH, bool CH>
+__device__ __noinline__ void cc_tile_q(const BInst &in, int tm, int tn, float *As, float *Bs, int tid) {
     const int64_t M = in.M, N = in.N, K = in.K;
     const float *A = in.A, *B = in.B;
     const int tx = tid % 16, ty = tid / 16;
@@ -141,31 +144,38 @@ MOA_DEV void cc_tile(const BInst &in, int tm, int tn, float *As, float *Bs, int 
     for (int64_t p = 0; p < panels; ++p) {
         const int buf = (int)(p & 1);
         if (p + 1 < panels) load((p + 1) * CC_BK);
-        const float *as = As + buf * CC_BK * CC_LD + ty * 8, *bs = Bs + buf * CC_BK * CC_LD + tx * 8;
+        // two groups of 4 rows / columns half a tile apart: conflict-free 16-byte reads
+        const float *as = As + buf * CC_BK * CC_LD + ty * 4, *bs = Bs + buf * CC_BK * CC_LD + tx * 4;
         if (p < full) {
 #pragma unroll
             for (int kk = 0; kk < CC_BK; kk += 2) {
                 float a0[8], b0[8], a1[8], b1[8];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) a0[i] = as[kk * CC_LD + i], a1[i] = as[(kk + 1) * CC_LD + i];
+                for (int i = 0; i < 8; ++i) {
+                    const int r = (i & 3) + (i >> 2) * 64;
+                    a0[i] = as[kk * CC_LD + r], a1[i] = as[(kk + 1) * CC_LD + r];
+                }
 #pragma unroll
-                for (int j = 0; j < 8; ++j) b0[j] = bs[kk * CC_LD + j], b1[j] = bs[(kk + 1) * CC_LD + j];
+                for (int j = 0; j < 8; ++j) {
+                    const int c = (j & 3) + (j >> 2) * 64;
+                    b0[j] = bs[kk * CC_LD + c], b1[j] = bs[(kk + 1) * CC_LD + c];
+                }
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
+                for (int i = 0; i < (RH ? 8 : 4); ++i)
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) acc[i][j] = Op::step2(acc[i][j], a0[i], b0[j], a1[i], b1[j]);
+                    for (int j = 0; j < (CH ? 8 : 4); ++j) acc[i][j] = Op::step2(acc[i][j], a0[i], b0[j], a1[i], b1[j]);
             }
         } else {
             for (int kk = 0; kk < tail; ++kk) {
                 float a0[8], b0[8];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) a0[i] = as[kk * CC_LD + i];
+                for (int i = 0; i < 8; ++i) a0[i] = as[kk * CC_LD + (i & 3) + (i >> 2) * 64];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) b0[j] = bs[kk * CC_LD + j];
+                for (int j = 0; j < 8; ++j) b0[j] = bs[kk * CC_LD + (j & 3) + (j >> 2) * 64];
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
+                for (int i = 0; i < (RH ? 8 : 4); ++i)
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) acc[i][j] = Op::step(acc[i][j], a0[i], b0[j]);
+                    for (int j = 0; j < (CH ? 8 : 4); ++j) acc[i][j] = Op::step(acc[i][j], a0[i], b0[j]);
             }
         }
         if (p + 1 < panels) stash(buf ^ 1);
@@ -173,14 +183,23 @@ MOA_DEV void cc_tile(const BInst &in, int tm, int tn, float *As, float *Bs, int 
     }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        const int64_t m = m0 + ty * 8 + i;
+        const int64_t m = m0 + ty * 4 + (i & 3) + (i >> 2) * 64;
         if (m >= M) continue;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            const int64_t n = n0 + tx * 8 + j;
+            const int64_t n = n0 + tx * 4 + (j & 3) + (j >> 2) * 64;
             if (n < N) in.D[m * N + n] = acc[i][j];
         }
     }
+}
+
+template <class Op>
+MOA_DEV void cc_tile(const BInst &in, int tm, int tn, float *As, float *Bs, int tid) {
+    const bool rh = (int64_t)tm * 128 + 64 < in.M, ch = (int64_t)tn * 128 + 64 < in.N;
+    if (rh && ch) cc_tile_q<Op, true, true>(in, tm, tn, As, Bs, tid);
+    else if (rh) cc_tile_q<Op, true, false>(in, tm, tn, As, Bs, tid);
+    else if (ch) cc_tile_q<Op, false, true>(in, tm, tn, As, Bs, tid);
+    else cc_tile_q<Op, false, false>(in, tm, tn, As, Bs, tid);
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -422,22 +441,25 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-// Grouped split pre-pass: each job is a block of rows of one operand.
+// Grouped split pre-pass: each job is a block of rows of one operand; the
+// threads of a CTA walk the job's (row, column) elements as one flat range,
+// so short rows still keep every thread busy.
 __global__ void __launch_bounds__(256) batch_split_kernel(const SplitJob *__restrict__ jobs, int n_jobs) {
     for (int j = blockIdx.x; j < n_jobs; j += gridDim.x) {
         const SplitJob jb = jobs[j];
-        for (int64_t r = jb.r0; r < jb.r1; ++r) {
-            const float *src = jb.src + r * jb.cols;
-            __nv_bfloat16 *dst = jb.dst + r * jb.colsp;
-            for (int64_t c = threadIdx.x; c < jb.colsp; c += blockDim.x) {
-                const float x = c < jb.cols ? __ldg(src + c) : 0.0f;
-                const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-                const float r1 = __fsub_rn(x, __bfloat162float(hi));
-                const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
-                dst[c] = hi;
-                dst[jb.plane + c] = mid;
-                dst[2 * jb.plane + c] = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(mid)));
-            }
+        const int colsp = (int)jb.colsp;  // < 2^31 (checked at plan creation)
+        const int count = (int)((jb.r1 - jb.r0) * jb.colsp);  // <= ~64K + one row
+        for (int e = threadIdx.x; e < count; e += blockDim.x) {
+            const int rr = e / colsp, c = e - rr * colsp;
+            const int64_t r = jb.r0 + rr;
+            const float x = c < jb.cols ? __ldg(jb.src + r * jb.cols + c) : 0.0f;
+            const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+            const float r1 = __fsub_rn(x, __bfloat162float(hi));
+            const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+            __nv_bfloat16 *dst = jb.dst + r * jb.colsp + c;
+            dst[0] = hi;
+            dst[jb.plane] = mid;
+            dst[2 * jb.plane] = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(mid)));
         }
     }
 }

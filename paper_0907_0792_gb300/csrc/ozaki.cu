@@ -140,6 +140,9 @@ size_t ozaki_workspace_bytes(int64_t M, int64_t N, int64_t K) {
 
 moa_status tc_inner_ozaki(const double *A, const double *B, double *D, int64_t M, int64_t N, int64_t K,
                           cudaStream_t s) {
+    // the int32 sum of one weight class (at most S pairs of K digit products
+    // below 127^2) must stay below 2^31
+    if ((double)ozaki_slices(K) * (double)K * 127.0 * 127.0 >= 2147483648.0) return MOA_ERR_UNSUPPORTED;
     const int64_t Kp = round8(K), Np = round8(N);
     moa_status st;
     uint8_t *ws = (uint8_t *)workspace_get(s, ozaki_workspace_bytes(M, N, K), &st);

@@ -9,7 +9,9 @@
 // panels of depth BK staged in shared memory (double-buffered through
 // registers), and an 8 x 8 register micro-tile per thread.  Every element of
 // an A panel is reused 128 times from shared memory and every loaded value 8
-// times from registers.
+// times from registers.  A thread's 8 rows (and 8 columns) are two groups of
+// 4 that lie half a tile apart, so the 16-byte shared-memory reads of a
+// half-warp cover one contiguous 256-byte row segment (no bank conflicts).
 //
 // Exactness: min / max / integer results do not depend on the order of the
 // reduction, and each combine is one correctly rounded operation, so the
@@ -74,6 +76,7 @@ __global__ void __launch_bounds__(Tile<BM, BN, BK, TM, TN>::NT, 2)  // two CTAs 
         for (int r = 0; r < TL::LB; ++r) Bs[buf][b_k + r * B_KSTEP][b_n] = rb[r];
     };
 
+    constexpr int HM = TM / 2, HN = TN / 2;  // each half of the micro-tile
     T acc[TM][TN];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
@@ -91,16 +94,24 @@ __global__ void __launch_bounds__(Tile<BM, BN, BK, TM, TN>::NT, 2)  // two CTAs 
     for (int64_t p = 0; p < panels; ++p) {
         const int buf = (int)(p & 1);
         if (p + 1 < panels) load((p + 1) * BK);  // next panel in flight during compute
-        const T *as = &As[buf][0][ty * TM];
-        const T *bs = &Bs[buf][0][tx * TN];
+        const T *as = &As[buf][0][ty * HM];
+        const T *bs = &Bs[buf][0][tx * HN];
         if (p < full_panels) {
 #pragma unroll
             for (int kk = 0; kk < BK; kk += 2) {
                 T a0[TM], b0[TN], a1[TM], b1[TN];
 #pragma unroll
-                for (int i = 0; i < TM; ++i) { a0[i] = as[kk * (BM + TL::PAD) + i]; a1[i] = as[(kk + 1) * (BM + TL::PAD) + i]; }
+                for (int i = 0; i < TM; ++i) {
+                    const int r = (i % HM) + (i / HM) * (BM / 2);
+                    a0[i] = as[kk * (BM + TL::PAD) + r];
+                    a1[i] = as[(kk + 1) * (BM + TL::PAD) + r];
+                }
 #pragma unroll
-                for (int j = 0; j < TN; ++j) { b0[j] = bs[kk * (BN + TL::PAD) + j]; b1[j] = bs[(kk + 1) * (BN + TL::PAD) + j]; }
+                for (int j = 0; j < TN; ++j) {
+                    const int c = (j % HN) + (j / HN) * (BN / 2);
+                    b0[j] = bs[kk * (BN + TL::PAD) + c];
+                    b1[j] = bs[(kk + 1) * (BN + TL::PAD) + c];
+                }
 #pragma unroll
                 for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -110,9 +121,9 @@ __global__ void __launch_bounds__(Tile<BM, BN, BK, TM, TN>::NT, 2)  // two CTAs 
             for (int kk = 0; kk < tail; ++kk) {  // contraction tail: shortened loop, no padding values
                 T a0[TM], b0[TN];
 #pragma unroll
-                for (int i = 0; i < TM; ++i) a0[i] = as[kk * (BM + TL::PAD) + i];
+                for (int i = 0; i < TM; ++i) a0[i] = as[kk * (BM + TL::PAD) + (i % HM) + (i / HM) * (BM / 2)];
 #pragma unroll
-                for (int j = 0; j < TN; ++j) b0[j] = bs[kk * (BN + TL::PAD) + j];
+                for (int j = 0; j < TN; ++j) b0[j] = bs[kk * (BN + TL::PAD) + (j % HN) + (j / HN) * (BN / 2)];
 #pragma unroll
                 for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -127,11 +138,11 @@ __global__ void __launch_bounds__(Tile<BM, BN, BK, TM, TN>::NT, 2)  // two CTAs 
 
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
-        const int64_t m = m0 + ty * TM + i;
+        const int64_t m = m0 + ty * HM + (i % HM) + (i / HM) * (BM / 2);
         if (m >= M) continue;
 #pragma unroll
         for (int j = 0; j < TN; ++j) {
-            const int64_t n = n0 + tx * TN + j;
+            const int64_t n = n0 + tx * HN + (j % HN) + (j / HN) * (BN / 2);
             if (n < N) D[m * N + n] = acc[i][j];
         }
     }

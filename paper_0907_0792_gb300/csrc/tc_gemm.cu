@@ -16,6 +16,12 @@
 // the main loop of tile t+1.  Tiles are walked in groups of 16 row-tiles so
 // the A and B panels in flight stay resident in L2.
 //
+// Cluster pairs (CL = 2): two CTAs on adjacent row tiles of the same column
+// tile each load half of the B tile and multicast it to both, so the L2 ->
+// SM traffic per k-block drops from A + B to A + B/2.  A stage is refilled
+// only after the MMAs of both CTAs have released it (each MMA warp commits
+// to the stage barrier of both CTAs).
+//
 // Promoted accumulation (PROMOTE): the tensor core's FP32 accumulation is
 // not round-to-nearest (its error grows with the number of MMAs folded into
 // one accumulator), so for the split-BF16x3 form every 64-deep k-block is
@@ -36,14 +42,16 @@
 //
 // Ozaki mode (MODE_OZAKI): the planes hold fixed-point digit slices (small
 // integers, exact in bf16) and the terms are the slice pairs (s, u) with
-// s + u < S.  Each term's contraction is cut into chunks short enough that
-// the FP32 accumulator holds the exact integer sum; the epilogue adds each
-// chunk, scaled exactly by the pair's power-of-two weight, to a double-float
-// (hi + lo FP32 pair, TwoSum) accumulator per output element: FP32 ALU
-// only, ~48 bits relative to the running sum.  The hi / lo sums live in the
-// upper half of TMEM (columns 2*BN .. 4*BN), next to the two accumulators.  FP64 arithmetic (scarce on
-// this part) is used once per output: hi + lo in FP64 and the power-of-two
-// scaling by the row / column exponents.
+// s + u < S, ordered by weight class g = s + u.  Each term's contraction is
+// cut into chunks short enough that the FP32 accumulator holds the exact
+// integer sum; the epilogue adds the chunks of one weight class exactly in
+// int32 registers, and at the end of the class folds that integer, scaled
+// by the class's power-of-two weight, into a double-float running sum
+// (hi + lo FP32 pair, TwoSum; ~48 bits relative to the running sum) kept in
+// the output buffer itself (each FP64 slot holds the FP32 pair until the
+// tile is finished).  FP64 arithmetic (scarce on this part) is used once
+// per output: hi + lo in FP64 and the power-of-two scaling by the row /
+// column exponents.
 //
 // Every mbarrier wait is bounded; a wait that gives up sets the CTA's abort
 // flag and the device status word, lets in-flight copies and MMAs land, frees
@@ -51,6 +59,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <cstdlib>
 #include <mutex>
 
 #include "common.cuh"
@@ -67,8 +76,11 @@ namespace {
 constexpr int BM = 128;
 constexpr int BK = 64;  // bf16 elements per k-block: 64 x 2 B = 128 B = one swizzle row
 constexpr int kMaxTerms = 8;
-constexpr int kThreads = 320;  // 1 producer, 1 MMA, 8 epilogue warps
-constexpr int kEpiWarps = 8;
+// Warps: 1 producer, 1 MMA, and 8 epilogue warps (2 per TMEM lane quarter),
+// or 16 (4 per quarter) for the FP8 mode, whose epilogue scales and adds
+// every accumulator once per k-block, so each thread holds fewer columns.
+__host__ __device__ constexpr int epi_warps(int mode) { return mode == 3 ? 16 : 8; }
+__host__ __device__ constexpr int cta_threads(int mode) { return 64 + 32 * epi_warps(mode); }
 
 enum Mode { MODE_STORE = 0, MODE_PROMOTE = 1, MODE_OZAKI = 2, MODE_FP8 = 3 };
 
@@ -128,7 +140,10 @@ template <int BN, int STAGES, int MODE = 0> struct Cfg {
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int NBARS = 2 * STAGES + 5;
     static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 1024;  // + barriers, + alignment slack
-    static constexpr int TMEM_COLS = (MODE == 2 ? 4 : 2) * BN;  // Ozaki: + hi / lo running sums
+    // TMEM is allocated in powers of two (>= 32 columns): two BN-wide
+    // accumulators, the second starting at a power-of-two column
+    static constexpr int ACC_STRIDE = BN <= 128 ? 128 : 256;
+    static constexpr int TMEM_COLS = 2 * ACC_STRIDE;
     static constexpr uint32_t IDESC = MODE == 3 ? ptx::idesc_e4m3_f32(BM, BN, 1) : ptx::idesc_bf16_f32(BM, BN, 1);
     static_assert(NBARS * 8 + 16 <= 1024, "barrier area");
     static_assert(TMEM_COLS <= 512, "TMEM has 512 columns");
@@ -153,8 +168,8 @@ MOA_DEV bool drain_wait(uint32_t bar, uint32_t parity) {
     return true;
 }
 
-template <int BN, int STAGES, int MODE>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int BN, int STAGES, int MODE, int CL>
+__global__ void __launch_bounds__(cta_threads(MODE), 1)
     tc_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const GemmParams p) {
     using C = Cfg<BN, STAGES, MODE>;
     extern __shared__ uint8_t smem_raw[];
@@ -175,11 +190,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             ptx::mbar_init(full(s), 1);
-            ptx::mbar_init(empty(s), 1);
+            ptx::mbar_init(empty(s), CL);  // released by the MMA warp of every CTA sharing the stage
         }
         for (int b = 0; b < 2; ++b) {
             ptx::mbar_init(tfull(b), 1);
-            ptx::mbar_init(tempty(b), kEpiWarps);  // one arrival per epilogue warp
+            ptx::mbar_init(tempty(b), epi_warps(MODE));  // one arrival per epilogue warp
         }
         ptx::mbar_init(drain, 1);
         *abort_flag = 0u;
@@ -194,20 +209,28 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     ptx::tc_fence_before();
     __syncthreads();
+    if constexpr (CL > 1) ptx::cluster_sync();  // peers' barriers exist before any multicast
     ptx::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const int num_tiles = p.tiles_m * p.tiles_n;
+    // work of this CTA: tile (tmc * CL + crank, tn) for cluster tiles (tmc, tn)
+    const int crank = CL > 1 ? (int)ptx::cluster_ctarank() : 0;
+    const int cfirst = CL > 1 ? (int)ptx::cluster_id_x() : (int)blockIdx.x;
+    const int cstride = CL > 1 ? (int)ptx::nclusters_x() : (int)gridDim.x;
+    const int tiles_mc = (p.tiles_m + CL - 1) / CL;
+    const int num_tiles = tiles_mc * p.tiles_n;
     const int kiters = p.kblocks * p.n_terms;
+    constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1u);
 
     if (warp == 0 && lane == 0) {
         // ------------------------------------------------ TMA producer
         int stage = 0;
         uint32_t phase = 0, issued = 0, last_par = 0;
         bool ok = true;
-        for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+        for (int t = cfirst; t < num_tiles && ok; t += cstride) {
             int tm, tn;
-            tile_of(t, p.tiles_m, p.tiles_n, tm, tn);
+            tile_of(t, tiles_mc, p.tiles_n, tm, tn);
+            tm = tm * CL + crank;
             for (int it = 0; it < kiters; ++it) {
                 int kb, pa, pb;
                 if constexpr (MODE == MODE_OZAKI) {  // term-major: all k-blocks of one slice pair
@@ -227,9 +250,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t sa = tiles0 + stage * C::STAGE_BYTES, sb = sa + C::A_BYTES;
                 ptx::mbar_arrive_expect_tx(full(stage), C::STAGE_BYTES);
                 ptx::tma_load_3d(sa, &tmA, full(stage), kb * C::BKE, tm * BM, pa);
+                if constexpr (CL > 1) {  // this CTA's share of the B boxes, multicast to the pair
 #pragma unroll
-                for (int j = 0; j < BN / C::BOXN; ++j)
-                    ptx::tma_load_3d(sb + j * C::BOX_BYTES, &tmB, full(stage), tn * BN + j * C::BOXN, kb * C::BKE, pb);
+                    constexpr int NBOX = BN / C::BOXN, PER = (NBOX + CL - 1) / CL;
+                    for (int j = crank * PER; j < (crank + 1) * PER && j < NBOX; ++j)
+                        ptx::tma_load_3d_mc(sb + j * C::BOX_BYTES, &tmB, full(stage), tn * BN + j * C::BOXN, kb * C::BKE,
+                                            pb, kMask);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < BN / C::BOXN; ++j)
+                        ptx::tma_load_3d(sb + j * C::BOX_BYTES, &tmB, full(stage), tn * BN + j * C::BOXN, kb * C::BKE, pb);
+                }
                 issued |= 1u << stage;
                 last_par = (last_par & ~(1u << stage)) | (phase << stage);
                 if (++stage == STAGES) {
@@ -250,7 +281,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // an accumulator is handed to the epilogue once per tile (store),
         // once per k-block with all its terms (promote), or once per chunk of
         // a slice pair (Ozaki)
-        for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+        for (int t = cfirst; t < num_tiles && ok; t += cstride) {
             for (int it = 0; it < kiters; ++it) {
                 int j, last;  // position inside the current accumulator; whether it is its last step
                 if constexpr (MODE == MODE_STORE) {
@@ -271,7 +302,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     ptx::tc_fence_after();
                 }
-                const uint32_t dacc = tmem + (uint32_t)(abuf * BN);
+                const uint32_t dacc = tmem + (uint32_t)(abuf * C::ACC_STRIDE);
                 if (!ptx::mbar_wait(full(stage), phase, abort_flag, &g_tc_status)) {
                     ok = false;
                     break;
@@ -288,7 +319,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     else
                         ptx::mma_bf16(dacc, ad, bd, C::IDESC, (j > 0 || k > 0) ? 1u : 0u);
                 }
-                ptx::mma_commit(empty(stage));
+                if constexpr (CL > 1)
+                    ptx::mma_commit_mc(empty(stage), kMask);
+                else
+                    ptx::mma_commit(empty(stage));
                 if (++stage == STAGES) {
                     stage = 0;
                     phase ^= 1u;
@@ -307,8 +341,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp >= 2) {
         // ------------------------------------------------ epilogue
         const int q = warp & 3;                  // TMEM lane quarter this warp may access
-        const int half = (warp - 2) / 4;         // which half of the BN columns
-        constexpr int HC = BN / 2;               // columns per epilogue warp
+        const int half = (warp - 2) / 4;                 // which part of the BN columns
+        constexpr int HC = BN / (epi_warps(MODE) / 4);   // columns per epilogue warp
         int abuf = 0;
         uint32_t aphase = 0;
         auto wait_acc = [&]() -> bool {
@@ -341,83 +375,88 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         };
         bool ok = true;
-        for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+        for (int t = cfirst; t < num_tiles && ok; t += cstride) {
             int tm, tn;
-            tile_of(t, p.tiles_m, p.tiles_n, tm, tn);
+            tile_of(t, tiles_mc, p.tiles_n, tm, tn);
+            tm = tm * CL + crank;
             const int64_t row = (int64_t)tm * BM + q * 32 + lane;
             const int64_t colh = (int64_t)tn * BN + half * HC;
             if constexpr (MODE == MODE_OZAKI) {
-                // double-float accumulator (hi + lo) in TMEM, units of 2^-lsb of 2^(e_row + e_col)
                 const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
-                const uint32_t thi = lane_base + (uint32_t)(2 * BN + half * HC);
-                const uint32_t tlo = lane_base + (uint32_t)(3 * BN + half * HC);
-                {
-                    uint32_t z[16];
+                const bool row_ok = row < p.M;
+                double *drow = p.D64 + row * p.ldd;
+                bool first = true;  // no running sum stored yet for this tile
+                int qacc[HC];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) z[j] = 0u;
-#pragma unroll
-                    for (int c0 = 0; c0 < HC; c0 += 16) {
-                        ptx::tmem_st16(thi + c0, z);
-                        ptx::tmem_st16(tlo + c0, z);
-                    }
-                    ptx::tmem_st_wait();
-                }
+                for (int j = 0; j < HC; ++j) qacc[j] = 0;
                 const int chunks = (p.kblocks + p.chunk - 1) / p.chunk;
                 for (int term = 0; term < p.n_terms && ok; ++term) {
-                    int sa_, sb_;
+                    int sa_, sb_, ns = -1, nu = -1;
                     ozaki_pair(term, p.slices, sa_, sb_);
-                    // weight of this pair, 2^k with 0 <= k < 128: exact in FP32
-                    const float w = __int_as_float((127 + p.lsb - (sa_ + sb_ + 2) * p.beta) << 23);
+                    if (term + 1 < p.n_terms) ozaki_pair(term + 1, p.slices, ns, nu);
+                    const int cls = sa_ + sb_;
+                    const bool class_ends = (term + 1 == p.n_terms) || (ns + nu != cls);
+                    // the class's power-of-two weight in accumulator units, exact in FP32
+                    const float w = __int_as_float((127 + p.lsb - (cls + 2) * p.beta) << 23);
                     for (int c = 0; c < chunks; ++c) {
                         if (!wait_acc()) {
                             ok = false;
                             break;
                         }
-                        const uint32_t tb = lane_base + (uint32_t)(abuf * BN + half * HC);
-#pragma unroll 1
+                        const bool fold = class_ends && c == chunks - 1 && row_ok;
+                        const uint32_t tb = lane_base + (uint32_t)(abuf * C::ACC_STRIDE + half * HC);
+#pragma unroll
                         for (int c0 = 0; c0 < HC; c0 += 16) {
-                            uint32_t r[16], h[16], l[16];
+                            uint32_t r[16];
                             ptx::tmem_ld16(tb + c0, r);
-                            ptx::tmem_ld16(thi + c0, h);
-                            ptx::tmem_ld16(tlo + c0, l);
                             ptx::tmem_ld_wait();
 #pragma unroll
-                            for (int j = 0; j < 16; ++j) {
-                                // the chunk sum is an exact integer below 2^24; scaling by w is exact
-                                const float x = __fmul_rn(__uint_as_float(r[j]), w);
-                                const float hv = __uint_as_float(h[j]);
-                                const float sum = __fadd_rn(hv, x);  // TwoSum (Knuth)
-                                const float bv = __fsub_rn(sum, hv);
-                                const float err = __fadd_rn(__fsub_rn(hv, __fsub_rn(sum, bv)), __fsub_rn(x, bv));
-                                h[j] = __float_as_uint(sum);
-                                l[j] = __float_as_uint(__fadd_rn(__uint_as_float(l[j]), err));
+                            for (int j = 0; j < 16; ++j)  // exact: chunk sums are integers below 2^24
+                                qacc[c0 + j] += __float2int_rz(__uint_as_float(r[j]));
+                            if (fold) {  // end of the class: add 2^k * qacc to the running sum (hi, lo)
+#pragma unroll
+                                for (int j = 0; j < 16; ++j) {
+                                    const int64_t col = colh + c0 + j;
+                                    if (col < p.N) {
+                                        const int qv = qacc[c0 + j];
+                                        const float xh = __int2float_rn(qv);
+                                        const float xl = __int2float_rn(qv - __float2int_rn(xh));  // exact remainder
+                                        const float ah = __fmul_rn(xh, w), al = __fmul_rn(xl, w);  // exact scaling
+                                        float2 *slot = reinterpret_cast<float2 *>(drow + col);
+                                        float H = 0.0f, L = 0.0f;
+                                        if (!first) {
+                                            const float2 v = *slot;
+                                            H = v.x, L = v.y;
+                                        }
+                                        const float sum = __fadd_rn(H, ah);  // TwoSum(H, ah)
+                                        const float bv = __fsub_rn(sum, H);
+                                        float e = __fadd_rn(__fsub_rn(H, __fsub_rn(sum, bv)), __fsub_rn(ah, bv));
+                                        e = __fadd_rn(e, __fadd_rn(L, al));
+                                        const float nh = __fadd_rn(sum, e);  // FastTwoSum renormalisation
+                                        *slot = make_float2(nh, __fsub_rn(e, __fsub_rn(nh, sum)));
+                                    }
+                                }
                             }
-                            ptx::tmem_st16(thi + c0, h);
-                            ptx::tmem_st16(tlo + c0, l);
                         }
-                        ptx::tmem_st_wait();
                         release_acc();
+                    }
+                    if (!ok) break;
+                    if (class_ends) {
+#pragma unroll
+                        for (int j = 0; j < HC; ++j) qacc[j] = 0;
+                        first = false;
                     }
                 }
                 if (!ok) break;
-#pragma unroll 1
-                for (int c0 = 0; c0 < HC; c0 += 16) {
-                    uint32_t h[16], l[16];
-                    ptx::tmem_ld16(thi + c0, h);
-                    ptx::tmem_ld16(tlo + c0, l);
-                    ptx::tmem_ld_wait();
-                    if (row < p.M) {
-                        const int er = scale_exponent(p.row_max[row]);
-                        double *dst = p.D64 + row * p.ldd;
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const int64_t col = colh + c0 + j;
-                            if (col < p.N) {
-                                const int ec = scale_exponent(p.col_max[col]);
-                                dst[col] = ldexp((double)__uint_as_float(h[j]) + (double)__uint_as_float(l[j]),
-                                                 er + ec - p.lsb);
-                            }
-                        }
+                if (row_ok) {  // running sums -> FP64 with the row / column scales
+                    const int er = scale_exponent(p.row_max[row]);
+#pragma unroll 4
+                    for (int j = 0; j < HC; ++j) {
+                        const int64_t col = colh + j;
+                        if (col >= p.N) break;
+                        const float2 v = *reinterpret_cast<const float2 *>(drow + col);
+                        const int ec = scale_exponent(p.col_max[col]);
+                        drow[col] = ldexp((double)v.x + (double)v.y, er + ec - p.lsb);
                     }
                 }
             } else if constexpr (MODE == MODE_FP8) {
@@ -433,14 +472,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     const float sa = row_ok ? p.scale_a[row * p.kblocks + kb] : 0.0f;
                     const float f = __fmul_rn(sa, colh < p.N ? p.scale_b[(int64_t)kb * p.nblk_b + colblk] : 0.0f);
-                    const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(abuf * BN + half * HC);
+                    const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(abuf * C::ACC_STRIDE + half * HC);
 #pragma unroll
-                    for (int c = 0; c < HC; c += 32) {
-                        uint32_t r[32];
-                        ptx::tmem_ld32(tb + c, r);
+                    for (int c = 0; c < HC; c += 16) {
+                        uint32_t r[16];
+                        ptx::tmem_ld16(tb + c, r);
                         ptx::tmem_ld_wait();
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) acc[c + j] = fmaf(__uint_as_float(r[j]), f, acc[c + j]);
+                        for (int j = 0; j < 16; ++j) acc[c + j] = fmaf(__uint_as_float(r[j]), f, acc[c + j]);
                     }
                     release_acc();
                 }
@@ -461,7 +500,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         ok = false;
                         break;
                     }
-                    const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(abuf * BN + half * HC);
+                    const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(abuf * C::ACC_STRIDE + half * HC);
 #pragma unroll
                     for (int c = 0; c < HC; c += 32) {
                         uint32_t r[32];
@@ -482,7 +521,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             } else {
                 if (!wait_acc()) break;
-                const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(abuf * BN + half * HC);
+                const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(abuf * C::ACC_STRIDE + half * HC);
 #pragma unroll 1
                 for (int c = 0; c < HC; c += 32) {
                     uint32_t r[32];
@@ -496,6 +535,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     ptx::tc_fence_before();
     __syncthreads();
+    if constexpr (CL > 1) ptx::cluster_sync();  // no CTA leaves while its peer may still write to it
     if (warp == 1) {
         __syncwarp();
         ptx::tc_fence_after();
@@ -504,6 +544,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // ------------------------------------------------------------------ host
+// Cluster pairs with B multicast; MOA_CLUSTER_PAIRS=0 turns them off.
+bool cluster_pairs_enabled() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = std::getenv("MOA_CLUSTER_PAIRS");
+        v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
+
 int num_sms() {
     static int n = 0;
     if (!n) {
@@ -515,22 +565,42 @@ int num_sms() {
     return n;
 }
 
-template <int BN, int STAGES, int MODE>
+template <int BN, int STAGES, int MODE, int CL = 1>
 cudaError_t launch_tc(const CUtensorMap &ta, const CUtensorMap &tb, GemmParams &p, cudaStream_t s) {
     using C = Cfg<BN, STAGES, MODE>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e =
-            cudaFuncSetAttribute(tc_gemm_bf16<BN, STAGES, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    auto kern = tc_gemm_bf16<BN, STAGES, MODE, CL>;
+    static int max_clusters = -1;
+    if (max_clusters < 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
         if (e != cudaSuccess) return e;
-        attr = true;
+        max_clusters = num_sms() / CL;
+        if (CL > 1) {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = CL, at[0].val.clusterDim.y = 1, at[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(CL * max_clusters), cfg.blockDim = dim3(cta_threads(MODE)), cfg.dynamicSmemBytes = C::SMEM;
+            cfg.attrs = at, cfg.numAttrs = 1;
+            int n = 0;
+            if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n > 0 && n < max_clusters) max_clusters = n;
+            cudaGetLastError();
+        }
     }
     p.tiles_m = (p.M + BM - 1) / BM;
     p.tiles_n = (p.N + BN - 1) / BN;
-    const int tiles = p.tiles_m * p.tiles_n;
-    const int grid = tiles < num_sms() ? tiles : num_sms();
-    tc_gemm_bf16<BN, STAGES, MODE><<<grid, kThreads, C::SMEM, s>>>(ta, tb, p);
-    return cudaGetLastError();
+    const int ctiles = (p.tiles_m + CL - 1) / CL * p.tiles_n;
+    const int clusters = ctiles < max_clusters ? ctiles : max_clusters;
+    if (CL == 1) {
+        kern<<<clusters, cta_threads(MODE), C::SMEM, s>>>(ta, tb, p);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL, at[0].val.clusterDim.y = 1, at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(CL * clusters), cfg.blockDim = dim3(cta_threads(MODE)), cfg.dynamicSmemBytes = C::SMEM, cfg.stream = s;
+    cfg.attrs = at, cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, ta, tb, p);
 }
 
 }  // namespace
@@ -591,10 +661,13 @@ moa_status tc_gemm_planes(const __nv_bfloat16 *A, int64_t lda, int planesA, cons
     p.ldd = ldd;
     p.vec_store = ((uintptr_t)D % 16 == 0) && (ldd % 4 == 0);
     cudaError_t e;
+    const bool pair = BN == 256 && M > BM && cluster_pairs_enabled();
     if (promote)
-        e = BN == 128 ? launch_tc<128, 6, MODE_PROMOTE>(ta, tb, p, s) : launch_tc<256, 4, MODE_PROMOTE>(ta, tb, p, s);
+        e = BN == 128 ? launch_tc<128, 6, MODE_PROMOTE>(ta, tb, p, s)
+                      : (pair ? launch_tc<256, 4, MODE_PROMOTE, 2>(ta, tb, p, s) : launch_tc<256, 4, MODE_PROMOTE>(ta, tb, p, s));
     else
-        e = BN == 128 ? launch_tc<128, 6, MODE_STORE>(ta, tb, p, s) : launch_tc<256, 4, MODE_STORE>(ta, tb, p, s);
+        e = BN == 128 ? launch_tc<128, 6, MODE_STORE>(ta, tb, p, s)
+                      : (pair ? launch_tc<256, 4, MODE_STORE, 2>(ta, tb, p, s) : launch_tc<256, 4, MODE_STORE>(ta, tb, p, s));
     return e == cudaSuccess ? MOA_OK : MOA_ERR_CUDA;
 }
 
@@ -619,7 +692,8 @@ moa_status tc_gemm_fp8(const uint8_t *A, int64_t lda, const uint8_t *B, int64_t 
     p.D = D, p.ldd = ldd;
     p.vec_store = ((uintptr_t)D % 16 == 0) && (ldd % 4 == 0);
     p.scale_a = scale_a, p.scale_b = scale_b, p.nblk_b = (int)((N + 127) / 128);
-    cudaError_t e = launch_tc<256, 4, MODE_FP8>(ta, tb, p, s);
+    cudaError_t e = (M > BM && cluster_pairs_enabled()) ? launch_tc<256, 4, MODE_FP8, 2>(ta, tb, p, s)
+                                                        : launch_tc<256, 4, MODE_FP8>(ta, tb, p, s);
     return e == cudaSuccess ? MOA_OK : MOA_ERR_CUDA;
 }
 
@@ -631,7 +705,10 @@ moa_status tc_gemm_ozaki(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat1
                          int lsb, int chunk_kblocks, const uint64_t *row_max, const uint64_t *col_max, double *D,
                          int64_t ldd, int64_t M, int64_t N, int64_t K, cudaStream_t s) {
     if (M >= (1ll << 31) || N >= (1ll << 31) || K >= (1ll << 31)) return MOA_ERR_OVERFLOW;
-    if (S < 1 || S > 10 || chunk_kblocks < 1 || lsb - 2 * beta > 100 || lsb - (S + 1) * beta < 0)
+    // weights 2^(lsb - (g+2) beta) must be exact FP32 powers of two >= 1, and a
+    // class sum (g+1 <= S pairs of K * (2^beta-1)^2) must stay below 2^31
+    if (S < 1 || S > 10 || chunk_kblocks < 1 || lsb - 2 * beta > 100 || lsb - (S + 1) * beta < 0 ||
+        (double)S * (double)K * ((1 << beta) - 1) * ((1 << beta) - 1) >= 2147483648.0)
         return MOA_ERR_INTERNAL;
     if ((uintptr_t)A % 16 || (uintptr_t)B % 16 || lda % 8 || ldb % 8) return MOA_ERR_INTERNAL;
     CUtensorMap ta, tb;
@@ -645,7 +722,10 @@ moa_status tc_gemm_ozaki(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat1
     p.n_terms = S * (S + 1) / 2;
     p.slices = S, p.beta = beta, p.lsb = lsb, p.chunk = chunk_kblocks;
     p.D64 = D, p.ldd = ldd, p.row_max = row_max, p.col_max = col_max;
-    cudaError_t e = launch_tc<128, 6, MODE_OZAKI>(ta, tb, p, s);
+    // 192-wide tiles: two accumulators fit TMEM and the int32 class sums of a
+    // thread's 96 columns fit its registers
+    cudaError_t e = (M > BM && cluster_pairs_enabled()) ? launch_tc<192, 5, MODE_OZAKI, 2>(ta, tb, p, s)
+                                                        : launch_tc<192, 5, MODE_OZAKI>(ta, tb, p, s);
     return e == cudaSuccess ? MOA_OK : MOA_ERR_CUDA;
 }
 

@@ -72,6 +72,38 @@ MOA_DEV void tma_load_3d(uint32_t dst, const CUtensorMap *m, uint32_t bar, int c
         : "memory");
 }
 
+// Same load, delivered to the same shared-memory offset of every CTA in
+// cta_mask (a cluster multicast); each destination CTA's barrier at `bar`'s
+// offset receives the bytes.
+MOA_DEV void tma_load_3d_mc(uint32_t dst, const CUtensorMap *m, uint32_t bar, int c0, int c1, int c2, uint16_t cta_mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster "
+        "[%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(dst),
+        "l"((uint64_t)m), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "h"(cta_mask)
+        : "memory");
+}
+
+// ---------------------------------------------------------------- cluster
+MOA_DEV uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+MOA_DEV uint32_t cluster_id_x() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+MOA_DEV uint32_t nclusters_x() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+// All threads of every CTA of the cluster.
+MOA_DEV void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // ---------------------------------------------------------------- tcgen05
 MOA_DEV void tmem_alloc(uint32_t slot_smem, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot_smem), "r"(ncols)
@@ -143,6 +175,14 @@ MOA_DEV void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t 
 // Arrive once on `bar` when every tcgen05 op issued so far by this thread is done.
 MOA_DEV void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Arrive once on the barrier at `bar`'s offset in every CTA of cta_mask when
+// this thread's tcgen05 ops are done.
+MOA_DEV void mma_commit_mc(uint32_t bar, uint16_t cta_mask) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+                 "h"(cta_mask)
+                 : "memory");
 }
 
 // 32 lanes x 32 consecutive 32-bit columns: thread t gets lane (base + t).
