@@ -43,11 +43,16 @@ __global__ void quant_a_kernel(const float *__restrict__ A, int64_t M, int64_t K
         const int64_t k0 = kb * 128 + lane * 4;
         float x[4];
         float amax = 0.0f;
+        const float *src = A + row * K + k0;
+        if (k0 + 4 <= K && ((uintptr_t)src & 15) == 0) {  // one 16-byte load
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(src));
+            x[0] = v.x, x[1] = v.y, x[2] = v.z, x[3] = v.w;
+        } else {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            x[i] = (k0 + i < K) ? __ldg(A + row * K + k0 + i) : 0.0f;
-            amax = fmaxf(amax, fabsf(x[i]));
+            for (int i = 0; i < 4; ++i) x[i] = (k0 + i < K) ? __ldg(src + i) : 0.0f;
         }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) amax = fmaxf(amax, fabsf(x[i]));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
         float inv;
@@ -62,16 +67,31 @@ __global__ void quant_a_kernel(const float *__restrict__ A, int64_t M, int64_t K
     }
 }
 
-// One block per 128 x 128 tile of B.
+// One block per 128 x 128 tile of B.  Thread t owns columns 4 (t % 32) .. +3
+// of rows t / 32, t / 32 + 8, ...: one 16-byte load per row when aligned, the
+// 64 values kept in registers between the maximum and the quantisation, and
+// one packed 4-byte store per row.
 __global__ void __launch_bounds__(256) quant_b_kernel(const float *__restrict__ B, int64_t K, int64_t N, int64_t Np,
                                                       int64_t NB, uint8_t *__restrict__ B8, float *__restrict__ sB) {
     __shared__ float red[8];
     const int64_t kb = blockIdx.y, nb = blockIdx.x;
     const int t = threadIdx.x;
+    const int64_t n0 = nb * 128 + (t % 32) * 4;
+    const bool vec = (N % 4 == 0) && (((uintptr_t)B & 15) == 0) && (n0 + 4 <= N);
+    float x[16][4];
     float amax = 0.0f;
-    for (int e = t; e < 128 * 128; e += 256) {
-        const int64_t k = kb * 128 + e / 128, n = nb * 128 + e % 128;
-        if (k < K && n < N) amax = fmaxf(amax, fabsf(__ldg(B + k * N + n)));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int64_t k = kb * 128 + t / 32 + 8 * i;
+        if (k < K && vec) {
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(B + k * N + n0));
+            x[i][0] = v.x, x[i][1] = v.y, x[i][2] = v.z, x[i][3] = v.w;
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) x[i][c] = (k < K && n0 + c < N) ? __ldg(B + k * N + n0 + c) : 0.0f;
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) amax = fmaxf(amax, fabsf(x[i][c]));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
@@ -82,9 +102,17 @@ __global__ void __launch_bounds__(256) quant_b_kernel(const float *__restrict__ 
     for (int i = 1; i < 8; ++i) amax = fmaxf(amax, red[i]);
     float inv;
     const float sc = block_scale(amax, &inv);
-    for (int e = t; e < 128 * 128; e += 256) {
-        const int64_t k = kb * 128 + e / 128, n = nb * 128 + e % 128;
-        if (k < K && n < Np) B8[k * Np + n] = n < N ? to_e4m3(__fmul_rn(__ldg(B + k * N + n), inv)) : (uint8_t)0;
+    if (n0 < Np) {  // Np is a multiple of 16, so n0 .. n0 + 3 are all inside a padded row
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int64_t k = kb * 128 + t / 32 + 8 * i;
+            if (k >= K) break;
+            uint32_t packed = 0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (n0 + c < N) packed |= (uint32_t)to_e4m3(__fmul_rn(x[i][c], inv)) << (8 * c);
+            *reinterpret_cast<uint32_t *>(B8 + k * Np + n0) = packed;
+        }
     }
     if (t == 0) sB[kb * NB + nb] = sc;
 }

@@ -403,7 +403,6 @@ __global__ void __launch_bounds__(cta_threads(MODE), 1)
                             ok = false;
                             break;
                         }
-                        const bool fold = class_ends && c == chunks - 1 && row_ok;
                         const uint32_t tb = lane_base + (uint32_t)(abuf * C::ACC_STRIDE + half * HC);
 #pragma unroll
                         for (int c0 = 0; c0 < HC; c0 += 16) {
@@ -413,32 +412,42 @@ __global__ void __launch_bounds__(cta_threads(MODE), 1)
 #pragma unroll
                             for (int j = 0; j < 16; ++j)  // exact: chunk sums are integers below 2^24
                                 qacc[c0 + j] += __float2int_rz(__uint_as_float(r[j]));
-                            if (fold) {  // end of the class: add 2^k * qacc to the running sum (hi, lo)
+                        }
+                        release_acc();  // the accumulator is consumed; the MMA may refill it during the fold
+                    }
+                    if (!ok) break;
+                    if (class_ends && row_ok) {
+                        // end of the class: add 2^k * qacc to the running sum (hi, lo), 16 columns at a
+                        // time with all loads issued before any store
 #pragma unroll
-                                for (int j = 0; j < 16; ++j) {
-                                    const int64_t col = colh + c0 + j;
-                                    if (col < p.N) {
-                                        const int qv = qacc[c0 + j];
-                                        const float xh = __int2float_rn(qv);
-                                        const float xl = __int2float_rn(qv - __float2int_rn(xh));  // exact remainder
-                                        const float ah = __fmul_rn(xh, w), al = __fmul_rn(xl, w);  // exact scaling
-                                        float2 *slot = reinterpret_cast<float2 *>(drow + col);
-                                        float H = 0.0f, L = 0.0f;
-                                        if (!first) {
-                                            const float2 v = *slot;
-                                            H = v.x, L = v.y;
-                                        }
-                                        const float sum = __fadd_rn(H, ah);  // TwoSum(H, ah)
-                                        const float bv = __fsub_rn(sum, H);
-                                        float e = __fadd_rn(__fsub_rn(H, __fsub_rn(sum, bv)), __fsub_rn(ah, bv));
-                                        e = __fadd_rn(e, __fadd_rn(L, al));
-                                        const float nh = __fadd_rn(sum, e);  // FastTwoSum renormalisation
-                                        *slot = make_float2(nh, __fsub_rn(e, __fsub_rn(nh, sum)));
-                                    }
-                                }
+                        for (int c0 = 0; c0 < HC; c0 += 16) {
+                            float2 old[16];
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                const int64_t col = colh + c0 + j;
+                                old[j] = (!first && col < p.N) ? *reinterpret_cast<const float2 *>(drow + col)
+                                                               : make_float2(0.0f, 0.0f);
+                            }
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                const int qv = qacc[c0 + j];
+                                const float xh = __int2float_rn(qv);
+                                const float xl = __int2float_rn(qv - __float2int_rn(xh));  // exact remainder
+                                const float ah = __fmul_rn(xh, w), al = __fmul_rn(xl, w);  // exact scaling
+                                const float H = old[j].x, L = old[j].y;
+                                const float sum = __fadd_rn(H, ah);  // TwoSum(H, ah)
+                                const float bv = __fsub_rn(sum, H);
+                                float e = __fadd_rn(__fsub_rn(H, __fsub_rn(sum, bv)), __fsub_rn(ah, bv));
+                                e = __fadd_rn(e, __fadd_rn(L, al));
+                                const float nh = __fadd_rn(sum, e);  // FastTwoSum renormalisation
+                                old[j] = make_float2(nh, __fsub_rn(e, __fsub_rn(nh, sum)));
+                            }
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                const int64_t col = colh + c0 + j;
+                                if (col < p.N) *reinterpret_cast<float2 *>(drow + col) = old[j];
                             }
                         }
-                        release_acc();
                     }
                     if (!ok) break;
                     if (class_ends) {
@@ -464,14 +473,21 @@ __global__ void __launch_bounds__(cta_threads(MODE), 1)
 #pragma unroll
                 for (int j = 0; j < HC; ++j) acc[j] = 0.0f;
                 const int colblk = (int)(colh / 128);  // HC <= 128 columns, all in one B scale block
-                const bool row_ok = row < p.M;
+                const bool row_ok = row < p.M, col_ok = colh < p.N;
+                // scales of the next k-block are loaded while this one is added
+                float sa_next = row_ok ? p.scale_a[row * p.kblocks] : 0.0f;
+                float sb_next = col_ok ? p.scale_b[colblk] : 0.0f;
                 for (int kb = 0; kb < p.kblocks; ++kb) {
+                    const float sa = sa_next, sb = sb_next;
+                    if (kb + 1 < p.kblocks) {
+                        sa_next = row_ok ? p.scale_a[row * p.kblocks + kb + 1] : 0.0f;
+                        sb_next = col_ok ? p.scale_b[(int64_t)(kb + 1) * p.nblk_b + colblk] : 0.0f;
+                    }
                     if (!wait_acc()) {
                         ok = false;
                         break;
                     }
-                    const float sa = row_ok ? p.scale_a[row * p.kblocks + kb] : 0.0f;
-                    const float f = __fmul_rn(sa, colh < p.N ? p.scale_b[(int64_t)kb * p.nblk_b + colblk] : 0.0f);
+                    const float f = __fmul_rn(sa, sb);
                     const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(abuf * C::ACC_STRIDE + half * HC);
 #pragma unroll
                     for (int c = 0; c < HC; c += 16) {
