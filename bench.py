@@ -46,7 +46,7 @@ def kernel_source_hash() -> str:
     """SHA-256 over the sources that make up the tensor-core GEMM kernel."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("tc_gemm.cu", "tc_ptx.cuh", "common.cuh"):
+    for f in ("tc_gemm.cu", "tc_gemm_pair.cu", "tc_ptx.cuh", "common.cuh"):
         with open(os.path.join(ROOT, "paper_0907_0792_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -494,7 +494,7 @@ def main():
     torch.cuda.empty_cache()
 
     peak_tc = peaks["bf16_tflops"]
-    kname = "tc_gemm_bf16<256,4,0,2>"
+    kname = "tc_gemm_pair<0>"
     roofline = {"bound": "tensor", "achieved": round(kernel_tflops, 1), "peak": peak_tc, "unit": "TFLOP/s",
                 "frac": round(kernel_tflops / peak_tc, 3), "traffic": _ncu_traffic(kname),
                 "algorithmic_bytes": 2 * n * n * 2 + n * n * 4,

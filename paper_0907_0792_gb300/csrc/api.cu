@@ -316,10 +316,11 @@ const char *moa_status_string(moa_status s) {
 
 moa_status moa_device_status(moa_stream stream) {
     if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return MOA_ERR_CUDA;
-    uint32_t flags = 0, bflags = 0;
+    uint32_t flags = 0, bflags = 0, pflags = 0;
     if (tc_read_and_clear_status(&flags) != cudaSuccess) return MOA_ERR_CUDA;
     if (batch_read_and_clear_status(&bflags) != cudaSuccess) return MOA_ERR_CUDA;
-    if ((flags | bflags) & kStatusTimeout) return MOA_ERR_TIMEOUT;
+    if (pair_read_and_clear_status(&pflags) != cudaSuccess) return MOA_ERR_CUDA;
+    if ((flags | bflags | pflags) & kStatusTimeout) return MOA_ERR_TIMEOUT;
     return MOA_OK;
 }
 

@@ -37,6 +37,15 @@ moa_status tc_inner_ozaki(const double *A, const double *B, double *D, int64_t M
 size_t tc_bf16x3_scratch_bytes(int64_t M, int64_t N, int64_t K);
 moa_status tc_inner_bf16x3_scratch(const float *A, const float *B, float *D, int64_t M, int64_t N, int64_t K,
                                    void *scratch, cudaStream_t stream);
+// Pair-MMA GEMM (tc_gemm_pair.cu): 256 x 256 tiles on CTA pairs, the same
+// tensor maps and term encoding as the single-CTA kernel (A boxes 64 x 128,
+// B boxes 64 x 64); promote = FP32 register accumulation per k-block.
+// MOA_PAIR_MMA=0 turns the pair path off.
+bool pair_mma_enabled();
+cudaError_t tc_gemm_pair_launch(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, int K, int n_terms,
+                                uint32_t term_a, uint32_t term_b, float *D, int64_t ldd, bool promote,
+                                cudaStream_t stream);
+cudaError_t pair_read_and_clear_status(uint32_t *flags);
 // Launch the bounded-wait self-test (a wait that can only time out).
 cudaError_t tc_wait_probe(uint64_t limit_ns, cudaStream_t stream);
 // Read and clear the status word of the tensor-core kernels (bounded waits).

@@ -677,6 +677,10 @@ moa_status tc_gemm_planes(const __nv_bfloat16 *A, int64_t lda, int planesA, cons
     p.ldd = ldd;
     p.vec_store = ((uintptr_t)D % 16 == 0) && (ldd % 4 == 0);
     cudaError_t e;
+    if (BN == 256 && M > BM && pair_mma_enabled()) {
+        e = tc_gemm_pair_launch(ta, tb, p.M, p.N, p.K, n_terms, p.term_a, p.term_b, D, ldd, promote, s);
+        return e == cudaSuccess ? MOA_OK : MOA_ERR_CUDA;
+    }
     const bool pair = BN == 256 && M > BM && cluster_pairs_enabled();
     if (promote)
         e = BN == 128 ? launch_tc<128, 6, MODE_PROMOTE>(ta, tb, p, s)

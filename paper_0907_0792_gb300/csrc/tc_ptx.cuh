@@ -55,6 +55,26 @@ MOA_DEV bool mbar_wait(uint32_t bar, uint32_t parity, volatile uint32_t *abort, 
     }
 }
 
+// One lane of the (converged) warp gets true: the issuing lane of a warp
+// that runs a loop together.
+MOA_DEV bool elect_one() {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t.reg .b32 l;\n\t"
+        "elect.sync l|p, 0xffffffff;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}"
+        : "=r"(r));
+    return r != 0;
+}
+
+// mbar_wait for a whole warp: lane 0 waits, the outcome is broadcast, and
+// the warp leaves converged.
+MOA_DEV bool mbar_wait_warp(uint32_t bar, uint32_t parity, volatile uint32_t *abort, uint32_t *status) {
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort, status) ? 1 : 0;
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
 // ---------------------------------------------------------------- TMA
 MOA_DEV void prefetch_tmap(const CUtensorMap *m) {
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)m) : "memory");
@@ -81,6 +101,23 @@ MOA_DEV void tma_load_3d_mc(uint32_t dst, const CUtensorMap *m, uint32_t bar, in
         "[%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(dst),
         "l"((uint64_t)m), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "h"(cta_mask)
         : "memory");
+}
+
+// 3-D tiled store shared -> global, tracked by this thread's bulk
+// async-groups; elements outside the tensor are not written.
+MOA_DEV void tma_store_3d(const CUtensorMap *m, uint32_t src, int c0, int c1, int c2) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                     (uint64_t)m),
+                 "r"(src), "r"(c0), "r"(c1), "r"(c2)
+                 : "memory");
+}
+MOA_DEV void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// This thread's bulk stores have finished reading shared memory.
+MOA_DEV void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// This thread's bulk stores are complete.
+MOA_DEV void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+MOA_DEV void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
 
 // ---------------------------------------------------------------- cluster
@@ -135,6 +172,16 @@ MOA_DEV uint64_t smem_desc_sw128(uint32_t addr, uint32_t lbo, uint32_t sbo) {
     d |= (uint64_t)2 << 61;
     return d;
 }
+
+// A descriptor split into its 32-bit halves.  The issuing thread of an MMA
+// loop is a single thread whose every instruction is on the critical path:
+// the start address lives in the low 14 bits, and shared-memory offsets
+// below 256 KB never carry out of them, so the descriptor of a stage / k-step
+// is the low half of a base descriptor plus (byte offset >> 4).
+struct DescHalves {
+    uint32_t lo, hi;
+};
+MOA_DEV DescHalves desc_halves(uint64_t d) { return DescHalves{(uint32_t)d, (uint32_t)(d >> 32)}; }
 
 // Instruction descriptor, kind::f16: D f32, A/B bf16, A K-major, B MN-major
 // (b_mn = 1) or K-major (b_mn = 0), shape M x N.
@@ -207,6 +254,74 @@ MOA_DEV void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         : "r"(taddr));
 }
 MOA_DEV void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ------------------------------------------------- CTA pairs (cta_group::2)
+// Two CTAs of a cluster (ranks 2i, 2i+1) drive one MMA together: the even
+// CTA issues it, each CTA supplies half of A (its 128 rows) and half of B
+// (its half of the N columns) from the same shared-memory offset, and each
+// receives its 128 rows of D in its own TMEM.  A kernel uses one cta_group
+// for all of its tcgen05 instructions.
+
+// Address of the same shared-memory variable in CTA `rank` of the cluster.
+MOA_DEV uint32_t mapa(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+// Arrive on an mbarrier given by its shared::cluster address (any CTA).
+MOA_DEV void mbar_arrive_cluster(uint32_t bar_cluster) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
+}
+// Both CTAs of the pair execute these (one warp each), collectively.
+MOA_DEV void tmem_alloc_pair(uint32_t slot_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot_smem), "r"(ncols)
+                 : "memory");
+}
+MOA_DEV void tmem_relinquish_pair() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+MOA_DEV void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// 3-D tiled load into this CTA's shared memory whose completion (bytes) is
+// counted on an mbarrier of either CTA of the pair (shared::cluster address).
+MOA_DEV void tma_load_3d_pair(uint32_t dst, const CUtensorMap *m, uint32_t bar_cluster, int c0, int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.cta_group::2 "
+        "[%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+        "l"((uint64_t)m), "r"(bar_cluster), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+// D[tmem of both CTAs] (+)= A[smem of both] * B[smem of both], one
+// 256 x N x 16 bf16 step issued by the even CTA.
+MOA_DEV void mma_bf16_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// The same step with the descriptors given as halves (a_lo/b_lo carry the
+// start address); `accumulate` is a predicate input.
+MOA_DEV void mma_bf16_pair_h(uint32_t tmem_d, uint32_t a_lo, uint32_t a_hi, uint32_t b_lo, uint32_t b_hi, uint32_t idesc,
+                             uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\t"
+        "mov.b64 da, {%1, %2};\n\t"
+        "mov.b64 db, {%3, %4};\n\t"
+        "setp.ne.b32 p, %6, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], da, db, %5, p;\n\t}" ::"r"(tmem_d),
+        "r"(a_lo), "r"(a_hi), "r"(b_lo), "r"(b_hi), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// Arrive once on the barrier at `bar`'s offset in every CTA of cta_mask when
+// the pair MMAs issued so far by this thread are done.
+MOA_DEV void mma_commit_pair_mc(uint32_t bar, uint16_t cta_mask) {
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+                 "h"(cta_mask)
+                 : "memory");
+}
 // 32 lanes x 16 consecutive 32-bit columns, register -> TMEM.
 MOA_DEV void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
     asm volatile(
