@@ -9,7 +9,8 @@
 // SM holds its 128 rows of A and its 128 of the 256 columns of B; the MMA
 // of the pair reads both halves of B, so each SM feeds 4 KB + 4 KB per
 // 128 x 256 x 16 of its own output, and its shared-memory stage shrinks
-// from 48 KB to 32 KB (six stages in flight).
+// from 48 KB to 32 KB (six stages in flight).  Each k-block's MMAs are
+// issued by one elected lane of a converged warp.
 //
 // Roles (both CTAs run the same code; rank 0 of the cluster leads):
 //   warp 0     TMA producer in both CTAs: this CTA's 128 x 64 slice of A
@@ -20,9 +21,12 @@
 //   warp 1     both CTAs: collective TMEM allocation (512 columns each).
 //              Leader only: issues the 256 x 256 x 16 MMAs and commits to
 //              the stage barriers and accumulator barriers of both CTAs.
-//   warps 2-9  epilogue in both CTAs: its own 128 TMEM lanes = its 128
-//              rows of the tile; tells the leader when an accumulator is
-//              free (8 arrivals from each CTA).
+//   warps 2-   epilogue in both CTAs (4 warps, or 8 for MODE_PROMOTE): its
+//              own 128 TMEM lanes = its 128 rows of the tile, written out
+//              32 x 32 at a time through a swizzled staging tile and a TMA
+//              store (whole 128-B lines instead of 16-B pieces of 32 rows);
+//              tells the leader when an accumulator is free (one arrival
+//              per epilogue warp of each CTA).
 // Two 256-column TMEM accumulators let the epilogue of tile t overlap the
 // main loop of tile t+1.  MODE_PROMOTE accumulates every 64-deep k-block in
 // a fresh accumulator and adds it into FP32 registers (IEEE adds), as the
@@ -52,15 +56,18 @@ constexpr int BN = 256;                // columns per pair tile; each CTA holds 
 constexpr int BK = 64;                 // bf16 per k-block: one 128-B swizzle row
 constexpr int UK = 16;                 // contraction depth of one MMA
 constexpr int STAGES = 6;
-constexpr int EPI_WARPS = 8;           // 2 per TMEM lane quarter
-constexpr int THREADS = 64 + 32 * EPI_WARPS;
+// Epilogue warps: one per TMEM lane quarter when the accumulator is stored
+// as it is (4), two per quarter when every k-block is added into registers
+// (8; each thread then holds 128 running sums).
+__host__ __device__ constexpr int epi_warps(int mode) { return mode == 1 ? 8 : 4; }
+__host__ __device__ constexpr int threads(int mode) { return 64 + 32 * epi_warps(mode); }
 constexpr int A_BYTES = BM * BK * 2;   // 16 KB
 constexpr int BOX_BYTES = BK * 128;    // 64 k-rows x 64 columns x 2 B
 constexpr int B_BYTES = (BN / 2) * BK * 2;  // 16 KB: two boxes
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int STG_BYTES = 32 * 32 * 4;  // an epilogue warp's staging tile: 32 rows x 32 FP32
 constexpr int NBARS = 2 * STAGES + 5;
-constexpr int SMEM = STAGES * STAGE_BYTES + EPI_WARPS * STG_BYTES + 1024 + 1024;
+constexpr int SMEM = STAGES * STAGE_BYTES + 8 * STG_BYTES + 1024 + 1024;  // staging for up to 8 warps
 constexpr int ACC_STRIDE = BN;
 constexpr int TMEM_COLS = 2 * ACC_STRIDE;
 constexpr uint32_t IDESC = ptx::idesc_bf16_f32(2 * BM, BN, 1);
@@ -102,12 +109,12 @@ MOA_DEV bool drain_wait(uint32_t bar, uint32_t parity) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(threads(MODE), 1)
     tc_gemm_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  const __grid_constant__ CUtensorMap tmD, const PairParams p) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t *bars = (uint64_t *)(smem + STAGES * STAGE_BYTES + EPI_WARPS * STG_BYTES);
+    uint64_t *bars = (uint64_t *)(smem + STAGES * STAGE_BYTES + 8 * STG_BYTES);
     uint32_t *tmem_slot = (uint32_t *)(bars + NBARS);
     volatile uint32_t *abort_flag = tmem_slot + 1;
 
@@ -127,7 +134,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         for (int b = 0; b < 2; ++b) {
             ptx::mbar_init(tfull(b), 1);
-            ptx::mbar_init(tempty(b), 2 * EPI_WARPS);  // leader's: every epilogue warp of both CTAs
+            ptx::mbar_init(tempty(b), 2 * epi_warps(MODE));  // leader's: every epilogue warp of both CTAs
         }
         ptx::mbar_init(drain, 1);
         *abort_flag = 0u;
@@ -254,8 +261,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     } else if (warp >= 2) {
         // ------------------------------------------------ epilogue (both CTAs)
         const int q = warp & 3;          // TMEM lane quarter this warp may access
-        const int half = (warp - 2) / 4;  // which 128 of the 256 columns
-        constexpr int HC = BN / 2;
+        const int half = (warp - 2) / 4;                 // which part of the 256 columns
+        constexpr int HC = BN / (epi_warps(MODE) / 4);  // columns per epilogue warp
         const uint32_t tempty_leader0 = ptx::mapa(tempty(0), 0), tempty_leader1 = ptx::mapa(tempty(1), 0);
         int abuf = 0;
         uint32_t aphase = 0;
@@ -388,7 +395,7 @@ cudaError_t launch_pair(const CUtensorMap &ta, const CUtensorMap &tb, const CUte
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = 2, at[0].val.clusterDim.y = 1, at[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(THREADS), cfg.dynamicSmemBytes = SMEM;
+    cfg.blockDim = dim3(threads(MODE)), cfg.dynamicSmemBytes = SMEM;
     cfg.attrs = at, cfg.numAttrs = 1;
     if (max_clusters < 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
