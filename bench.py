@@ -278,6 +278,60 @@ def _row_plain_method(moa, torch, reps, stream):
             "outer_ms": round(ms_o, 4), "outer_gbs": round((C.numel() + A.size) * 8 / (ms_o * 1e-3) / 1e9, 1)}
 
 
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor) nominal peak
+
+
+def _row_skinny(moa, torch, reps, stream, peaks, n=None, cpu=True):
+    """The method's own measurement (Sec. IV): D (m x n) = A (m x 128) .
+    B (128 x n), m = 1..4, n = 2^26, FP64 and FP32.  B (up to 64 GiB) is
+    drawn on the device by the seeded generator; it is read once per call,
+    far larger than L2."""
+    import oracle
+    import synth
+    n = n or synth.SKINNY_N_MAX
+    k = synth.SKINNY_K
+    out = []
+    for dt in ("f64", "f32"):
+        tdt = torch.float64 if dt == "f64" else torch.float32
+        esz = 8 if dt == "f64" else 4
+        B = synth.device_uniform(synth.SKINNY_SEED, 1, (k, n), -1.0, 1.0, "cuda", dtype=tdt)
+        for m in synth.SKINNY_M:
+            A64, _ = synth.skinny(m, 1, k)
+            A = torch.from_numpy(A64).to(tdt).cuda()
+            D = torch.empty((m, n), dtype=tdt, device="cuda")
+            call = lambda: moa.moa_inner("add", "mul", dt, "native", (m, k), A, (k, n), B, D, dt, stream)
+            call()
+            ms = _events_time(call, reps, stream)
+            nbytes = (m * k + k * n + m * n) * esz
+            flops = 2.0 * m * k * n
+            row = {"dtype": dt, "m": m, "k": k, "n": n, "ms": round(ms, 4), "gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
+                   "gflops": round(flops / (ms * 1e-3) / 1e9, 1),
+                   "frac_hbm": round(nbytes / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 3)}
+            if dt == "f64":
+                row["frac_fp64_nominal"] = round(flops / (ms * 1e-3) / 1e12 / FP64_NOMINAL_TFLOPS, 3)
+                row["bound"] = "fp64" if flops / (FP64_NOMINAL_TFLOPS * 1e12) > nbytes / (peaks["hbm_gbs"] * 1e9) \
+                    else "hbm"
+            else:
+                row["bound"] = "hbm"
+            out.append(row)
+            del A, D
+        del B
+        torch.cuda.empty_cache()
+    res = {"rows": out}
+    if cpu:  # the appendix-order loop on a column sample of the m = 4 FP64 product
+        ns = 1 << 18
+        A64, B64 = synth.skinny(4, ns, k)
+        cpu_rows = []
+        for th in sorted({1, oracle.max_threads()}):
+            t0 = time.perf_counter()
+            oracle.rowwise("f64", A64, B64, threads=th)
+            dt_s = time.perf_counter() - t0
+            cpu_rows.append({"threads": th, "gflops": round(2.0 * 4 * k * ns / dt_s / 1e9, 2),
+                             "sample": f"m=4, n={ns} columns, FP64"})
+        res["cpu_oracle"] = cpu_rows
+    return res
+
+
 def _row_batched(moa, torch, reps, stream, compare=True, count=10000):
     """The uneven batch: 10,000 problems (70% split-BF16x3, 20% (min,+),
     10% outer) through one plan (grouped persistent kernel in a CUDA graph),
@@ -383,7 +437,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="moa", choices=["moa", "reference"])
     ap.add_argument("--rows", default="all",
-                    help="comma list of extra rows to measure: sweep,semirings,outer,plain,batched (all / none)")
+                    help="comma list of extra rows to measure: sweep,semirings,outer,plain,batched,skinny (all / none)")
+    ap.add_argument("--skinny-n", type=int, default=None, help="n of the skinny row (default 2^26)")
     ap.add_argument("--no-rows", action="store_true", help="same as --rows none")
     ap.add_argument("--sweep-n", type=int, default=N_HEAD, help="matrix size of the sweep row")
     ap.add_argument("--sweep-forms", default="all",
@@ -502,7 +557,7 @@ def main():
 
     rows = {}
     want = set() if args.no_rows or args.rows == "none" else (
-        {"sweep", "semirings", "outer", "plain", "batched"} if args.rows == "all" else set(args.rows.split(",")))
+        {"sweep", "semirings", "outer", "plain", "batched", "skinny"} if args.rows == "all" else set(args.rows.split(",")))
     if want:
         flush_buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
         flush = lambda: _flush_l2(flush_buf)
@@ -529,6 +584,9 @@ def main():
                                             ("mul", "bf16"), ("div", "bf16"), ("mul", "i32"))]
         if "plain" in want:
             rows["plain_method_f64_rank4x3"] = _row_plain_method(moa, torch, 20, stream)
+        if "skinny" in want:
+            rows["skinny_paper_m_x_128_x_n"] = _row_skinny(moa, torch, 10, stream, peaks, n=args.skinny_n,
+                                                            cpu=not args.no_cpu)
         if "batched" in want:
             rows["batched_10000"] = _row_batched(moa, torch, 10, stream, compare=not args.batched_no_compare,
                                                  count=args.batched_count)

@@ -211,9 +211,13 @@ static moa_status inner_run(moa_op reduce, moa_op combine, moa_dtype dtype, moa_
     case MOA_I32: return from_cuda(launch_semiring(SR_I32_PLUS_TIMES, A, B, out, M, N, K, s));
     case MOA_F64:
         if (form == MOA_FORM_OZAKI) return tc_inner_ozaki((const double *)A, (const double *)B, (double *)out, M, N, K, s);
+        if (skinny_applies(M, N, K)) return from_cuda(launch_skinny(true, A, B, out, M, N, K, s));
         return from_cuda(launch_semiring(SR_F64_PLUS_TIMES, A, B, out, M, N, K, s));
     case MOA_F32:
-        if (form == MOA_FORM_NATIVE) return from_cuda(launch_semiring(SR_F32_PLUS_TIMES, A, B, out, M, N, K, s));
+        if (form == MOA_FORM_NATIVE) {
+            if (skinny_applies(M, N, K)) return from_cuda(launch_skinny(false, A, B, out, M, N, K, s));
+            return from_cuda(launch_semiring(SR_F32_PLUS_TIMES, A, B, out, M, N, K, s));
+        }
         return tc_inner_f32(form, (const float *)A, (const float *)B, (float *)out, M, N, K, s);
     case MOA_BF16: return tc_inner_bf16((const __nv_bfloat16 *)A, (const __nv_bfloat16 *)B, (float *)out, M, N, K, s);
     default: break;

@@ -37,6 +37,13 @@ enum SemiringKind {
 cudaError_t launch_semiring(SemiringKind kind, const void *A, const void *B, void *D, int64_t M, int64_t N, int64_t K,
                             cudaStream_t stream);
 
+// skinny.cu — (add, mul) with a result of at most kSkinnyMaxM rows, FP64 or
+// FP32: a stream over B (the shape of the method's own measurement).
+constexpr int64_t kSkinnyMaxM = 8;
+bool skinny_applies(int64_t M, int64_t N, int64_t K);
+cudaError_t launch_skinny(bool f64, const void *A, const void *B, void *D, int64_t M, int64_t N, int64_t K,
+                          cudaStream_t stream);
+
 // bits.cu — (or, and) on packed bits.  A, B, D use the MOA_B1_U32 stream
 // layout; ws is scratch of bits_workspace_bytes(M, N, K) bytes (may be NULL
 // when that is 0).

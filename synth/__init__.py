@@ -60,6 +60,49 @@ def uniform(seed: int, stream: int, shape, lo: float, hi: float) -> np.ndarray:
     return (lo + (hi - lo) * uniform01(seed, stream, n)).reshape(shape)
 
 
+def uniform_at(seed: int, stream: int, idx, lo: float, hi: float) -> np.ndarray:
+    """The elements of ``uniform(seed, stream, shape, lo, hi)`` at the given
+    flat (row-major) positions, without drawing the rest of the stream."""
+    key = _key(seed, stream)
+    i = np.asarray(idx, dtype=np.uint64) + np.uint64(1)
+    with np.errstate(over="ignore"):
+        z = _mix(key + i * GAMMA)
+    return lo + (hi - lo) * ((z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53))
+
+
+def _i64(u: int) -> int:
+    """A 64-bit pattern as the signed integer torch stores it as."""
+    u &= 0xFFFFFFFFFFFFFFFF
+    return u - (1 << 64) if u >= (1 << 63) else u
+
+
+def device_uniform(seed: int, stream: int, shape, lo: float, hi: float, device, dtype=None, chunk: int = 1 << 26):
+    """``uniform(seed, stream, shape, lo, hi)`` drawn directly in device memory
+    with torch integer ops (int64 arithmetic wraps modulo 2^64; logical
+    shifts by masking), then cast to ``dtype`` (RNE, as ``to_f32``).  For
+    operands too large to draw on the host; the values are identical."""
+    import torch
+    dtype = dtype or torch.float64
+    n = int(np.prod(shape, dtype=np.int64))
+    out = torch.empty(n, dtype=dtype, device=device)
+    key = _i64(int(_key(seed, stream)))
+    g, m1, m2 = _i64(int(GAMMA)), _i64(int(_M1)), _i64(int(_M2))
+
+    def lsr(z, s):
+        return (z >> s) & ((1 << (64 - s)) - 1)
+
+    for o in range(0, n, chunk):
+        c = min(chunk, n - o)
+        z = torch.arange(o + 1, o + c + 1, dtype=torch.int64, device=device) * g + key
+        z = (z ^ lsr(z, 30)) * m1
+        z = (z ^ lsr(z, 27)) * m2
+        z = z ^ lsr(z, 31)
+        u = lsr(z, 11).to(torch.float64) * (2.0 ** -53)
+        out[o:o + c] = (lo + (hi - lo) * u).to(dtype)
+        del z, u
+    return out.view(*shape)
+
+
 def int_uniform(seed: int, stream: int, shape, lo: int, hi: int) -> np.ndarray:
     """Integers uniform in [lo, hi] (inclusive) as int32; modulo bias < 2^-40."""
     n = int(np.prod(shape, dtype=np.int64))
@@ -145,6 +188,12 @@ C3_SHAPE_B = (512, 64, 64)
 C4_SHAPE_A = (128, 64, 32)
 C4_SHAPE_B = (32, 64)
 C2_SIZES = (256, 512, 1024, 2048, 4096, 8192)
+# the method's own measurement (Sec. IV): an m x 128 array times a 128 x n
+# array, m = 1..4, n = 2^10 .. 2^26; values unstated there, U(-1, 1) here
+SKINNY_K = 128
+SKINNY_M = (1, 2, 3, 4)
+SKINNY_N_MAX = 1 << 26
+SKINNY_SEED = 6
 
 
 def rank4x3_f64(seed: int = 1, shape_a=C1_SHAPE_A, shape_b=C1_SHAPE_B):
@@ -170,6 +219,23 @@ def square(n: int, dist: str = "uniform", seed: int = 2, m: int | None = None, k
     if dist == "loguniform":
         return log_uniform_signed(seed, tag, (m, k)), log_uniform_signed(seed, tag + 1, (k, n))
     raise ValueError(dist)
+
+
+def skinny_shapes(m: int, n: int, k: int = SKINNY_K):
+    return (m, k), (k, n)
+
+
+def skinny(m: int, n: int, k: int = SKINNY_K, seed: int = SKINNY_SEED):
+    """A (m x k) and B (k x n), U(-1, 1) FP64: streams 0 and 1 of the seed."""
+    sa, sb = skinny_shapes(m, n, k)
+    return uniform(seed, 0, sa, -1.0, 1.0), uniform(seed, 1, sb, -1.0, 1.0)
+
+
+def skinny_columns(cols, n: int, k: int = SKINNY_K, seed: int = SKINNY_SEED) -> np.ndarray:
+    """Columns ``cols`` of the k x n operand B of ``skinny`` (k x len(cols))."""
+    cols = np.asarray(cols, dtype=np.int64)
+    idx = np.arange(k, dtype=np.int64)[:, None] * n + cols[None, :]
+    return uniform_at(seed, 1, idx.reshape(-1), -1.0, 1.0).reshape(k, len(cols))
 
 
 def semiring_inputs(kind: str, seed: int = 3, shape_a=C3_SHAPE_A, shape_b=C3_SHAPE_B):

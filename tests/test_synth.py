@@ -59,3 +59,18 @@ def test_bit_packing_layout():
     assert w[0] == 1 and w[1] == 2 and w[2] == 0 and w[3] == (1 << (119 - 96))
     y = synth.semiring_inputs("bool", shape_a=(7, 96), shape_b=(96, 3))[0]
     assert np.array_equal(synth.unpack_bits(synth.pack_bits(y), y.size).reshape(y.shape), y)
+
+
+def test_positional_and_torch_draws_match_the_stream():
+    """uniform_at (any positions) and device_uniform (torch integer ops, here
+    on the CPU) reproduce uniform() exactly, including across chunk edges."""
+    import torch
+    a = synth.uniform(6, 1, (16, 1000), -1.0, 1.0)
+    idx = np.array([0, 1, 999, 1000, 15999, 7777], dtype=np.int64)
+    assert np.array_equal(synth.uniform_at(6, 1, idx, -1.0, 1.0), a.ravel()[idx])
+    b = synth.device_uniform(6, 1, (16, 1000), -1.0, 1.0, "cpu", chunk=333).numpy()
+    assert np.array_equal(a, b)
+    b32 = synth.device_uniform(6, 1, (16, 1000), -1.0, 1.0, "cpu", dtype=torch.float32).numpy()
+    assert np.array_equal(synth.to_f32(a), b32)
+    cols = synth.skinny_columns([3, 500, 999], 1000, k=16)
+    assert np.array_equal(cols, a[:, [3, 500, 999]])
