@@ -19,7 +19,8 @@ namespace moa {
 // aligned, strides multiples of 16 bytes).  False if encoding failed.
 bool make_tmap(CUtensorMap *m, const void *base, uint64_t inner, uint64_t rows, uint64_t planes, uint64_t row_bytes,
                uint64_t plane_bytes, uint32_t box_inner, uint32_t box_rows,
-               CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+               CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+               CUtensorMapSwizzle swizzle = CU_TENSOR_MAP_SWIZZLE_128B);
 
 // bf16 operands as given, FP32 out.
 moa_status tc_inner_bf16(const __nv_bfloat16 *A, const __nv_bfloat16 *B, float *D, int64_t M, int64_t N, int64_t K,
@@ -45,6 +46,17 @@ bool pair_mma_enabled();
 cudaError_t tc_gemm_pair_launch(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, int K, int n_terms,
                                 uint32_t term_a, uint32_t term_b, float *D, int64_t ldd, bool promote,
                                 cudaStream_t stream);
+// FP8 (e4m3) pair GEMM with block-scaled MMAs: A8 [M][lda] and B
+// transposed, Bt8 [N][ldb] (both K-major, lda and ldb multiples of 16,
+// 16-byte aligned).  Scale factors as UE8M0 bytes, each repeated in the four
+// bytes of a word, in the TMEM-word order of the kernel (k-block kb = k / 128):
+//   sfa [ceil(M/128)][kb][128]: word 4 l + c = row 128 rb + 32 c + l;
+//   sfb [ceil(N/T)][kb][256] with T = pair_fp8_tile_n(): word 128 h + 4 l + c
+//   = column T tn + 32 (4 h + c) + l (columns at or past T or N: any value).
+int pair_fp8_tile_n();
+cudaError_t tc_gemm_pair_fp8_launch(const uint8_t *A8, int64_t lda, const uint8_t *Bt8, int64_t ldb, int M, int N,
+                                    int K, const uint32_t *sfa, const uint32_t *sfb, float *D, int64_t ldd,
+                                    cudaStream_t stream);
 cudaError_t pair_read_and_clear_status(uint32_t *flags);
 // Launch the bounded-wait self-test (a wait that can only time out).
 cudaError_t tc_wait_probe(uint64_t limit_ns, cudaStream_t stream);

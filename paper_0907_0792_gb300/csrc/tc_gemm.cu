@@ -635,10 +635,11 @@ PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
     return fn;
 }
 
-// 3-D bf16 tensor [planes][rows][inner] with the given strides (bytes),
-// 128-B swizzled boxes of box_inner x box_rows.
+// 3-D tensor [planes][rows][inner] of `dt` with the given strides (bytes),
+// boxes of box_inner x box_rows (128-B swizzled unless `swizzle` says otherwise).
 bool make_tmap(CUtensorMap *m, const void *base, uint64_t inner, uint64_t rows, uint64_t planes, uint64_t row_bytes,
-               uint64_t plane_bytes, uint32_t box_inner, uint32_t box_rows, CUtensorMapDataType dt) {
+               uint64_t plane_bytes, uint32_t box_inner, uint32_t box_rows, CUtensorMapDataType dt,
+               CUtensorMapSwizzle swizzle) {
     auto enc = tmap_encoder();
     if (!enc) return false;
     cuuint64_t dims[3] = {inner, rows, planes};
@@ -646,7 +647,7 @@ bool make_tmap(CUtensorMap *m, const void *base, uint64_t inner, uint64_t rows, 
     cuuint32_t box[3] = {box_inner, box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     return enc(m, dt, 3, const_cast<void *>(base), dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

@@ -52,30 +52,64 @@ __device__ uint32_t g_pair_status;
 namespace {
 
 constexpr int BM = 128;                // rows per CTA; the pair covers 2 * BM
-constexpr int BN = 256;                // columns per pair tile; each CTA holds BN / 2 of B
-constexpr int BK = 64;                 // bf16 per k-block: one 128-B swizzle row
-constexpr int UK = 16;                 // contraction depth of one MMA
 constexpr int STAGES = 6;
-// Epilogue warps: one per TMEM lane quarter when the accumulator is stored
-// as it is (4), two per quarter when every k-block is added into registers
-// (8; each thread then holds 128 running sums).
-__host__ __device__ constexpr int epi_warps(int mode) { return mode == 1 ? 8 : 4; }
+constexpr int MODE_STORE = 0, MODE_PROMOTE = 1, MODE_FP8 = 2;
+// Columns per pair tile; each CTA holds bn / 2 of B.  The FP8 mode leaves
+// TMEM room for its scale factors: 2 x 224 accumulator columns + 4 x 16.
+__host__ __device__ constexpr int bn(int mode) { return mode == MODE_FP8 ? 224 : 256; }
+// Per mode: element bytes (bf16 2, e4m3 1); a k-block is one 128-B swizzle
+// row of A (bk elements), an MMA contracts 32 bytes' worth (uk elements).
+__host__ __device__ constexpr int esz(int mode) { return mode == MODE_FP8 ? 1 : 2; }
+__host__ __device__ constexpr int bk(int mode) { return 128 / esz(mode); }
+__host__ __device__ constexpr int uk(int mode) { return 32 / esz(mode); }
+// bf16 modes: B is MN-major (rows of B as given); its boxes are 128 B wide
+// (boxn elements) and bk k-rows high, and a CTA's bn / 2 columns take
+// (bn / 2) / boxn of them.  FP8 mode: B is K-major (B transposed by the
+// quantisation pre-pass), one box of bn / 2 rows of 128 B.
+__host__ __device__ constexpr int boxn(int mode) { return 128 / esz(mode); }
+__host__ __device__ constexpr int nbox(int mode) { return mode == MODE_FP8 ? 1 : (bn(mode) / 2) / boxn(mode); }
+__host__ __device__ constexpr int box_bytes(int mode) { return mode == MODE_FP8 ? (bn(mode) / 2) * 128 : bk(mode) * 128; }
+// Warps: producer, MMA, and epilogue warps: one per TMEM lane quarter when
+// the accumulator is stored as it is, two per quarter when every k-block is
+// added into registers (each thread then holds 128 running sums).
+__host__ __device__ constexpr int epi_warps(int mode) { return mode == MODE_PROMOTE ? 8 : 4; }
 __host__ __device__ constexpr int threads(int mode) { return 64 + 32 * epi_warps(mode); }
-constexpr int A_BYTES = BM * BK * 2;   // 16 KB
-constexpr int BOX_BYTES = BK * 128;    // 64 k-rows x 64 columns x 2 B
-constexpr int B_BYTES = (BN / 2) * BK * 2;  // 16 KB: two boxes
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int A_BYTES = BM * 128;            // 16 KB: 128 rows of one 128-B k-block
+__host__ __device__ constexpr int b_bytes(int mode) { return (bn(mode) / 2) * 128; }  // this CTA's part of B
+// FP8 scale factors ride in each stage after A and B: A's 128 row scales
+// (512 B) and B's scales of the tile's bn columns (two 512-B blocks), laid
+// out as the TMEM words they are copied to (see tmem_cp_32x128b_pair).
+constexpr int SFA_BYTES = 512, SFB_BYTES = 1024;
+__host__ __device__ constexpr int sf_off(int mode) { return A_BYTES + b_bytes(mode); }
+__host__ __device__ constexpr int stage_bytes(int mode) {
+    return mode == MODE_FP8 ? (A_BYTES + b_bytes(mode) + SFA_BYTES + SFB_BYTES + 1023) / 1024 * 1024
+                            : A_BYTES + b_bytes(mode);
+}
+__host__ __device__ constexpr int stage_tx(int mode) {  // bytes the TMA delivers per stage and CTA
+    return A_BYTES + b_bytes(mode) + (mode == MODE_FP8 ? SFA_BYTES + SFB_BYTES : 0);
+}
 constexpr int STG_BYTES = 32 * 32 * 4;  // an epilogue warp's staging tile: 32 rows x 32 FP32
+constexpr int SF_BUFS = 4;              // scale-factor buffers in TMEM (FP8), used in turn
+constexpr int SF_COL0 = 448;            // first scale-factor column; buffer s at SF_COL0 + 16 s
 constexpr int NBARS = 2 * STAGES + 5;
-constexpr int SMEM = STAGES * STAGE_BYTES + 8 * STG_BYTES + 1024 + 1024;  // staging for up to 8 warps
-constexpr int ACC_STRIDE = BN;
-constexpr int TMEM_COLS = 2 * ACC_STRIDE;
-constexpr uint32_t IDESC = ptx::idesc_bf16_f32(2 * BM, BN, 1);
+// Shared memory: the stages, the epilogue staging tiles (room for 8 warps),
+// then the barriers.
+__host__ __device__ constexpr int bar_offset(int mode) { return STAGES * stage_bytes(mode) + 8 * STG_BYTES; }
+__host__ __device__ constexpr int smem_bytes(int mode) { return bar_offset(mode) + 1024 + 1024; }
+constexpr int TMEM_COLS = 512;
+__host__ __device__ constexpr uint32_t idesc(int mode) {
+    // FP8: kind::mxf8f6f4 with UE8M0 block scales (bit 23), both operands K-major
+    return mode == MODE_FP8
+               ? (1u << 23) | ((uint32_t)(bn(mode) >> 3) << 17) | ((uint32_t)((2 * BM) >> 4) << 24)
+               : ptx::idesc_bf16_f32(2 * BM, bn(mode), 1);
+}
 constexpr uint16_t kPair = 3;          // multicast mask: both CTAs
-constexpr int MODE_STORE = 0, MODE_PROMOTE = 1;
+static_assert(box_bytes(MODE_STORE) * nbox(MODE_STORE) == b_bytes(MODE_STORE), "B slice bytes");
+static_assert(stage_bytes(MODE_FP8) % 1024 == 0 && stage_bytes(MODE_STORE) % 1024 == 0, "1024-B aligned stages");
 static_assert(NBARS * 8 + 16 <= 1024, "barrier area");
-static_assert(TMEM_COLS <= 512, "TMEM has 512 columns");
-static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
+static_assert(2 * bn(MODE_STORE) <= TMEM_COLS && SF_COL0 >= 2 * bn(MODE_FP8) && SF_COL0 + 16 * SF_BUFS <= TMEM_COLS,
+              "TMEM columns");
+static_assert(smem_bytes(MODE_STORE) <= 227 * 1024 && smem_bytes(MODE_FP8) <= 227 * 1024, "shared memory per CTA");
 
 struct PairParams {
     int M, N, K;
@@ -111,10 +145,12 @@ MOA_DEV bool drain_wait(uint32_t bar, uint32_t parity) {
 template <int MODE>
 __global__ void __launch_bounds__(threads(MODE), 1)
     tc_gemm_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                 const __grid_constant__ CUtensorMap tmD, const PairParams p) {
+                 const __grid_constant__ CUtensorMap tmD, const __grid_constant__ CUtensorMap tmSA,
+                 const __grid_constant__ CUtensorMap tmSB, const PairParams p) {
+    constexpr int BN = bn(MODE), STAGE_BYTES = stage_bytes(MODE), ACC_STRIDE = BN;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t *bars = (uint64_t *)(smem + STAGES * STAGE_BYTES + 8 * STG_BYTES);
+    uint64_t *bars = (uint64_t *)(smem + bar_offset(MODE));
     uint32_t *tmem_slot = (uint32_t *)(bars + NBARS);
     volatile uint32_t *abort_flag = tmem_slot + 1;
 
@@ -143,6 +179,10 @@ __global__ void __launch_bounds__(threads(MODE), 1)
         ptx::prefetch_tmap(&tmA);
         ptx::prefetch_tmap(&tmB);
         if (p.tma_store) ptx::prefetch_tmap(&tmD);
+        if constexpr (MODE == MODE_FP8) {
+            ptx::prefetch_tmap(&tmSA);
+            ptx::prefetch_tmap(&tmSB);
+        }
     }
     if (warp == 1) {
         ptx::tmem_alloc_pair(ptx::smem_u32(tmem_slot), TMEM_COLS);
@@ -183,10 +223,19 @@ __global__ void __launch_bounds__(threads(MODE), 1)
                 if (ptx::elect_one()) {
                     const uint32_t sa = tiles0 + stage * STAGE_BYTES, sb = sa + A_BYTES;
                     const uint32_t fbar = ptx::mapa(full(stage), 0);
-                    if (leader) ptx::mbar_arrive_expect_tx(full(stage), 2 * STAGE_BYTES);
-                    ptx::tma_load_3d_pair(sa, &tmA, fbar, kb * BK, row0, pa);
-                    ptx::tma_load_3d_pair(sb, &tmB, fbar, col0, kb * BK, pb);
-                    ptx::tma_load_3d_pair(sb + BOX_BYTES, &tmB, fbar, col0 + 64, kb * BK, pb);
+                    if (leader) ptx::mbar_arrive_expect_tx(full(stage), 2 * stage_tx(MODE));
+                    ptx::tma_load_3d_pair(sa, &tmA, fbar, kb * bk(MODE), row0, pa);
+                    if constexpr (MODE == MODE_FP8) {  // K-major B: rows = columns of B; then the scale blocks
+                        ptx::tma_load_3d_pair(sb, &tmB, fbar, kb * bk(MODE), col0, pb);
+                        const uint32_t ssf = sa + sf_off(MODE);
+                        ptx::tma_load_3d_pair(ssf, &tmSA, fbar, 0, (tm * 2 + crank) * p.kblocks + kb, 0);
+                        ptx::tma_load_3d_pair(ssf + SFA_BYTES, &tmSB, fbar, 0, tn * p.kblocks + kb, 0);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < nbox(MODE); ++j)
+                            ptx::tma_load_3d_pair(sb + j * box_bytes(MODE), &tmB, fbar, col0 + j * boxn(MODE), kb * bk(MODE),
+                                                  pb);
+                    }
                 }
                 __syncwarp();
                 issued |= 1u << stage;
@@ -203,20 +252,26 @@ __global__ void __launch_bounds__(threads(MODE), 1)
         }
     } else if (warp == 1 && leader) {
         // ------------------------------------------------ MMA issuer (leader; one elected lane issues)
-        int stage = 0, abuf = 0;
+        int stage = 0, abuf = 0, sfb = 0;
         uint32_t phase = 0, aphase = 0;
         bool ok = true, any = false;
         // descriptors of stage 0, k-step 0; A steps +32 B along the swizzled
-        // K row, B +UK rows of 128 B, a stage +STAGE_BYTES (offsets >> 4)
+        // K row, B (MN-major) +uk rows of 128 B or (K-major, FP8) +32 B, a
+        // stage +STAGE_BYTES (offsets >> 4)
+        constexpr uint32_t B_KSTEP = MODE == MODE_FP8 ? (32 >> 4) : (uk(MODE) * 128 >> 4);
         const ptx::DescHalves a0 = ptx::desc_halves(ptx::smem_desc_sw128(tiles0, 16, 1024));
-        const ptx::DescHalves b0 = ptx::desc_halves(ptx::smem_desc_sw128(tiles0 + A_BYTES, BOX_BYTES, 1024));
+        const ptx::DescHalves b0 = ptx::desc_halves(
+            MODE == MODE_FP8 ? ptx::smem_desc_sw128(tiles0 + A_BYTES, 16, 1024)
+                             : ptx::smem_desc_sw128(tiles0 + A_BYTES, box_bytes(MODE), 1024));
+        // FP8: the stage's scale blocks, rows of 16 B in 8-row groups (no swizzle)
+        const ptx::DescHalves s0 = ptx::desc_halves(ptx::smem_desc_plain(tiles0 + sf_off(MODE), 128));
         for (int t = cfirst; t < num_tiles && ok; t += cstride) {
             for (int it = 0; it < kiters; ++it) {
                 int j, last;  // position inside the current accumulator; whether it is its last step
-                if constexpr (MODE == MODE_STORE) {
+                if constexpr (MODE == MODE_STORE || MODE == MODE_FP8) {
                     j = it;
                     last = it == kiters - 1;
-                } else {
+                } else {  // a fresh accumulator per k-block (all its terms)
                     j = it % p.n_terms;
                     last = j == p.n_terms - 1;
                 }
@@ -235,15 +290,33 @@ __global__ void __launch_bounds__(threads(MODE), 1)
                 ptx::tc_fence_after();
                 const uint32_t so = (uint32_t)stage * (STAGE_BYTES >> 4);
                 if (ptx::elect_one()) {  // the same lane issues every MMA and commit
+                    if constexpr (MODE == MODE_FP8) {
+                        // this k-block's scale blocks: shared memory -> TMEM buffer sfb of both CTAs,
+                        // ordered before the MMAs below in the tensor pipe
+                        const uint32_t sfa = tmem + (uint32_t)(SF_COL0 + 16 * sfb);
+                        const uint32_t slo = s0.lo + so;
+                        ptx::tmem_cp_32x128b_pair(sfa, slo, s0.hi);
+                        ptx::tmem_cp_32x128b_pair(sfa + 4, slo + (SFA_BYTES >> 4), s0.hi);
+                        ptx::tmem_cp_32x128b_pair(sfa + 8, slo + ((SFA_BYTES + 512) >> 4), s0.hi);
+                    }
 #pragma unroll
-                    for (int k = 0; k < BK / UK; ++k)
-                        ptx::mma_bf16_pair_h(dacc, a0.lo + so + k * (32 >> 4), a0.hi, b0.lo + so + k * (UK * 128 >> 4),
-                                             b0.hi, IDESC, (j > 0 || k > 0) ? 1u : 0u);
+                    for (int k = 0; k < bk(MODE) / uk(MODE); ++k) {
+                        const uint32_t alo = a0.lo + so + k * (32 >> 4), blo = b0.lo + so + k * B_KSTEP;
+                        if constexpr (MODE == MODE_FP8) {
+                            // k-step k uses byte k of each scale word (all four hold the block's scale)
+                            const uint32_t sfa = tmem + (uint32_t)(SF_COL0 + 16 * sfb);
+                            ptx::mma_mxf8_pair_h(dacc, alo, a0.hi, blo, b0.hi, idesc(MODE) | ((uint32_t)k << 4) | ((uint32_t)k << 29),
+                                                 sfa, sfa + 4, (j > 0 || k > 0) ? 1u : 0u);
+                        } else {
+                            ptx::mma_bf16_pair_h(dacc, alo, a0.hi, blo, b0.hi, idesc(MODE), (j > 0 || k > 0) ? 1u : 0u);
+                        }
+                    }
                     ptx::mma_commit_pair_mc(empty(stage), kPair);
                     if (last) ptx::mma_commit_pair_mc(tfull(abuf), kPair);
                 }
                 __syncwarp();
                 any = true;
+                if constexpr (MODE == MODE_FP8) sfb = (sfb + 1) % SF_BUFS;
                 if (++stage == STAGES) {
                     stage = 0;
                     phase ^= 1u;
@@ -258,7 +331,7 @@ __global__ void __launch_bounds__(threads(MODE), 1)
             ptx::mma_commit_pair_mc(drain, 1);
             drain_wait(drain, 0);
         }
-    } else if (warp >= 2) {
+    } else if (warp >= 2 && warp < 2 + epi_warps(MODE)) {
         // ------------------------------------------------ epilogue (both CTAs)
         const int q = warp & 3;          // TMEM lane quarter this warp may access
         const int half = (warp - 2) / 4;                 // which part of the 256 columns
@@ -333,12 +406,12 @@ __global__ void __launch_bounds__(threads(MODE), 1)
                     }
                     const uint32_t tb = lanes + (uint32_t)(abuf * ACC_STRIDE);
 #pragma unroll
-                    for (int c = 0; c < HC; c += 32) {
-                        uint32_t r[32];
-                        ptx::tmem_ld32(tb + c, r);
+                    for (int c = 0; c < HC; c += 16) {
+                        uint32_t r[16];
+                        ptx::tmem_ld16(tb + c, r);
                         ptx::tmem_ld_wait();
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) acc[c + j] = __fadd_rn(acc[c + j], __uint_as_float(r[j]));
+                        for (int j = 0; j < 16; ++j) acc[c + j] = __fadd_rn(acc[c + j], __uint_as_float(r[j]));
                     }
                     release_acc();
                 }
@@ -387,18 +460,18 @@ int pair_sms() {
 }
 
 template <int MODE>
-cudaError_t launch_pair(const CUtensorMap &ta, const CUtensorMap &tb, const CUtensorMap &td, PairParams &p,
-                        cudaStream_t s) {
+cudaError_t launch_pair(const CUtensorMap &ta, const CUtensorMap &tb, const CUtensorMap &td, const CUtensorMap &tsa,
+                        const CUtensorMap &tsb, PairParams &p, cudaStream_t s) {
     auto kern = tc_gemm_pair<MODE>;
     static int max_clusters = -1;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = 2, at[0].val.clusterDim.y = 1, at[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(threads(MODE)), cfg.dynamicSmemBytes = SMEM;
+    cfg.blockDim = dim3(threads(MODE)), cfg.dynamicSmemBytes = smem_bytes(MODE);
     cfg.attrs = at, cfg.numAttrs = 1;
     if (max_clusters < 0) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(MODE));
         if (e != cudaSuccess) return e;
         max_clusters = pair_sms() / 2;
         cfg.gridDim = dim3(2 * max_clusters);
@@ -407,12 +480,12 @@ cudaError_t launch_pair(const CUtensorMap &ta, const CUtensorMap &tb, const CUte
         cudaGetLastError();
     }
     p.tiles_m = (p.M + 2 * BM - 1) / (2 * BM);
-    p.tiles_n = (p.N + BN - 1) / BN;
+    p.tiles_n = (p.N + bn(MODE) - 1) / bn(MODE);
     const int tiles = p.tiles_m * p.tiles_n;
     const int clusters = tiles < max_clusters ? tiles : max_clusters;
     cfg.gridDim = dim3(2 * clusters);
     cfg.stream = s;
-    return cudaLaunchKernelEx(&cfg, kern, ta, tb, td, p);
+    return cudaLaunchKernelEx(&cfg, kern, ta, tb, td, tsa, tsb, p);
 }
 
 }  // namespace
@@ -436,22 +509,55 @@ bool pair_mma_enabled() {
     return v == 1;
 }
 
+// D's tensor map for TMA stores (16-byte aligned base and row stride); false
+// when D's layout rules TMA out and the epilogue stores directly.
+static bool d_tmap(CUtensorMap *td, float *D, int64_t ldd, int M, int N) {
+    std::memset(td, 0, sizeof(*td));
+    return ((uintptr_t)D % 16 == 0) && (ldd % 4 == 0) && tma_store_enabled() &&
+           make_tmap(td, D, (uint64_t)N, (uint64_t)M, 1, (uint64_t)ldd * 4, (uint64_t)ldd * 4 * (uint64_t)M, 32, 32,
+                     CU_TENSOR_MAP_DATA_TYPE_FLOAT32);
+}
+
+int pair_fp8_tile_n() { return bn(MODE_FP8); }
+
+cudaError_t tc_gemm_pair_fp8_launch(const uint8_t *A8, int64_t lda, const uint8_t *Bt8, int64_t ldb, int M, int N, int K,
+                                    const uint32_t *sfa, const uint32_t *sfb, float *D, int64_t ldd, cudaStream_t s) {
+    const int64_t kb = (K + bk(MODE_FP8) - 1) / bk(MODE_FP8);
+    const int64_t mb = (M + BM - 1) / BM, tn = (N + bn(MODE_FP8) - 1) / bn(MODE_FP8);
+    CUtensorMap ta, tb, tsa, tsb;
+    if (!make_tmap(&ta, A8, (uint64_t)K, (uint64_t)M, 1, (uint64_t)lda, (uint64_t)lda * (uint64_t)M, 128, BM,
+                   CU_TENSOR_MAP_DATA_TYPE_UINT8) ||
+        !make_tmap(&tb, Bt8, (uint64_t)K, (uint64_t)N, 1, (uint64_t)ldb, (uint64_t)ldb * (uint64_t)N, 128, bn(MODE_FP8) / 2,
+                   CU_TENSOR_MAP_DATA_TYPE_UINT8) ||
+        // scale blocks: [row block][k-block] of 128 words, [column tile][k-block] of 256 words
+        !make_tmap(&tsa, sfa, 128, (uint64_t)(mb * kb), 1, 512, (uint64_t)(512 * mb * kb), 128, 1,
+                   CU_TENSOR_MAP_DATA_TYPE_UINT32, CU_TENSOR_MAP_SWIZZLE_NONE) ||
+        !make_tmap(&tsb, sfb, 256, (uint64_t)(tn * kb), 1, 1024, (uint64_t)(1024 * tn * kb), 256, 1,
+                   CU_TENSOR_MAP_DATA_TYPE_UINT32, CU_TENSOR_MAP_SWIZZLE_NONE))
+        return cudaErrorInvalidValue;
+    PairParams p{};
+    p.M = M, p.N = N, p.K = K;
+    p.kblocks = (int)kb;
+    p.n_terms = 1;
+    p.D = D, p.ldd = ldd;
+    p.vec_store = ((uintptr_t)D % 16 == 0) && (ldd % 4 == 0);
+    CUtensorMap td;
+    p.tma_store = d_tmap(&td, D, ldd, M, N);
+    return launch_pair<MODE_FP8>(ta, tb, td, tsa, tsb, p, s);
+}
+
 cudaError_t tc_gemm_pair_launch(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, int K, int n_terms,
                                 uint32_t term_a, uint32_t term_b, float *D, int64_t ldd, bool promote, cudaStream_t s) {
     PairParams p{};
     p.M = M, p.N = N, p.K = K;
-    p.kblocks = (K + BK - 1) / BK;
+    p.kblocks = (K + bk(MODE_STORE) - 1) / bk(MODE_STORE);
     p.n_terms = n_terms;
     p.term_a = term_a, p.term_b = term_b;
     p.D = D, p.ldd = ldd;
     p.vec_store = ((uintptr_t)D % 16 == 0) && (ldd % 4 == 0);
-    // TMA store rules: 16-byte aligned base and row stride
     CUtensorMap td;
-    std::memset(&td, 0, sizeof(td));
-    p.tma_store = p.vec_store && tma_store_enabled() &&
-                  make_tmap(&td, D, (uint64_t)N, (uint64_t)M, 1, (uint64_t)ldd * 4, (uint64_t)ldd * 4 * (uint64_t)M, 32, 32,
-                            CU_TENSOR_MAP_DATA_TYPE_FLOAT32);
-    return promote ? launch_pair<MODE_PROMOTE>(ta, tb, td, p, s) : launch_pair<MODE_STORE>(ta, tb, td, p, s);
+    p.tma_store = d_tmap(&td, D, ldd, M, N);
+    return promote ? launch_pair<MODE_PROMOTE>(ta, tb, td, td, td, p, s) : launch_pair<MODE_STORE>(ta, tb, td, td, td, p, s);
 }
 
 cudaError_t pair_read_and_clear_status(uint32_t *flags) {

@@ -120,6 +120,15 @@ MOA_DEV void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uin
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
 
+// Per-thread asynchronous 4-byte copy global -> shared, in this thread's
+// current commit group; cp_async_wait<N> waits until at most N of this
+// thread's groups are still in flight.
+MOA_DEV void cp_async4(void *smem_dst, const void *gsrc) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+}
+MOA_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> MOA_DEV void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // ---------------------------------------------------------------- cluster
 MOA_DEV uint32_t cluster_ctarank() {
     uint32_t r;
@@ -170,6 +179,16 @@ MOA_DEV uint64_t smem_desc_sw128(uint32_t addr, uint32_t lbo, uint32_t sbo) {
     d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
     d |= (uint64_t)1 << 46;
     d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Shared-memory descriptor of a matrix without swizzling: 8-row groups of
+// 16-byte rows (128 B), `sbo` bytes apart.
+MOA_DEV uint64_t smem_desc_plain(uint32_t addr, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
     return d;
 }
 
@@ -313,6 +332,46 @@ MOA_DEV void mma_bf16_pair_h(uint32_t tmem_d, uint32_t a_lo, uint32_t a_hi, uint
         "setp.ne.b32 p, %6, 0;\n\t"
         "tcgen05.mma.cta_group::2.kind::f16 [%0], da, db, %5, p;\n\t}" ::"r"(tmem_d),
         "r"(a_lo), "r"(a_hi), "r"(b_lo), "r"(b_hi), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// One 256 x N x 32 e4m3 step of the pair with per-32-element UE8M0 scale
+// factors of A (sfa) and B (sfb) read from TMEM (kind::mxf8f6f4, 1X).  The
+// scale words of a CTA: A's row r at lane r, column sfa + r / 32; B's column
+// n at column sfb + n / 32 of lane n % 32 in every lane quarter (each CTA
+// holds all N); the instruction descriptor's scale-factor ids pick the byte.
+MOA_DEV void mma_mxf8_pair_h(uint32_t tmem_d, uint32_t a_lo, uint32_t a_hi, uint32_t b_lo, uint32_t b_hi, uint32_t idesc,
+                             uint32_t sfa, uint32_t sfb, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\t"
+        "mov.b64 da, {%1, %2};\n\t"
+        "mov.b64 db, {%3, %4};\n\t"
+        "setp.ne.b32 p, %8, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::mxf8f6f4.block_scale.scale_vec::1X [%0], da, db, %5, [%6], [%7], p;\n\t}" ::"r"(tmem_d),
+        "r"(a_lo), "r"(a_hi), "r"(b_lo), "r"(b_hi), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accumulate)
+        : "memory");
+}
+// One 256 x N x 32 e4m3 step of the pair (kind::f8f6f4), descriptors as halves.
+MOA_DEV void mma_e4m3_pair_h(uint32_t tmem_d, uint32_t a_lo, uint32_t a_hi, uint32_t b_lo, uint32_t b_hi, uint32_t idesc,
+                             uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\t"
+        "mov.b64 da, {%1, %2};\n\t"
+        "mov.b64 db, {%3, %4};\n\t"
+        "setp.ne.b32 p, %6, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], da, db, %5, p;\n\t}" ::"r"(tmem_d),
+        "r"(a_lo), "r"(a_hi), "r"(b_lo), "r"(b_hi), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// Copy 32 rows of 16 bytes (a 512-byte block, descriptor halves) from the
+// shared memory of each CTA of the pair into its own TMEM at `taddr`: row l
+// becomes columns taddr .. taddr + 3 of lane l of every lane quarter.
+// Ordered with the issuing thread's other tcgen05 operations.
+MOA_DEV void tmem_cp_32x128b_pair(uint32_t taddr, uint32_t s_lo, uint32_t s_hi) {
+    asm volatile(
+        "{\n\t.reg .b64 ds;\n\t"
+        "mov.b64 ds, {%1, %2};\n\t"
+        "tcgen05.cp.cta_group::2.32x128b.warpx4 [%0], ds;\n\t}" ::"r"(taddr),
+        "r"(s_lo), "r"(s_hi)
         : "memory");
 }
 // Arrive once on the barrier at `bar`'s offset in every CTA of cta_mask when
