@@ -37,37 +37,56 @@ MOA_DEV float block_scale(float amax, float *inv) {
 
 MOA_DEV uint8_t to_e4m3(float x) { return (uint8_t)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3); }
 
-// One warp per (row, k-block) of A: 128 elements, 4 per lane.
-__global__ void quant_a_kernel(const float *__restrict__ A, int64_t M, int64_t K, int64_t Kp, int64_t KB,
-                               uint8_t *__restrict__ A8, float *__restrict__ sA) {
-    const int64_t nw = (int64_t)gridDim.x * blockDim.x / 32;
-    const int lane = threadIdx.x % 32;
-    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; w < M * KB; w += nw) {
-        const int64_t row = w / KB, kb = w - row * KB;
-        const int64_t k0 = kb * 128 + lane * 4;
-        float x[4];
-        float amax = 0.0f;
+// Scale factors of the block-scaled pair GEMM: UE8M0 byte = the exponent
+// field of the power-of-two FP32 scale (both have bias 127), repeated in the
+// four bytes of a word (one per 32-deep k-step of the 128-deep k-block), in
+// the kernel's TMEM-word order (tc.h, tc_gemm_pair_fp8_launch).
+MOA_DEV uint32_t ue8m0_word(float scale) { return ((__float_as_uint(scale) >> 23) & 255u) * 0x01010101u; }
+
+// Eight threads per (row, k-block) of A: 16 elements each (four 16-byte
+// loads when aligned), the block maximum by three shuffles inside the
+// group, one 16-byte store of codes per thread.  With `sfa`, the scale is
+// also written as the pair GEMM's scale word.
+__global__ void __launch_bounds__(256) quant_a_kernel(const float *__restrict__ A, int64_t M, int64_t K, int64_t Kp,
+                                                      int64_t KB, uint8_t *__restrict__ A8, float *__restrict__ sA,
+                                                      uint32_t *__restrict__ sfa) {
+    const int sub = threadIdx.x % 8;
+    for (int64_t blk = (int64_t)blockIdx.x * 32 + threadIdx.x / 8; blk < M * KB; blk += (int64_t)gridDim.x * 32) {
+        const int64_t row = blk / KB, kb = blk - row * KB;
+        const int64_t k0 = kb * 128 + sub * 16;
         const float *src = A + row * K + k0;
-        if (k0 + 4 <= K && ((uintptr_t)src & 15) == 0) {  // one 16-byte load
-            const float4 v = __ldg(reinterpret_cast<const float4 *>(src));
-            x[0] = v.x, x[1] = v.y, x[2] = v.z, x[3] = v.w;
+        float x[16];
+        if (k0 + 16 <= K && ((uintptr_t)src & 15) == 0) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(src) + i);
+                x[4 * i] = v.x, x[4 * i + 1] = v.y, x[4 * i + 2] = v.z, x[4 * i + 3] = v.w;
+            }
         } else {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) x[i] = (k0 + i < K) ? __ldg(src + i) : 0.0f;
+            for (int i = 0; i < 16; ++i) x[i] = (k0 + i < K) ? __ldg(src + i) : 0.0f;
         }
+        float amax = 0.0f;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) amax = fmaxf(amax, fabsf(x[i]));
+        for (int i = 0; i < 16; ++i) amax = fmaxf(amax, fabsf(x[i]));
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        for (int o = 4; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
         float inv;
         const float sc = block_scale(amax, &inv);
-        if (k0 < Kp) {
-            uint32_t packed = 0;
+        if (k0 < Kp) {  // Kp is a multiple of 16: all 16 codes lie inside the padded row
+            uint32_t w[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) packed |= (uint32_t)to_e4m3(__fmul_rn(x[i], inv)) << (8 * i);
-            *reinterpret_cast<uint32_t *>(A8 + row * Kp + k0) = packed;
+            for (int b = 0; b < 4; ++b) {
+                w[b] = 0;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) w[b] |= (uint32_t)to_e4m3(__fmul_rn(x[4 * b + c], inv)) << (8 * c);
+            }
+            *reinterpret_cast<uint4 *>(A8 + row * Kp + k0) = make_uint4(w[0], w[1], w[2], w[3]);
         }
-        if (lane == 0) sA[row * KB + kb] = sc;
+        if (sub == 0) {
+            sA[row * KB + kb] = sc;
+            if (sfa) sfa[((row / 128) * KB + kb) * 128 + (row % 32) * 4 + (row % 128) / 32] = ue8m0_word(sc);
+        }
     }
 }
 
@@ -122,12 +141,14 @@ __global__ void __launch_bounds__(256) quant_b_kernel(const float *__restrict__ 
 }
 
 // The same quantisation of B, written transposed: Bt [N][Kp] (K-major), the
-// operand layout of the block-scaled pair GEMM.  One block per 128 x 128
-// tile; thread t owns column t % 128 and 64 consecutive k of it (loads
-// coalesced across a warp along the row of B), and writes its 64 codes as
-// four 16-byte stores into the column's row of Bt.
+// operand layout of the block-scaled pair GEMM, with the scale also written
+// as that GEMM's scale word of every column.  One block per 128 x 128 tile;
+// thread t owns column t % 128 and 64 consecutive k of it (loads coalesced
+// across a warp along the row of B), and writes its 64 codes as four
+// 16-byte stores into the column's row of Bt.
 __global__ void __launch_bounds__(256) quant_bt_kernel(const float *__restrict__ B, int64_t K, int64_t N, int64_t Kp,
-                                                       int64_t NB, uint8_t *__restrict__ Bt, float *__restrict__ sB) {
+                                                       int64_t NB, uint8_t *__restrict__ Bt, float *__restrict__ sB,
+                                                       uint32_t *__restrict__ sfb, int T, int64_t KB) {
     __shared__ float red[8];
     const int64_t kb = blockIdx.y, nb = blockIdx.x;
     const int t = threadIdx.x;
@@ -165,32 +186,10 @@ __global__ void __launch_bounds__(256) quant_bt_kernel(const float *__restrict__
         }
     }
     if (t == 0) sB[kb * NB + nb] = sc;
-}
-
-// Scale factors of the block-scaled pair GEMM: UE8M0 byte = the exponent
-// field of the power-of-two FP32 scale (both have bias 127), repeated in the
-// four bytes of a word (one per 32-deep k-step of the 128-deep k-block), in
-// the kernel's TMEM-word order (tc.h, tc_gemm_pair_fp8_launch).
-MOA_DEV uint32_t ue8m0_word(float scale) { return ((__float_as_uint(scale) >> 23) & 255u) * 0x01010101u; }
-
-__global__ void pack_sfa_kernel(const float *__restrict__ sA, int64_t M, int64_t KB, uint32_t *__restrict__ out,
-                                int64_t total) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int w = (int)(i % 128);
-        const int64_t blk = i / 128, rb = blk / KB, kb = blk - rb * KB;
-        const int64_t row = rb * 128 + 32 * (w % 4) + w / 4;
-        out[i] = row < M ? ue8m0_word(sA[row * KB + kb]) : 0x7f7f7f7fu;
-    }
-}
-
-__global__ void pack_sfb_kernel(const float *__restrict__ sB, int64_t N, int64_t KB, int64_t NB, int T,
-                                uint32_t *__restrict__ out, int64_t total) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int w = (int)(i % 256);
-        const int64_t blk = i / 256, tn = blk / KB, kb = blk - tn * KB;
-        const int j = 4 * (w / 128) + w % 4, l = (w % 128) / 4;
-        const int64_t col = tn * T + 32 * j + l;
-        out[i] = (32 * j < T && col < N) ? ue8m0_word(sB[kb * NB + col / 128]) : 0x7f7f7f7fu;
+    if (t < 128 && n < N) {  // this column's scale word of the pair GEMM (tile T columns wide)
+        const int64_t tn = n / T;
+        const int j = (int)(n - tn * T) / 32, l = (int)(n % 32);
+        sfb[(tn * KB + kb) * 256 + (j / 4) * 128 + l * 4 + j % 4] = ue8m0_word(sc);
     }
 }
 
@@ -216,31 +215,26 @@ moa_status tc_inner_fp8(const float *A, const float *B, float *D, int64_t M, int
     // the block-scaled pair GEMM (256 x 224 tiles, B transposed) for large
     // products; the single-CTA kernel with scaled register accumulation else
     const bool pair = M > 128 && N > 128 && M < (1ll << 31) && N < (1ll << 31) && K < (1ll << 31) && pair_mma_enabled();
+    const int64_t T = pair_fp8_tile_n(), MB = (M + 127) / 128, TN = (N + T - 1) / T;
+    uint32_t *sfa = reinterpret_cast<uint32_t *>(((uintptr_t)(sb + KB * NB) + 15) & ~(uintptr_t)15);  // TMA: 16-B base
+    uint32_t *sfb = sfa + MB * KB * 128;
+    if (KB > 65535) return MOA_ERR_OVERFLOW;
+    if (pair && cudaMemsetAsync(sfa, 0x7f, (size_t)(MB * KB * 128 + TN * KB * 256) * 4, s) != cudaSuccess)
+        return MOA_ERR_CUDA;  // words no row or column writes: scale 1
     {
-        int64_t warps = M * KB;
-        int64_t blocks = (warps * 32 + 255) / 256;
+        int64_t blocks = (M * KB + 31) / 32;
         if (blocks > 152 * 16) blocks = 152 * 16;
-        quant_a_kernel<<<(unsigned)blocks, 256, 0, s>>>(A, M, K, Kp, KB, a8, sa);
-        if (KB > 65535) return MOA_ERR_OVERFLOW;
+        quant_a_kernel<<<(unsigned)blocks, 256, 0, s>>>(A, M, K, Kp, KB, a8, sa, pair ? sfa : nullptr);
         if (pair)
-            quant_bt_kernel<<<dim3((unsigned)NB, (unsigned)KB), 256, 0, s>>>(B, K, N, Kp, NB, b8, sb);
+            quant_bt_kernel<<<dim3((unsigned)NB, (unsigned)KB), 256, 0, s>>>(B, K, N, Kp, NB, b8, sb, sfb, (int)T, KB);
         else
             quant_b_kernel<<<dim3((unsigned)NB, (unsigned)KB), 256, 0, s>>>(B, K, N, Np, NB, b8, sb);
         if (cudaGetLastError() != cudaSuccess) return MOA_ERR_CUDA;
     }
-    if (pair) {
-        const int64_t T = pair_fp8_tile_n(), MB = (M + 127) / 128, TN = (N + T - 1) / T;
-        uint32_t *sfa = reinterpret_cast<uint32_t *>(((uintptr_t)(sb + KB * NB) + 15) & ~(uintptr_t)15);  // TMA: 16-B base
-        uint32_t *sfb = sfa + MB * KB * 128;
-        pack_sfa_kernel<<<(unsigned)std::min<int64_t>((MB * KB * 128 + 255) / 256, 152 * 8), 256, 0, s>>>(sa, M, KB, sfa,
-                                                                                                        MB * KB * 128);
-        pack_sfb_kernel<<<(unsigned)std::min<int64_t>((TN * KB * 256 + 255) / 256, 152 * 8), 256, 0, s>>>(
-            sb, N, KB, NB, (int)T, sfb, TN * KB * 256);
-        if (cudaGetLastError() != cudaSuccess) return MOA_ERR_CUDA;
+    if (pair)
         return tc_gemm_pair_fp8_launch(a8, Kp, b8, Kp, (int)M, (int)N, (int)K, sfa, sfb, D, N, s) == cudaSuccess
                    ? MOA_OK
                    : MOA_ERR_CUDA;
-    }
     return tc_gemm_fp8(a8, Kp, b8, Np, sa, sb, D, N, M, N, K, s);
 }
 
