@@ -42,9 +42,10 @@
 //
 // Ozaki mode (MODE_OZAKI): the planes hold fixed-point digit slices (small
 // integers, exact in bf16) and the terms are the slice pairs (s, u) with
-// s + u < S, ordered by weight class g = s + u.  Each term's contraction is
-// cut into chunks short enough that the FP32 accumulator holds the exact
-// integer sum; the epilogue adds the chunks of one weight class exactly in
+// s + u < S, grouped by weight class g = s + u.  The contraction is cut into
+// chunks short enough that the FP32 accumulator holds the exact integer sum
+// of one pair; a class runs chunk by chunk over all of its pairs (OzakiIter),
+// the epilogue adds every (chunk, pair) accumulator of the class exactly in
 // int32 registers, and at the end of the class folds that integer, scaled
 // by the class's power-of-two weight, into a double-float running sum
 // (hi + lo FP32 pair, TwoSum; ~48 bits relative to the running sum) kept in
@@ -107,19 +108,35 @@ struct GemmParams {
     int nblk_b;            // ceil(N / 128)
 };
 
-// Ozaki term -> slice pair (s, u): weight classes g = s + u from S-1
-// (lightest) down to 0, heaviest digit of A first within a class.
-MOA_DEV void ozaki_pair(int term, int S, int &s, int &u) {
-    for (int g = S - 1; g >= 0; --g) {
-        if (term <= g) {
-            s = term;
-            u = g - term;
+// Ozaki iteration order: weight class g from S-1 (lightest) down to 0, then
+// chunk c of the contraction (p.chunk k-blocks, the last one shorter), then
+// the class's slice pairs (s, g - s), s = 0..g, then the k-blocks of the
+// chunk.  Each (class, chunk, pair) is one exact FP32 accumulator; a class's
+// sum is complete, and folded once, after its last chunk.  Running the
+// class's pairs chunk by chunk keeps the slice panels of one chunk in L2
+// while every tile of a wave uses them.
+struct OzakiIter {
+    int g = 0, c = 0, s = 0, kk = 0, clen = 0;
+    MOA_DEV void start(int S, int chunk, int kblocks) {
+        g = S - 1;
+        c = s = kk = 0;
+        clen = min(chunk, kblocks);
+    }
+    MOA_DEV int kb(int chunk) const { return c * chunk + kk; }
+    MOA_DEV void next(int chunk, int kblocks) {
+        if (++kk < clen) return;
+        kk = 0;
+        if (++s <= g) return;
+        s = 0;
+        if (++c * chunk < kblocks) {
+            clen = min(chunk, kblocks - c * chunk);
             return;
         }
-        term -= g + 1;
+        c = 0;
+        clen = min(chunk, kblocks);
+        --g;
     }
-    s = u = 0;
-}
+};
 
 // Exponent e with |x| < 2^e for the largest |x| of a row / column, from its
 // FP64 bit pattern (0 for an all-zero row).
@@ -231,12 +248,15 @@ __global__ void __launch_bounds__(cta_threads(MODE), 1)
             int tm, tn;
             tile_of(t, tiles_mc, p.tiles_n, tm, tn);
             tm = tm * CL + crank;
+            OzakiIter oz;
+            oz.start(p.slices, p.chunk, p.kblocks);
             for (int it = 0; it < kiters; ++it) {
                 int kb, pa, pb;
-                if constexpr (MODE == MODE_OZAKI) {  // term-major: all k-blocks of one slice pair
-                    const int term = it / p.kblocks;
-                    kb = it - term * p.kblocks;
-                    ozaki_pair(term, p.slices, pa, pb);
+                if constexpr (MODE == MODE_OZAKI) {  // class, chunk, pair, k-block (OzakiIter)
+                    kb = oz.kb(p.chunk);
+                    pa = oz.s;
+                    pb = oz.g - oz.s;
+                    oz.next(p.chunk, p.kblocks);
                 } else {  // k-block-major: every term of one k-block
                     kb = it / p.n_terms;
                     const int term = it - kb * p.n_terms;
@@ -282,6 +302,8 @@ __global__ void __launch_bounds__(cta_threads(MODE), 1)
         // once per k-block with all its terms (promote), or once per chunk of
         // a slice pair (Ozaki)
         for (int t = cfirst; t < num_tiles && ok; t += cstride) {
+            OzakiIter oz;
+            oz.start(p.slices, p.chunk, p.kblocks);
             for (int it = 0; it < kiters; ++it) {
                 int j, last;  // position inside the current accumulator; whether it is its last step
                 if constexpr (MODE == MODE_STORE) {
@@ -290,10 +312,10 @@ __global__ void __launch_bounds__(cta_threads(MODE), 1)
                 } else if constexpr (MODE == MODE_PROMOTE || MODE == MODE_FP8) {
                     j = it % p.n_terms;
                     last = j == p.n_terms - 1;
-                } else {
-                    const int kb = it % p.kblocks;
-                    j = kb % p.chunk;
-                    last = (j == p.chunk - 1) || (kb == p.kblocks - 1);
+                } else {  // one accumulator per (class, chunk, pair)
+                    j = oz.kk;
+                    last = oz.kk == oz.clen - 1;
+                    oz.next(p.chunk, p.kblocks);
                 }
                 if (j == 0) {
                     if (!ptx::mbar_wait(tempty(abuf), aphase ^ 1u, abort_flag, &g_tc_status)) {
@@ -390,15 +412,11 @@ __global__ void __launch_bounds__(cta_threads(MODE), 1)
 #pragma unroll
                 for (int j = 0; j < HC; ++j) qacc[j] = 0;
                 const int chunks = (p.kblocks + p.chunk - 1) / p.chunk;
-                for (int term = 0; term < p.n_terms && ok; ++term) {
-                    int sa_, sb_, ns = -1, nu = -1;
-                    ozaki_pair(term, p.slices, sa_, sb_);
-                    if (term + 1 < p.n_terms) ozaki_pair(term + 1, p.slices, ns, nu);
-                    const int cls = sa_ + sb_;
-                    const bool class_ends = (term + 1 == p.n_terms) || (ns + nu != cls);
+                for (int cls = p.slices - 1; cls >= 0 && ok; --cls) {
+                    const bool class_ends = true;  // the loops below consume the whole class
                     // the class's power-of-two weight in accumulator units, exact in FP32
                     const float w = __int_as_float((127 + p.lsb - (cls + 2) * p.beta) << 23);
-                    for (int c = 0; c < chunks; ++c) {
+                    for (int c = 0; c < chunks * (cls + 1); ++c) {  // (chunk, pair) accumulators of the class
                         if (!wait_acc()) {
                             ok = false;
                             break;
