@@ -1,0 +1,111 @@
+// Device pieces of the Ozaki-sliced FP64 form shared by the tensor-core
+// kernels (tc_gemm.cu, tc_gemm_pair.cu): the order in which the slice-pair
+// products run, the fold of a weight class's exact integer sum into the
+// double-float running sum, and the final conversion to FP64.
+//
+// Slices: A = sum_s 2^(e_row - (s+1) beta) A_s and B likewise with digit
+// planes A_s, B_u of beta-bit integers; the product keeps the pairs
+// s + u < S, grouped by weight class g = s + u.  Accumulators count units of
+// 2^(e_row + e_col - lsb).
+#pragma once
+
+#include "common.cuh"
+
+namespace moa {
+namespace ozaki {
+
+// Iteration order: weight class g from S-1 (lightest) down to 0, then
+// chunk c of the contraction (`chunk` k-blocks, the last one shorter), then
+// the class's slice pairs (s, g - s), s = 0..g, then the k-blocks of the
+// chunk.  Each (class, chunk, pair) is one exact FP32 accumulator; a class's
+// sum is complete, and folded once, after its last chunk.  Running the
+// class's pairs chunk by chunk keeps the slice panels of one chunk in L2
+// while every tile of a wave uses them.
+struct Iter {
+    int g = 0, c = 0, s = 0, kk = 0, clen = 0;
+    MOA_DEV void start(int S, int chunk, int kblocks) {
+        g = S - 1;
+        c = s = kk = 0;
+        clen = min(chunk, kblocks);
+    }
+    MOA_DEV int kb(int chunk) const { return c * chunk + kk; }
+    MOA_DEV void next(int chunk, int kblocks) {
+        if (++kk < clen) return;
+        kk = 0;
+        if (++s <= g) return;
+        s = 0;
+        if (++c * chunk < kblocks) {
+            clen = min(chunk, kblocks - c * chunk);
+            return;
+        }
+        c = 0;
+        clen = min(chunk, kblocks);
+        --g;
+    }
+};
+
+// Exponent e with |x| < 2^e for the largest |x| of a row / column, from its
+// FP64 bit pattern (0 for an all-zero row).
+MOA_DEV int scale_exponent(uint64_t maxbits) {
+    const int be = (int)((maxbits >> 52) & 0x7FF);
+    if (be == 0) return maxbits == 0 ? 0 : -1022;
+    return be - 1022;
+}
+
+// The power-of-two weight of class g in accumulator units, exact in FP32.
+MOA_DEV float class_weight(int g, int lsb, int beta) { return __int_as_float((127 + lsb - (g + 2) * beta) << 23); }
+
+// End of a class: running sum (hi, lo) += w * qacc for this thread's HC
+// columns of one row, the pair kept in the row's FP64 slots (drow[col] holds
+// the FP32 pair until the tile is finished); `first` means no sum stored
+// yet.  16 columns at a time, all loads issued before any store.  TwoSum of
+// hi and the scaled high part, the low parts added into the error, then a
+// FastTwoSum renormalisation: ~48 bits relative to the running sum.
+template <int HC>
+MOA_DEV void fold(const int (&qacc)[HC], float w, double *drow, int64_t colh, int64_t N, bool first) {
+#pragma unroll
+    for (int c0 = 0; c0 < HC; c0 += 16) {
+        float2 old[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int64_t col = colh + c0 + j;
+            old[j] = (!first && col < N) ? *reinterpret_cast<const float2 *>(drow + col) : make_float2(0.0f, 0.0f);
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int qv = qacc[c0 + j];
+            const float xh = __int2float_rn(qv);
+            const float xl = __int2float_rn(qv - __float2int_rn(xh));  // exact remainder
+            const float ah = __fmul_rn(xh, w), al = __fmul_rn(xl, w);  // exact scaling
+            const float H = old[j].x, L = old[j].y;
+            const float sum = __fadd_rn(H, ah);  // TwoSum(H, ah)
+            const float bv = __fsub_rn(sum, H);
+            float e = __fadd_rn(__fsub_rn(H, __fsub_rn(sum, bv)), __fsub_rn(ah, bv));
+            e = __fadd_rn(e, __fadd_rn(L, al));
+            const float nh = __fadd_rn(sum, e);  // FastTwoSum renormalisation
+            old[j] = make_float2(nh, __fsub_rn(e, __fsub_rn(nh, sum)));
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int64_t col = colh + c0 + j;
+            if (col < N) *reinterpret_cast<float2 *>(drow + col) = old[j];
+        }
+    }
+}
+
+// End of the tile: each (hi, lo) pair -> FP64, scaled by 2^(e_row + e_col - lsb).
+template <int HC>
+MOA_DEV void finish(double *drow, int64_t colh, int64_t N, uint64_t row_maxbits, const uint64_t *col_max, int lsb) {
+    const int er = scale_exponent(row_maxbits);
+#pragma unroll 4
+    for (int j = 0; j < HC; ++j) {
+        const int64_t col = colh + j;
+        if (col >= N) break;
+        const float2 v = *reinterpret_cast<const float2 *>(drow + col);
+        const int ec = scale_exponent(col_max[col]);
+        drow[col] = ldexp((double)v.x + (double)v.y, er + ec - lsb);
+    }
+}
+
+}  // namespace ozaki
+}  // namespace moa

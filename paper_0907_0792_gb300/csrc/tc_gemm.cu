@@ -44,7 +44,7 @@
 // integers, exact in bf16) and the terms are the slice pairs (s, u) with
 // s + u < S, grouped by weight class g = s + u.  The contraction is cut into
 // chunks short enough that the FP32 accumulator holds the exact integer sum
-// of one pair; a class runs chunk by chunk over all of its pairs (OzakiIter),
+// of one pair; a class runs chunk by chunk over all of its pairs (ozaki::Iter),
 // the epilogue adds every (chunk, pair) accumulator of the class exactly in
 // int32 registers, and at the end of the class folds that integer, scaled
 // by the class's power-of-two weight, into a double-float running sum
@@ -66,6 +66,7 @@
 #include "common.cuh"
 #include "internal.h"
 #include "tc.h"
+#include "ozaki_epi.cuh"
 #include "tc_ptx.cuh"
 
 namespace moa {
@@ -107,44 +108,6 @@ struct GemmParams {
     const float *scale_b;  // [kblocks][ceil(N / 128)]: scale of B's 128 x 128 tiles
     int nblk_b;            // ceil(N / 128)
 };
-
-// Ozaki iteration order: weight class g from S-1 (lightest) down to 0, then
-// chunk c of the contraction (p.chunk k-blocks, the last one shorter), then
-// the class's slice pairs (s, g - s), s = 0..g, then the k-blocks of the
-// chunk.  Each (class, chunk, pair) is one exact FP32 accumulator; a class's
-// sum is complete, and folded once, after its last chunk.  Running the
-// class's pairs chunk by chunk keeps the slice panels of one chunk in L2
-// while every tile of a wave uses them.
-struct OzakiIter {
-    int g = 0, c = 0, s = 0, kk = 0, clen = 0;
-    MOA_DEV void start(int S, int chunk, int kblocks) {
-        g = S - 1;
-        c = s = kk = 0;
-        clen = min(chunk, kblocks);
-    }
-    MOA_DEV int kb(int chunk) const { return c * chunk + kk; }
-    MOA_DEV void next(int chunk, int kblocks) {
-        if (++kk < clen) return;
-        kk = 0;
-        if (++s <= g) return;
-        s = 0;
-        if (++c * chunk < kblocks) {
-            clen = min(chunk, kblocks - c * chunk);
-            return;
-        }
-        c = 0;
-        clen = min(chunk, kblocks);
-        --g;
-    }
-};
-
-// Exponent e with |x| < 2^e for the largest |x| of a row / column, from its
-// FP64 bit pattern (0 for an all-zero row).
-MOA_DEV int scale_exponent(uint64_t maxbits) {
-    const int be = (int)((maxbits >> 52) & 0x7FF);
-    if (be == 0) return maxbits == 0 ? 0 : -1022;
-    return be - 1022;
-}
 
 template <int BN, int STAGES, int MODE = 0> struct Cfg {
     static constexpr int ESZ = MODE == 3 ? 1 : 2;  // element bytes (e4m3 / bf16)
@@ -248,11 +211,11 @@ __global__ void __launch_bounds__(cta_threads(MODE), 1)
             int tm, tn;
             tile_of(t, tiles_mc, p.tiles_n, tm, tn);
             tm = tm * CL + crank;
-            OzakiIter oz;
+            ozaki::Iter oz;
             oz.start(p.slices, p.chunk, p.kblocks);
             for (int it = 0; it < kiters; ++it) {
                 int kb, pa, pb;
-                if constexpr (MODE == MODE_OZAKI) {  // class, chunk, pair, k-block (OzakiIter)
+                if constexpr (MODE == MODE_OZAKI) {  // class, chunk, pair, k-block (ozaki::Iter)
                     kb = oz.kb(p.chunk);
                     pa = oz.s;
                     pb = oz.g - oz.s;
@@ -302,7 +265,7 @@ __global__ void __launch_bounds__(cta_threads(MODE), 1)
         // once per k-block with all its terms (promote), or once per chunk of
         // a slice pair (Ozaki)
         for (int t = cfirst; t < num_tiles && ok; t += cstride) {
-            OzakiIter oz;
+            ozaki::Iter oz;
             oz.start(p.slices, p.chunk, p.kblocks);
             for (int it = 0; it < kiters; ++it) {
                 int j, last;  // position inside the current accumulator; whether it is its last step
@@ -415,7 +378,7 @@ __global__ void __launch_bounds__(cta_threads(MODE), 1)
                 for (int cls = p.slices - 1; cls >= 0 && ok; --cls) {
                     const bool class_ends = true;  // the loops below consume the whole class
                     // the class's power-of-two weight in accumulator units, exact in FP32
-                    const float w = __int_as_float((127 + p.lsb - (cls + 2) * p.beta) << 23);
+                    const float w = ozaki::class_weight(cls, p.lsb, p.beta);
                     for (int c = 0; c < chunks * (cls + 1); ++c) {  // (chunk, pair) accumulators of the class
                         if (!wait_acc()) {
                             ok = false;
@@ -434,39 +397,7 @@ __global__ void __launch_bounds__(cta_threads(MODE), 1)
                         release_acc();  // the accumulator is consumed; the MMA may refill it during the fold
                     }
                     if (!ok) break;
-                    if (class_ends && row_ok) {
-                        // end of the class: add 2^k * qacc to the running sum (hi, lo), 16 columns at a
-                        // time with all loads issued before any store
-#pragma unroll
-                        for (int c0 = 0; c0 < HC; c0 += 16) {
-                            float2 old[16];
-#pragma unroll
-                            for (int j = 0; j < 16; ++j) {
-                                const int64_t col = colh + c0 + j;
-                                old[j] = (!first && col < p.N) ? *reinterpret_cast<const float2 *>(drow + col)
-                                                               : make_float2(0.0f, 0.0f);
-                            }
-#pragma unroll
-                            for (int j = 0; j < 16; ++j) {
-                                const int qv = qacc[c0 + j];
-                                const float xh = __int2float_rn(qv);
-                                const float xl = __int2float_rn(qv - __float2int_rn(xh));  // exact remainder
-                                const float ah = __fmul_rn(xh, w), al = __fmul_rn(xl, w);  // exact scaling
-                                const float H = old[j].x, L = old[j].y;
-                                const float sum = __fadd_rn(H, ah);  // TwoSum(H, ah)
-                                const float bv = __fsub_rn(sum, H);
-                                float e = __fadd_rn(__fsub_rn(H, __fsub_rn(sum, bv)), __fsub_rn(ah, bv));
-                                e = __fadd_rn(e, __fadd_rn(L, al));
-                                const float nh = __fadd_rn(sum, e);  // FastTwoSum renormalisation
-                                old[j] = make_float2(nh, __fsub_rn(e, __fsub_rn(nh, sum)));
-                            }
-#pragma unroll
-                            for (int j = 0; j < 16; ++j) {
-                                const int64_t col = colh + c0 + j;
-                                if (col < p.N) *reinterpret_cast<float2 *>(drow + col) = old[j];
-                            }
-                        }
-                    }
+                    if (class_ends && row_ok) ozaki::fold<HC>(qacc, w, drow, colh, p.N, first);
                     if (!ok) break;
                     if (class_ends) {
 #pragma unroll
@@ -475,17 +406,7 @@ __global__ void __launch_bounds__(cta_threads(MODE), 1)
                     }
                 }
                 if (!ok) break;
-                if (row_ok) {  // running sums -> FP64 with the row / column scales
-                    const int er = scale_exponent(p.row_max[row]);
-#pragma unroll 4
-                    for (int j = 0; j < HC; ++j) {
-                        const int64_t col = colh + j;
-                        if (col >= p.N) break;
-                        const float2 v = *reinterpret_cast<const float2 *>(drow + col);
-                        const int ec = scale_exponent(p.col_max[col]);
-                        drow[col] = ldexp((double)v.x + (double)v.y, er + ec - p.lsb);
-                    }
-                }
+                if (row_ok) ozaki::finish<HC>(drow, colh, p.N, p.row_max[row], p.col_max, p.lsb);
             } else if constexpr (MODE == MODE_FP8) {
                 float acc[HC];
 #pragma unroll
@@ -761,6 +682,11 @@ moa_status tc_gemm_ozaki(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat1
     p.n_terms = S * (S + 1) / 2;
     p.slices = S, p.beta = beta, p.lsb = lsb, p.chunk = chunk_kblocks;
     p.D64 = D, p.ldd = ldd, p.row_max = row_max, p.col_max = col_max;
+    if (M > BM && N > 128 && pair_mma_enabled()) {  // 256 x 256 tiles on CTA pairs
+        const cudaError_t e = tc_gemm_pair_ozaki_launch(ta, tb, p.M, p.N, p.K, S, beta, lsb, chunk_kblocks, row_max, col_max,
+                                                        D, ldd, s);
+        return e == cudaSuccess ? MOA_OK : MOA_ERR_CUDA;
+    }
     // 192-wide tiles: two accumulators fit TMEM and the int32 class sums of a
     // thread's 96 columns fit its registers
     cudaError_t e = (M > BM && cluster_pairs_enabled()) ? launch_tc<192, 5, MODE_OZAKI, 2>(ta, tb, p, s)

@@ -43,6 +43,7 @@
 #include "common.cuh"
 #include "internal.h"
 #include "tc.h"
+#include "ozaki_epi.cuh"
 #include "tc_ptx.cuh"
 
 namespace moa {
@@ -53,7 +54,7 @@ namespace {
 
 constexpr int BM = 128;                // rows per CTA; the pair covers 2 * BM
 constexpr int STAGES = 6;
-constexpr int MODE_STORE = 0, MODE_PROMOTE = 1, MODE_FP8 = 2;
+constexpr int MODE_STORE = 0, MODE_PROMOTE = 1, MODE_FP8 = 2, MODE_OZAKI = 3;
 // Columns per pair tile; each CTA holds bn / 2 of B.  The FP8 mode leaves
 // TMEM room for its scale factors: 2 x 224 accumulator columns + 4 x 16.
 __host__ __device__ constexpr int bn(int mode) { return mode == MODE_FP8 ? 224 : 256; }
@@ -72,7 +73,9 @@ __host__ __device__ constexpr int box_bytes(int mode) { return mode == MODE_FP8 
 // Warps: producer, MMA, and epilogue warps: one per TMEM lane quarter when
 // the accumulator is stored as it is, two per quarter when every k-block is
 // added into registers (each thread then holds 128 running sums).
-__host__ __device__ constexpr int epi_warps(int mode) { return mode == MODE_PROMOTE ? 8 : 4; }
+// The Ozaki mode keeps a 64-column slice of int32 class sums per thread: 16
+// epilogue warps (four per quarter).
+__host__ __device__ constexpr int epi_warps(int mode) { return mode == MODE_PROMOTE ? 8 : mode == MODE_OZAKI ? 16 : 4; }
 __host__ __device__ constexpr int threads(int mode) { return 64 + 32 * epi_warps(mode); }
 constexpr int A_BYTES = BM * 128;            // 16 KB: 128 rows of one 128-B k-block
 __host__ __device__ constexpr int b_bytes(int mode) { return (bn(mode) / 2) * 128; }  // this CTA's part of B
@@ -120,6 +123,10 @@ struct PairParams {
     int64_t ldd;
     int vec_store;
     int tma_store;  // D written through per-warp staging tiles and TMA stores
+    // Ozaki mode (ozaki_epi.cuh)
+    int slices, beta, lsb, chunk;  // S, bits per digit, accumulator LSB, k-blocks per exact chunk
+    double *D64;
+    const uint64_t *row_max, *col_max;  // |A| row / |B| column maxima as FP64 bit patterns
 };
 
 // Groups of 16 row tiles, column tiles within a group: the A and B panels
@@ -211,11 +218,21 @@ __global__ void __launch_bounds__(threads(MODE), 1)
             pair_tile_of(t, p.tiles_m, p.tiles_n, tm, tn);
             const int row0 = tm * 2 * BM + crank * BM;
             const int col0 = tn * BN + crank * (BN / 2);
+            ozaki::Iter oz;
+            oz.start(p.slices, p.chunk, p.kblocks);
             for (int it = 0; it < kiters; ++it) {
-                const int kb = it / p.n_terms;
-                const int term = it - kb * p.n_terms;
-                const int pa = (int)((p.term_a >> (4 * term)) & 15u);
-                const int pb = (int)((p.term_b >> (4 * term)) & 15u);
+                int kb, pa, pb;
+                if constexpr (MODE == MODE_OZAKI) {  // class, chunk, pair, k-block
+                    kb = oz.kb(p.chunk);
+                    pa = oz.s;
+                    pb = oz.g - oz.s;
+                    oz.next(p.chunk, p.kblocks);
+                } else {  // k-block-major: every term of one k-block
+                    kb = it / p.n_terms;
+                    const int term = it - kb * p.n_terms;
+                    pa = (int)((p.term_a >> (4 * term)) & 15u);
+                    pb = (int)((p.term_b >> (4 * term)) & 15u);
+                }
                 if (!ptx::mbar_wait_warp(empty(stage), phase ^ 1u, abort_flag, &g_pair_status)) {
                     ok = false;
                     break;
@@ -266,11 +283,17 @@ __global__ void __launch_bounds__(threads(MODE), 1)
         // FP8: the stage's scale blocks, rows of 16 B in 8-row groups (no swizzle)
         const ptx::DescHalves s0 = ptx::desc_halves(ptx::smem_desc_plain(tiles0 + sf_off(MODE), 128));
         for (int t = cfirst; t < num_tiles && ok; t += cstride) {
+            ozaki::Iter oz;
+            oz.start(p.slices, p.chunk, p.kblocks);
             for (int it = 0; it < kiters; ++it) {
                 int j, last;  // position inside the current accumulator; whether it is its last step
                 if constexpr (MODE == MODE_STORE || MODE == MODE_FP8) {
                     j = it;
                     last = it == kiters - 1;
+                } else if constexpr (MODE == MODE_OZAKI) {  // one accumulator per (class, chunk, pair)
+                    j = oz.kk;
+                    last = oz.kk == oz.clen - 1;
+                    oz.next(p.chunk, p.kblocks);
                 } else {  // a fresh accumulator per k-block (all its terms)
                     j = it % p.n_terms;
                     last = j == p.n_terms - 1;
@@ -395,7 +418,43 @@ __global__ void __launch_bounds__(threads(MODE), 1)
             const int64_t row = (int64_t)tm * 2 * BM + crank * BM + q * 32 + lane;
             const int64_t colh = (int64_t)tn * BN + half * HC;
             const uint32_t lanes = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * HC);
-            if constexpr (MODE == MODE_PROMOTE) {
+            if constexpr (MODE == MODE_OZAKI) {
+                // every (class, chunk, pair) accumulator of a class added exactly into int32, the class
+                // folded into the double-float running sum kept in D's FP64 slots, FP64 at the end
+                const bool row_ok = row < p.M;
+                double *drow = p.D64 + row * p.ldd;
+                bool first = true;
+                int qacc[HC];
+#pragma unroll
+                for (int j = 0; j < HC; ++j) qacc[j] = 0;
+                const int chunks = (p.kblocks + p.chunk - 1) / p.chunk;
+                for (int cls = p.slices - 1; cls >= 0 && ok; --cls) {
+                    for (int a = 0; a < chunks * (cls + 1); ++a) {
+                        if (!wait_acc()) {
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t tb = lanes + (uint32_t)(abuf * ACC_STRIDE);
+#pragma unroll
+                        for (int c0 = 0; c0 < HC; c0 += 16) {
+                            uint32_t r[16];
+                            ptx::tmem_ld16(tb + c0, r);
+                            ptx::tmem_ld_wait();
+#pragma unroll
+                            for (int j = 0; j < 16; ++j)  // exact: chunk sums are integers below 2^24
+                                qacc[c0 + j] += __float2int_rz(__uint_as_float(r[j]));
+                        }
+                        release_acc();  // the MMA may refill the accumulator during the fold
+                    }
+                    if (!ok) break;
+                    if (row_ok) ozaki::fold<HC>(qacc, ozaki::class_weight(cls, p.lsb, p.beta), drow, colh, p.N, first);
+#pragma unroll
+                    for (int j = 0; j < HC; ++j) qacc[j] = 0;
+                    first = false;
+                }
+                if (!ok) break;
+                if (row_ok) ozaki::finish<HC>(drow, colh, p.N, p.row_max[row], p.col_max, p.lsb);
+            } else if constexpr (MODE == MODE_PROMOTE) {
                 float acc[HC];
 #pragma unroll
                 for (int j = 0; j < HC; ++j) acc[j] = 0.0f;
@@ -558,6 +617,20 @@ cudaError_t tc_gemm_pair_launch(const CUtensorMap &ta, const CUtensorMap &tb, in
     CUtensorMap td;
     p.tma_store = d_tmap(&td, D, ldd, M, N);
     return promote ? launch_pair<MODE_PROMOTE>(ta, tb, td, td, td, p, s) : launch_pair<MODE_STORE>(ta, tb, td, td, td, p, s);
+}
+
+cudaError_t tc_gemm_pair_ozaki_launch(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, int K, int S, int beta,
+                                      int lsb, int chunk_kblocks, const uint64_t *row_max, const uint64_t *col_max,
+                                      double *D, int64_t ldd, cudaStream_t s) {
+    PairParams p{};
+    p.M = M, p.N = N, p.K = K;
+    p.kblocks = (K + bk(MODE_OZAKI) - 1) / bk(MODE_OZAKI);
+    p.n_terms = S * (S + 1) / 2;
+    p.slices = S, p.beta = beta, p.lsb = lsb, p.chunk = chunk_kblocks;
+    p.D64 = D, p.ldd = ldd, p.row_max = row_max, p.col_max = col_max;
+    CUtensorMap none;
+    std::memset(&none, 0, sizeof(none));
+    return launch_pair<MODE_OZAKI>(ta, tb, none, none, none, p, s);
 }
 
 cudaError_t pair_read_and_clear_status(uint32_t *flags) {
