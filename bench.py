@@ -43,10 +43,10 @@ def _peaks():
 
 
 def kernel_source_hash() -> str:
-    """SHA-256 over the sources that make up the tensor-core GEMM kernel."""
+    """SHA-256 over the sources the headline kernel (tc_gemm_pair.cu) is compiled from."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("tc_gemm.cu", "tc_gemm_pair.cu", "tc_ptx.cuh", "common.cuh"):
+    for f in ("tc_gemm_pair.cu", "tc_ptx.cuh", "common.cuh", "ozaki_epi.cuh"):
         with open(os.path.join(ROOT, "paper_0907_0792_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
