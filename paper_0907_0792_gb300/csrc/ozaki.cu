@@ -33,7 +33,7 @@ namespace moa {
 
 moa_status tc_gemm_ozaki(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb, int S, int beta,
                          int lsb, int chunk_kblocks, const uint64_t *row_max, const uint64_t *col_max, double *D,
-                         int64_t ldd, int64_t M, int64_t N, int64_t K, cudaStream_t s);
+                         int64_t ldd, int64_t M, int64_t N, int64_t K, void *scratch, cudaStream_t s);
 
 namespace {
 
@@ -135,7 +135,8 @@ int ozaki_slices(int64_t K) {
 }
 
 size_t ozaki_workspace_bytes(int64_t M, int64_t N, int64_t K) {
-    return (size_t)ozaki_slices(K) * (size_t)(M * round8(K) + K * round8(N)) * 2 + (size_t)(M + N) * 8 + 256;
+    return (size_t)ozaki_slices(K) * (size_t)(M * round8(K) + K * round8(N)) * 2 + (size_t)(M + N) * 8 +
+           pair_ozaki_scratch_bytes() + 256;
 }
 
 moa_status tc_inner_ozaki(const double *A, const double *B, double *D, int64_t M, int64_t N, int64_t K,
@@ -152,6 +153,7 @@ moa_status tc_inner_ozaki(const double *A, const double *B, double *D, int64_t M
     __nv_bfloat16 *b = a + (int64_t)S * M * Kp;
     uint64_t *rmax = (uint64_t *)(((uintptr_t)(b + (int64_t)S * K * Np) + 15) & ~(uintptr_t)15);
     uint64_t *cmax = rmax + M;
+    void *rs = (void *)(((uintptr_t)(cmax + N) + 15) & ~(uintptr_t)15);  // running sums of the pair GEMM
     // scales
     {
         int64_t warps = M < 152 * 32 ? M : 152 * 32;
@@ -174,7 +176,7 @@ moa_status tc_inner_ozaki(const double *A, const double *B, double *D, int64_t M
     }
     // accumulator units 2^-lsb with lsb = (S + 1) beta: every kept pair weight 2^(lsb - (s+u+2) beta) >= 1
     const int lsb = (S + 1) * kBeta;
-    return tc_gemm_ozaki(a, Kp, b, Np, S, kBeta, lsb, kChunkKBlocks, rmax, cmax, D, N, M, N, K, s);
+    return tc_gemm_ozaki(a, Kp, b, Np, S, kBeta, lsb, kChunkKBlocks, rmax, cmax, D, N, M, N, K, rs, s);
 }
 
 }  // namespace moa

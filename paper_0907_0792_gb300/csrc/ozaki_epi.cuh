@@ -55,12 +55,27 @@ MOA_DEV int scale_exponent(uint64_t maxbits) {
 // The power-of-two weight of class g in accumulator units, exact in FP32.
 MOA_DEV float class_weight(int g, int lsb, int beta) { return __int_as_float((127 + lsb - (g + 2) * beta) << 23); }
 
+// (hi, lo) + w * q for an int32 q and a power of two w: q split exactly into
+// two FP32 parts and scaled exactly, TwoSum of hi and the scaled high part,
+// the low parts added into the error, then a FastTwoSum renormalisation:
+// ~48 bits relative to the running sum.
+MOA_DEV float2 add_scaled(float2 hl, int q, float w) {
+    const float xh = __int2float_rn(q);
+    const float xl = __int2float_rn(q - __float2int_rn(xh));  // exact remainder
+    const float ah = __fmul_rn(xh, w), al = __fmul_rn(xl, w);  // exact scaling
+    const float H = hl.x, L = hl.y;
+    const float sum = __fadd_rn(H, ah);  // TwoSum(H, ah)
+    const float bv = __fsub_rn(sum, H);
+    float e = __fadd_rn(__fsub_rn(H, __fsub_rn(sum, bv)), __fsub_rn(ah, bv));
+    e = __fadd_rn(e, __fadd_rn(L, al));
+    const float nh = __fadd_rn(sum, e);  // FastTwoSum renormalisation
+    return make_float2(nh, __fsub_rn(e, __fsub_rn(nh, sum)));
+}
+
 // End of a class: running sum (hi, lo) += w * qacc for this thread's HC
 // columns of one row, the pair kept in the row's FP64 slots (drow[col] holds
 // the FP32 pair until the tile is finished); `first` means no sum stored
-// yet.  16 columns at a time, all loads issued before any store.  TwoSum of
-// hi and the scaled high part, the low parts added into the error, then a
-// FastTwoSum renormalisation: ~48 bits relative to the running sum.
+// yet.  16 columns at a time, all loads issued before any store.
 template <int HC>
 MOA_DEV void fold(const int (&qacc)[HC], float w, double *drow, int64_t colh, int64_t N, bool first) {
 #pragma unroll
@@ -73,17 +88,7 @@ MOA_DEV void fold(const int (&qacc)[HC], float w, double *drow, int64_t colh, in
         }
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-            const int qv = qacc[c0 + j];
-            const float xh = __int2float_rn(qv);
-            const float xl = __int2float_rn(qv - __float2int_rn(xh));  // exact remainder
-            const float ah = __fmul_rn(xh, w), al = __fmul_rn(xl, w);  // exact scaling
-            const float H = old[j].x, L = old[j].y;
-            const float sum = __fadd_rn(H, ah);  // TwoSum(H, ah)
-            const float bv = __fsub_rn(sum, H);
-            float e = __fadd_rn(__fsub_rn(H, __fsub_rn(sum, bv)), __fsub_rn(ah, bv));
-            e = __fadd_rn(e, __fadd_rn(L, al));
-            const float nh = __fadd_rn(sum, e);  // FastTwoSum renormalisation
-            old[j] = make_float2(nh, __fsub_rn(e, __fsub_rn(nh, sum)));
+            old[j] = add_scaled(old[j], qacc[c0 + j], w);
         }
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
@@ -102,6 +107,39 @@ MOA_DEV void finish(double *drow, int64_t colh, int64_t N, uint64_t row_maxbits,
         const int64_t col = colh + j;
         if (col >= N) break;
         const float2 v = *reinterpret_cast<const float2 *>(drow + col);
+        const int ec = scale_exponent(col_max[col]);
+        drow[col] = ldexp((double)v.x + (double)v.y, er + ec - lsb);
+    }
+}
+
+// The same two steps with the running sums in a per-thread scratch strip
+// instead of D's slots: element j of the thread at rs[32 j] (the 32 lanes of
+// a warp interleaved), so every warp access is 256 contiguous bytes.
+template <int HC>
+MOA_DEV void fold_rs(const int (&qacc)[HC], float w, float2 *rs, bool first) {
+#pragma unroll
+    for (int c0 = 0; c0 < HC; c0 += 16) {
+        float2 old[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) old[j] = first ? make_float2(0.0f, 0.0f) : rs[32 * (c0 + j)];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            old[j] = add_scaled(old[j], qacc[c0 + j], w);
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) rs[32 * (c0 + j)] = old[j];
+    }
+}
+
+template <int HC>
+MOA_DEV void finish_rs(const float2 *rs, double *drow, int64_t colh, int64_t N, uint64_t row_maxbits,
+                       const uint64_t *col_max, int lsb) {
+    const int er = scale_exponent(row_maxbits);
+#pragma unroll 4
+    for (int j = 0; j < HC; ++j) {
+        const int64_t col = colh + j;
+        if (col >= N) break;
+        const float2 v = rs[32 * j];
         const int ec = scale_exponent(col_max[col]);
         drow[col] = ldexp((double)v.x + (double)v.y, er + ec - lsb);
     }

@@ -59,9 +59,12 @@ cudaError_t tc_gemm_pair_fp8_launch(const uint8_t *A8, int64_t lda, const uint8_
                                     cudaStream_t stream);
 // Ozaki slice-pair pair GEMM (same tensor maps and arguments as the
 // single-CTA tc_gemm_ozaki; 256 x 256 tiles on CTA pairs).
+// `scratch`: pair_ozaki_scratch_bytes() of device memory for the running
+// sums (16-byte aligned).
+size_t pair_ozaki_scratch_bytes();
 cudaError_t tc_gemm_pair_ozaki_launch(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, int K, int S, int beta,
                                       int lsb, int chunk_kblocks, const uint64_t *row_max, const uint64_t *col_max,
-                                      double *D, int64_t ldd, cudaStream_t stream);
+                                      double *D, int64_t ldd, void *scratch, cudaStream_t stream);
 cudaError_t pair_read_and_clear_status(uint32_t *flags);
 // Launch the bounded-wait self-test (a wait that can only time out).
 cudaError_t tc_wait_probe(uint64_t limit_ns, cudaStream_t stream);

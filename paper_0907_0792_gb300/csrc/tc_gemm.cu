@@ -663,7 +663,7 @@ moa_status tc_gemm_fp8(const uint8_t *A, int64_t lda, const uint8_t *B, int64_t 
 // every pair weight 2^(lsb - (s + u + 2) beta) is within FP32's range.
 moa_status tc_gemm_ozaki(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb, int S, int beta,
                          int lsb, int chunk_kblocks, const uint64_t *row_max, const uint64_t *col_max, double *D,
-                         int64_t ldd, int64_t M, int64_t N, int64_t K, cudaStream_t s) {
+                         int64_t ldd, int64_t M, int64_t N, int64_t K, void *scratch, cudaStream_t s) {
     if (M >= (1ll << 31) || N >= (1ll << 31) || K >= (1ll << 31)) return MOA_ERR_OVERFLOW;
     // weights 2^(lsb - (g+2) beta) must be exact FP32 powers of two >= 1, and a
     // class sum (g+1 <= S pairs of K * (2^beta-1)^2) must stay below 2^31
@@ -682,9 +682,9 @@ moa_status tc_gemm_ozaki(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat1
     p.n_terms = S * (S + 1) / 2;
     p.slices = S, p.beta = beta, p.lsb = lsb, p.chunk = chunk_kblocks;
     p.D64 = D, p.ldd = ldd, p.row_max = row_max, p.col_max = col_max;
-    if (M > BM && N > 128 && pair_mma_enabled()) {  // 256 x 256 tiles on CTA pairs
+    if (M > BM && N > 128 && pair_mma_enabled() && scratch) {  // 256 x 256 tiles on CTA pairs
         const cudaError_t e = tc_gemm_pair_ozaki_launch(ta, tb, p.M, p.N, p.K, S, beta, lsb, chunk_kblocks, row_max, col_max,
-                                                        D, ldd, s);
+                                                        D, ldd, scratch, s);
         return e == cudaSuccess ? MOA_OK : MOA_ERR_CUDA;
     }
     // 192-wide tiles: two accumulators fit TMEM and the int32 class sums of a

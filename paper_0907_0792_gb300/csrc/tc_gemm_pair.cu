@@ -127,6 +127,7 @@ struct PairParams {
     int slices, beta, lsb, chunk;  // S, bits per digit, accumulator LSB, k-blocks per exact chunk
     double *D64;
     const uint64_t *row_max, *col_max;  // |A| row / |B| column maxima as FP64 bit patterns
+    float2 *rs;  // running-sum scratch: per CTA, per epilogue warp, 64 columns x 32 lanes
 };
 
 // Groups of 16 row tiles, column tiles within a group: the A and B panels
@@ -423,6 +424,7 @@ __global__ void __launch_bounds__(threads(MODE), 1)
                 // folded into the double-float running sum kept in D's FP64 slots, FP64 at the end
                 const bool row_ok = row < p.M;
                 double *drow = p.D64 + row * p.ldd;
+                float2 *rs = p.rs + ((int64_t)blockIdx.x * epi_warps(MODE) + (warp - 2)) * (HC * 32) + lane;
                 bool first = true;
                 int qacc[HC];
 #pragma unroll
@@ -447,13 +449,13 @@ __global__ void __launch_bounds__(threads(MODE), 1)
                         release_acc();  // the MMA may refill the accumulator during the fold
                     }
                     if (!ok) break;
-                    if (row_ok) ozaki::fold<HC>(qacc, ozaki::class_weight(cls, p.lsb, p.beta), drow, colh, p.N, first);
+                    ozaki::fold_rs<HC>(qacc, ozaki::class_weight(cls, p.lsb, p.beta), rs, first);
 #pragma unroll
                     for (int j = 0; j < HC; ++j) qacc[j] = 0;
                     first = false;
                 }
                 if (!ok) break;
-                if (row_ok) ozaki::finish<HC>(drow, colh, p.N, p.row_max[row], p.col_max, p.lsb);
+                if (row_ok) ozaki::finish_rs<HC>(rs, drow, colh, p.N, p.row_max[row], p.col_max, p.lsb);
             } else if constexpr (MODE == MODE_PROMOTE) {
                 float acc[HC];
 #pragma unroll
@@ -621,8 +623,9 @@ cudaError_t tc_gemm_pair_launch(const CUtensorMap &ta, const CUtensorMap &tb, in
 
 cudaError_t tc_gemm_pair_ozaki_launch(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, int K, int S, int beta,
                                       int lsb, int chunk_kblocks, const uint64_t *row_max, const uint64_t *col_max,
-                                      double *D, int64_t ldd, cudaStream_t s) {
+                                      double *D, int64_t ldd, void *scratch, cudaStream_t s) {
     PairParams p{};
+    p.rs = (float2 *)scratch;
     p.M = M, p.N = N, p.K = K;
     p.kblocks = (K + bk(MODE_OZAKI) - 1) / bk(MODE_OZAKI);
     p.n_terms = S * (S + 1) / 2;
@@ -631,6 +634,10 @@ cudaError_t tc_gemm_pair_ozaki_launch(const CUtensorMap &ta, const CUtensorMap &
     CUtensorMap none;
     std::memset(&none, 0, sizeof(none));
     return launch_pair<MODE_OZAKI>(ta, tb, none, none, none, p, s);
+}
+
+size_t pair_ozaki_scratch_bytes() {  // one 128 x 256 strip of (hi, lo) pairs per CTA
+    return (size_t)pair_sms() * BM * bn(MODE_OZAKI) * sizeof(float2);
 }
 
 cudaError_t pair_read_and_clear_status(uint32_t *flags) {
