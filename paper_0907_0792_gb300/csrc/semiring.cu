@@ -113,9 +113,16 @@ __global__ void __launch_bounds__(Tile<BM, BN, BK, TM, TN>::NT, 2)  // two CTAs 
                     b1[j] = bs[(kk + 1) * (BN + TL::PAD) + c];
                 }
 #pragma unroll
-                for (int i = 0; i < TM; ++i)
+                for (int i = 0; i < TM; ++i) {
+                    if constexpr (Op::kPacked) {  // two adjacent columns per packed FP32 instruction
 #pragma unroll
-                    for (int j = 0; j < TN; ++j) acc[i][j] = Op::step2(acc[i][j], a0[i], b0[j], a1[i], b1[j]);
+                        for (int j = 0; j < TN; j += 2)
+                            Op::step2x2(acc[i][j], acc[i][j + 1], a0[i], b0[j], b0[j + 1], a1[i], b1[j], b1[j + 1]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < TN; ++j) acc[i][j] = Op::step2(acc[i][j], a0[i], b0[j], a1[i], b1[j]);
+                    }
+                }
             }
         } else {
             for (int kk = 0; kk < tail; ++kk) {  // contraction tail: shortened loop, no padding values

@@ -10,6 +10,29 @@
 namespace moa {
 namespace sr {
 
+// Packed FP32 pairs (sm_100+ add / mul / fma .rn.f32x2): two IEEE
+// round-to-nearest operations per instruction, lane by lane, so results are
+// identical to the scalar forms.  (x, x) + (y0, y1) and (x, x) * (y0, y1):
+MOA_DEV void add2(float x, float y0, float y1, float &r0, float &r1) {
+    asm("{\n\t.reg .b64 pa, pb;\n\tmov.b64 pa, {%2, %2};\n\tmov.b64 pb, {%3, %4};\n\t"
+        "add.rn.f32x2 pa, pa, pb;\n\tmov.b64 {%0, %1}, pa;\n\t}"
+        : "=f"(r0), "=f"(r1)
+        : "f"(x), "f"(y0), "f"(y1));
+}
+MOA_DEV void mul2(float x, float y0, float y1, float &r0, float &r1) {
+    asm("{\n\t.reg .b64 pa, pb;\n\tmov.b64 pa, {%2, %2};\n\tmov.b64 pb, {%3, %4};\n\t"
+        "mul.rn.f32x2 pa, pa, pb;\n\tmov.b64 {%0, %1}, pa;\n\t}"
+        : "=f"(r0), "=f"(r1)
+        : "f"(x), "f"(y0), "f"(y1));
+}
+// (c0, c1) = fma((x, x), (y0, y1), (c0, c1))
+MOA_DEV void fma2(float x, float y0, float y1, float &c0, float &c1) {
+    asm("{\n\t.reg .b64 pa, pb, pc;\n\tmov.b64 pa, {%2, %2};\n\tmov.b64 pb, {%3, %4};\n\t"
+        "mov.b64 pc, {%0, %1};\n\tfma.rn.f32x2 pc, pa, pb, pc;\n\tmov.b64 {%0, %1}, pc;\n\t}"
+        : "+f"(c0), "+f"(c1)
+        : "f"(x), "f"(y0), "f"(y1));
+}
+
 struct F32PlusTimes {
     using T = float;
     static MOA_DEV float identity() { return 0.0f; }
@@ -17,9 +40,16 @@ struct F32PlusTimes {
     static MOA_DEV float step2(float acc, float a0, float b0, float a1, float b1) {
         return fmaf(a1, b1, fmaf(a0, b0, acc));
     }
+    // two adjacent columns (c0: b*0, c1: b*1), two contraction steps
+    static constexpr bool kPacked = true;
+    static MOA_DEV void step2x2(float &c0, float &c1, float a0, float b00, float b01, float a1, float b10, float b11) {
+        fma2(a0, b00, b01, c0, c1);
+        fma2(a1, b10, b11, c0, c1);
+    }
 };
 struct F64PlusTimes {
     using T = double;
+    static constexpr bool kPacked = false;
     static MOA_DEV double identity() { return 0.0; }
     static MOA_DEV double step(double acc, double a, double b) { return fma(a, b, acc); }
     static MOA_DEV double step2(double acc, double a0, double b0, double a1, double b1) {
@@ -28,6 +58,7 @@ struct F64PlusTimes {
 };
 struct I32PlusTimes {
     using T = int32_t;
+    static constexpr bool kPacked = false;
     static MOA_DEV int32_t identity() { return 0; }
     static MOA_DEV int32_t step(int32_t acc, int32_t a, int32_t b) {
         return (int32_t)((uint32_t)acc + (uint32_t)a * (uint32_t)b);
@@ -43,6 +74,14 @@ struct F32MinPlus {
     static MOA_DEV float step2(float acc, float a0, float b0, float a1, float b1) {
         return fmin3(acc, __fadd_rn(a0, b0), __fadd_rn(a1, b1));
     }
+    static constexpr bool kPacked = true;
+    static MOA_DEV void step2x2(float &c0, float &c1, float a0, float b00, float b01, float a1, float b10, float b11) {
+        float s00, s01, s10, s11;
+        add2(a0, b00, b01, s00, s01);
+        add2(a1, b10, b11, s10, s11);
+        c0 = fmin3(c0, s00, s10);
+        c1 = fmin3(c1, s01, s11);
+    }
 };
 struct F32MaxPlus {
     using T = float;
@@ -50,6 +89,14 @@ struct F32MaxPlus {
     static MOA_DEV float step(float acc, float a, float b) { return fmaxf(acc, __fadd_rn(a, b)); }
     static MOA_DEV float step2(float acc, float a0, float b0, float a1, float b1) {
         return fmax3(acc, __fadd_rn(a0, b0), __fadd_rn(a1, b1));
+    }
+    static constexpr bool kPacked = true;
+    static MOA_DEV void step2x2(float &c0, float &c1, float a0, float b00, float b01, float a1, float b10, float b11) {
+        float s00, s01, s10, s11;
+        add2(a0, b00, b01, s00, s01);
+        add2(a1, b10, b11, s10, s11);
+        c0 = fmax3(c0, s00, s10);
+        c1 = fmax3(c1, s01, s11);
     }
 };
 struct F32MinTimes {
@@ -59,6 +106,14 @@ struct F32MinTimes {
     static MOA_DEV float step2(float acc, float a0, float b0, float a1, float b1) {
         return fmin3(acc, __fmul_rn(a0, b0), __fmul_rn(a1, b1));
     }
+    static constexpr bool kPacked = true;
+    static MOA_DEV void step2x2(float &c0, float &c1, float a0, float b00, float b01, float a1, float b10, float b11) {
+        float s00, s01, s10, s11;
+        mul2(a0, b00, b01, s00, s01);
+        mul2(a1, b10, b11, s10, s11);
+        c0 = fmin3(c0, s00, s10);
+        c1 = fmin3(c1, s01, s11);
+    }
 };
 struct F32MaxTimes {
     using T = float;
@@ -66,6 +121,14 @@ struct F32MaxTimes {
     static MOA_DEV float step(float acc, float a, float b) { return fmaxf(acc, __fmul_rn(a, b)); }
     static MOA_DEV float step2(float acc, float a0, float b0, float a1, float b1) {
         return fmax3(acc, __fmul_rn(a0, b0), __fmul_rn(a1, b1));
+    }
+    static constexpr bool kPacked = true;
+    static MOA_DEV void step2x2(float &c0, float &c1, float a0, float b00, float b01, float a1, float b10, float b11) {
+        float s00, s01, s10, s11;
+        mul2(a0, b00, b01, s00, s01);
+        mul2(a1, b10, b11, s10, s11);
+        c0 = fmax3(c0, s00, s10);
+        c1 = fmax3(c1, s01, s11);
     }
 };
 
