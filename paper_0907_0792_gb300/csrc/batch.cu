@@ -161,9 +161,16 @@ __device__ __noinline__ void cc_tile_q(const BInst &in, int tm, int tn, float *A
                     b0[j] = bs[kk * CC_LD + c], b1[j] = bs[(kk + 1) * CC_LD + c];
                 }
 #pragma unroll
-                for (int i = 0; i < (RH ? 8 : 4); ++i)
+                for (int i = 0; i < (RH ? 8 : 4); ++i) {
+                    if constexpr (Op::kPacked) {  // two adjacent columns per packed FP32 instruction
 #pragma unroll
-                    for (int j = 0; j < (CH ? 8 : 4); ++j) acc[i][j] = Op::step2(acc[i][j], a0[i], b0[j], a1[i], b1[j]);
+                        for (int j = 0; j < (CH ? 8 : 4); j += 2)
+                            Op::step2x2(acc[i][j], acc[i][j + 1], a0[i], b0[j], b0[j + 1], a1[i], b1[j], b1[j + 1]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < (CH ? 8 : 4); ++j) acc[i][j] = Op::step2(acc[i][j], a0[i], b0[j], a1[i], b1[j]);
+                    }
+                }
             }
         } else {
             for (int kk = 0; kk < tail; ++kk) {
