@@ -412,6 +412,14 @@ def cpu_oracle_sample(seconds: float = 12.0, threads: int | None = None):
                       f"({2.0 * R * n * n / 1e9:.1f} GFLOP in {dt:.2f} s)"}
 
 
+def headline_config(ws: int) -> dict:
+    """The workload both arms report (the reference arm samples its rows)."""
+    n = N_HEAD
+    return {"workload": "square (+,*) inner product n=8192, bf16 operands, FP32 accumulate/out",
+            "M": n, "K": n, "N": n, "seed": 2, "values": "U(-1,1) rounded to bf16",
+            "l2": "inputs 2 x 128 MiB > L2, no flush", "parallelism": f"replicas x{ws}"}
+
+
 def run_reference(args, rank, ws):
     if rank != 0:
         return
@@ -423,7 +431,7 @@ def run_reference(args, rank, ws):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "square (+,*) inner product n=8192, rows sampled"},
+            "config": headline_config(ws),
             "cpu_baseline": {"kind": "oracle", "cores": samples[0]["cores"], "sample": samples[0]["sample"], "value": v},
             "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -609,9 +617,7 @@ def main():
         line = {"metric": METRIC, "value": round(value, 2), "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-                "config": {"workload": "square (+,*) inner product n=8192, bf16 operands, FP32 accumulate/out",
-                           "M": n, "K": n, "N": n, "seed": 2, "values": "U(-1,1) rounded to bf16",
-                           "l2": "inputs 2 x 128 MiB > L2, no flush", "parallelism": f"replicas x{ws}"},
+                "config": headline_config(ws),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
                 "clocks": clk.summary(), "device_status": "ok", "rows": rows}
         print(json.dumps(line))
