@@ -197,6 +197,11 @@ static moa_status inner_run(moa_op reduce, moa_op combine, moa_dtype dtype, moa_
 
     if (reduce == MOA_OP_OR) {
         moa_status st;
+        if (or_and_tc_applies(M, N, K)) {  // tensor cores, exact counting
+            void *ws = workspace_get(s, or_and_tc_workspace_bytes(M, N, K), &st);
+            if (st != MOA_OK) return st;
+            return from_cuda(launch_or_and_tc((const uint32_t *)A, (const uint32_t *)B, (uint32_t *)out, M, N, K, ws, s));
+        }
         void *ws = workspace_get(s, bits_workspace_bytes(M, N, K), &st);
         if (st != MOA_OK) return st;
         return from_cuda(launch_or_and((const uint32_t *)A, (const uint32_t *)B, (uint32_t *)out, M, N, K, ws, s));

@@ -51,6 +51,13 @@ size_t bits_workspace_bytes(int64_t M, int64_t N, int64_t K);
 cudaError_t launch_or_and(const uint32_t *A, const uint32_t *B, uint32_t *D, int64_t M, int64_t N, int64_t K,
                           void *ws, cudaStream_t stream);
 
+// bits_tc.cu — (or, and) by exact counting on the FP8 pair-MMA kernel, for
+// results with more than 128 rows and a multiple of 32 (> 128) columns.
+bool or_and_tc_applies(int64_t M, int64_t N, int64_t K);
+size_t or_and_tc_workspace_bytes(int64_t M, int64_t N, int64_t K);
+cudaError_t launch_or_and_tc(const uint32_t *A, const uint32_t *B, uint32_t *D, int64_t M, int64_t N, int64_t K,
+                             void *ws, cudaStream_t stream);
+
 // batch.cu — read and clear the grouped kernel's status word (bounded waits).
 cudaError_t batch_read_and_clear_status(uint32_t *flags);
 

@@ -54,9 +54,11 @@ cudaError_t tc_gemm_pair_launch(const CUtensorMap &ta, const CUtensorMap &tb, in
 //   sfb [ceil(N/T)][kb][256] with T = pair_fp8_tile_n(): word 128 h + 4 l + c
 //   = column T tn + 32 (4 h + c) + l (columns at or past T or N: any value).
 int pair_fp8_tile_n();
+// With `bits_out` (N a multiple of 32) the result is written as the packed
+// bit stream of [D > 0] instead of D (the exact-count (or, and) form).
 cudaError_t tc_gemm_pair_fp8_launch(const uint8_t *A8, int64_t lda, const uint8_t *Bt8, int64_t ldb, int M, int N,
                                     int K, const uint32_t *sfa, const uint32_t *sfb, float *D, int64_t ldd,
-                                    cudaStream_t stream);
+                                    cudaStream_t stream, uint32_t *bits_out = nullptr);
 // Ozaki slice-pair pair GEMM (same tensor maps and arguments as the
 // single-CTA tc_gemm_ozaki; 256 x 256 tiles on CTA pairs).
 // `scratch`: pair_ozaki_scratch_bytes() of device memory for the running

@@ -123,6 +123,7 @@ struct PairParams {
     int64_t ldd;
     int vec_store;
     int tma_store;  // D written through per-warp staging tiles and TMA stores
+    uint32_t *bits_out;  // store mode: write [D > 0] as the packed bit stream (N % 32 == 0) instead of D
     // Ozaki mode (ozaki_epi.cuh)
     int slices, beta, lsb, chunk;  // S, bits per digit, accumulator LSB, k-blocks per exact chunk
     double *D64;
@@ -492,7 +493,15 @@ __global__ void __launch_bounds__(threads(MODE), 1)
                     uint32_t r[32];
                     ptx::tmem_ld32(tb + c, r);
                     ptx::tmem_ld_wait();
-                    store32(row, colh + c, r);
+                    if (p.bits_out) {  // 32 columns of one row -> one word of the bit stream
+                        const int64_t col0 = colh + c;
+                        uint32_t word = 0u;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) word |= (__uint_as_float(r[j]) > 0.0f ? 1u : 0u) << j;
+                        if (row < p.M && col0 < p.N) p.bits_out[(row * p.N + col0) >> 5] = word;
+                    } else {
+                        store32(row, colh + c, r);
+                    }
                 }
                 release_acc();
             }
@@ -582,7 +591,8 @@ static bool d_tmap(CUtensorMap *td, float *D, int64_t ldd, int M, int N) {
 int pair_fp8_tile_n() { return bn(MODE_FP8); }
 
 cudaError_t tc_gemm_pair_fp8_launch(const uint8_t *A8, int64_t lda, const uint8_t *Bt8, int64_t ldb, int M, int N, int K,
-                                    const uint32_t *sfa, const uint32_t *sfb, float *D, int64_t ldd, cudaStream_t s) {
+                                    const uint32_t *sfa, const uint32_t *sfb, float *D, int64_t ldd, cudaStream_t s,
+                                    uint32_t *bits_out) {
     const int64_t kb = (K + bk(MODE_FP8) - 1) / bk(MODE_FP8);
     const int64_t mb = (M + BM - 1) / BM, tn = (N + bn(MODE_FP8) - 1) / bn(MODE_FP8);
     CUtensorMap ta, tb, tsa, tsb;
@@ -603,7 +613,9 @@ cudaError_t tc_gemm_pair_fp8_launch(const uint8_t *A8, int64_t lda, const uint8_
     p.D = D, p.ldd = ldd;
     p.vec_store = ((uintptr_t)D % 16 == 0) && (ldd % 4 == 0);
     CUtensorMap td;
-    p.tma_store = d_tmap(&td, D, ldd, M, N);
+    std::memset(&td, 0, sizeof(td));
+    p.bits_out = bits_out;
+    p.tma_store = bits_out ? 0 : d_tmap(&td, D, ldd, M, N);
     return launch_pair<MODE_FP8>(ta, tb, td, tsa, tsb, p, s);
 }
 

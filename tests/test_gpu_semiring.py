@@ -93,6 +93,19 @@ def test_bool_small(shA, shB):
     check_status()
 
 
+@pytest.mark.parametrize("shA,shB,dens", [((300, 100), (100, 320), 0.05), ((129, 16), (16, 160), 0.5),
+                                          ((257, 1000), (1000, 256), 0.002), ((4, 130, 77), (77, 8, 32), 0.05),
+                                          ((300, 48), (48, 448), 0.0)])
+def test_bool_tensor_core_path(shA, shB, dens):
+    """(or, and) by exact counting on the tensor cores (results with more
+    than 128 rows and a multiple of 32 columns): bit-exact, at densities from
+    none to half, K not a multiple of 32 or of 128."""
+    A = synth.bernoulli(19, 0, shA, dens)
+    B = synth.bernoulli(19, 1, shB, dens)
+    assert np.array_equal(_bool(A, B), oracle.inner_bool(A, B))
+    check_status()
+
+
 def test_bool_full_size_sampled():
     A, B = synth.semiring_inputs("bool")
     D = _bool(A, B)
