@@ -233,8 +233,9 @@ def _row_semiring(moa, torch, kind, reduce, combine, reps, stream, flush):
         flush()
         times.append(_events_time(call, 1, stream))
     ms = statistics.median(times)
+    path = {"bool": "tensor cores, e4m3 exact count", "int32": "tensor cores, bf16 exact (int8-range values)"}
     return {"semiring": f"({reduce},{combine})", "dtype": dt, "shape": "<32,128,512>x<512,64,64>", "ms": round(ms, 4),
-            "gops": round(M * N * K / (ms * 1e-3) / 1e9, 1)}
+            "gops": round(M * N * K / (ms * 1e-3) / 1e9, 1), "path": path.get(kind, "CUDA cores")}
 
 
 def _row_outer(moa, torch, op, dt, reps, stream, peaks):

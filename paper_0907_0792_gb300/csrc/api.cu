@@ -213,7 +213,14 @@ static moa_status inner_run(moa_op reduce, moa_op combine, moa_dtype dtype, moa_
     }
     // (add, mul)
     switch (dtype) {
-    case MOA_I32: return from_cuda(launch_semiring(SR_I32_PLUS_TIMES, A, B, out, M, N, K, s));
+    case MOA_I32:
+        if (i32_tc_applies(M, N, K)) {  // tensor cores when the values are int8-range, checked on the device
+            moa_status st;
+            void *ws = workspace_get(s, i32_tc_workspace_bytes(M, N, K), &st);
+            if (st != MOA_OK) return st;
+            return tc_inner_i32((const int32_t *)A, (const int32_t *)B, (int32_t *)out, M, N, K, ws, s);
+        }
+        return from_cuda(launch_semiring(SR_I32_PLUS_TIMES, A, B, out, M, N, K, s));
     case MOA_F64:
         if (form == MOA_FORM_OZAKI) return tc_inner_ozaki((const double *)A, (const double *)B, (double *)out, M, N, K, s);
         if (skinny_applies(M, N, K)) return from_cuda(launch_skinny(true, A, B, out, M, N, K, s));

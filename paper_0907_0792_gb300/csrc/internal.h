@@ -34,8 +34,10 @@ enum SemiringKind {
     SR_F32_MAX_TIMES = 5,
     SR_I32_PLUS_TIMES = 6,
 };
+// With `run_if`, every CTA returns at once unless *run_if is non-zero (a
+// flag an earlier kernel on the stream sets).
 cudaError_t launch_semiring(SemiringKind kind, const void *A, const void *B, void *D, int64_t M, int64_t N, int64_t K,
-                            cudaStream_t stream);
+                            cudaStream_t stream, const uint32_t *run_if = nullptr);
 
 // skinny.cu — (add, mul) with a result of at most kSkinnyMaxM rows, FP64 or
 // FP32: a stream over B (the shape of the method's own measurement).

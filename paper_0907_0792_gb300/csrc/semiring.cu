@@ -38,7 +38,8 @@ template <int BM, int BN, int BK, int TM, int TN> struct Tile {
 template <class Op, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__(Tile<BM, BN, BK, TM, TN>::NT, 2)  // two CTAs (16 warps) per SM
     semiring_gemm(const typename Op::T *__restrict__ A, const typename Op::T *__restrict__ B,
-                  typename Op::T *__restrict__ D, int64_t M, int64_t N, int64_t K) {
+                  typename Op::T *__restrict__ D, int64_t M, int64_t N, int64_t K, const uint32_t *run_if) {
+    if (run_if && __ldg(run_if) == 0u) return;  // uniform over the grid
     using T = typename Op::T;
     using TL = Tile<BM, BN, BK, TM, TN>;
     constexpr int NT = TL::NT;
@@ -156,26 +157,27 @@ __global__ void __launch_bounds__(Tile<BM, BN, BK, TM, TN>::NT, 2)  // two CTAs 
 }
 
 template <class Op, int BM, int BN, int BK, int TM, int TN>
-cudaError_t run(const void *A, const void *B, void *D, int64_t M, int64_t N, int64_t K, cudaStream_t s) {
+cudaError_t run(const void *A, const void *B, void *D, int64_t M, int64_t N, int64_t K, cudaStream_t s,
+              const uint32_t *run_if) {
     const int64_t gx = (N + BN - 1) / BN, gy = (M + BM - 1) / BM;
     if (gy > 65535 || gx > 0x7fffffff) return cudaErrorInvalidConfiguration;
     semiring_gemm<Op, BM, BN, BK, TM, TN><<<dim3((unsigned)gx, (unsigned)gy), Tile<BM, BN, BK, TM, TN>::NT, 0, s>>>(
-        (const typename Op::T *)A, (const typename Op::T *)B, (typename Op::T *)D, M, N, K);
+        (const typename Op::T *)A, (const typename Op::T *)B, (typename Op::T *)D, M, N, K, run_if);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_semiring(SemiringKind kind, const void *A, const void *B, void *D, int64_t M, int64_t N, int64_t K,
-                            cudaStream_t s) {
+                            cudaStream_t s, const uint32_t *run_if) {
     switch (kind) {
-    case SR_F64_PLUS_TIMES: return run<sr::F64PlusTimes, 64, 64, 8, 4, 4>(A, B, D, M, N, K, s);
-    case SR_F32_PLUS_TIMES: return run<sr::F32PlusTimes, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s);
-    case SR_F32_MIN_PLUS: return run<sr::F32MinPlus, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s);
-    case SR_F32_MAX_PLUS: return run<sr::F32MaxPlus, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s);
-    case SR_F32_MIN_TIMES: return run<sr::F32MinTimes, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s);
-    case SR_F32_MAX_TIMES: return run<sr::F32MaxTimes, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s);
-    case SR_I32_PLUS_TIMES: return run<sr::I32PlusTimes, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s);
+    case SR_F64_PLUS_TIMES: return run<sr::F64PlusTimes, 64, 64, 8, 4, 4>(A, B, D, M, N, K, s, run_if);
+    case SR_F32_PLUS_TIMES: return run<sr::F32PlusTimes, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s, run_if);
+    case SR_F32_MIN_PLUS: return run<sr::F32MinPlus, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s, run_if);
+    case SR_F32_MAX_PLUS: return run<sr::F32MaxPlus, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s, run_if);
+    case SR_F32_MIN_TIMES: return run<sr::F32MinTimes, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s, run_if);
+    case SR_F32_MAX_TIMES: return run<sr::F32MaxTimes, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s, run_if);
+    case SR_I32_PLUS_TIMES: return run<sr::I32PlusTimes, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s, run_if);
     }
     return cudaErrorInvalidValue;
 }

@@ -33,6 +33,12 @@ moa_status tc_inner_fp8(const float *A, const float *B, float *D, int64_t M, int
 // FP64 operands, FP64 out, Ozaki-sliced on bf16 tensor cores.
 moa_status tc_inner_ozaki(const double *A, const double *B, double *D, int64_t M, int64_t N, int64_t K,
                           cudaStream_t stream);
+// int32 operands, int32 out, on bf16 tensor cores when every operand value
+// lies in [-128, 127] (else on CUDA cores): see tc_forms.cu.
+bool i32_tc_applies(int64_t M, int64_t N, int64_t K);
+size_t i32_tc_workspace_bytes(int64_t M, int64_t N, int64_t K);
+moa_status tc_inner_i32(const int32_t *A, const int32_t *B, int32_t *D, int64_t M, int64_t N, int64_t K, void *ws,
+                        cudaStream_t stream);
 // Split-BF16x3 with caller-provided scratch of tc_bf16x3_scratch_bytes()
 // bytes (16-byte aligned); allocates nothing.
 size_t tc_bf16x3_scratch_bytes(int64_t M, int64_t N, int64_t K);
@@ -40,12 +46,13 @@ moa_status tc_inner_bf16x3_scratch(const float *A, const float *B, float *D, int
                                    void *scratch, cudaStream_t stream);
 // Pair-MMA GEMM (tc_gemm_pair.cu): 256 x 256 tiles on CTA pairs, the same
 // tensor maps and term encoding as the single-CTA kernel (A boxes 64 x 128,
-// B boxes 64 x 64); promote = FP32 register accumulation per k-block.
-// MOA_PAIR_MMA=0 turns the pair path off.
+// B boxes 64 x 64); promote = FP32 register accumulation per k-block;
+// i32_out = D is int32, each accumulator rounded to the nearest integer
+// (store mode only).  MOA_PAIR_MMA=0 turns the pair path off.
 bool pair_mma_enabled();
 cudaError_t tc_gemm_pair_launch(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, int K, int n_terms,
                                 uint32_t term_a, uint32_t term_b, float *D, int64_t ldd, bool promote,
-                                cudaStream_t stream);
+                                cudaStream_t stream, bool i32_out = false);
 // FP8 (e4m3) pair GEMM with block-scaled MMAs: A8 [M][lda] and B
 // transposed, Bt8 [N][ldb] (both K-major, lda and ldb multiples of 16,
 // 16-byte aligned).  Scale factors as UE8M0 bytes, each repeated in the four

@@ -7,10 +7,17 @@
 //       the previous ones left), then accumulate the six cross products of
 //       total order <= 2 (hh, hm, mh, hl, lh, mm) in one FP32 accumulator
 //       (Henry, Tang & Heinecke, "Leveraging the bfloat16 AI datatype for
-//       higher-precision computations", ARITH 2019).
+//       higher-precision computations", ARITH 2019);
+//   int32 operands (the integer (add, mul) of Sec. I) -> when every value
+//       lies in [-128, 127], each is a bf16 exactly, every product and partial
+//       sum is an integer of magnitude <= 2^14 K <= 2^24 for K <= 1024, so the
+//       FP32 accumulation is exact in any order and the result equals the
+//       int32 definition bit for bit (no sum reaches the wrap-around).
 // The pre-pass is memory bound: one read of the FP32 operand, one write of
 // each bf16 plane, rows padded to a multiple of 8 elements (16 bytes) so the
 // planes meet the TMA stride rule.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 #include "tc.h"
@@ -19,7 +26,7 @@ namespace moa {
 
 moa_status tc_gemm_planes(const __nv_bfloat16 *A, int64_t lda, int planesA, const __nv_bfloat16 *B, int64_t ldb,
                           int planesB, int n_terms, const int *term_a, const int *term_b, float *D, int64_t ldd,
-                          int64_t M, int64_t N, int64_t K, bool promote, cudaStream_t s);
+                          int64_t M, int64_t N, int64_t K, bool promote, cudaStream_t s, bool i32_out = false);
 
 namespace {
 
@@ -49,6 +56,50 @@ __global__ void __launch_bounds__(256) split_planes(const Tin *__restrict__ X, i
 }
 
 int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
+
+// int32 X (rows x cols) -> bf16 rows x colsp, zero columns past cols; sets
+// *out_of_range when a value lies outside [-128, 127].  V consecutive
+// columns per thread (V = 4 needs cols % 4 == 0 and a 16-byte aligned X).
+template <int V>
+__global__ void __launch_bounds__(256) i8range_to_bf16(const int32_t *__restrict__ X, int64_t rows, int64_t cols,
+                                                        int64_t colsp, __nv_bfloat16 *__restrict__ out,
+                                                        uint32_t *out_of_range) {
+    bool bad = false;
+    const int64_t groups = colsp / V, total = rows * groups;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = idx / groups, c = (idx - r * groups) * V;
+        int32_t x[V];
+        if constexpr (V == 4) {
+            const int4 v = c < cols ? __ldg(reinterpret_cast<const int4 *>(X + r * cols + c)) : make_int4(0, 0, 0, 0);
+            x[0] = v.x, x[1] = v.y, x[2] = v.z, x[3] = v.w;
+        } else {
+            x[0] = c < cols ? __ldg(X + r * cols + c) : 0;
+        }
+        __align__(8) __nv_bfloat16 y[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            bad |= (x[j] < -128) | (x[j] > 127);
+            y[j] = __float2bfloat16_rn((float)x[j]);
+        }
+        if constexpr (V == 4)
+            *reinterpret_cast<uint2 *>(out + r * colsp + c) = *reinterpret_cast<const uint2 *>(y);
+        else
+            out[r * colsp + c] = y[0];
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(out_of_range, 1u);
+}
+
+cudaError_t run_i8range(const int32_t *X, int64_t rows, int64_t cols, int64_t colsp, __nv_bfloat16 *out, uint32_t *flag,
+                        cudaStream_t s) {
+    const bool vec = cols % 4 == 0 && (uintptr_t)X % 16 == 0;  // colsp is a multiple of 8
+    const int64_t total = rows * colsp / (vec ? 4 : 1);
+    const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    if (vec)
+        i8range_to_bf16<4><<<grid, 256, 0, s>>>(X, rows, cols, colsp, out, flag);
+    else
+        i8range_to_bf16<1><<<grid, 256, 0, s>>>(X, rows, cols, colsp, out, flag);
+    return cudaGetLastError();
+}
 
 template <typename Tin, int NPL>
 cudaError_t run_split(const Tin *X, int64_t rows, int64_t cols, int64_t colsp, __nv_bfloat16 *out, cudaStream_t s) {
@@ -120,6 +171,30 @@ moa_status tc_inner_bf16x3_scratch(const float *A, const float *B, float *D, int
     const int ta[6] = {1, 0, 2, 0, 1, 0};
     const int tb[6] = {1, 2, 0, 1, 0, 0};
     return tc_gemm_planes(a, Kp, 3, b, Np, 3, 6, ta, tb, D, N, M, N, K, true, s);
+}
+
+bool i32_tc_applies(int64_t M, int64_t N, int64_t K) {
+    return M > 128 && N > 128 && K >= 1 && K <= 1024 && M < (1ll << 31) && N < (1ll << 31) && pair_mma_enabled();
+}
+
+size_t i32_tc_workspace_bytes(int64_t M, int64_t N, int64_t K) {
+    return 16 + (size_t)(M * round8(K) + K * round8(N)) * 2;
+}
+
+// The range flag sits at the start of the workspace: the CUDA-core kernel
+// launched after the GEMM recomputes D only when the flag is set.
+moa_status tc_inner_i32(const int32_t *A, const int32_t *B, int32_t *D, int64_t M, int64_t N, int64_t K, void *ws,
+                        cudaStream_t s) {
+    const int64_t Kp = round8(K), Np = round8(N);
+    uint32_t *flag = (uint32_t *)ws;
+    __nv_bfloat16 *a = (__nv_bfloat16 *)((uint8_t *)ws + 16), *b = a + M * Kp;
+    if (cudaMemsetAsync(flag, 0, sizeof(uint32_t), s) != cudaSuccess) return MOA_ERR_CUDA;
+    if (run_i8range(A, M, K, Kp, a, flag, s) != cudaSuccess) return MOA_ERR_CUDA;
+    if (run_i8range(B, K, N, Np, b, flag, s) != cudaSuccess) return MOA_ERR_CUDA;
+    const int ta[1] = {0}, tb[1] = {0};
+    const moa_status st = tc_gemm_planes(a, Kp, 1, b, Np, 1, 1, ta, tb, (float *)D, N, M, N, K, false, s, true);
+    if (st != MOA_OK) return st;
+    return launch_semiring(SR_I32_PLUS_TIMES, A, B, D, M, N, K, s, flag) == cudaSuccess ? MOA_OK : MOA_ERR_CUDA;
 }
 
 }  // namespace moa

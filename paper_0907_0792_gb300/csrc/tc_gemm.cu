@@ -594,7 +594,7 @@ bool make_tmap(CUtensorMap *m, const void *base, uint64_t inner, uint64_t rows, 
 // lda, ldb multiples of 8 and the bases 16-byte aligned (TMA rules).
 moa_status tc_gemm_planes(const __nv_bfloat16 *A, int64_t lda, int planesA, const __nv_bfloat16 *B, int64_t ldb,
                           int planesB, int n_terms, const int *term_a, const int *term_b, float *D, int64_t ldd,
-                          int64_t M, int64_t N, int64_t K, bool promote, cudaStream_t s) {
+                          int64_t M, int64_t N, int64_t K, bool promote, cudaStream_t s, bool i32_out) {
     if (M >= (1ll << 31) || N >= (1ll << 31) || K >= (1ll << 31)) return MOA_ERR_OVERFLOW;
     if (n_terms < 1 || n_terms > kMaxTerms) return MOA_ERR_INTERNAL;
     if ((uintptr_t)A % 16 || (uintptr_t)B % 16 || lda % 8 || ldb % 8) return MOA_ERR_INTERNAL;
@@ -618,9 +618,10 @@ moa_status tc_gemm_planes(const __nv_bfloat16 *A, int64_t lda, int planesA, cons
     p.vec_store = ((uintptr_t)D % 16 == 0) && (ldd % 4 == 0);
     cudaError_t e;
     if (BN == 256 && M > BM && pair_mma_enabled()) {
-        e = tc_gemm_pair_launch(ta, tb, p.M, p.N, p.K, n_terms, p.term_a, p.term_b, D, ldd, promote, s);
+        e = tc_gemm_pair_launch(ta, tb, p.M, p.N, p.K, n_terms, p.term_a, p.term_b, D, ldd, promote, s, i32_out);
         return e == cudaSuccess ? MOA_OK : MOA_ERR_CUDA;
     }
+    if (i32_out) return MOA_ERR_INTERNAL;  // int32 results only from the pair kernel
     const bool pair = BN == 256 && M > BM && cluster_pairs_enabled();
     if (promote)
         e = BN == 128 ? launch_tc<128, 6, MODE_PROMOTE>(ta, tb, p, s)

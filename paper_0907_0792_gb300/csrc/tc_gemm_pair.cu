@@ -124,6 +124,7 @@ struct PairParams {
     int vec_store;
     int tma_store;  // D written through per-warp staging tiles and TMA stores
     uint32_t *bits_out;  // store mode: write [D > 0] as the packed bit stream (N % 32 == 0) instead of D
+    int i32_out;  // store mode: D holds int32 (every accumulator an exact integer, |x| <= 2^24)
     // Ozaki mode (ozaki_epi.cuh)
     int slices, beta, lsb, chunk;  // S, bits per digit, accumulator LSB, k-blocks per exact chunk
     double *D64;
@@ -500,6 +501,10 @@ __global__ void __launch_bounds__(threads(MODE), 1)
                         for (int j = 0; j < 32; ++j) word |= (__uint_as_float(r[j]) > 0.0f ? 1u : 0u) << j;
                         if (row < p.M && col0 < p.N) p.bits_out[(row * p.N + col0) >> 5] = word;
                     } else {
+                        if (p.i32_out) {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) r[j] = (uint32_t)__float2int_rn(__uint_as_float(r[j]));
+                        }
                         store32(row, colh + c, r);
                     }
                 }
@@ -620,8 +625,11 @@ cudaError_t tc_gemm_pair_fp8_launch(const uint8_t *A8, int64_t lda, const uint8_
 }
 
 cudaError_t tc_gemm_pair_launch(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, int K, int n_terms,
-                                uint32_t term_a, uint32_t term_b, float *D, int64_t ldd, bool promote, cudaStream_t s) {
+                                uint32_t term_a, uint32_t term_b, float *D, int64_t ldd, bool promote, cudaStream_t s,
+                                bool i32_out) {
+    if (promote && i32_out) return cudaErrorInvalidValue;
     PairParams p{};
+    p.i32_out = i32_out ? 1 : 0;
     p.M = M, p.N = N, p.K = K;
     p.kblocks = (K + bk(MODE_STORE) - 1) / bk(MODE_STORE);
     p.n_terms = n_terms;

@@ -72,6 +72,55 @@ def test_i32_full_size_sampled():
     assert np.array_equal(got, oracle.inner_i32(A, B, out_idx=idx))
 
 
+def _i32(A, B):
+    import torch
+    D = empty(A.shape[:-1] + B.shape[1:], torch.int32)
+    moa.moa_inner("add", "mul", "i32", "native", A.shape, to_dev(A), B.shape, to_dev(B), D, "i32")
+    return D.cpu().numpy()
+
+
+# more than 128 rows and columns and K <= 1024: the bf16 tensor-core path
+# when the values are int8-range; ragged tiles and contraction tails
+I8_SHAPES = [((300, 77), (77, 260)), ((129, 1024), (1024, 136)), ((4, 64, 33), (33, 3, 100)), ((257, 8), (8, 129)),
+             ((520, 1), (1, 515))]
+
+
+@pytest.mark.parametrize("shA,shB", I8_SHAPES)
+def test_i32_int8_range_tensor_core_path(shA, shB):
+    A = synth.int_uniform(21, 0, shA, -128, 127)
+    B = synth.int_uniform(21, 1, shB, -128, 127)
+    assert np.array_equal(_i32(A, B), oracle.inner_i32(A, B))
+    check_status()
+
+
+@pytest.mark.parametrize("K", [1024, 1025])
+def test_i32_int8_range_largest_sums(K):
+    """Every value -128: each sum is 2^14 K, at K = 1024 exactly 2^24, the
+    largest the FP32 accumulation has to hold; K = 1025 runs on CUDA cores.
+    Alternating signs in B give sums of both signs."""
+    A = np.full((130, K), -128, np.int32)
+    B = np.full((K, 200), -128, np.int32)
+    B[:, 1::2] = 127
+    got = _i32(A, B)
+    assert np.array_equal(got, oracle.inner_i32(A, B))
+    assert got[0, 0] == 16384 * K
+    check_status()
+
+
+@pytest.mark.parametrize("where,value", [("A", 128), ("A", -129), ("B", 2 ** 31 - 1), ("B", -(2 ** 31))])
+def test_i32_out_of_range_value_recomputed_on_cuda_cores(where, value):
+    """One value outside [-128, 127] anywhere: the range flag sends the whole
+    product to the CUDA-core kernel, with wrap-around where it occurs."""
+    A = synth.int_uniform(22, 0, (200, 300), -128, 127)
+    B = synth.int_uniform(22, 1, (300, 180), -128, 127)
+    if where == "A":
+        A[199, 299] = value
+    else:
+        B[0, 90] = value
+    assert np.array_equal(_i32(A, B), oracle.inner_i32(A, B))
+    check_status()
+
+
 def _bool(A, B):
     import torch
     shD = A.shape[:-1] + B.shape[1:]
