@@ -107,7 +107,7 @@ def inner_dot2(A, B, out_idx=None):
 
 
 def inner_f32(reduce: str, combine: str, A, B, out_idx=None):
-    """(min,+), (max,+), (max,*) (and (min|max, -)) over FP32, bit-exact definition."""
+    """reduce min or max, combine +, -, *, min or max, over FP32: the bit-exact definition."""
     A = _c(A, dtype=np.float32)
     B = _c(B, dtype=np.float32)
     shD = inner_shape(A.shape, B.shape)

@@ -191,9 +191,12 @@ static float f32_identity(int reduce) {
 
 /*
  * Eq. (2) generalised to D = reduce_p (A_{i..,p} combine B_{p,j..}) over
- * FP32 values: (min,+), (max,+), (max,*).  The fold starts at the reduction
- * identity and runs in increasing p; min and max make the result independent
- * of that order.  NaN is treated as missing (C99 fminf / fmaxf).
+ * FP32 values, Sec. I letting the operation be any binary one: reduce min or
+ * max, combine +, -, *, min or max ((min,+) shortest paths, (max,+) longest,
+ * (max,*) most reliable, (max,min) widest / bottleneck, (min,max) minimax).
+ * The fold starts at the reduction identity and runs in increasing p; min and
+ * max make the result independent of that order.  NaN is treated as missing
+ * (C99 fminf / fmaxf).
  */
 int oracle_inner_f32(int reduce, int combine, int rankA, const int64_t *shA, const float *A, int rankB,
                      const int64_t *shB, const float *B, int64_t n_out, const int64_t *out_idx, float *out) {
@@ -201,7 +204,8 @@ int oracle_inner_f32(int reduce, int combine, int rankA, const int64_t *shA, con
     int st = inner_check(rankA, shA, rankB, shB, &nD);
     if (st) return st;
     if (!(reduce == OP_MIN || reduce == OP_MAX)) return ORC_ERR_OP;
-    if (!(combine == OP_ADD || combine == OP_MUL || combine == OP_SUB)) return ORC_ERR_OP;
+    if (!(combine == OP_ADD || combine == OP_MUL || combine == OP_SUB || combine == OP_MIN || combine == OP_MAX))
+        return ORC_ERR_OP;
     const int64_t P = shA[rankA - 1];
     for (int64_t k = 0; k < n_out; ++k) {
         int64_t o = out_idx ? out_idx[k] : k;

@@ -182,7 +182,8 @@ def _closure(semiring, w, squarings=3):
     return x
 
 
-@pytest.mark.parametrize("name", ["minplus_apsp", "maxplus_dag_longest", "maxmul_reliability", "orand_reachability"])
+@pytest.mark.parametrize("name", ["minplus_apsp", "maxplus_dag_longest", "maxmul_reliability", "maxmin_widest",
+                                  "minmax_minimax", "orand_reachability"])
 def test_path_closures_hand_computed(name):
     g = _gold("semiring_paths.json")[name]
     if g["semiring"][0] == "or":
@@ -193,6 +194,41 @@ def test_path_closures_hand_computed(name):
         want = np.array([[_num(v) for v in r] for r in g["closure"]], dtype=np.float32)
     got = _closure(g["semiring"], w)
     assert np.array_equal(got, want), got
+
+
+def test_minmax_combines_on_booleans_reduce_to_or_and():
+    """On {0, 1} values (max, min) is (or, and), and (min, max) is its De
+    Morgan dual: min_p max(a, b) = not or_p (not a and not b)."""
+    Ab, Bb = synth.semiring_inputs("bool", seed=20, shape_a=(4, 3, 45), shape_b=(45, 7))
+    Ab = Ab | synth.bernoulli(20, 9, Ab.shape, 0.3)  # denser, so that both outcomes occur
+    A, B = Ab.astype(np.float32), Bb.astype(np.float32)
+    ref = oracle.inner_bool(Ab, Bb)
+    assert ref.any() and not ref.all()
+    assert np.array_equal(oracle.inner_f32("max", "min", A, B), ref.astype(np.float32))
+    dual = ~oracle.inner_bool(~Ab, ~Bb)
+    assert np.array_equal(oracle.inner_f32("min", "max", A, B), dual.astype(np.float32))
+
+
+def test_sub_combine_is_add_of_the_negation():
+    """a - b and a + (-b) are the same IEEE operation, so (min|max, -) with B
+    equals (min|max, +) with -B bit for bit."""
+    A, B = synth.semiring_inputs("tropical_finite", seed=21, shape_a=(5, 33), shape_b=(33, 6))
+    for red in ("min", "max"):
+        assert np.array_equal(oracle.inner_f32(red, "sub", A, B), oracle.inner_f32(red, "add", A, -B))
+
+
+def test_idempotent_combines_against_closed_forms():
+    """(max, max) and (min, min) split into reductions of each operand:
+    max_p max(a, b) = max(max_p a, max_p b); (max, min) with a constant row
+    of A is that constant capped by each column maximum of B."""
+    A, B = synth.semiring_inputs("tropical", seed=22, shape_a=(6, 40), shape_b=(40, 5))
+    want = np.maximum(A.max(axis=1)[:, None], B.max(axis=0)[None, :])
+    assert np.array_equal(oracle.inner_f32("max", "max", A, B), want)
+    want = np.minimum(A.min(axis=1)[:, None], B.min(axis=0)[None, :])
+    assert np.array_equal(oracle.inner_f32("min", "min", A, B), want)
+    c = np.float32(37.5)
+    got = oracle.inner_f32("max", "min", np.full((2, 40), c, np.float32), B)
+    assert np.array_equal(got, np.minimum(c, B.max(axis=0))[None, :].repeat(2, axis=0))
 
 
 def test_tropical_identity_operand():
