@@ -141,7 +141,9 @@ typedef enum {
  *   (add, mul) F32 -> F32      NATIVE | BF16 | FP8_T128 | BF16X3
  *   (add, mul) BF16 -> F32     NATIVE
  *   (add, mul) I32 -> I32      NATIVE (wraps modulo 2^32)
- *   (min|max, add|mul) F32 -> F32   NATIVE
+ *   (min|max, add|sub|mul|min|max) F32 -> F32   NATIVE
+ *       ((min, add) shortest paths, (max, min) widest paths, (min, max)
+ *       minimax paths, ...; NaN counts as missing, as C's fminf / fmaxf)
  *   (or, and) B1_U32 -> B1_U32      NATIVE
  * rankA, rankB in [1, 8].  Returns MOA_ERR_SHAPE_MISMATCH when
  * rho A[-1] != rho B[0], MOA_ERR_UNSUPPORTED for any other tuple.
@@ -149,6 +151,32 @@ typedef enum {
 moa_status moa_inner(moa_op reduce, moa_op combine, moa_dtype dtype, moa_form form, int rankA,
                      const int64_t *shapeA, const void *A, int rankB, const int64_t *shapeB, const void *B,
                      void *out, moa_dtype out_dtype, moa_stream stream);
+
+/*
+ * moa_inner_axes — Eq. (2) contracting axis `axisA` of A with axis `axisB`
+ * of B (equal lengths) instead of A's last and B's first:
+ *   D[i.., j..] = reduce_p ( A[.., p at axisA, ..] combine B[.., p at axisB, ..] ),
+ *   rho D = (rho A without axisA) ++ (rho B without axisB).
+ * Equals moa_inner on A transposed to move axisA last and B transposed to
+ * move axisB first (moa_transpose below, into a stream-ordered temporary of
+ * those sizes that is freed on `stream` after use; MOA_ERR_WORKSPACE when it
+ * cannot be had).  Same tuples, forms, errors and exactness as moa_inner;
+ * 0 <= axisA < rankA and 0 <= axisB < rankB, else MOA_ERR_INVALID.  Packed
+ * Booleans are supported only where no transpose is needed.
+ */
+moa_status moa_inner_axes(moa_op reduce, moa_op combine, moa_dtype dtype, moa_form form, int rankA,
+                          const int64_t *shapeA, const void *A, int axisA, int rankB, const int64_t *shapeB,
+                          const void *B, int axisB, void *out, moa_dtype out_dtype, moa_stream stream);
+
+/*
+ * moa_transpose — out = A with its axes permuted: output axis k is input
+ * axis perm[k], rho out[k] = rho A[perm[k]] (both row-major element
+ * vectors).  rank in [0, 8]; perm a permutation of 0..rank-1, else
+ * MOA_ERR_INVALID; dtype any but MOA_B1_U32 (MOA_ERR_UNSUPPORTED); out must
+ * not overlap A.  Bit-exact data movement; asynchronous on `stream`.
+ */
+moa_status moa_transpose(moa_dtype dtype, int rank, const int64_t *shape, const int *perm, const void *A, void *out,
+                         moa_stream stream);
 
 /*
  * moa_outer — generalized outer product, Eq. (1) (Sec. I; the operator of

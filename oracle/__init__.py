@@ -150,6 +150,15 @@ def inner_bool(A, B, out_idx=None):
 _OUT_KIND = {"f64": (0, np.float64), "f32": (1, np.float32), "bf16": (2, np.uint16)}
 
 
+def move_axes(A, B, axis_a: int, axis_b: int):
+    """The operands of a contraction over axis_a of A and axis_b of B in the
+    form Eq. (2) contracts: axis_a moved last in A, axis_b moved first in B,
+    the other axes keeping their order (numpy's moveaxis as the transpose).
+    Any inner_* function then gives D with rho D = (rho A without axis_a) ++
+    (rho B without axis_b)."""
+    return np.ascontiguousarray(np.moveaxis(A, axis_a, -1)), np.ascontiguousarray(np.moveaxis(B, axis_b, 0))
+
+
 def outer_f(op: str, A, B, out: str = "f64", out_idx=None):
     """Eq. (1) over floating operands given exactly as float64.
 

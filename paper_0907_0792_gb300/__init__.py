@@ -66,6 +66,8 @@ def lib():
         V, I, P, I64 = C.c_void_p, C.c_int, C.c_void_p, C.c_int64
         L.moa_inner.argtypes = [I, I, I, I, I, _I64P, P, I, _I64P, P, P, I, V]
         L.moa_outer.argtypes = [I, I, I, _I64P, P, I, _I64P, P, P, I, V]
+        L.moa_inner_axes.argtypes = [I, I, I, I, I, _I64P, P, I, I, _I64P, P, I, P, I, V]
+        L.moa_transpose.argtypes = [I, I, _I64P, C.POINTER(C.c_int), P, P, V]
         L.moa_inner_shape.argtypes = [I, _I64P, I, _I64P, C.POINTER(C.c_int), _I64P]
         L.moa_outer_shape.argtypes = [I, _I64P, I, _I64P, C.POINTER(C.c_int), _I64P]
         L.moa_status_string.argtypes = [I]
@@ -130,6 +132,29 @@ def moa_inner(reduce, combine, dtype, form, shapeA, A, shapeB, B, out, out_dtype
                          _stream(stream))
     if check:
         _check(st, "moa_inner")
+    return st
+
+
+def moa_inner_axes(reduce, combine, dtype, form, shapeA, A, axisA, shapeB, B, axisB, out, out_dtype, stream=None,
+                   check=True):
+    """C ABI moa_inner_axes: Eq. (2) contracting axis axisA of A with axis axisB of B."""
+    sa, _ka = _shape(shapeA)
+    sb, _kb = _shape(shapeB)
+    st = lib().moa_inner_axes(_enum(OPS, reduce), _enum(OPS, combine), _enum(DTYPES, dtype), _enum(FORMS, form),
+                              len(shapeA), sa, _ptr(A), int(axisA), len(shapeB), sb, _ptr(B), int(axisB), _ptr(out),
+                              _enum(DTYPES, out_dtype), _stream(stream))
+    if check:
+        _check(st, "moa_inner_axes")
+    return st
+
+
+def moa_transpose(dtype, shape, A, perm, out, stream=None, check=True):
+    """C ABI moa_transpose: output axis k is input axis perm[k]."""
+    sa, _ka = _shape(shape)
+    pm = (C.c_int * max(1, len(perm)))(*[int(p) for p in perm])
+    st = lib().moa_transpose(_enum(DTYPES, dtype), len(shape), sa, pm, _ptr(A), _ptr(out), _stream(stream))
+    if check:
+        _check(st, "moa_transpose")
     return st
 
 

@@ -160,7 +160,9 @@ static moa_status inner_validate(moa_op reduce, moa_op combine, moa_dtype dtype,
                form == MOA_FORM_FP8_T128)) ||
              (dtype == MOA_BF16 && out_dtype == MOA_F32 && form == MOA_FORM_NATIVE) ||
              (dtype == MOA_I32 && out_dtype == MOA_I32 && form == MOA_FORM_NATIVE);
-    } else if ((reduce == MOA_OP_MIN || reduce == MOA_OP_MAX) && (combine == MOA_OP_ADD || combine == MOA_OP_MUL)) {
+    } else if ((reduce == MOA_OP_MIN || reduce == MOA_OP_MAX) &&
+               (combine == MOA_OP_ADD || combine == MOA_OP_SUB || combine == MOA_OP_MUL || combine == MOA_OP_MIN ||
+                combine == MOA_OP_MAX)) {
         ok = dtype == MOA_F32 && out_dtype == MOA_F32 && form == MOA_FORM_NATIVE;
     } else if (reduce == MOA_OP_OR && combine == MOA_OP_AND) {
         ok = dtype == MOA_B1_U32 && out_dtype == MOA_B1_U32 && form == MOA_FORM_NATIVE;
@@ -207,8 +209,16 @@ static moa_status inner_run(moa_op reduce, moa_op combine, moa_dtype dtype, moa_
         return from_cuda(launch_or_and((const uint32_t *)A, (const uint32_t *)B, (uint32_t *)out, M, N, K, ws, s));
     }
     if (reduce == MOA_OP_MIN || reduce == MOA_OP_MAX) {
-        SemiringKind k = reduce == MOA_OP_MIN ? (combine == MOA_OP_ADD ? SR_F32_MIN_PLUS : SR_F32_MIN_TIMES)
-                                              : (combine == MOA_OP_ADD ? SR_F32_MAX_PLUS : SR_F32_MAX_TIMES);
+        const bool mx = reduce == MOA_OP_MAX;
+        SemiringKind k;
+        switch (combine) {
+        case MOA_OP_ADD: k = mx ? SR_F32_MAX_PLUS : SR_F32_MIN_PLUS; break;
+        case MOA_OP_SUB: k = mx ? SR_F32_MAX_MINUS : SR_F32_MIN_MINUS; break;
+        case MOA_OP_MUL: k = mx ? SR_F32_MAX_TIMES : SR_F32_MIN_TIMES; break;
+        case MOA_OP_MIN: k = mx ? SR_F32_MAX_MIN : SR_F32_MIN_MIN; break;
+        case MOA_OP_MAX: k = mx ? SR_F32_MAX_MAX : SR_F32_MIN_MAX; break;
+        default: return MOA_ERR_UNSUPPORTED;
+        }
         return from_cuda(launch_semiring(k, A, B, out, M, N, K, s));
     }
     // (add, mul)
@@ -283,6 +293,78 @@ moa_status moa_inner(moa_op reduce, moa_op combine, moa_dtype dtype, moa_form fo
     moa_status st = inner_validate(reduce, combine, dtype, form, rankA, shapeA, A, rankB, shapeB, B, out, out_dtype, &pl);
     if (st != MOA_OK) return st;
     return inner_run(reduce, combine, dtype, form, A, B, out, out_dtype, pl, (cudaStream_t)stream);
+}
+
+moa_status moa_transpose(moa_dtype dtype, int rank, const int64_t *shape, const int *perm, const void *A, void *out,
+                         moa_stream stream) {
+    if (rank < 0 || rank > kMaxRank) return MOA_ERR_RANK;
+    if (rank > 0 && (!shape || !perm)) return MOA_ERR_NULL;
+    if ((unsigned)dtype > MOA_B1_U32) return MOA_ERR_INVALID;
+    if (dtype == MOA_B1_U32) return MOA_ERR_UNSUPPORTED;  // a packed bit stream has no per-element address
+    bool seen[kMaxRank] = {};
+    for (int k = 0; k < rank; ++k) {
+        if (perm[k] < 0 || perm[k] >= rank || seen[perm[k]]) return MOA_ERR_INVALID;
+        seen[perm[k]] = true;
+    }
+    int64_t n;
+    moa_status st;
+    if ((st = count_elems(rank, shape, &n)) != MOA_OK) return st;
+    if (n == 0) return MOA_OK;
+    if (!A || !out) return MOA_ERR_NULL;
+    if (A == out) return MOA_ERR_INVALID;
+    if (!aligned_to(A, elem_bytes(dtype)) || !aligned_to(out, elem_bytes(dtype))) return MOA_ERR_ALIGNMENT;
+    return from_cuda(launch_transpose(elem_bytes(dtype), rank, shape, perm, A, out, (cudaStream_t)stream));
+}
+
+moa_status moa_inner_axes(moa_op reduce, moa_op combine, moa_dtype dtype, moa_form form, int rankA,
+                          const int64_t *shapeA, const void *A, int axisA, int rankB, const int64_t *shapeB,
+                          const void *B, int axisB, void *out, moa_dtype out_dtype, moa_stream stream) {
+    if (rankA < 1 || rankB < 1 || rankA > kMaxRank || rankB > kMaxRank) return MOA_ERR_RANK;
+    if (!shapeA || !shapeB) return MOA_ERR_NULL;
+    if (axisA < 0 || axisA >= rankA || axisB < 0 || axisB >= rankB) return MOA_ERR_INVALID;
+    // A with axisA moved last, B with axisB moved first: the form of Eq. (2)
+    int64_t sa[kMaxRank], sb[kMaxRank];
+    int pa[kMaxRank], pb[kMaxRank];
+    int r = 0;
+    for (int k = 0; k < rankA; ++k)
+        if (k != axisA) pa[r] = k, sa[r++] = shapeA[k];
+    pa[r] = axisA, sa[r] = shapeA[axisA];
+    pb[0] = axisB, sb[0] = shapeB[axisB];
+    r = 1;
+    for (int k = 0; k < rankB; ++k)
+        if (k != axisB) pb[r] = k, sb[r++] = shapeB[k];
+    InnerPlan pl;
+    moa_status st = inner_validate(reduce, combine, dtype, form, rankA, sa, A, rankB, sb, B, out, out_dtype, &pl);
+    if (st != MOA_OK) return st;
+    const bool moveA = axisA != rankA - 1, moveB = axisB != 0;
+    if (!moveA && !moveB) return inner_run(reduce, combine, dtype, form, A, B, out, out_dtype, pl, (cudaStream_t)stream);
+    if (pl.M == 0 || pl.N == 0 || pl.K == 0)  // nothing to read
+        return inner_run(reduce, combine, dtype, form, A, B, out, out_dtype, pl, (cudaStream_t)stream);
+    if (dtype == MOA_B1_U32) return MOA_ERR_UNSUPPORTED;  // bit streams are not transposed
+    // transposed copies in their own stream-ordered allocation (the inner
+    // product may use the per-stream workspace itself)
+    const cudaStream_t s = (cudaStream_t)stream;
+    const size_t es = elem_bytes(dtype);
+    const size_t bytesA = moveA ? (size_t)(pl.M * pl.K) * es : 0, bytesB = moveB ? (size_t)(pl.K * pl.N) * es : 0;
+    const size_t offB = (bytesA + 255) & ~(size_t)255;
+    void *tmp = nullptr;
+    if (inject_workspace_failure() || cudaMallocAsync(&tmp, offB + bytesB, s) != cudaSuccess) {
+        cudaGetLastError();
+        return MOA_ERR_WORKSPACE;
+    }
+    const void *a = A, *b = B;
+    cudaError_t e = cudaSuccess;
+    if (moveA) {
+        e = launch_transpose(es, rankA, shapeA, pa, A, tmp, s);
+        a = tmp;
+    }
+    if (moveB && e == cudaSuccess) {
+        e = launch_transpose(es, rankB, shapeB, pb, B, (uint8_t *)tmp + offB, s);
+        b = (uint8_t *)tmp + offB;
+    }
+    st = e == cudaSuccess ? inner_run(reduce, combine, dtype, form, a, b, out, out_dtype, pl, s) : MOA_ERR_CUDA;
+    cudaFreeAsync(tmp, s);  // stream-ordered: after the kernels that read it
+    return st;
 }
 
 moa_status moa_outer(moa_op op, moa_dtype dtype, int rankA, const int64_t *shapeA, const void *A, int rankB,

@@ -33,11 +33,22 @@ enum SemiringKind {
     SR_F32_MIN_TIMES = 4,
     SR_F32_MAX_TIMES = 5,
     SR_I32_PLUS_TIMES = 6,
+    SR_F32_MIN_MINUS = 7,
+    SR_F32_MAX_MINUS = 8,
+    SR_F32_MAX_MIN = 9,   // widest (bottleneck) paths
+    SR_F32_MIN_MAX = 10,  // minimax paths
+    SR_F32_MIN_MIN = 11,
+    SR_F32_MAX_MAX = 12,
 };
 // With `run_if`, every CTA returns at once unless *run_if is non-zero (a
 // flag an earlier kernel on the stream sets).
 cudaError_t launch_semiring(SemiringKind kind, const void *A, const void *B, void *D, int64_t M, int64_t N, int64_t K,
                             cudaStream_t stream, const uint32_t *run_if = nullptr);
+
+// transpose.cu — out (rank axes, output axis k = input axis perm[k]) from
+// in (row-major, extents `shape`), elements of elem_bytes (1, 2, 4, 8).
+cudaError_t launch_transpose(size_t elem_bytes, int rank, const int64_t *shape, const int *perm, const void *in,
+                             void *out, cudaStream_t stream);
 
 // skinny.cu — (add, mul) with a result of at most kSkinnyMaxM rows, FP64 or
 // FP32: a stream over B (the shape of the method's own measurement).

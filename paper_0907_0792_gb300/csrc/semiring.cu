@@ -178,6 +178,12 @@ cudaError_t launch_semiring(SemiringKind kind, const void *A, const void *B, voi
     case SR_F32_MIN_TIMES: return run<sr::F32MinTimes, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s, run_if);
     case SR_F32_MAX_TIMES: return run<sr::F32MaxTimes, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s, run_if);
     case SR_I32_PLUS_TIMES: return run<sr::I32PlusTimes, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s, run_if);
+    case SR_F32_MIN_MINUS: return run<sr::F32MinMax<false, sr::C_SUB>, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s, run_if);
+    case SR_F32_MAX_MINUS: return run<sr::F32MinMax<true, sr::C_SUB>, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s, run_if);
+    case SR_F32_MAX_MIN: return run<sr::F32MinMax<true, sr::C_MIN>, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s, run_if);
+    case SR_F32_MIN_MAX: return run<sr::F32MinMax<false, sr::C_MAX>, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s, run_if);
+    case SR_F32_MIN_MIN: return run<sr::F32MinMax<false, sr::C_MIN>, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s, run_if);
+    case SR_F32_MAX_MAX: return run<sr::F32MinMax<true, sr::C_MAX>, 128, 128, 16, 8, 8>(A, B, D, M, N, K, s, run_if);
     }
     return cudaErrorInvalidValue;
 }

@@ -61,6 +61,8 @@ def test_validation_before_launch(L):
     assert _inner_status("min", "add", "f64", "native", (4, 5), (5, 7), "f64") == 5
     assert _inner_status("or", "and", "f32", "native", (4, 5), (5, 7), "f32") == 5
     assert _inner_status("add", "mul", "i32", "native", (4, 5), (5, 7), "f32") == 5
+    assert _inner_status("min", "div", "f32", "native", (4, 5), (5, 7), "f32") == 5
+    assert _inner_status("add", "min", "f32", "native", (4, 5), (5, 7), "f32") == 5
     # negative extent, overflow
     assert _inner_status("add", "mul", "f32", "native", (-1, 5), (5, 7), "f32") == 4
     assert _inner_status("add", "mul", "f32", "native", (2 ** 40, 5), (5, 2 ** 40), "f32") == 4
@@ -73,6 +75,27 @@ def test_validation_before_launch(L):
     assert _inner_status(99, "mul", "f32", "native", (4, 5), (5, 7), "f32") == 11
     # empty result: a no-op that succeeds without touching the device
     assert _inner_status("add", "mul", "f32", "native", (0, 5), (5, 7), "f32", A=0, out=0) == 0
+
+
+def test_axes_and_transpose_validation(L):
+    def ax(sa, a, sb, b, dt="f32", A=0x1000, B=0x2000, out=0x3000):
+        return moa.moa_inner_axes("add", "mul", dt, "native", sa, A, a, sb, B, b, out, dt, stream=0, check=False)
+    assert ax((4, 5), 2, (5, 7), 0) == 11  # axis out of range
+    assert ax((4, 5), 0, (5, 7), -1) == 11
+    assert ax((4, 5), 0, (5, 7), 0) == 3  # contracted lengths 4 and 5 differ
+    assert ax((0, 5), 1, (5, 7), 0, A=0, out=0) == 0  # empty result
+    assert moa.moa_inner_axes("or", "and", "b1", "native", (4, 5), 0x1000, 0, (4, 7), 0x2000, 0, 0x3000, "b1",
+                              stream=0, check=False) == 5  # bit streams are not transposed
+
+    def tr(shape, perm, dt="f32", A=0x1000, out=0x2000):
+        return moa.moa_transpose(dt, shape, A, perm, out, stream=0, check=False)
+    assert tr((2, 3), (0, 0)) == 11
+    assert tr((2, 3), (0, 2)) == 11
+    assert tr((1,) * 9, tuple(range(9))) == 2
+    assert tr((2, 3), (1, 0), dt="b1") == 5
+    assert tr((2, 0, 3), (2, 1, 0), A=0, out=0) == 0
+    assert tr((2, 3), (1, 0), A=0x1000, out=0x1000) == 11
+    assert tr((2, 3), (1, 0), dt="f64", A=0x1004) == 10
 
 
 def test_outer_validation(L):

@@ -12,7 +12,10 @@ from gpu_helpers import assert_norm_err, check_status, empty, sample_idx, to_dev
 pytestmark = pytest.mark.gpu
 
 SEMIRINGS = [("min", "add", "tropical"), ("max", "add", "tropical"), ("max", "mul", "maxmul"),
-             ("min", "mul", "maxmul"), ("max", "add", "tropical_finite"), ("min", "add", "tropical_finite")]
+             ("min", "mul", "maxmul"), ("max", "add", "tropical_finite"), ("min", "add", "tropical_finite"),
+             # widest and minimax paths, differences, and the idempotent pairs
+             ("max", "min", "tropical"), ("min", "max", "tropical"), ("min", "sub", "tropical_finite"),
+             ("max", "sub", "tropical_finite"), ("min", "min", "tropical"), ("max", "max", "maxmul")]
 # several 128 x 128 tiles, ragged M, N and a contraction tail
 RAGGED = [((3, 100, 77), (77, 5, 53)), ((1, 129), (129, 1)), ((257, 16), (16, 129)), ((7, 33), (33, 300))]
 
@@ -33,7 +36,7 @@ def test_f32_semirings_small(reduce, combine, kind, shA, shB):
     check_status()
 
 
-@pytest.mark.parametrize("reduce,combine,kind", SEMIRINGS[:3])
+@pytest.mark.parametrize("reduce,combine,kind", SEMIRINGS[:3] + SEMIRINGS[6:9])
 def test_f32_semirings_full_size_sampled(reduce, combine, kind):
     """A <32,128,512>, B <512,64,64>: 16.8M outputs, 20,000 sampled."""
     import torch

@@ -231,6 +231,20 @@ def test_idempotent_combines_against_closed_forms():
     assert np.array_equal(got, np.minimum(c, B.max(axis=0))[None, :].repeat(2, axis=0))
 
 
+@pytest.mark.parametrize("sa,sb,ax_a,ax_b", [((4, 9, 3), (5, 9, 2), 1, 1), ((7, 2, 3), (3, 4), 0, 1),
+                                              ((6,), (2, 6, 3), 0, 1), ((3, 5), (5, 2), 1, 0)])
+def test_move_axes_matches_tensordot(sa, sb, ax_a, ax_b):
+    """Contraction over arbitrary axes: move_axes then the definition equals
+    numpy's tensordot over the same pair of axes (exact for integers)."""
+    sb = list(sb)
+    sb[ax_b] = sa[ax_a]  # the contracted axes have equal length
+    A = synth.int_uniform(23, 0, sa, -1000, 1000)
+    B = synth.int_uniform(23, 1, tuple(sb), -1000, 1000)
+    D = oracle.inner_i32(*oracle.move_axes(A, B, ax_a, ax_b))
+    R = np.tensordot(A.astype(np.int64), B.astype(np.int64), axes=([ax_a], [ax_b]))
+    assert D.shape == R.shape and np.array_equal(D, R.astype(np.int32))
+
+
 def test_tropical_identity_operand():
     A = synth.semiring_inputs("tropical", seed=18, shape_a=(5, 8), shape_b=(8, 2))[0]
     E = np.full((8, 8), np.inf, dtype=np.float32)
