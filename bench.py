@@ -263,6 +263,46 @@ def _row_outer(moa, torch, op, dt, reps, stream, peaks):
     return row
 
 
+def _row_axes(moa, torch, reps, stream, peaks, flush):
+    """Contraction over non-adjacent axes: the transpose pre-pass alone
+    (GB/s of read + write against the copy bandwidth, both kernels) and
+    moa_inner_axes on the semiring shapes with the contracted axes moved
+    inside the operands, next to moa_inner on the adjacent layout."""
+    import numpy as np
+
+    import synth
+    out = []
+    for shape, perm in (((1024, 512, 512), (2, 0, 1)), ((512, 1024, 512), (1, 0, 2))):
+        x = torch.empty(shape, dtype=torch.float32, device="cuda").uniform_()
+        y = torch.empty(tuple(shape[a] for a in perm), dtype=torch.float32, device="cuda")
+        call = lambda: moa.moa_transpose("f32", shape, x, perm, y, stream)
+        call()
+        ms = _events_time(call, reps, stream)  # 2 GiB moved per call, far above L2
+        gbs = 2 * x.numel() * 4 / (ms * 1e-3) / 1e9
+        out.append({"op": "transpose", "shape": list(shape), "perm": list(perm), "ms": round(ms, 4),
+                    "gbs": round(gbs, 1), "frac_hbm": round(gbs / peaks["hbm_gbs"], 3)})
+        del x, y
+    A, B = synth.semiring_inputs("tropical")  # <32,128,512> x <512,64,64>
+    Am = np.ascontiguousarray(np.moveaxis(A, 2, 1))  # <32,512,128>: contract axis 1
+    Bm = np.ascontiguousarray(np.moveaxis(B, 0, 2))  # <64,64,512>: contract axis 2
+    a, b, am, bm = (torch.from_numpy(v).cuda() for v in (A, B, Am, Bm))
+    D = torch.empty((32, 128, 64, 64), dtype=torch.float32, device="cuda")
+    for label, call in (("adjacent (moa_inner)",
+                         lambda: moa.moa_inner("min", "add", "f32", "native", A.shape, a, B.shape, b, D, "f32", stream)),
+                        ("axes 1 and 2 (moa_inner_axes)",
+                         lambda: moa.moa_inner_axes("min", "add", "f32", "native", Am.shape, am, 1, Bm.shape, bm, 2, D,
+                                                    "f32", stream))):
+        call()
+        times = []
+        for _ in range(reps):
+            flush()
+            times.append(_events_time(call, 1, stream))
+        out.append({"op": "(min,add) " + label, "ms": round(statistics.median(times), 4)})
+    del a, b, am, bm, D
+    torch.cuda.empty_cache()
+    return out
+
+
 def _row_plain_method(moa, torch, reps, stream):
     import synth
     A, B = synth.rank4x3_f64()
@@ -446,7 +486,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="moa", choices=["moa", "reference"])
     ap.add_argument("--rows", default="all",
-                    help="comma list of extra rows to measure: sweep,semirings,outer,plain,batched,skinny (all / none)")
+                    help="comma list of extra rows to measure: sweep,semirings,outer,plain,batched,skinny,axes (all / none)")
     ap.add_argument("--skinny-n", type=int, default=None, help="n of the skinny row (default 2^26)")
     ap.add_argument("--no-rows", action="store_true", help="same as --rows none")
     ap.add_argument("--sweep-n", type=int, default=N_HEAD, help="matrix size of the sweep row")
@@ -572,7 +612,8 @@ def main():
 
     rows = {}
     want = set() if args.no_rows or args.rows == "none" else (
-        {"sweep", "semirings", "outer", "plain", "batched", "skinny"} if args.rows == "all" else set(args.rows.split(",")))
+        {"sweep", "semirings", "outer", "plain", "batched", "skinny", "axes"} if args.rows == "all"
+        else set(args.rows.split(",")))
     if want:
         flush_buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
         flush = lambda: _flush_l2(flush_buf)
@@ -591,6 +632,7 @@ def main():
                 _row_semiring(moa, torch, "tropical", "min", "add", 5, stream, flush),
                 _row_semiring(moa, torch, "tropical", "max", "add", 5, stream, flush),
                 _row_semiring(moa, torch, "maxmul", "max", "mul", 5, stream, flush),
+                _row_semiring(moa, torch, "tropical", "max", "min", 5, stream, flush),
                 _row_semiring(moa, torch, "int32", "add", "mul", 5, stream, flush),
                 _row_semiring(moa, torch, "bool", "or", "and", 5, stream, flush)]
         if "outer" in want:
@@ -599,6 +641,8 @@ def main():
                                             ("mul", "bf16"), ("div", "bf16"), ("mul", "i32"))]
         if "plain" in want:
             rows["plain_method_f64_rank4x3"] = _row_plain_method(moa, torch, 20, stream)
+        if "axes" in want:
+            rows["axes_transpose"] = _row_axes(moa, torch, 10, stream, peaks, flush)
         if "skinny" in want:
             rows["skinny_paper_m_x_128_x_n"] = _row_skinny(moa, torch, 10, stream, peaks, n=args.skinny_n,
                                                             cpu=not args.no_cpu)

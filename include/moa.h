@@ -158,9 +158,8 @@ moa_status moa_inner(moa_op reduce, moa_op combine, moa_dtype dtype, moa_form fo
  *   D[i.., j..] = reduce_p ( A[.., p at axisA, ..] combine B[.., p at axisB, ..] ),
  *   rho D = (rho A without axisA) ++ (rho B without axisB).
  * Equals moa_inner on A transposed to move axisA last and B transposed to
- * move axisB first (moa_transpose below, into a stream-ordered temporary of
- * those sizes that is freed on `stream` after use; MOA_ERR_WORKSPACE when it
- * cannot be had).  Same tuples, forms, errors and exactness as moa_inner;
+ * move axisB first (moa_transpose below, into a library workspace of those
+ * sizes kept per stream; MOA_ERR_WORKSPACE when it cannot be had).  Same tuples, forms, errors and exactness as moa_inner;
  * 0 <= axisA < rankA and 0 <= axisB < rankB, else MOA_ERR_INVALID.  Packed
  * Booleans are supported only where no transpose is needed.
  */

@@ -67,7 +67,12 @@ namespace {
 struct WsKey {
     int device;
     cudaStream_t stream;
-    bool operator<(const WsKey &o) const { return device != o.device ? device < o.device : stream < o.stream; }
+    int slot;
+    bool operator<(const WsKey &o) const {
+        if (device != o.device) return device < o.device;
+        if (stream != o.stream) return stream < o.stream;
+        return slot < o.slot;
+    }
 };
 struct WsBuf {
     void *ptr = nullptr;
@@ -77,7 +82,7 @@ std::mutex g_ws_mu;
 std::map<WsKey, WsBuf> g_ws;
 }  // namespace
 
-void *workspace_get(cudaStream_t stream, size_t bytes, moa_status *st) {
+void *workspace_get(cudaStream_t stream, size_t bytes, moa_status *st, int slot) {
     *st = MOA_OK;
     if (bytes == 0) return nullptr;
     if (inject_workspace_failure()) {
@@ -90,7 +95,7 @@ void *workspace_get(cudaStream_t stream, size_t bytes, moa_status *st) {
         return nullptr;
     }
     std::lock_guard<std::mutex> lk(g_ws_mu);
-    WsBuf &b = g_ws[WsKey{dev, stream}];
+    WsBuf &b = g_ws[WsKey{dev, stream, slot}];
     if (b.bytes >= bytes) return b.ptr;
     // grow: stream-ordered free + allocation, so work already queued on this
     // stream keeps its buffer until it has finished with it
@@ -341,17 +346,14 @@ moa_status moa_inner_axes(moa_op reduce, moa_op combine, moa_dtype dtype, moa_fo
     if (pl.M == 0 || pl.N == 0 || pl.K == 0)  // nothing to read
         return inner_run(reduce, combine, dtype, form, A, B, out, out_dtype, pl, (cudaStream_t)stream);
     if (dtype == MOA_B1_U32) return MOA_ERR_UNSUPPORTED;  // bit streams are not transposed
-    // transposed copies in their own stream-ordered allocation (the inner
-    // product may use the per-stream workspace itself)
+    // transposed copies in the stream's second workspace slot (the inner
+    // product may use the first itself)
     const cudaStream_t s = (cudaStream_t)stream;
     const size_t es = elem_bytes(dtype);
     const size_t bytesA = moveA ? (size_t)(pl.M * pl.K) * es : 0, bytesB = moveB ? (size_t)(pl.K * pl.N) * es : 0;
     const size_t offB = (bytesA + 255) & ~(size_t)255;
-    void *tmp = nullptr;
-    if (inject_workspace_failure() || cudaMallocAsync(&tmp, offB + bytesB, s) != cudaSuccess) {
-        cudaGetLastError();
-        return MOA_ERR_WORKSPACE;
-    }
+    void *tmp = workspace_get(s, offB + bytesB, &st, 1);
+    if (st != MOA_OK) return st;
     const void *a = A, *b = B;
     cudaError_t e = cudaSuccess;
     if (moveA) {
@@ -362,9 +364,7 @@ moa_status moa_inner_axes(moa_op reduce, moa_op combine, moa_dtype dtype, moa_fo
         e = launch_transpose(es, rankB, shapeB, pb, B, (uint8_t *)tmp + offB, s);
         b = (uint8_t *)tmp + offB;
     }
-    st = e == cudaSuccess ? inner_run(reduce, combine, dtype, form, a, b, out, out_dtype, pl, s) : MOA_ERR_CUDA;
-    cudaFreeAsync(tmp, s);  // stream-ordered: after the kernels that read it
-    return st;
+    return e == cudaSuccess ? inner_run(reduce, combine, dtype, form, a, b, out, out_dtype, pl, s) : MOA_ERR_CUDA;
 }
 
 moa_status moa_outer(moa_op op, moa_dtype dtype, int rankA, const int64_t *shapeA, const void *A, int rankB,

@@ -12,8 +12,10 @@
 namespace moa {
 
 // Workspace: scratch device memory owned by the library, one buffer per
-// (device, stream), grown with stream-ordered allocation (api.cu).
-void *workspace_get(cudaStream_t stream, size_t bytes, moa_status *st);
+// (device, stream, slot), grown with stream-ordered allocation (api.cu).
+// Slot 0 serves the inner and outer products, slot 1 the transposed operands
+// of moa_inner_axes.
+void *workspace_get(cudaStream_t stream, size_t bytes, moa_status *st, int slot = 0);
 
 // outer.cu — Eq. (1) over the flattened operands (C is M x N, M = |A|, N = |B|).
 cudaError_t launch_outer(int op, moa_dtype dtype, moa_dtype out_dtype, const void *A, const void *B, void *C,

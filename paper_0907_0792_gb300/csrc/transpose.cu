@@ -8,11 +8,12 @@
 // adjacent and in order in the output (their elements then move as one run).
 // Two kernels remain:
 //   * the input's innermost axis stays innermost: each row of that axis is
-//     copied as a contiguous run, reads and writes coalesced;
-//   * otherwise a 32 x 32 tile over (input innermost axis x, the input axis y
-//     that becomes the output's innermost) goes through shared memory, so the
-//     reads run along x and the writes along y; the remaining axes index
-//     independent tiles.
+//     copied as a contiguous run (16-byte vectors where aligned), reads and
+//     writes coalesced, the rows' offsets stepped without division;
+//   * otherwise a square tile (64 x 64, 32 x 32 for 8-byte elements) over
+//     (input innermost axis x, the input axis y that becomes the output's
+//     innermost) goes through shared memory, so the reads run along x and the
+//     writes along y; the remaining axes index independent tiles.
 #include <algorithm>
 
 #include "common.cuh"
@@ -39,52 +40,122 @@ MOA_DEV void outer_offsets(const Outer &o, int64_t b, int64_t &in_off, int64_t &
     }
 }
 
-// Rows of n contiguous elements; rows indexed over `o`.
-template <typename T>
-__global__ void __launch_bounds__(256) copy_rows(const T *__restrict__ in, T *__restrict__ out, Outer o, int64_t rows,
-                                                 int64_t n) {
-    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
-        int64_t ib, ob;
-        outer_offsets(o, r, ib, ob);
-        for (int64_t c = threadIdx.x; c < n; c += blockDim.x) out[ob + c] = __ldg(in + ib + c);
+// The multi-index of a row over the outer axes and its two offsets,
+// advanced by a fixed step with carries (no division after the start).
+struct Odometer {
+    int64_t idx[kMaxDims];
+    int64_t in_off, out_off;
+    MOA_DEV void start(const Outer &o, int64_t b) {
+        in_off = 0, out_off = 0;
+        for (int k = o.nd - 1; k >= 0; --k) {
+            const int64_t e = o.ext[k], q = b / e;
+            idx[k] = b - q * e;
+            in_off += idx[k] * o.is[k];
+            out_off += idx[k] * o.os[k];
+            b = q;
+        }
+    }
+    MOA_DEV void advance(const Outer &o, int64_t step) {
+        for (int k = o.nd - 1; k >= 0 && step > 0; --k) {
+            const int64_t e = o.ext[k];
+            int64_t v = idx[k] + step;
+            step = 0;
+            while (v >= e) v -= e, ++step;  // step is small: the carry into the next axis
+            in_off += (v - idx[k]) * o.is[k];
+            out_off += (v - idx[k]) * o.os[k];
+            idx[k] = v;
+        }
+    }
+};
+
+// Rows of n contiguous units (U: the element type, or 16-byte vectors when
+// every row start is 16-byte aligned).  A block copies a contiguous range of
+// rows, W threads per row and 256 / W rows at a time; each thread walks its
+// rows with an odometer.
+template <typename U>
+__global__ void __launch_bounds__(256) copy_rows(const U *__restrict__ in, U *__restrict__ out, Outer o, int64_t rows,
+                                                 int64_t n, int W, int64_t per_block) {
+    const int R = 256 / W, tr = threadIdx.x / W, lane = threadIdx.x % W;
+    const int64_t r0 = (int64_t)blockIdx.x * per_block, r1 = min(rows, r0 + per_block);
+    int64_t r = r0 + tr;
+    if (r >= r1) return;
+    Odometer od;
+    od.start(o, r);
+    for (;;) {
+        for (int64_t k = lane; k < n; k += W) out[od.out_off + k] = __ldg(in + od.in_off + k);
+        r += R;
+        if (r >= r1) break;
+        od.advance(o, R);
     }
 }
 
-// 32 x 32 tiles of the (y, x) plane: in[y * isy + x] -> out[x * osx + y].
-template <typename T>
+// TS x TS tiles of the (y, x) plane: in[y * isy + x] -> out[x * osx + y],
+// 32 x 8 threads, TS * TS / 256 elements per thread in flight; blockIdx.x /
+// y / z: tile column, tile row, independent plane.
+template <typename T, int TS>
 __global__ void __launch_bounds__(256) tile_transpose(const T *__restrict__ in, T *__restrict__ out, Outer o,
                                                       int64_t nb, int64_t nx, int64_t ny, int64_t isy, int64_t osx) {
-    __shared__ T t[32][33];
-    const int64_t tx = (nx + 31) / 32, ty = (ny + 31) / 32, tiles = nb * tx * ty;
-    for (int64_t id = blockIdx.x; id < tiles; id += gridDim.x) {
-        const int64_t b = id / (tx * ty), rem = id - b * (tx * ty);
-        const int64_t y0 = (rem / tx) * 32, x0 = (rem % tx) * 32;
+    __shared__ T t[TS][TS + 1];
+    const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+    for (int64_t b = blockIdx.z; b < nb; b += gridDim.z) {
         int64_t ib, ob;
         outer_offsets(o, b, ib, ob);
-        const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;  // 32 x 8 threads
-        for (int j = ly; j < 32; j += 8) {
-            const int64_t y = y0 + j, x = x0 + lx;
-            if (y < ny && x < nx) t[j][lx] = __ldg(in + ib + y * isy + x);
+        for (int64_t y0 = (int64_t)blockIdx.y * TS; y0 < ny; y0 += (int64_t)gridDim.y * TS) {
+            for (int64_t x0 = (int64_t)blockIdx.x * TS; x0 < nx; x0 += (int64_t)gridDim.x * TS) {
+#pragma unroll
+                for (int j = 0; j < TS; j += 8) {
+#pragma unroll
+                    for (int i = 0; i < TS; i += 32) {
+                        const int64_t y = y0 + j + ly, x = x0 + i + lx;
+                        if (y < ny && x < nx) t[j + ly][i + lx] = __ldg(in + ib + y * isy + x);
+                    }
+                }
+                __syncthreads();
+#pragma unroll
+                for (int j = 0; j < TS; j += 8) {
+#pragma unroll
+                    for (int i = 0; i < TS; i += 32) {
+                        const int64_t x = x0 + j + ly, y = y0 + i + lx;
+                        if (x < nx && y < ny) out[ob + x * osx + y] = t[i + lx][j + ly];
+                    }
+                }
+                __syncthreads();
+            }
         }
-        __syncthreads();
-        for (int j = ly; j < 32; j += 8) {
-            const int64_t x = x0 + j, y = y0 + lx;
-            if (x < nx && y < ny) out[ob + x * osx + y] = t[lx][j];
-        }
-        __syncthreads();
     }
 }
 
+unsigned clamp_grid(int64_t v, int64_t lim) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(v, lim)); }
+
 template <typename T>
-cudaError_t run(const void *in, void *out, const Outer &o, bool rows_case, int64_t nb, int64_t nx, int64_t ny,
-                int64_t isy, int64_t osx, cudaStream_t s) {
-    constexpr int64_t kMaxGrid = 152 * 32;
+cudaError_t run(const void *in, void *out, Outer o, bool rows_case, int64_t nb, int64_t nx, int64_t ny, int64_t isy,
+                int64_t osx, cudaStream_t s) {
     if (rows_case) {
-        copy_rows<T><<<(unsigned)std::min<int64_t>(nb, kMaxGrid), 256, 0, s>>>((const T *)in, (T *)out, o, nb, nx);
+        // 16-byte units when the row length, every row start and both bases allow
+        bool vec = sizeof(T) < 16 && (nx * (int64_t)sizeof(T)) % 16 == 0 && (uintptr_t)in % 16 == 0 &&
+                   (uintptr_t)out % 16 == 0;
+        for (int k = 0; k < o.nd && vec; ++k)
+            vec = (o.is[k] * (int64_t)sizeof(T)) % 16 == 0 && (o.os[k] * (int64_t)sizeof(T)) % 16 == 0;
+        int64_t n = nx;
+        if (vec) {
+            const int64_t f = 16 / (int64_t)sizeof(T);
+            n = nx / f;
+            for (int k = 0; k < o.nd; ++k) o.is[k] /= f, o.os[k] /= f;
+        }
+        int W = 32;  // threads per row: the row length rounded up to a power of two, 32..256
+        while (W < 256 && W < n) W *= 2;
+        const int64_t blocks = std::min<int64_t>((nb + 256 / W - 1) / (256 / W), 152 * 16);
+        const int64_t per_block = (nb + blocks - 1) / blocks;
+        const unsigned grid = (unsigned)((nb + per_block - 1) / per_block);
+        if (vec)
+            copy_rows<uint4><<<grid, 256, 0, s>>>((const uint4 *)in, (uint4 *)out, o, nb, n, W, per_block);
+        else
+            copy_rows<T><<<grid, 256, 0, s>>>((const T *)in, (T *)out, o, nb, n, W, per_block);
     } else {
-        const int64_t tiles = nb * ((nx + 31) / 32) * ((ny + 31) / 32);
-        tile_transpose<T><<<(unsigned)std::min<int64_t>(tiles, kMaxGrid), 256, 0, s>>>((const T *)in, (T *)out, o, nb,
-                                                                                        nx, ny, isy, osx);
+        constexpr int TS = sizeof(T) == 8 ? 32 : 64;
+        const dim3 grid(clamp_grid((nx + TS - 1) / TS, 1 << 30), clamp_grid((ny + TS - 1) / TS, 65535),
+                        clamp_grid(nb, 65535));
+        tile_transpose<T, TS><<<grid, 256, 0, s>>>((const T *)in, (T *)out, o, nb, nx, ny, isy, osx);
     }
     return cudaGetLastError();
 }

@@ -19,7 +19,9 @@ TORCH_DT = {"f64": "float64", "f32": "float32", "i32": "int32", "bf16": "bfloat1
 TRANSPOSES = [((), ()), ((5,), (0,)), ((3, 4), (1, 0)), ((37, 65), (1, 0)), ((3, 37, 65), (2, 0, 1)),
               ((3, 37, 65), (1, 0, 2)), ((2, 1, 33, 1, 40), (4, 3, 2, 1, 0)), ((4, 5, 6, 7), (0, 2, 3, 1)),
               ((2, 3, 2, 3, 2, 3, 2, 3), (7, 0, 6, 1, 5, 2, 4, 3)), ((64, 1000), (1, 0)), ((1000, 3), (1, 0)),
-              ((3, 1000), (1, 0)), ((1, 1, 1), (2, 0, 1))]
+              ((3, 1000), (1, 0)), ((1, 1, 1), (2, 0, 1)),
+              # rows copied as 16-byte vectors; more rows than one grid dimension holds
+              ((6, 5, 64), (1, 0, 2)), ((70000, 2, 8), (1, 0, 2)), ((3, 70000, 5), (2, 1, 0))]
 
 
 def _dev(x, dt):
