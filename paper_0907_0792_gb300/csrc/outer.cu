@@ -8,7 +8,22 @@
 //  - A[i] is one broadcast load per row;
 //  - stores are 128-bit streaming stores (st.global.cs: C is written once
 //    and not re-read, so it should not displace other lines in L2);
-//  - the grid is a multiple of the SM count, each block striding over rows.
+//  - the grid is a multiple of the SM count, each block striding over rows;
+//  - bf16 / bf16 -> bf16 multiplies by the correctly rounded FP32 reciprocal
+//    of each B element (taken once per column) instead of dividing.  The
+//    result is the same bf16: an 8-bit significand over an 8-bit significand
+//    is never an odd multiple of half a bf16 unit (the odd part of m * B_sig,
+//    m >= 257 odd, exceeds any 8-bit odd part), so the exact quotient lies at
+//    least 2^-17 (relative) from every bf16 rounding midpoint, while both
+//    RN(a / b) and RN(a * RN(1 / b)) stay within 2^-22 of it.  Below 2^-126
+//    a quotient is either at least 2^-143 from every midpoint (the two
+//    roundings err by at most 2^-149) or exactly on one, a multiple of
+//    2^-149 that both roundings return unchanged (the reciprocal's error
+//    moves it by less than 2^-150).  Columns whose reciprocal is neither a
+//    normal FP32 number nor exact (|b| < 2^-126 or 2^126 < |b| < inf)
+//    divide.
+#include <type_traits>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -25,6 +40,16 @@ template <typename Tout, typename Tc> MOA_DEV Tout narrow(Tc x) { return (Tout)x
 template <> MOA_DEV __nv_bfloat16 narrow<__nv_bfloat16, float>(float x) { return __float2bfloat16_rn(x); }
 
 template <int OP, typename Tc> MOA_DEV Tc apply(Tc a, Tc b) { return op_apply(OP, a, b); }
+
+template <int OP, typename Tin, typename Tout>
+constexpr bool kRcpDiv = OP == MOA_OP_DIV && std::is_same<Tin, __nv_bfloat16>::value &&
+                         std::is_same<Tout, __nv_bfloat16>::value;
+
+// 1 / b is a normal FP32 number, or b is 0, inf or NaN (exact specials).
+MOA_DEV bool rcp_usable(float b) {
+    const float m = fabsf(b);
+    return !(m > 0.0f && m < 0x1p-126f) && !(m > 0x1p126f && m <= 3.4028234663852886e38f);
+}
 
 // One 16-byte vector of output elements.
 template <typename Tout> struct alignas(16) Vec16 {
@@ -54,12 +79,31 @@ __global__ void __launch_bounds__(kThreads) outer_rows(const Tin *__restrict__ A
     Tc b[VEC];
 #pragma unroll
     for (int k = 0; k < VEC; ++k) b[k] = widen(B[cv * VEC + k]);
+    [[maybe_unused]] float rb[VEC];
+    [[maybe_unused]] bool rcp_all = true;
+    if constexpr (kRcpDiv<OP, Tin, Tout>) {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+            rb[k] = __frcp_rn(b[k]);
+            rcp_all &= rcp_usable(b[k]);
+        }
+    }
     const int64_t step = (int64_t)gridDim.y * rows_per_iter;
     for (int64_t r = (int64_t)blockIdx.y * rows_per_iter + ro; r < M; r += step) {
         const Tc a = widen(__ldg(A + r));
         Vec16<Tout> o;
+        if constexpr (kRcpDiv<OP, Tin, Tout>) {
+            if (rcp_all) {
 #pragma unroll
-        for (int k = 0; k < VEC; ++k) o.v[k] = narrow<Tout>(apply<OP>(a, b[k]));
+                for (int k = 0; k < VEC; ++k) o.v[k] = narrow<Tout>(__fmul_rn(a, rb[k]));
+            } else {
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) o.v[k] = narrow<Tout>(apply<OP>(a, b[k]));
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) o.v[k] = narrow<Tout>(apply<OP>(a, b[k]));
+        }
         store_cs(C + r * N + cv * VEC, o);
     }
 }

@@ -53,6 +53,37 @@ def test_small_ragged_f32_bf16(op, shA, shB):
     check_status()
 
 
+def _bf16_values(bits):
+    return (bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+def _same_bf16(got, want):
+    """Equal bit patterns, except that any NaN matches any NaN."""
+    nan_w = (want & 0x7F80) == 0x7F80
+    nan_w &= (want & 0x7F) != 0
+    nan_g = ((got & 0x7F80) == 0x7F80) & ((got & 0x7F) != 0)
+    return np.array_equal(nan_g, nan_w) and np.array_equal(got[~nan_w], want[~nan_w])
+
+
+def test_bf16_division_every_divisor_and_dividend():
+    """bf16 / bf16 -> bf16 (reciprocal multiply where it is exact, division
+    elsewhere) against the FP32 quotient rounded once to bf16: every one of
+    the 65536 bit patterns as divisor, and as dividend, against 48 values
+    that cover zeros, subnormals, normals of all sizes, the largest
+    finite, infinities and NaN."""
+    every = np.arange(65536, dtype=np.uint32).astype(np.uint16)
+    pick = np.array([0x0000, 0x8000, 0x0001, 0x8001, 0x007F, 0x0080, 0x8080, 0x00FF, 0x3F80, 0xBF80, 0x3F81, 0x4049,
+                     0xC0A0, 0x7F7F, 0xFF7F, 0x7F80, 0xFF80, 0x7FC0, 0x0100, 0x3C00, 0x4300, 0x5F00, 0x7E80, 0x0200,
+                     0x3E4D, 0x3DCD, 0xBDCD, 0x41FF, 0x42C8, 0x7F00, 0x00A0, 0x8055, 0x1234, 0x9234, 0x2F00, 0x6F00,
+                     0x3F00, 0x3FFF, 0x407F, 0xC0FF, 0x4B7F, 0x0C00, 0x7300, 0x0080 | 0x8000, 0x3F7F, 0x7F7E, 0x0040,
+                     0x4F7F], dtype=np.uint16)
+    for a_bits, b_bits in ((pick, every), (every, pick)):
+        C = _run("div", "bf16", bf16_dev(a_bits), bf16_dev(b_bits), "bf16", a_bits.shape, b_bits.shape)
+        want = oracle.outer_f("div", _bf16_values(a_bits), _bf16_values(b_bits), out="bf16")
+        assert _same_bf16(_host(C), want)
+    check_status()
+
+
 @pytest.mark.parametrize("op", ["mul", "add", "sub"])
 def test_small_i32(op):
     A, B = synth.outer_inputs(op, "i32", shape_a=(7, 9), shape_b=(5, 13))
