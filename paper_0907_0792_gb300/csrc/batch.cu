@@ -449,24 +449,40 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // Grouped split pre-pass: each job is a block of rows of one operand; the
-// threads of a CTA walk the job's (row, column) elements as one flat range,
-// so short rows still keep every thread busy.
+// threads of a CTA walk the job's rows as one flat range of 4-column groups
+// (padded rows are a multiple of 8 columns), so short rows still keep every
+// thread busy; each group is one 16-byte load where the source row allows it
+// and one 8-byte store per plane.
 __global__ void __launch_bounds__(256) batch_split_kernel(const SplitJob *__restrict__ jobs, int n_jobs) {
     for (int j = blockIdx.x; j < n_jobs; j += gridDim.x) {
         const SplitJob jb = jobs[j];
-        const int colsp = (int)jb.colsp;  // < 2^31 (checked at plan creation)
-        const int count = (int)((jb.r1 - jb.r0) * jb.colsp);  // <= ~64K + one row
+        const int gpr = (int)(jb.colsp / 4);  // colsp < 2^31 (checked at plan creation)
+        const int count = (int)((jb.r1 - jb.r0) * gpr);  // <= ~16K + one row
+        const bool vec = (jb.cols & 3) == 0 && ((uintptr_t)jb.src & 15) == 0;
         for (int e = threadIdx.x; e < count; e += blockDim.x) {
-            const int rr = e / colsp, c = e - rr * colsp;
+            const int rr = e / gpr, c = (e - rr * gpr) * 4;
             const int64_t r = jb.r0 + rr;
-            const float x = c < jb.cols ? __ldg(jb.src + r * jb.cols + c) : 0.0f;
-            const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-            const float r1 = __fsub_rn(x, __bfloat162float(hi));
-            const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+            const float *src = jb.src + r * jb.cols + c;
+            float x[4];
+            if (vec) {
+                const float4 v = c < jb.cols ? __ldg(reinterpret_cast<const float4 *>(src)) : make_float4(0, 0, 0, 0);
+                x[0] = v.x, x[1] = v.y, x[2] = v.z, x[3] = v.w;
+            } else {
+#pragma unroll
+                for (int t = 0; t < 4; ++t) x[t] = c + t < jb.cols ? __ldg(src + t) : 0.0f;
+            }
+            __align__(8) __nv_bfloat16 hi[4], mid[4], lo[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                hi[t] = __float2bfloat16_rn(x[t]);
+                const float r1 = __fsub_rn(x[t], __bfloat162float(hi[t]));
+                mid[t] = __float2bfloat16_rn(r1);
+                lo[t] = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(mid[t])));
+            }
             __nv_bfloat16 *dst = jb.dst + r * jb.colsp + c;
-            dst[0] = hi;
-            dst[jb.plane] = mid;
-            dst[2 * jb.plane] = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(mid)));
+            *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(hi);
+            *reinterpret_cast<uint2 *>(dst + jb.plane) = *reinterpret_cast<const uint2 *>(mid);
+            *reinterpret_cast<uint2 *>(dst + 2 * jb.plane) = *reinterpret_cast<const uint2 *>(lo);
         }
     }
 }

@@ -45,9 +45,13 @@ MOA_DEV void outer_offsets(const Outer &o, int64_t b, int64_t &in_off, int64_t &
 struct Odometer {
     int64_t idx[kMaxDims];
     int64_t in_off, out_off;
+    // loops unrolled over the fixed maximum so that idx stays in registers
     MOA_DEV void start(const Outer &o, int64_t b) {
         in_off = 0, out_off = 0;
-        for (int k = o.nd - 1; k >= 0; --k) {
+#pragma unroll
+        for (int k = kMaxDims - 1; k >= 0; --k) {
+            idx[k] = 0;
+            if (k >= o.nd) continue;
             const int64_t e = o.ext[k], q = b / e;
             idx[k] = b - q * e;
             in_off += idx[k] * o.is[k];
@@ -56,7 +60,9 @@ struct Odometer {
         }
     }
     MOA_DEV void advance(const Outer &o, int64_t step) {
-        for (int k = o.nd - 1; k >= 0 && step > 0; --k) {
+#pragma unroll
+        for (int k = kMaxDims - 1; k >= 0; --k) {
+            if (k >= o.nd || step == 0) continue;
             const int64_t e = o.ext[k];
             int64_t v = idx[k] + step;
             step = 0;
@@ -73,7 +79,7 @@ struct Odometer {
 // rows, W threads per row and 256 / W rows at a time; each thread walks its
 // rows with an odometer.
 template <typename U>
-__global__ void __launch_bounds__(256) copy_rows(const U *__restrict__ in, U *__restrict__ out, Outer o, int64_t rows,
+__global__ void __launch_bounds__(256, 4) copy_rows(const U *__restrict__ in, U *__restrict__ out, Outer o, int64_t rows,
                                                  int64_t n, int W, int64_t per_block) {
     const int R = 256 / W, tr = threadIdx.x / W, lane = threadIdx.x % W;
     const int64_t r0 = (int64_t)blockIdx.x * per_block, r1 = min(rows, r0 + per_block);
