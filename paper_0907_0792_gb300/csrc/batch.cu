@@ -13,16 +13,22 @@
 // split planes and the item list are uploaded once.
 //
 // Execute (moa_batch_execute): a CUDA graph, captured on the first execute
-// and replayed after, holding (1) the grouped split pre-pass (FP32 -> three
-// bf16 planes for every BF16x3 problem) and (2) one persistent grouped
-// kernel (one CTA per SM).  In that kernel the TMA warp pulls item indices
-// from a device-side queue (one atomic counter) and hands each to the MMA
-// warp and the 8 epilogue warps through a 4-slot ring of shared-memory slots
-// guarded by mbarriers.  TC items run the tcgen05 pipeline of tc_gemm.cu in
-// its promoted form (per-k-block FP32 promotion); CC / OUT / FILL items are
-// computed by the 8 epilogue warps while the TMA and MMA warps run ahead on
-// the next tensor-core item, so tensor-core and CUDA-core work overlap.
-// Every wait is bounded and reports through the batch status word.
+// and replayed after.  Under the default schedules it holds (1) persistent
+// CUDA-core kernels, one per (operator, occupied tile halves) present, two
+// 256-thread CTAs per SM, each pulling its CC items from its own queue
+// counter; (2) the grouped split pre-pass (FP32 -> three bf16 planes for
+// every BF16x3 problem); (3) one persistent grouped kernel (one CTA per SM)
+// for the TC / OUT / FILL items.  In that kernel the TMA warp pulls item
+// indices from a device-side queue (one atomic counter) and hands each to
+// the MMA warp and the 8 epilogue warps through a 4-slot ring of
+// shared-memory slots guarded by mbarriers.  TC items run the tcgen05
+// pipeline of tc_gemm.cu in its promoted form (per-k-block FP32 promotion);
+// OUT / FILL items are computed by the 8 epilogue warps.  The third schedule
+// instead runs the CC items inside the grouped kernel too, on its epilogue
+// warps (the FP32 promotion of TC items keeps those warps busy, so there the
+// two kinds of work mostly serialise); the autotuner times the schedules on
+// the first execute.  Every wait is bounded and reports through the batch
+// status word.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -50,6 +56,7 @@ namespace {
 
 enum ItemType { IT_TC = 0, IT_CC = 1, IT_OUT = 2, IT_FILL = 3 };
 enum CcOp { CC_MIN_PLUS = 0, CC_MAX_PLUS = 1, CC_MIN_TIMES = 2, CC_MAX_TIMES = 3, CC_PLUS_TIMES = 4 };
+constexpr int kCcOps = 5, kCcGroups = 4 * kCcOps;  // CUDA-core kernels: operator x occupied tile halves
 
 struct alignas(16) BInst {
     int32_t type;  // IT_*
@@ -101,7 +108,7 @@ MOA_DEV void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 // halves a thread would compute outside the problem are skipped (the flags
 // are the same for every thread of the tile, so no warp diverges).
 template <class Op, bool RH, bool CH>
-__device__ __noinline__ void cc_tile_q(const BInst &in, int tm, int tn, float *As, float *Bs, int tid) {
+__device__ __forceinline__ void cc_tile_body(const BInst &in, int tm, int tn, float *As, float *Bs, int tid) {
     const int64_t M = in.M, N = in.N, K = in.K;
     const float *A = in.A, *B = in.B;
     const int tx = tid % 16, ty = tid / 16;
@@ -198,6 +205,22 @@ __device__ __noinline__ void cc_tile_q(const BInst &in, int tm, int tn, float *A
             if (n < N) in.D[m * N + n] = acc[i][j];
         }
     }
+}
+
+// Out of line in the grouped kernel (its register budget is set by the
+// tensor-core roles); inlined in the CUDA-core kernel.
+template <class Op, bool RH, bool CH>
+__device__ __noinline__ void cc_tile_q(const BInst &in, int tm, int tn, float *As, float *Bs, int tid) {
+    cc_tile_body<Op, RH, CH>(in, tm, tn, As, Bs, tid);
+}
+
+template <class Op>
+MOA_DEV void cc_tile_inline(const BInst &in, int tm, int tn, float *As, float *Bs, int tid) {
+    const bool rh = (int64_t)tm * 128 + 64 < in.M, ch = (int64_t)tn * 128 + 64 < in.N;
+    if (rh && ch) cc_tile_body<Op, true, true>(in, tm, tn, As, Bs, tid);
+    else if (rh) cc_tile_body<Op, true, false>(in, tm, tn, As, Bs, tid);
+    else if (ch) cc_tile_body<Op, false, true>(in, tm, tn, As, Bs, tid);
+    else cc_tile_body<Op, false, false>(in, tm, tn, As, Bs, tid);
 }
 
 template <class Op>
@@ -487,6 +510,26 @@ __global__ void __launch_bounds__(256) batch_split_kernel(const SplitJob *__rest
     }
 }
 
+// CUDA-core items on their own: a persistent kernel of two 256-thread CTAs
+// per SM (16 warps, against the grouped kernel's 8 epilogue warps per SM)
+// pulling CC items from a second queue counter.
+template <class Op, bool RH, bool CH>
+__global__ void __launch_bounds__(256, 2)
+    batch_cc_kernel(const BInst *__restrict__ inst, const BItem *__restrict__ items, int n_items, int *queue) {
+    __shared__ __align__(16) float cc_smem[CC_BYTES / 4];
+    __shared__ int s_next;
+    float *ccA = cc_smem, *ccB = cc_smem + 2 * CC_BK * CC_LD;
+    for (;;) {
+        if (threadIdx.x == 0) s_next = atomicAdd(queue, 1);
+        __syncthreads();
+        const int i = s_next;
+        __syncthreads();  // every thread has read s_next before it is overwritten
+        if (i >= n_items) break;
+        const BItem it = items[i];
+        cc_tile_body<Op, RH, CH>(inst[it.inst], it.a, it.b, ccA, ccB, (int)threadIdx.x);
+    }
+}
+
 int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
 
 int sm_count_dev() {
@@ -512,6 +555,22 @@ moa_status count_elems(int rank, const int64_t *shape, int64_t *n) {
     }
     *n = c;
     return MOA_OK;
+}
+
+// Which halves of a CUDA-core tile hold output: bit 1 rows 64..127, bit 0
+// columns 64..127 (the kernel variant that runs the item).
+int cc_quadrants(const Problem &p, const BItem &it) {
+    return ((int64_t)it.a * 128 + 64 < p.M ? 2 : 0) | ((int64_t)it.b * 128 + 64 < p.N ? 1 : 0);
+}
+
+template <class Op>
+void launch_cc_quad(int q, int grid, const BInst *inst, const BItem *items, int cnt, int *queue, cudaStream_t s) {
+    switch (q) {
+    case 3: batch_cc_kernel<Op, true, true><<<grid, 256, 0, s>>>(inst, items, cnt, queue); break;
+    case 2: batch_cc_kernel<Op, true, false><<<grid, 256, 0, s>>>(inst, items, cnt, queue); break;
+    case 1: batch_cc_kernel<Op, false, true><<<grid, 256, 0, s>>>(inst, items, cnt, queue); break;
+    default: batch_cc_kernel<Op, false, false><<<grid, 256, 0, s>>>(inst, items, cnt, queue); break;
+    }
 }
 
 // Validate one problem like its single call and reduce it to (type, op, M, N, K).
@@ -608,7 +667,11 @@ int tune_mode() {  // 0 off, 1 cached, 2 force
     return 1;
 }
 
-constexpr int kPolicies = 3;  // 0 longest first, 1 tensor-core items first, 2 interleaved by kind
+// Schedules the autotuner picks from: 0 CUDA-core items in their own kernel
+// (before the split pass), the grouped queue longest first; 1 the same with
+// tensor-core items first in the grouped queue; 2 every item in the grouped
+// kernel, tensor-core and CUDA-core items interleaved.
+constexpr int kPolicies = 3;
 
 }  // namespace
 }  // namespace moa
@@ -622,12 +685,15 @@ struct moa_batch_plan {
     std::vector<BItem> items;  // unordered
     std::vector<double> cost;
     int n_items = 0, n_jobs = 0;
+    int n_grouped = 0, n_cc = 0;  // items in the grouped kernel / the CUDA-core kernels (set by the policy)
+    int cc_off[kCcGroups] = {}, cc_cnt[kCcGroups] = {};  // CUDA-core items of each kernel in d_cc_items
     double work = 0.0;
     std::string signature;
     int policy = -1;
     // device memory owned by the plan
     BInst *d_inst = nullptr;
     BItem *d_items = nullptr;
+    BItem *d_cc_items = nullptr;
     CUtensorMap *d_tmaps = nullptr;
     SplitJob *d_jobs = nullptr;
     int *d_queue = nullptr;
@@ -641,40 +707,54 @@ struct moa_batch_plan {
 namespace moa {
 namespace {
 
-std::vector<BItem> order_items(const moa_batch_plan &pl, int policy) {
+int cc_group(const moa_batch_plan &pl, const BItem &it) {
+    const Problem &p = pl.probs[it.inst];
+    return 4 * p.op + cc_quadrants(p, it);
+}
+
+// The grouped kernel's queue and the CUDA-core kernels' queues for a policy.
+void order_items(const moa_batch_plan &pl, int policy, std::vector<BItem> &grouped, std::vector<BItem> &cc) {
     std::vector<int> idx(pl.items.size());
     for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
     auto by_cost = [&](int a, int b) { return pl.cost[a] > pl.cost[b]; };
-    std::vector<BItem> out;
-    out.reserve(idx.size());
+    std::stable_sort(idx.begin(), idx.end(), by_cost);
+    grouped.clear();
+    cc.clear();
+    std::vector<int> tc, ccs, other;
+    for (int i : idx) (pl.items[i].type == IT_TC ? tc : pl.items[i].type == IT_CC ? ccs : other).push_back(i);
     if (policy == 0) {
-        std::stable_sort(idx.begin(), idx.end(), by_cost);
-        for (int i : idx) out.push_back(pl.items[i]);
-    } else {
-        std::vector<int> tc, cc, other;
-        for (int i : idx) (pl.items[i].type == IT_TC ? tc : pl.items[i].type == IT_CC ? cc : other).push_back(i);
-        std::stable_sort(tc.begin(), tc.end(), by_cost);
-        std::stable_sort(cc.begin(), cc.end(), by_cost);
-        std::stable_sort(other.begin(), other.end(), by_cost);
-        if (policy == 1) {
-            for (int i : tc) out.push_back(pl.items[i]);
-            for (int i : cc) out.push_back(pl.items[i]);
-        } else {  // interleave tensor-core and CUDA-core items so both kinds of unit stay busy
-            size_t a = 0, b = 0;
-            while (a < tc.size() || b < cc.size()) {
-                if (a < tc.size()) out.push_back(pl.items[tc[a++]]);
-                if (b < cc.size()) out.push_back(pl.items[cc[b++]]);
-            }
+        for (int i : idx)
+            if (pl.items[i].type != IT_CC) grouped.push_back(pl.items[i]);
+    } else if (policy == 1) {
+        for (int i : tc) grouped.push_back(pl.items[i]);
+        for (int i : other) grouped.push_back(pl.items[i]);
+    } else {  // interleave tensor-core and CUDA-core items so both kinds of unit stay busy
+        size_t a = 0, b = 0;
+        while (a < tc.size() || b < ccs.size()) {
+            if (a < tc.size()) grouped.push_back(pl.items[tc[a++]]);
+            if (b < ccs.size()) grouped.push_back(pl.items[ccs[b++]]);
         }
-        for (int i : other) out.push_back(pl.items[i]);
+        for (int i : other) grouped.push_back(pl.items[i]);
+        return;
     }
-    return out;
+    for (int g = 0; g < kCcGroups; ++g)  // by kernel (operator, tile halves), longest first within each
+        for (int i : ccs)
+            if (cc_group(pl, pl.items[i]) == g) cc.push_back(pl.items[i]);
 }
 
 moa_status upload_order(moa_batch_plan *pl, int policy, cudaStream_t s) {
-    std::vector<BItem> ord = order_items(*pl, policy);
-    if (ord.empty()) return MOA_OK;
-    if (cudaMemcpyAsync(pl->d_items, ord.data(), ord.size() * sizeof(BItem), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    std::vector<BItem> grouped, cc;
+    order_items(*pl, policy, grouped, cc);
+    pl->n_grouped = (int)grouped.size();
+    pl->n_cc = (int)cc.size();
+    for (int g = 0; g < kCcGroups; ++g) pl->cc_cnt[g] = 0;
+    for (const BItem &it : cc) ++pl->cc_cnt[cc_group(*pl, it)];
+    for (int g = 0, off = 0; g < kCcGroups; ++g) pl->cc_off[g] = off, off += pl->cc_cnt[g];
+    if (!grouped.empty() && cudaMemcpyAsync(pl->d_items, grouped.data(), grouped.size() * sizeof(BItem),
+                                            cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return MOA_ERR_CUDA;
+    if (!cc.empty() &&
+        cudaMemcpyAsync(pl->d_cc_items, cc.data(), cc.size() * sizeof(BItem), cudaMemcpyHostToDevice, s) != cudaSuccess)
         return MOA_ERR_CUDA;
     return cudaStreamSynchronize(s) == cudaSuccess ? MOA_OK : MOA_ERR_CUDA;
 }
@@ -687,23 +767,46 @@ cudaError_t enqueue(moa_batch_plan *pl, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         attr = true;
     }
+    if (pl->n_grouped > 0 || pl->n_cc > 0) {
+        cudaError_t e = cudaMemsetAsync(pl->d_queue, 0, (1 + kCcGroups) * sizeof(int), s);
+        if (e != cudaSuccess) return e;
+    }
+    // one persistent kernel per (operator, occupied tile halves) present, each with its own queue
+    for (int g = 0; g < kCcGroups; ++g) {
+        const int cnt = pl->cc_cnt[g];
+        if (cnt == 0) continue;
+        const int grid = std::min(2 * sm_count_dev(), cnt);
+        const BItem *items = pl->d_cc_items + pl->cc_off[g];
+        int *queue = pl->d_queue + 1 + g;
+        const int q = g % 4;
+        switch (g / 4) {
+        case CC_MIN_PLUS: launch_cc_quad<sr::F32MinPlus>(q, grid, pl->d_inst, items, cnt, queue, s); break;
+        case CC_MAX_PLUS: launch_cc_quad<sr::F32MaxPlus>(q, grid, pl->d_inst, items, cnt, queue, s); break;
+        case CC_MIN_TIMES: launch_cc_quad<sr::F32MinTimes>(q, grid, pl->d_inst, items, cnt, queue, s); break;
+        case CC_MAX_TIMES: launch_cc_quad<sr::F32MaxTimes>(q, grid, pl->d_inst, items, cnt, queue, s); break;
+        default: launch_cc_quad<sr::F32PlusTimes>(q, grid, pl->d_inst, items, cnt, queue, s); break;
+        }
+    }
     if (pl->n_jobs > 0) {
         const int blocks = std::min(pl->n_jobs, sm_count_dev() * 8);
         batch_split_kernel<<<blocks, 256, 0, s>>>(pl->d_jobs, pl->n_jobs);
     }
-    if (pl->n_items > 0) {
-        cudaError_t e = cudaMemsetAsync(pl->d_queue, 0, sizeof(int), s);
-        if (e != cudaSuccess) return e;
-        BatchParams bp{pl->d_inst, pl->d_items, pl->n_items, pl->d_queue, pl->d_tmaps};
-        const int grid = std::min(sm_count_dev(), std::max(1, pl->n_items));
+    if (pl->n_grouped > 0) {
+        BatchParams bp{pl->d_inst, pl->d_items, pl->n_grouped, pl->d_queue, pl->d_tmaps};
+        const int grid = std::min(sm_count_dev(), std::max(1, pl->n_grouped));
         batch_grouped_kernel<<<grid, kThreads, SMEM, s>>>(bp);
     }
     return cudaGetLastError();
 }
 
 moa_status autotune(moa_batch_plan *pl, cudaStream_t s) {
+    const char *force = std::getenv("MOA_BATCH_SCHEDULE");  // a fixed schedule (0..kPolicies-1), no timing
+    if (force && force[0] >= '0' && force[0] < '0' + kPolicies && !force[1]) {
+        pl->policy = force[0] - '0';
+        return upload_order(pl, pl->policy, s);
+    }
     const int mode = tune_mode();
-    const std::string key = gpu_signature() + "|" + pl->signature;
+    const std::string key = gpu_signature() + "|s2|" + pl->signature;  // s2: the schedules listed at kPolicies
     if (mode == 0) {
         pl->policy = 0;
         return upload_order(pl, 0, s);
@@ -764,6 +867,7 @@ void plan_free(moa_batch_plan *pl) {
     if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
     cudaFree(pl->d_inst);
     cudaFree(pl->d_items);
+    cudaFree(pl->d_cc_items);
     cudaFree(pl->d_tmaps);
     cudaFree(pl->d_jobs);
     cudaFree(pl->d_queue);
@@ -875,9 +979,10 @@ moa_status moa_batch_plan_create(int count, const moa_problem *problems, moa_bat
     }
     bool ok = cudaMalloc(&pl->d_inst, std::max<size_t>(1, inst.size()) * sizeof(BInst)) == cudaSuccess &&
               cudaMalloc(&pl->d_items, std::max<size_t>(1, pl->items.size()) * sizeof(BItem)) == cudaSuccess &&
+              cudaMalloc(&pl->d_cc_items, std::max<size_t>(1, pl->items.size()) * sizeof(BItem)) == cudaSuccess &&
               cudaMalloc(&pl->d_tmaps, std::max<size_t>(1, tmaps.size()) * sizeof(CUtensorMap)) == cudaSuccess &&
               cudaMalloc(&pl->d_jobs, std::max<size_t>(1, jobs.size()) * sizeof(SplitJob)) == cudaSuccess &&
-              cudaMalloc(&pl->d_queue, sizeof(int)) == cudaSuccess;
+              cudaMalloc(&pl->d_queue, (1 + kCcGroups) * sizeof(int)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         plan_free(pl);
@@ -926,7 +1031,18 @@ moa_status moa_batch_plan_info(const moa_batch_plan *plan, int64_t *n_problems, 
                                double *work_flops) {
     if (!plan) return MOA_ERR_NULL;
     if (n_problems) *n_problems = plan->count;
-    if (n_launches) *n_launches = (plan->n_jobs > 0 ? 1 : 0) + (plan->n_items > 0 ? 1 : 0);
+    if (n_launches) {  // before the first execute: the default schedule (CUDA-core items in their own kernel)
+        int64_t cc = 0;
+        for (const BItem &it : plan->items) cc += it.type == IT_CC;
+        const bool sep = plan->policy != 2;
+        const int64_t grouped = sep ? plan->n_items - cc : plan->n_items;
+        bool used[kCcGroups] = {};  // one CUDA-core kernel per (operator, tile halves) present
+        for (const BItem &it : plan->items)
+            if (it.type == IT_CC) used[cc_group(*plan, it)] = true;
+        int ops = 0;
+        for (bool u : used) ops += u;
+        *n_launches = (plan->n_jobs > 0 ? 1 : 0) + (grouped > 0 ? 1 : 0) + (sep ? ops : 0);
+    }
     if (n_tiles) *n_tiles = plan->n_items;
     if (work_flops) *work_flops = plan->work;
     return MOA_OK;

@@ -60,7 +60,7 @@ def test_batch_small_all_problems():
     plan = moa.moa_batch_plan_create(arr)
     try:
         info = moa.moa_batch_plan_info(plan)
-        assert info["problems"] == 400 and info["launches"] <= 2
+        assert info["problems"] == 400 and info["launches"] <= 2 + 4  # split, grouped, (min,+) by tile halves
         moa.moa_batch_execute(plan)
         torch.cuda.synchronize()
         first = dout.cpu().numpy()
@@ -93,6 +93,53 @@ def test_batch_full_10000_sampled():
     kinds = [probs[i]["kind"] for i in which]
     assert "outer" in kinds and "minplus" in kinds and "bf16x3" in kinds
     _check(probs, pool, oa, ob, od, out, which)
+    check_status()
+
+
+@pytest.mark.parametrize("schedule", ["0", "1", "2"])
+def test_batch_every_cuda_core_operator_and_schedule(schedule, monkeypatch):
+    """Every CUDA-core (reduce, combine) of the batch, tiles with one, two or
+    four occupied halves and several tiles per problem, under each schedule
+    (CUDA-core items in their own kernels, or inside the grouped kernel)."""
+    import torch
+    monkeypatch.setenv("MOA_BATCH_SCHEDULE", schedule)
+    ops = [("min", "add", "tropical"), ("max", "add", "tropical"), ("min", "mul", "maxmul"), ("max", "mul", "maxmul"),
+           ("add", "mul", "maxmul")]
+    shapes = [((40, 33), (33, 50)), ((100, 70), (70, 30)), ((20, 90), (90, 200)), ((300, 17), (17, 140)),
+              ((1, 5), (5, 1))]
+    cases, chunks, off = [], [], 0
+    for t, (red, comb, kind) in enumerate(ops):
+        for u, (sa, sb) in enumerate(shapes):
+            A, B = synth.semiring_inputs(kind, seed=40 + 5 * t + u, shape_a=sa, shape_b=sb)
+            cases.append((red, comb, A, B, off))
+            chunks += [A.ravel(), B.ravel()]
+            off += A.size + B.size
+    pool = np.concatenate(chunks).astype(np.float32)
+    dpool = torch.from_numpy(pool).cuda()
+    n_out = sum(c[2].shape[0] * c[3].shape[1] for c in cases)
+    dout = torch.full((n_out,), float("nan"), dtype=torch.float32, device="cuda")
+    specs, outs, o = [], [], 0
+    for red, comb, A, B, a_off in cases:
+        base = dpool.data_ptr()
+        specs.append(dict(kind="inner", reduce=red, combine=comb, shapeA=A.shape, shapeB=B.shape, A=base + 4 * a_off,
+                          B=base + 4 * (a_off + A.size), out=dout.data_ptr() + 4 * o))
+        outs.append(o)
+        o += A.shape[0] * B.shape[1]
+    arr, keep = moa.make_problems(specs)
+    plan = moa.moa_batch_plan_create(arr)
+    try:
+        moa.moa_batch_execute(plan)
+        torch.cuda.synchronize()
+        got = dout.cpu().numpy()
+    finally:
+        moa.moa_batch_plan_destroy(plan)
+    for (red, comb, A, B, _), o in zip(cases, outs):
+        D = got[o:o + A.shape[0] * B.shape[1]].reshape(A.shape[0], B.shape[1])
+        if red == "add":
+            ref, S = oracle.inner_dot2(A.astype(np.float64), B.astype(np.float64))
+            assert oracle.normalised_error(D, ref, S) <= 2e-6, (red, comb, A.shape, B.shape)
+        else:
+            assert np.array_equal(D, oracle.inner_f32(red, comb, A, B)), (red, comb, A.shape, B.shape)
     check_status()
 
 
