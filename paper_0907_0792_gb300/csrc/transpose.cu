@@ -87,9 +87,21 @@ __global__ void __launch_bounds__(256, 4) copy_rows(const U *__restrict__ in, U 
     if (r >= r1) return;
     Odometer od;
     od.start(o, r);
-    for (;;) {
-        for (int64_t k = lane; k < n; k += W) out[od.out_off + k] = __ldg(in + od.in_off + k);
-        r += R;
+    for (;;) {  // two rows per pass: both rows' loads in flight before the stores
+        const bool two = r + R < r1;
+        const int64_t i0 = od.in_off, o0 = od.out_off;
+        if (two) od.advance(o, R);
+        for (int64_t k = lane; k < n; k += W) {
+            const U v0 = __ldg(in + i0 + k);
+            if (two) {
+                const U v1 = __ldg(in + od.in_off + k);
+                out[o0 + k] = v0;
+                out[od.out_off + k] = v1;
+            } else {
+                out[o0 + k] = v0;
+            }
+        }
+        r += 2 * R;
         if (r >= r1) break;
         od.advance(o, R);
     }
