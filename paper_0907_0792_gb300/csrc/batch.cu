@@ -31,6 +31,7 @@
 // status word.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <sys/stat.h>
 
 #include <algorithm>
 #include <cstdio>
@@ -847,13 +848,8 @@ moa_status autotune(moa_batch_plan *pl, cudaStream_t s) {
     {
         const std::string path = tune_cache_path();
         const size_t slash = path.find_last_of('/');
-        if (slash != std::string::npos) {
-            std::string dir = path.substr(0, slash);
-            std::string cmd = dir;  // create the cache directory if missing (best effort)
-            (void)cmd;
-            std::FILE *test = std::fopen(path.c_str(), "a");
-            if (test) std::fclose(test);
-        }
+        if (slash != std::string::npos && slash > 0)  // the cache directory, if missing (best effort)
+            mkdir(path.substr(0, slash).c_str(), 0755);
         std::ofstream f(path, std::ios::app);
         if (f) f << key << " " << best_pol << " " << best * 1000.0 << "\n";
     }
