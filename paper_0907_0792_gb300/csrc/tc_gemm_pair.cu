@@ -123,6 +123,7 @@ struct PairParams {
     int64_t ldd;
     int vec_store;
     int tma_store;  // D written through per-warp staging tiles and TMA stores
+    int d_evict_first;  // those stores under an evict-first L2 policy (D is not re-read)
     uint32_t *bits_out;  // store mode: write [D > 0] as the packed bit stream (N % 32 == 0) instead of D
     int i32_out;  // store mode: D holds int32 (every accumulator an exact integer, |x| <= 2^24)
     // Ozaki mode (ozaki_epi.cuh)
@@ -396,7 +397,10 @@ __global__ void __launch_bounds__(threads(MODE), 1)
                 ptx::fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) {
-                    ptx::tma_store_3d(&tmD, stg, (int)col0, (int)(row - lane), 0);
+                    if (p.d_evict_first)
+                        ptx::tma_store_3d_hint(&tmD, stg, (int)col0, (int)(row - lane), 0, ptx::policy_evict_first());
+                    else
+                        ptx::tma_store_3d(&tmD, stg, (int)col0, (int)(row - lane), 0);
                     ptx::bulk_commit();
                 }
                 return;
@@ -575,6 +579,19 @@ static bool tma_store_enabled() {
     return v == 1;
 }
 
+// D goes out through the TMA stores under an evict-first L2 policy, so the
+// stream of results does not push the A and B panels out of L2 (measured:
+// bf16 8192 x 256 x 16384 +11 %, 8192 x 512 x 8192 +6 %, 8192^3 unchanged);
+// MOA_D_EVICT_FIRST=0 stores with the default policy.
+static int d_evict_first() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = std::getenv("MOA_D_EVICT_FIRST");
+        v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v;
+}
+
 bool pair_mma_enabled() {
     static int v = -1;
     if (v < 0) {
@@ -621,6 +638,7 @@ cudaError_t tc_gemm_pair_fp8_launch(const uint8_t *A8, int64_t lda, const uint8_
     std::memset(&td, 0, sizeof(td));
     p.bits_out = bits_out;
     p.tma_store = bits_out ? 0 : d_tmap(&td, D, ldd, M, N);
+    p.d_evict_first = d_evict_first();
     return launch_pair<MODE_FP8>(ta, tb, td, tsa, tsb, p, s);
 }
 
@@ -638,6 +656,7 @@ cudaError_t tc_gemm_pair_launch(const CUtensorMap &ta, const CUtensorMap &tb, in
     p.vec_store = ((uintptr_t)D % 16 == 0) && (ldd % 4 == 0);
     CUtensorMap td;
     p.tma_store = d_tmap(&td, D, ldd, M, N);
+    p.d_evict_first = d_evict_first();
     return promote ? launch_pair<MODE_PROMOTE>(ta, tb, td, td, td, p, s) : launch_pair<MODE_STORE>(ta, tb, td, td, td, p, s);
 }
 

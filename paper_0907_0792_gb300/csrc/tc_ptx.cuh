@@ -111,6 +111,18 @@ MOA_DEV void tma_store_3d(const CUtensorMap *m, uint32_t src, int c0, int c1, in
                  "r"(src), "r"(c0), "r"(c1), "r"(c2)
                  : "memory");
 }
+// The same with an L2 cache policy (createpolicy) for the written lines.
+MOA_DEV void tma_store_3d_hint(const CUtensorMap *m, uint32_t src, int c0, int c1, int c2, uint64_t policy) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group.L2::cache_hint [%0, {%2, %3, %4}], [%1], %5;"
+                 ::"l"((uint64_t)m), "r"(src), "r"(c0), "r"(c1), "r"(c2), "l"(policy)
+                 : "memory");
+}
+// L2 policy: lines written under it are the first candidates for eviction.
+MOA_DEV uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
 MOA_DEV void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // This thread's bulk stores have finished reading shared memory.
 MOA_DEV void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
