@@ -17,6 +17,7 @@
 // each bf16 plane, rows padded to a multiple of 8 elements (16 bytes) so the
 // planes meet the TMA stride rule.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -34,23 +35,41 @@ template <typename Tin> MOA_DEV float to_f32(Tin x) { return (float)x; }
 template <> MOA_DEV float to_f32<__nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
 
 // X: rows x cols (row stride cols); out: NPL planes of rows x colsp, plane
-// stride plane_elems; columns cols..colsp-1 are zero.
-template <typename Tin, int NPL>
+// stride plane_elems; columns cols..colsp-1 are zero.  Four consecutive
+// columns per thread (colsp is a multiple of 8): one 16-byte load when the
+// rows allow it (VEC) and one 8-byte store per plane.
+template <typename Tin, int NPL, bool VEC>
 __global__ void __launch_bounds__(256) split_planes(const Tin *__restrict__ X, int64_t rows, int64_t cols, int64_t colsp,
                                                      __nv_bfloat16 *__restrict__ out, int64_t plane_elems) {
+    const int64_t groups = colsp / 4;
     for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
         const Tin *src = X + r * cols;
         __nv_bfloat16 *dst = out + r * colsp;
-        for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < colsp; c += (int64_t)gridDim.x * blockDim.x) {
-            const float x = c < cols ? to_f32(src[c]) : 0.0f;
-            const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-            dst[c] = hi;
-            if (NPL > 1) {
-                const float r1 = __fsub_rn(x, __bfloat162float(hi));  // exact
-                const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
-                dst[plane_elems + c] = mid;
-                if (NPL > 2) dst[2 * plane_elems + c] = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(mid)));
+        for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t c = 4 * g;
+            float x[4];
+            if constexpr (VEC) {  // float rows, cols % 4 == 0, 16-byte aligned: the group is all in or all out
+                const float4 v = c < cols ? __ldg(reinterpret_cast<const float4 *>(src + c)) : make_float4(0, 0, 0, 0);
+                x[0] = v.x, x[1] = v.y, x[2] = v.z, x[3] = v.w;
+            } else {
+#pragma unroll
+                for (int t = 0; t < 4; ++t) x[t] = c + t < cols ? to_f32(src[c + t]) : 0.0f;
             }
+            __align__(8) __nv_bfloat16 pl[NPL][4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const __nv_bfloat16 hi = __float2bfloat16_rn(x[t]);
+                pl[0][t] = hi;
+                if constexpr (NPL > 1) {
+                    const float r1 = __fsub_rn(x[t], __bfloat162float(hi));  // exact
+                    const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+                    pl[1][t] = mid;
+                    if constexpr (NPL > 2) pl[2][t] = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(mid)));
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < NPL; ++q)
+                *reinterpret_cast<uint2 *>(dst + q * plane_elems + c) = *reinterpret_cast<const uint2 *>(pl[q]);
         }
     }
 }
@@ -104,9 +123,16 @@ cudaError_t run_i8range(const int32_t *X, int64_t rows, int64_t cols, int64_t co
 template <typename Tin, int NPL>
 cudaError_t run_split(const Tin *X, int64_t rows, int64_t cols, int64_t colsp, __nv_bfloat16 *out, cudaStream_t s) {
     if (rows == 0 || colsp == 0) return cudaSuccess;
-    const int64_t gx = colsp >= 256 * 4 ? 4 : (colsp + 255) / 256;
+    const int64_t groups = colsp / 4;
+    const int64_t gx = groups >= 256 * 4 ? 4 : (groups + 255) / 256;
     int64_t gy = rows < 2048 ? rows : 2048;
-    split_planes<Tin, NPL><<<dim3((unsigned)gx, (unsigned)gy), 256, 0, s>>>(X, rows, cols, colsp, out, rows * colsp);
+    const dim3 grid((unsigned)gx, (unsigned)gy);
+    bool vec = false;
+    if constexpr (std::is_same<Tin, float>::value) {
+        vec = cols % 4 == 0 && (uintptr_t)X % 16 == 0;
+        if (vec) split_planes<Tin, NPL, true><<<grid, 256, 0, s>>>(X, rows, cols, colsp, out, rows * colsp);
+    }
+    if (!vec) split_planes<Tin, NPL, false><<<grid, 256, 0, s>>>(X, rows, cols, colsp, out, rows * colsp);
     return cudaGetLastError();
 }
 
