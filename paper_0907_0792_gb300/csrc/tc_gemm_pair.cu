@@ -418,40 +418,6 @@ __global__ void __launch_bounds__(threads(MODE), 1)
                     if (col0 + j < p.N) dst[j] = __uint_as_float(v[j]);
             }
         };
-        // Two 32 x 32 pieces (columns col0 and col0 + 32) through the warp's two
-        // staging tiles (w and w + 4; 4 epilogue warps leave room for both) with
-        // one proxy fence and one bulk group: half the fences of store32.
-        auto store64 = [&](int64_t row, int64_t col0, const uint32_t (&v0)[32], const uint32_t (&v1)[32], bool two) {
-            if (col0 >= p.N || row - lane >= p.M) return;  // warp-uniform
-            const bool second = two && col0 + 32 < p.N;
-            const uint32_t stg1 = stg + 4u * STG_BYTES;
-            if (lane == 0) ptx::bulk_wait_read0();  // the previous stores have left both staging tiles
-            __syncwarp();
-            const uint32_t sw = (uint32_t)lane * 128u;
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                ptx::st_shared_v4(stg + sw + ((uint32_t)(j ^ (lane & 7)) << 4), v0[4 * j], v0[4 * j + 1], v0[4 * j + 2],
-                                  v0[4 * j + 3]);
-            if (second) {
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    ptx::st_shared_v4(stg1 + sw + ((uint32_t)(j ^ (lane & 7)) << 4), v1[4 * j], v1[4 * j + 1],
-                                      v1[4 * j + 2], v1[4 * j + 3]);
-            }
-            ptx::fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) {
-                const uint64_t pol = ptx::policy_evict_first();
-                if (p.d_evict_first) {
-                    ptx::tma_store_3d_hint(&tmD, stg, (int)col0, (int)(row - lane), 0, pol);
-                    if (second) ptx::tma_store_3d_hint(&tmD, stg1, (int)col0 + 32, (int)(row - lane), 0, pol);
-                } else {
-                    ptx::tma_store_3d(&tmD, stg, (int)col0, (int)(row - lane), 0);
-                    if (second) ptx::tma_store_3d(&tmD, stg1, (int)col0 + 32, (int)(row - lane), 0);
-                }
-                ptx::bulk_commit();
-            }
-        };
         bool ok = true;
         for (int t = cfirst; t < num_tiles && ok; t += cstride) {
             int tm, tn;
@@ -528,36 +494,22 @@ __global__ void __launch_bounds__(threads(MODE), 1)
                 if (!wait_acc()) break;
                 const uint32_t tb = lanes + (uint32_t)(abuf * ACC_STRIDE);
 #pragma unroll 1
-                for (int c = 0; c < HC; c += 64) {  // 64 columns a pass (the FP8 mode's last pass: 32)
-                    const bool two = c + 32 < HC;
-                    uint32_t r0[32], r1[32];
-                    ptx::tmem_ld32(tb + c, r0);
-                    if (two) ptx::tmem_ld32(tb + c + 32, r1);
+                for (int c = 0; c < HC; c += 32) {
+                    uint32_t r[32];
+                    ptx::tmem_ld32(tb + c, r);
                     ptx::tmem_ld_wait();
                     if (p.bits_out) {  // 32 columns of one row -> one word of the bit stream
                         const int64_t col0 = colh + c;
-                        uint32_t w0 = 0u, w1 = 0u;
+                        uint32_t word = 0u;
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            w0 |= (__uint_as_float(r0[j]) > 0.0f ? 1u : 0u) << j;
-                            w1 |= (__uint_as_float(r1[j]) > 0.0f ? 1u : 0u) << j;
-                        }
-                        if (row < p.M && col0 < p.N) p.bits_out[(row * p.N + col0) >> 5] = w0;
-                        if (two && row < p.M && col0 + 32 < p.N) p.bits_out[(row * p.N + col0 + 32) >> 5] = w1;
+                        for (int j = 0; j < 32; ++j) word |= (__uint_as_float(r[j]) > 0.0f ? 1u : 0u) << j;
+                        if (row < p.M && col0 < p.N) p.bits_out[(row * p.N + col0) >> 5] = word;
                     } else {
                         if (p.i32_out) {
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) {
-                                r0[j] = (uint32_t)__float2int_rn(__uint_as_float(r0[j]));
-                                r1[j] = (uint32_t)__float2int_rn(__uint_as_float(r1[j]));
-                            }
+                            for (int j = 0; j < 32; ++j) r[j] = (uint32_t)__float2int_rn(__uint_as_float(r[j]));
                         }
-                        if (p.tma_store) {
-                            store64(row, colh + c, r0, r1, two);
-                        } else {
-                            store32(row, colh + c, r0);
-                            if (two) store32(row, colh + c + 32, r1);
-                        }
+                        store32(row, colh + c, r);
                     }
                 }
                 release_acc();
