@@ -86,7 +86,9 @@ constexpr int A_BYTES = BM * BK * 2, B_BYTES = BK * BN * 2, STAGE_BYTES = A_BYTE
 constexpr int CC_BK = 16, CC_PAD = 4, CC_LD = 128 + CC_PAD;
 constexpr int CC_BYTES = 2 * 2 * CC_BK * CC_LD * 4;  // As[2][16][132] + Bs[2][16][132]
 constexpr int NBARS = 2 * STAGES + 5 + 2 * RING;
-constexpr int SMEM = STAGES * STAGE_BYTES + CC_BYTES + 1024 + 1024;
+constexpr int TC_STG_FLOATS = 32 * 33;                  // an epilogue warp's 32 x 32 staging slice (padded rows)
+constexpr int TC_STG_BYTES = kEpiWarps * TC_STG_FLOATS * 4;
+constexpr int SMEM = STAGES * STAGE_BYTES + CC_BYTES + 1024 + TC_STG_BYTES + 1024;
 constexpr int TMEM_COLS = 2 * BN;
 constexpr uint32_t IDESC = ptx::idesc_bf16_f32(BM, BN, 1);
 // split-BF16x3 terms (plane of A, plane of B): small products first, hi*hi last
@@ -240,6 +242,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     float *ccA = (float *)(smem + STAGES * STAGE_BYTES);
     float *ccB = ccA + 2 * CC_BK * CC_LD;
     uint64_t *bars = (uint64_t *)(smem + STAGES * STAGE_BYTES + CC_BYTES);
+    float *tcstg = (float *)(smem + STAGES * STAGE_BYTES + CC_BYTES + 1024);  // TC epilogue staging, per warp
     uint32_t *tmem_slot = (uint32_t *)(bars + NBARS);
     volatile uint32_t *abort_flag = tmem_slot + 1;
     volatile int *ring = (volatile int *)(tmem_slot + 2);
@@ -428,17 +431,25 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (!abuf) aphase ^= 1u;
                 }
                 if (!ok) break;
-                const int64_t row = (int64_t)it.a * BM + q * 32 + lane;
+                // the warp's 32 rows x HC columns leave through its own shared-memory
+                // slice, 32 columns at a time, so that every store instruction writes
+                // 32 consecutive columns of one row (128 contiguous bytes)
+                const int64_t row0 = (int64_t)it.a * BM + q * 32;
                 const int64_t col0 = (int64_t)it.b * BN + half * HC;
-                if (row < in.M) {
-                    float *dst = in.D + row * in.N + col0;
-                    if (in.vec && col0 + HC <= in.N) {
+                const int rows_here = (int)min((int64_t)32, in.M - row0);
+                float *sl = tcstg + (warp - 2) * TC_STG_FLOATS;
+                if (rows_here > 0) {
 #pragma unroll
-                        for (int j = 0; j < HC; j += 4) *reinterpret_cast<float4 *>(dst + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
-                    } else {
+                    for (int c = 0; c < HC; c += 32) {
 #pragma unroll
-                        for (int j = 0; j < HC; ++j)
-                            if (col0 + j < in.N) dst[j] = acc[j];
+                        for (int j = 0; j < 32; ++j) sl[lane * 33 + j] = acc[c + j];
+                        __syncwarp();
+                        const int64_t gcol = col0 + c + lane;
+                        if (gcol < in.N) {
+                            float *dst = in.D + row0 * in.N + gcol;
+                            for (int r = 0; r < rows_here; ++r) dst[r * in.N] = sl[r * 33 + lane];
+                        }
+                        __syncwarp();
                     }
                 }
             } else if (it.type == IT_CC) {
