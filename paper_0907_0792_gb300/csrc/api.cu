@@ -54,12 +54,11 @@ static moa_status from_cuda(cudaError_t e) { return e == cudaSuccess ? MOA_OK : 
 // Fault injection for tests: MOA_FAULT_INJECT=workspace makes every
 // workspace allocation fail (read once per process).
 static bool inject_workspace_failure() {
-    static int v = -1;
-    if (v < 0) {
+    static const bool on = [] {  // read once, thread-safe
         const char *e = std::getenv("MOA_FAULT_INJECT");
-        v = (e && std::strcmp(e, "workspace") == 0) ? 1 : 0;
-    }
-    return v == 1;
+        return e && std::strcmp(e, "workspace") == 0;
+    }();
+    return on;
 }
 
 // ------------------------------------------------------------- workspace

@@ -773,11 +773,15 @@ moa_status upload_order(moa_batch_plan *pl, int policy, cudaStream_t s) {
 
 // The work of one execute, enqueued on s (also what the graph captures).
 cudaError_t enqueue(moa_batch_plan *pl, cudaStream_t s) {
+    static std::mutex attr_mu;  // the grouped kernel's shared-memory attribute, set once (retried on failure)
     static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(batch_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-        if (e != cudaSuccess) return e;
-        attr = true;
+    {
+        std::lock_guard<std::mutex> lk(attr_mu);
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(batch_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
     }
     if (pl->n_grouped > 0 || pl->n_cc > 0) {
         cudaError_t e = cudaMemsetAsync(pl->d_queue, 0, (1 + kCcGroups) * sizeof(int), s);

@@ -124,12 +124,11 @@ int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
 
 // Slices per operand for a contraction of length K (MOA_OZAKI_SLICES overrides, 4..10).
 int ozaki_slices(int64_t K) {
-    static int forced = -1;
-    if (forced < 0) {
+    static const int forced = [] {  // read once, thread-safe
         const char *e = std::getenv("MOA_OZAKI_SLICES");
-        forced = e ? std::atoi(e) : 0;
-        if (forced < 4 || forced > kMaxSlices) forced = 0;
-    }
+        const int v = e ? std::atoi(e) : 0;
+        return (v < 4 || v > kMaxSlices) ? 0 : v;
+    }();
     if (forced) return forced;
     return K <= 256 ? 10 : (K <= 2048 ? 9 : 8);
 }

@@ -501,22 +501,20 @@ __global__ void __launch_bounds__(cta_threads(MODE), 1)
 // ------------------------------------------------------------------ host
 // Cluster pairs with B multicast; MOA_CLUSTER_PAIRS=0 turns them off.
 bool cluster_pairs_enabled() {
-    static int v = -1;
-    if (v < 0) {
+    static const bool on = [] {  // read once, thread-safe
         const char *e = std::getenv("MOA_CLUSTER_PAIRS");
-        v = (e && e[0] == '0') ? 0 : 1;
-    }
-    return v == 1;
+        return !(e && e[0] == '0');
+    }();
+    return on;
 }
 
 int num_sms() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
+    static const int n = [] {
+        int dev = 0, v = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v > 0 ? v : 1;
+    }();
     return n;
 }
 
@@ -524,22 +522,31 @@ template <int BN, int STAGES, int MODE, int CL = 1>
 cudaError_t launch_tc(const CUtensorMap &ta, const CUtensorMap &tb, GemmParams &p, cudaStream_t s) {
     using C = Cfg<BN, STAGES, MODE>;
     auto kern = tc_gemm_bf16<BN, STAGES, MODE, CL>;
-    static int max_clusters = -1;
-    if (max_clusters < 0) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-        if (e != cudaSuccess) return e;
-        max_clusters = num_sms() / CL;
-        if (CL > 1) {
-            cudaLaunchConfig_t cfg = {};
-            cudaLaunchAttribute at[1];
-            at[0].id = cudaLaunchAttributeClusterDimension;
-            at[0].val.clusterDim.x = CL, at[0].val.clusterDim.y = 1, at[0].val.clusterDim.z = 1;
-            cfg.gridDim = dim3(CL * max_clusters), cfg.blockDim = dim3(cta_threads(MODE)), cfg.dynamicSmemBytes = C::SMEM;
-            cfg.attrs = at, cfg.numAttrs = 1;
-            int n = 0;
-            if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n > 0 && n < max_clusters) max_clusters = n;
-            cudaGetLastError();
+    // shared-memory attribute and resident clusters, set up once per process
+    // (under a lock, so concurrent first calls agree; a failure is retried)
+    static std::mutex mu;
+    static int cached = 0;
+    int max_clusters;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!cached) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+            if (e != cudaSuccess) return e;
+            int mc = num_sms() / CL;
+            if (CL > 1) {
+                cudaLaunchConfig_t cfg = {};
+                cudaLaunchAttribute at[1];
+                at[0].id = cudaLaunchAttributeClusterDimension;
+                at[0].val.clusterDim.x = CL, at[0].val.clusterDim.y = 1, at[0].val.clusterDim.z = 1;
+                cfg.gridDim = dim3(CL * mc), cfg.blockDim = dim3(cta_threads(MODE)), cfg.dynamicSmemBytes = C::SMEM;
+                cfg.attrs = at, cfg.numAttrs = 1;
+                int n = 0;
+                if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n > 0 && n < mc) mc = n;
+                cudaGetLastError();
+            }
+            cached = mc;
         }
+        max_clusters = cached;
     }
     p.tiles_m = (p.M + BM - 1) / BM;
     p.tiles_n = (p.N + BN - 1) / BN;

@@ -39,6 +39,7 @@
 
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 #include "internal.h"
@@ -528,13 +529,12 @@ __global__ void __launch_bounds__(threads(MODE), 1)
 }
 
 int pair_sms() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
+    static const int n = [] {  // read once, thread-safe
+        int dev = 0, v = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 2;
-    }
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v > 0 ? v : 2;
+    }();
     return n;
 }
 
@@ -542,21 +542,30 @@ template <int MODE>
 cudaError_t launch_pair(const CUtensorMap &ta, const CUtensorMap &tb, const CUtensorMap &td, const CUtensorMap &tsa,
                         const CUtensorMap &tsb, PairParams &p, cudaStream_t s) {
     auto kern = tc_gemm_pair<MODE>;
-    static int max_clusters = -1;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = 2, at[0].val.clusterDim.y = 1, at[0].val.clusterDim.z = 1;
     cfg.blockDim = dim3(threads(MODE)), cfg.dynamicSmemBytes = smem_bytes(MODE);
     cfg.attrs = at, cfg.numAttrs = 1;
-    if (max_clusters < 0) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(MODE));
-        if (e != cudaSuccess) return e;
-        max_clusters = pair_sms() / 2;
-        cfg.gridDim = dim3(2 * max_clusters);
-        int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n > 0 && n < max_clusters) max_clusters = n;
-        cudaGetLastError();
+    // shared-memory attribute and resident clusters, set up once per process
+    // (under a lock, so concurrent first calls agree; a failure is retried)
+    static std::mutex mu;
+    static int cached = 0;
+    int max_clusters;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!cached) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(MODE));
+            if (e != cudaSuccess) return e;
+            int mc = pair_sms() / 2;
+            cfg.gridDim = dim3(2 * mc);
+            int n = 0;
+            if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n > 0 && n < mc) mc = n;
+            cudaGetLastError();
+            cached = mc;
+        }
+        max_clusters = cached;
     }
     p.tiles_m = (p.M + 2 * BM - 1) / (2 * BM);
     p.tiles_n = (p.N + bn(MODE) - 1) / bn(MODE);
@@ -571,12 +580,11 @@ cudaError_t launch_pair(const CUtensorMap &ta, const CUtensorMap &tb, const CUte
 
 // MOA_TMA_STORE=0 makes the epilogue store D directly from registers.
 static bool tma_store_enabled() {
-    static int v = -1;
-    if (v < 0) {
+    static const bool on = [] {  // read once, thread-safe
         const char *e = std::getenv("MOA_TMA_STORE");
-        v = (e && e[0] == '0') ? 0 : 1;
-    }
-    return v == 1;
+        return !(e && e[0] == '0');
+    }();
+    return on;
 }
 
 // D goes out through the TMA stores under an evict-first L2 policy, so the
@@ -584,21 +592,19 @@ static bool tma_store_enabled() {
 // bf16 8192 x 256 x 16384 +11 %, 8192 x 512 x 8192 +6 %, 8192^3 unchanged);
 // MOA_D_EVICT_FIRST=0 stores with the default policy.
 static int d_evict_first() {
-    static int v = -1;
-    if (v < 0) {
+    static const int on = [] {
         const char *e = std::getenv("MOA_D_EVICT_FIRST");
-        v = (e && e[0] == '0') ? 0 : 1;
-    }
-    return v;
+        return (e && e[0] == '0') ? 0 : 1;
+    }();
+    return on;
 }
 
 bool pair_mma_enabled() {
-    static int v = -1;
-    if (v < 0) {
+    static const bool on = [] {
         const char *e = std::getenv("MOA_PAIR_MMA");
-        v = (e && e[0] == '0') ? 0 : 1;
-    }
-    return v == 1;
+        return !(e && e[0] == '0');
+    }();
+    return on;
 }
 
 // D's tensor map for TMA stores (16-byte aligned base and row stride); false
