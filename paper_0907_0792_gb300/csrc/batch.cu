@@ -494,11 +494,9 @@ __global__ void __launch_bounds__(256) batch_split_kernel(const SplitJob *__rest
         const int gpr = (int)(jb.colsp / 4);  // colsp < 2^31 (checked at plan creation)
         const int count = (int)((jb.r1 - jb.r0) * gpr);  // <= ~16K + one row
         const bool vec = (jb.cols & 3) == 0 && ((uintptr_t)jb.src & 15) == 0;
-        for (int e = threadIdx.x; e < count; e += blockDim.x) {
+        auto load = [&](int e, float (&x)[4]) {
             const int rr = e / gpr, c = (e - rr * gpr) * 4;
-            const int64_t r = jb.r0 + rr;
-            const float *src = jb.src + r * jb.cols + c;
-            float x[4];
+            const float *src = jb.src + (jb.r0 + rr) * jb.cols + c;
             if (vec) {
                 const float4 v = c < jb.cols ? __ldg(reinterpret_cast<const float4 *>(src)) : make_float4(0, 0, 0, 0);
                 x[0] = v.x, x[1] = v.y, x[2] = v.z, x[3] = v.w;
@@ -506,6 +504,9 @@ __global__ void __launch_bounds__(256) batch_split_kernel(const SplitJob *__rest
 #pragma unroll
                 for (int t = 0; t < 4; ++t) x[t] = c + t < jb.cols ? __ldg(src + t) : 0.0f;
             }
+        };
+        auto split_store = [&](int e, const float (&x)[4]) {
+            const int rr = e / gpr, c = (e - rr * gpr) * 4;
             __align__(8) __nv_bfloat16 hi[4], mid[4], lo[4];
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
@@ -514,10 +515,19 @@ __global__ void __launch_bounds__(256) batch_split_kernel(const SplitJob *__rest
                 mid[t] = __float2bfloat16_rn(r1);
                 lo[t] = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(mid[t])));
             }
-            __nv_bfloat16 *dst = jb.dst + r * jb.colsp + c;
+            __nv_bfloat16 *dst = jb.dst + (jb.r0 + rr) * jb.colsp + c;
             *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(hi);
             *reinterpret_cast<uint2 *>(dst + jb.plane) = *reinterpret_cast<const uint2 *>(mid);
             *reinterpret_cast<uint2 *>(dst + 2 * jb.plane) = *reinterpret_cast<const uint2 *>(lo);
+        };
+        // two groups per pass, both loads in flight before the stores
+        for (int e = threadIdx.x; e < count; e += 2 * blockDim.x) {
+            const int e1 = e + blockDim.x;
+            float x0[4], x1[4];
+            load(e, x0);
+            if (e1 < count) load(e1, x1);
+            split_store(e, x0);
+            if (e1 < count) split_store(e1, x1);
         }
     }
 }
