@@ -18,11 +18,12 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "transpose_plan.h"
 
 namespace moa {
 namespace {
 
-constexpr int kMaxDims = 8;
+constexpr int kMaxDims = kTransposeMaxDims;
 
 // Independent axes (outer loop) with their input and output strides.
 struct Outer {
@@ -182,57 +183,24 @@ cudaError_t run(const void *in, void *out, Outer o, bool rows_case, int64_t nb, 
 
 cudaError_t launch_transpose(size_t elem_bytes, int rank, const int64_t *shape, const int *perm, const void *in,
                              void *out, cudaStream_t s) {
-    int64_t total = 1;
-    for (int k = 0; k < rank; ++k) total *= shape[k];
-    if (total == 0) return cudaSuccess;
-    // input axes with extent > 1, in output order; an axis that follows the
-    // previous one in the input too (extent-1 axes between them aside)
-    // merges into it
-    int64_t ext[kMaxDims];   // merged axes, output order
-    int first[kMaxDims], last[kMaxDims];  // their first and last input axes
-    int n = 0;
-    for (int k = 0; k < rank; ++k) {
-        const int a = perm[k];
-        if (shape[a] == 1) continue;
-        if (n > 0) {
-            int nxt = last[n - 1] + 1;
-            while (nxt < rank && shape[nxt] == 1) ++nxt;
-            if (nxt == a) {
-                ext[n - 1] *= shape[a];
-                last[n - 1] = a;
-                continue;
-            }
-        }
-        ext[n] = shape[a], first[n] = last[n] = a, ++n;
+    TransposePlan pl;
+    if (!plan_transpose(rank, shape, perm, &pl)) return cudaErrorInvalidValue;
+    if (pl.total == 0) return cudaSuccess;
+    if (pl.n <= 1) return cudaMemcpyAsync(out, in, (size_t)pl.total * elem_bytes, cudaMemcpyDeviceToDevice, s);
+    Outer o;  // every merged axis but the two the kernels walk
+    int64_t nb = 1;
+    for (int k = 0; k < pl.n; ++k) {
+        if (k == pl.xin || k == pl.yout) continue;
+        o.ext[o.nd] = pl.ext[k], o.is[o.nd] = pl.is[k], o.os[o.nd] = pl.os[k], ++o.nd;
+        nb *= pl.ext[k];
     }
-    if (n == 0) return cudaMemcpyAsync(out, in, elem_bytes, cudaMemcpyDeviceToDevice, s);
-    // the merged axes in input order give the input strides
-    int order[kMaxDims];
-    for (int k = 0; k < n; ++k) order[k] = k;
-    std::sort(order, order + n, [&](int x, int y) { return first[x] < first[y]; });
-    int64_t is[kMaxDims], os[kMaxDims];
-    int64_t st = 1;
-    for (int k = n - 1; k >= 0; --k) is[order[k]] = st, st *= ext[order[k]];
-    st = 1;
-    for (int k = n - 1; k >= 0; --k) os[k] = st, st *= ext[k];
-    if (n == 1) return cudaMemcpyAsync(out, in, (size_t)total * elem_bytes, cudaMemcpyDeviceToDevice, s);
-
-    const int xin = order[n - 1];  // merged axis innermost in the input
-    const int yout = n - 1;        // merged axis innermost in the output
-    Outer o;
-    bool rows_case = xin == yout;
-    int64_t nb = 1, nx = ext[xin], ny = rows_case ? 1 : ext[yout];
-    for (int k = 0; k < n; ++k) {
-        if (k == xin || k == yout) continue;
-        o.ext[o.nd] = ext[k], o.is[o.nd] = is[k], o.os[o.nd] = os[k], ++o.nd;
-        nb *= ext[k];
-    }
-    const int64_t isy = rows_case ? 0 : is[yout], osx = os[xin];
+    const int64_t nx = pl.ext[pl.xin], ny = pl.rows_case ? 1 : pl.ext[pl.yout];
+    const int64_t isy = pl.rows_case ? 0 : pl.is[pl.yout], osx = pl.os[pl.xin];
     switch (elem_bytes) {
-    case 1: return run<uint8_t>(in, out, o, rows_case, nb, nx, ny, isy, osx, s);
-    case 2: return run<uint16_t>(in, out, o, rows_case, nb, nx, ny, isy, osx, s);
-    case 4: return run<uint32_t>(in, out, o, rows_case, nb, nx, ny, isy, osx, s);
-    case 8: return run<uint64_t>(in, out, o, rows_case, nb, nx, ny, isy, osx, s);
+    case 1: return run<uint8_t>(in, out, o, pl.rows_case, nb, nx, ny, isy, osx, s);
+    case 2: return run<uint16_t>(in, out, o, pl.rows_case, nb, nx, ny, isy, osx, s);
+    case 4: return run<uint32_t>(in, out, o, pl.rows_case, nb, nx, ny, isy, osx, s);
+    case 8: return run<uint64_t>(in, out, o, pl.rows_case, nb, nx, ny, isy, osx, s);
     }
     return cudaErrorInvalidValue;
 }
