@@ -8,7 +8,7 @@ import pytest
 import oracle
 import paper_0907_0792_gb300 as moa
 import synth
-from gpu_helpers import assert_norm_err, check_status, empty, to_dev
+from gpu_helpers import assert_norm_err, check_status, empty, sample_idx, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -113,4 +113,22 @@ def test_inner_axes_without_transpose_is_moa_inner():
     moa.moa_inner_axes("or", "and", "b1", "native", A.shape, a, 1, B.shape, b, 0, D, "b1")
     got = np.unpackbits(D.cpu().numpy().view(np.uint8), bitorder="little")[:200 * 160].reshape(200, 160)
     assert np.array_equal(got.astype(bool), oracle.inner_bool(A, B))
+    check_status()
+
+
+def test_inner_axes_full_size_sampled():
+    """The bench's configuration: the semiring shapes with the contracted axes
+    inside the operands, A <32,512,128> over axis 1 and B <64,64,512> over
+    axis 2, (min,+) with 5% +inf; 20,000 outputs sampled."""
+    import torch
+    A, B = synth.semiring_inputs("tropical")  # <32,128,512> x <512,64,64>
+    Am = np.ascontiguousarray(np.moveaxis(A, 2, 1))
+    Bm = np.ascontiguousarray(np.moveaxis(B, 0, 2))
+    D = empty((32, 128, 64, 64), torch.float32)
+    moa.moa_inner_axes("min", "add", "f32", "native", Am.shape, to_dev(Am), 1, Bm.shape, to_dev(Bm), 2, D, "f32")
+    idx = sample_idx(D.numel(), 20000)
+    got = D.view(-1)[torch.from_numpy(idx).to(D.device)].cpu().numpy()
+    want = oracle.inner_f32("min", "add", *oracle.move_axes(Am, Bm, 1, 2), out_idx=idx)
+    assert np.array_equal(got, want)
+    assert np.array_equal(want, oracle.inner_f32("min", "add", A, B, out_idx=idx))  # the moves undo each other
     check_status()
