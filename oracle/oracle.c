@@ -369,8 +369,9 @@ int oracle_outer_i32(int op, int rankA, const int64_t *shA, const int32_t *A, in
  * Plain recursive summation in the working type (no compensation).  This is
  * the second formulation the definition loops are cross-checked against, and
  * the loop the CPU baseline times.  kind: 0 f64 (+,*); 1 f32 with
- * (reduce, combine) any of (add,mul), (min,add), (max,add), (max,mul);
- * 2 i32 (+,*) wrapping; 3 bool (or,and) bytes.
+ * (reduce, combine) (add,mul), or reduce min or max with combine add, sub,
+ * mul, min or max (each step one correctly rounded FP32 operation, as in
+ * the definition loop); 2 i32 (+,*) wrapping; 3 bool (or,and) bytes.
  */
 int oracle_rowwise(int kind, int reduce, int combine, int rankA, const int64_t *shA, const void *A, int rankB,
                    const int64_t *shB, const void *B, void *D, int nthreads) {
@@ -382,7 +383,10 @@ int oracle_rowwise(int kind, int reduce, int combine, int rankA, const int64_t *
     const int64_t elsinop = tau(rankB - 1, shB + 1);
     const int64_t lstride = rowsinred, rstride = elsinop, restride = elsinop;
     if (nthreads < 1) nthreads = 1;
-    if (kind == 1 && !((reduce == OP_ADD && combine == OP_MUL) || reduce == OP_MIN || reduce == OP_MAX))
+    if (kind == 1 && !((reduce == OP_ADD && combine == OP_MUL) ||
+                       ((reduce == OP_MIN || reduce == OP_MAX) &&
+                        (combine == OP_ADD || combine == OP_SUB || combine == OP_MUL || combine == OP_MIN ||
+                         combine == OP_MAX))))
         return ORC_ERR_OP;
 #ifdef _OPENMP
 #pragma omp parallel for schedule(static, 1) num_threads(nthreads)
@@ -400,9 +404,8 @@ int oracle_rowwise(int kind, int reduce, int combine, int rankA, const int64_t *
             for (int64_t j = 0; j < elsinop; ++j) res[j] = reduce == OP_ADD ? 0.0f : f32_identity(reduce);
             for (int64_t l = 0; l < rowsinred; ++l)
                 for (int64_t j = 0; j < elsinop; ++j) {
-                    float t = combine == OP_MUL ? l_[l + i * lstride] * r_[l * rstride + j]
-                                                : l_[l + i * lstride] + r_[l * rstride + j];
-                    res[j] = reduce == OP_ADD ? res[j] + t : reduce == OP_MIN ? fminf(res[j], t) : fmaxf(res[j], t);
+                    const float t = f32_combine(combine, l_[l + i * lstride], r_[l * rstride + j]);
+                    res[j] = f32_combine(reduce, res[j], t);
                 }
         } else if (kind == 2) {
             uint32_t *res = (uint32_t *)D + i * restride;

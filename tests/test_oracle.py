@@ -171,6 +171,17 @@ def test_rowwise_agrees_with_definition():
     assert np.all(np.abs(oracle.rowwise("f64", A64, B64, threads=4) - D) <= 31 * U64 * S)
 
 
+@pytest.mark.parametrize("reduce", ["min", "max"])
+@pytest.mark.parametrize("combine", ["add", "sub", "mul", "min", "max"])
+def test_rowwise_agrees_with_definition_every_fp32_pair(reduce, combine):
+    """The appendix-order loop and the definition loop, bit for bit, for
+    every FP32 (reduce, combine) the library supports."""
+    kind = "tropical_finite" if combine == "sub" else "tropical"
+    A, B = synth.semiring_inputs(kind, seed=24, shape_a=(3, 4, 27), shape_b=(27, 5, 2))
+    assert np.array_equal(oracle.rowwise("f32", A, B, reduce, combine, threads=2),
+                          oracle.inner_f32(reduce, combine, A, B))
+
+
 def _closure(semiring, w, squarings=3):
     red, comb = semiring
     x = w
