@@ -230,24 +230,29 @@ typedef struct moa_batch_plan moa_batch_plan;
 
 /*
  * moa_batch_plan_create — validate `count` problems (each as its single call
- * would), group them by kernel, choose tiles for each group (from the tile
- * cache, timing candidates on first use when tuning is enabled), lay out the
- * device descriptor array and work queue, and allocate the plan's own device
- * memory on the current device.  On error nothing is left allocated and
- * *plan is NULL; the index of the first bad problem is written to
- * *bad_index (if not NULL).  Supported problems: (add, mul) F32 with forms
- * BF16X3 or NATIVE; (min|max, add) F32; outer F32 ops.
+ * would), cut them into work items (128 x 128 tiles of inner products, row
+ * blocks of outer products), lay out the device descriptor array, the item
+ * queues, the split-plane scratch and the tensor maps, and allocate the
+ * plan's own device memory on the current device.  On error nothing is left
+ * allocated and *plan is NULL; the index of the first bad problem is written
+ * to *bad_index (if not NULL).  Supported problems: (add, mul) F32 with forms
+ * BF16X3 or NATIVE; (min|max, add|mul) F32; outer F32 ops.
  */
 moa_status moa_batch_plan_create(int count, const moa_problem *problems, moa_batch_plan **plan, int *bad_index);
 
 /*
  * moa_batch_execute — run every problem of the plan on `stream`.  The first
- * execute on a stream records the launch sequence into a CUDA graph; later
- * executes on that stream replay it.  Problems write disjoint outputs.
+ * execute times the plan's schedules on `stream` (the choice is cached per
+ * GPU and plan signature in $MOA_TUNE_CACHE, default
+ * ~/.cache/moa_autotune.txt; MOA_AUTOTUNE=off|cached|force,
+ * MOA_BATCH_SCHEDULE=0|1|2 fixes one) and records the chosen launch
+ * sequence into a CUDA graph; every execute then launches that graph on
+ * `stream`.  Problems write disjoint outputs.
  */
 moa_status moa_batch_execute(moa_batch_plan *plan, moa_stream stream);
 
-/* Plan statistics: problem count, grouped launches per execute, total tiles, total flop-equivalent work. */
+/* Plan statistics: problem count, kernels per execute (of the chosen schedule; before the first execute, of the
+ * default one), total work items, total flop-equivalent work. */
 moa_status moa_batch_plan_info(const moa_batch_plan *plan, int64_t *n_problems, int64_t *n_launches,
                                int64_t *n_tiles, double *work_flops);
 
