@@ -140,11 +140,14 @@ typedef enum {
  *   (add, mul) F64 -> F64      NATIVE | OZAKI
  *   (add, mul) F32 -> F32      NATIVE | BF16 | FP8_T128 | BF16X3
  *   (add, mul) BF16 -> F32     NATIVE
- *   (add, mul) I32 -> I32      NATIVE (wraps modulo 2^32)
+ *   (add, mul) I32 -> I32      NATIVE (wraps modulo 2^32; when every value lies in
+ *                              [-128, 127] and K <= 1024 it runs on tensor cores,
+ *                              with the same bits)
  *   (min|max, add|sub|mul|min|max) F32 -> F32   NATIVE
  *       ((min, add) shortest paths, (max, min) widest paths, (min, max)
  *       minimax paths, ...; NaN counts as missing, as C's fminf / fmaxf)
- *   (or, and) B1_U32 -> B1_U32      NATIVE
+ *   (or, and) B1_U32 -> B1_U32      NATIVE (tensor cores by exact counting when
+ *                                   M, N > 128 and N % 32 == 0)
  * rankA, rankB in [1, 8].  Returns MOA_ERR_SHAPE_MISMATCH when
  * rho A[-1] != rho B[0], MOA_ERR_UNSUPPORTED for any other tuple.
  */
