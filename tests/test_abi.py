@@ -98,6 +98,38 @@ def test_axes_and_transpose_validation(L):
     assert tr((2, 3), (1, 0), dt="f64", A=0x1004) == 10
 
 
+def test_batch_plan_validation(L):
+    """moa_batch_plan_create validates every problem as its single call would,
+    before touching the device, and reports the first bad one by index."""
+    import ctypes as C
+    good = dict(kind="inner", reduce="min", combine="add", shapeA=(4, 5), shapeB=(5, 3), A=0x1000, B=0x2000,
+                out=0x3000)
+
+    def create(bad_spec, at=2, n=4):
+        specs = [dict(good) for _ in range(n)]
+        specs[at] = dict(good, **bad_spec)
+        arr, keep = moa.make_problems(specs)
+        plan, bad = C.c_void_p(), C.c_int(-1)
+        st = moa.lib().moa_batch_plan_create(len(arr), arr, C.byref(plan), C.byref(bad))
+        assert not plan.value
+        return st, bad.value
+
+    assert create(dict(shapeB=(6, 3))) == (3, 2)  # contracted lengths differ (Eq. 2)
+    assert create(dict(shapeA=(1,) * 9)) == (2, 2)  # rank above 8
+    assert create(dict(shapeA=(-1, 5))) == (4, 2)  # negative extent
+    assert create(dict(dtype="f64", out_dtype="f64")) == (5, 2)  # the batch is FP32
+    assert create(dict(form="bf16x3")) == (5, 2)  # a form only (add, mul) has
+    assert create(dict(reduce="or", combine="and")) == (5, 2)
+    assert create(dict(kind="outer", combine="or", shapeA=(4,), shapeB=(3,))) == (5, 2)
+    assert create(dict(out=0)) == (1, 2)
+    assert create(dict(A=0x1002)) == (10, 2)  # not FP32-aligned
+    assert create(dict(kind="outer", shapeA=(4,), shapeB=(3,), out=0x3001)) == (10, 2)
+    assert create(dict(shapeA=(4, 5), shapeB=(6, 3)), at=0, n=1) == (3, 0)
+    plan, bad = C.c_void_p(), C.c_int(-1)
+    assert moa.lib().moa_batch_plan_create(-1, None, C.byref(plan), C.byref(bad)) == 11
+    assert moa.lib().moa_batch_plan_create(2, None, C.byref(plan), C.byref(bad)) == 1
+
+
 def test_outer_validation(L):
     def st(op, dt, sa, sb, odt, A=0x1000, B=0x2000, out=0x3000):
         return moa.moa_outer(op, dt, sa, A, sb, B, out, odt, stream=0, check=False)
