@@ -141,6 +141,26 @@ def test_outer_validation(L):
     assert st("mul", "f32", (0,), (2,), "f32", A=0, out=0) == 0
 
 
+def test_noalloc_and_selftest_validation(L):
+    """Host checks of the fixed-scratch entry point and of the wait self-test,
+    all answered before any device work."""
+    def na(sa, sb, A=0x1000, B=0x2000, out=0x3000):
+        return moa.moa_inner_bf16x3_noalloc(sa, A, sb, B, out, stream=0, check=False)
+    assert na((4, 5), (6, 3)) == 3
+    assert na((), (5, 3)) == 2
+    assert na((4, 5), (5, 3), out=0) == 1
+    assert na((4, 5), (5, 3), A=0x1002) == 10
+    assert na((0, 5), (5, 3), A=0, B=0, out=0) == 0  # empty result
+    # 6 (M Kp + K Np) bytes of planes must fit the 32 MiB buffer: 4096 x 1024 . 1024 x 1024 needs 30 MiB, 4096 x 2048
+    # . 2048 x 1024 needs 60 MiB
+    assert na((4096, 2048), (2048, 1024)) == 12
+    st = moa.lib().moa_selftest_wait_timeout(0, None)
+    assert st == 11
+    assert moa.lib().moa_selftest_wait_timeout(2000000, None) == 11
+    for code in range(13):
+        assert moa.moa_status_string(code) != "unknown status"
+
+
 def test_status_strings(L):
     assert moa.moa_status_string(0) == "ok"
     assert "shape" in moa.moa_status_string(3)
