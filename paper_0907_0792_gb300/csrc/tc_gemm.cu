@@ -234,7 +234,6 @@ __global__ void __launch_bounds__(cta_threads(MODE), 1)
                 ptx::mbar_arrive_expect_tx(full(stage), C::STAGE_BYTES);
                 ptx::tma_load_3d(sa, &tmA, full(stage), kb * C::BKE, tm * BM, pa);
                 if constexpr (CL > 1) {  // this CTA's share of the B boxes, multicast to the pair
-#pragma unroll
                     constexpr int NBOX = BN / C::BOXN, PER = (NBOX + CL - 1) / CL;
                     for (int j = crank * PER; j < (crank + 1) * PER && j < NBOX; ++j)
                         ptx::tma_load_3d_mc(sb + j * C::BOX_BYTES, &tmB, full(stage), tn * BN + j * C::BOXN, kb * C::BKE,

@@ -14,8 +14,6 @@
 
 #include <stdint.h>
 
-#include <algorithm>
-
 namespace moa {
 
 constexpr int kTransposeMaxDims = 8;
@@ -54,9 +52,12 @@ inline bool plan_transpose(int rank, const int64_t *shape, const int *perm, Tran
     }
     p->n = n;
     if (n == 0) return true;
-    int order[kTransposeMaxDims];  // merged axes in input order
-    for (int k = 0; k < n; ++k) order[k] = k;
-    std::sort(order, order + n, [&](int x, int y) { return first[x] < first[y]; });
+    int order[kTransposeMaxDims];  // merged axes in input order (insertion sort of at most 8)
+    for (int k = 0; k < n; ++k) {
+        int j = k;
+        for (; j > 0 && first[order[j - 1]] > first[k]; --j) order[j] = order[j - 1];
+        order[j] = k;
+    }
     int64_t st = 1;
     for (int k = n - 1; k >= 0; --k) p->is[order[k]] = st, st *= p->ext[order[k]];
     st = 1;
