@@ -11,7 +11,6 @@ e4m3 roundings (unit roundoff u = 2^-4), so |error| <= (2u + u^2) sum|a||b|
 inside one scale block (entries far below the block maximum round to
 subnormals or zero), so short, single-product-dominated contractions of
 such data are outside this form's accuracy; the square sweep keeps them."""
-import numpy as np
 import pytest
 
 import paper_0907_0792_gb300 as moa

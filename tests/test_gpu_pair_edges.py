@@ -4,7 +4,6 @@ column counts one past a 256- or 224-wide tile, contractions of 1, of one
 past a k-block and of several exact chunks, for every form that runs on the
 pair kernel (bf16 operands, BF16 and split-BF16x3 forms, FP8 block-scaled,
 Ozaki).  Tolerances as in the per-form tests."""
-import numpy as np
 import pytest
 
 import paper_0907_0792_gb300 as moa

@@ -2,10 +2,8 @@
 against the oracle (Dot2 FP64 reference of the operands as given), within
 the normalised tolerance of each form: bf16 operands as given and the
 split-BF16x3 form <= 2e-6, the BF16 form <= 1e-2."""
-import numpy as np
 import pytest
 
-import oracle
 import paper_0907_0792_gb300 as moa
 import synth
 from gpu_helpers import assert_norm_err, bf16_dev, check_status, empty, sample_idx, to_dev
