@@ -161,6 +161,26 @@ def test_noalloc_and_selftest_validation(L):
         assert moa.moa_status_string(code) != "unknown status"
 
 
+def test_problem_struct_layout_matches_header(tmp_path):
+    """The binding's ctypes moa_problem has the size and field offsets the C
+    compiler gives the header's struct (a plain C program built with gcc)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    fields = [f for f, _ in moa.MoaProblem._fields_]
+    prog = tmp_path / "layout.c"
+    prog.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"moa.h\"\nint main(void) {\n"
+                    '    printf("%zu\\n", sizeof(moa_problem));\n' +
+                    "".join(f'    printf("%zu\\n", offsetof(moa_problem, {f}));\n' for f in fields) + "    return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert got[0] == C.sizeof(moa.MoaProblem)
+    assert got[1:] == [getattr(moa.MoaProblem, f).offset for f in fields]
+
+
 def test_status_strings(L):
     assert moa.moa_status_string(0) == "ok"
     assert "shape" in moa.moa_status_string(3)
