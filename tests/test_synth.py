@@ -74,3 +74,31 @@ def test_positional_and_torch_draws_match_the_stream():
     assert np.array_equal(synth.to_f32(a), b32)
     cols = synth.skinny_columns([3, 500, 999], 1000, k=16)
     assert np.array_equal(cols, a[:, [3, 500, 999]])
+
+
+def test_batched_workload_matches_its_recipe():
+    """The 10,000-problem batch: kinds in the stated mix, ranks 1..5 per
+    operand, contraction 8..512, flattened M and N within 1..2048 and equal to
+    the products of the shape vectors (rho of the operands), octave-uniform
+    sizes (each octave of M holds a similar share)."""
+    probs = synth.batched_problems()
+    assert len(probs) == 10000
+    kinds = [p["kind"] for p in probs]
+    share = {k: kinds.count(k) / len(kinds) for k in ("bf16x3", "minplus", "outer")}
+    assert abs(share["bf16x3"] - 0.7) < 0.02 and abs(share["minplus"] - 0.2) < 0.02 and abs(share["outer"] - 0.1) < 0.02
+    octaves = np.zeros(12)
+    for p in probs:
+        sa, sb = p["shapeA"], p["shapeB"]
+        assert 1 <= len(sa) <= 5 and 1 <= len(sb) <= 5 and all(e >= 1 for e in sa + sb)
+        if p["kind"] == "outer":
+            assert int(np.prod(sa)) == p["M"] and int(np.prod(sb)) == p["N"] and p["K"] == 0
+        else:
+            assert sa[-1] == sb[0] == p["K"] and 8 <= p["K"] <= 512
+            assert int(np.prod(sa[:-1])) == p["M"] and int(np.prod(sb[1:])) == p["N"]
+        assert 1 <= p["M"] <= 2048 and 1 <= p["N"] <= 2048
+        if p["kind"] == "outer" or len(sa) > 1:
+            octaves[int(np.log2(p["M"]))] += 1
+    share = octaves[:11] / octaves[:11].sum()
+    # about 1/11 per octave; rounding 2^0 (1 + f) sends half of the first octave to M = 2
+    assert 0.07 < share[1:].min() and share[1:].max() < 0.13 and 0.02 < share[0] < 0.08
+
