@@ -27,7 +27,10 @@
  *  Shapes     Host arrays of int64_t, read during the call only (the library
  *             keeps no pointer to them).  Entries must be >= 0, rank <= 8,
  *             and the element count must not overflow int64_t.
- *  Memory     A, B and out are device pointers owned by the caller.  out
+ *  Memory     A, B and out are device pointers owned by the caller, in
+ *             memory of the current device (device or managed allocations;
+ *             host memory or another GPU's memory returns
+ *             MOA_ERR_NOT_DEVICE).  out
  *             holds prod(rho D) (inner) or prod(rho A)*prod(rho B) (outer)
  *             elements of out_dtype and must not overlap A or B.  The
  *             library owns only an internal scratch workspace, kept per
@@ -74,7 +77,8 @@ typedef enum {
     MOA_ERR_INTERNAL = 9,
     MOA_ERR_ALIGNMENT = 10,     /* pointer not aligned to its element size */
     MOA_ERR_INVALID = 11,       /* malformed argument (e.g. bad enum, bad plan) */
-    MOA_ERR_SCRATCH_LIMIT = 12  /* problem needs more scratch than the fixed no-allocation buffer holds */
+    MOA_ERR_SCRATCH_LIMIT = 12, /* problem needs more scratch than the fixed no-allocation buffer holds */
+    MOA_ERR_NOT_DEVICE = 13     /* A, B or out is not device memory of the current device */
 } moa_status;
 
 typedef enum {

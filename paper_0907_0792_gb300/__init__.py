@@ -32,7 +32,8 @@ DTYPES = {"f64": 0, "f32": 1, "bf16": 2, "fp8e4m3": 3, "i32": 4, "b1": 5}
 FORMS = {"native": 0, "bf16": 1, "fp8_t128": 2, "bf16x3": 3, "ozaki": 4}
 STATUS = {0: "MOA_OK", 1: "MOA_ERR_NULL", 2: "MOA_ERR_RANK", 3: "MOA_ERR_SHAPE_MISMATCH", 4: "MOA_ERR_OVERFLOW",
           5: "MOA_ERR_UNSUPPORTED", 6: "MOA_ERR_WORKSPACE", 7: "MOA_ERR_CUDA", 8: "MOA_ERR_TIMEOUT",
-          9: "MOA_ERR_INTERNAL", 10: "MOA_ERR_ALIGNMENT", 11: "MOA_ERR_INVALID", 12: "MOA_ERR_SCRATCH_LIMIT"}
+          9: "MOA_ERR_INTERNAL", 10: "MOA_ERR_ALIGNMENT", 11: "MOA_ERR_INVALID", 12: "MOA_ERR_SCRATCH_LIMIT",
+          13: "MOA_ERR_NOT_DEVICE"}
 
 _lib = None
 _I64P = C.POINTER(C.c_int64)

@@ -51,6 +51,29 @@ static bool aligned_to(const void *p, size_t a) { return a == 0 || ((uintptr_t)p
 
 static moa_status from_cuda(cudaError_t e) { return e == cudaSuccess ? MOA_OK : MOA_ERR_CUDA; }
 
+moa_status check_device_ptrs(const void *const *ptrs, int n) {
+    int dev = -1;
+    bool have_dev = false;
+    for (int i = 0; i < n; ++i) {
+        if (!ptrs[i]) continue;
+        if (!have_dev) {
+            if (cudaGetDevice(&dev) != cudaSuccess) {
+                cudaGetLastError();
+                return MOA_ERR_NOT_DEVICE;
+            }
+            have_dev = true;
+        }
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, ptrs[i]) != cudaSuccess) {
+            cudaGetLastError();  // not an address the runtime knows: not device memory
+            return MOA_ERR_NOT_DEVICE;
+        }
+        if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != dev)
+            return MOA_ERR_NOT_DEVICE;
+    }
+    return MOA_OK;
+}
+
 // Fault injection for tests: MOA_FAULT_INJECT=workspace makes every
 // workspace allocation fail (read once per process).
 static bool inject_workspace_failure() {
@@ -137,7 +160,7 @@ struct InnerPlan {
 
 static moa_status inner_validate(moa_op reduce, moa_op combine, moa_dtype dtype, moa_form form, int rankA,
                                  const int64_t *shapeA, const void *A, int rankB, const int64_t *shapeB, const void *B,
-                                 const void *out, moa_dtype out_dtype, InnerPlan *pl) {
+                                 const void *out, moa_dtype out_dtype, InnerPlan *pl, bool check_ptrs = true) {
     if (rankA < 1 || rankB < 1 || rankA > kMaxRank || rankB > kMaxRank) return MOA_ERR_RANK;
     if (!shapeA || !shapeB) return MOA_ERR_NULL;
     if ((unsigned)reduce > MOA_OP_AND || (unsigned)combine > MOA_OP_AND || (unsigned)dtype > MOA_B1_U32 ||
@@ -181,6 +204,10 @@ static moa_status inner_validate(moa_op reduce, moa_op combine, moa_dtype dtype,
     if (!aligned_to(A, elem_bytes(dtype)) || !aligned_to(B, elem_bytes(dtype)) ||
         !aligned_to(out, elem_bytes(out_dtype)))
         return MOA_ERR_ALIGNMENT;
+    if (check_ptrs && M * N > 0) {  // only operands the call reads, and the result it writes
+        const void *used[3] = {M * K > 0 ? A : nullptr, K * N > 0 ? B : nullptr, out};
+        if ((st = check_device_ptrs(used, 3)) != MOA_OK) return st;
+    }
     pl->M = M, pl->K = K, pl->N = N;
     return MOA_OK;
 }
@@ -317,6 +344,8 @@ moa_status moa_transpose(moa_dtype dtype, int rank, const int64_t *shape, const 
     if (!A || !out) return MOA_ERR_NULL;
     if (A == out) return MOA_ERR_INVALID;
     if (!aligned_to(A, elem_bytes(dtype)) || !aligned_to(out, elem_bytes(dtype))) return MOA_ERR_ALIGNMENT;
+    const void *used[2] = {A, out};
+    if ((st = check_device_ptrs(used, 2)) != MOA_OK) return st;
     return from_cuda(launch_transpose(elem_bytes(dtype), rank, shape, perm, A, out, (cudaStream_t)stream));
 }
 
@@ -338,13 +367,17 @@ moa_status moa_inner_axes(moa_op reduce, moa_op combine, moa_dtype dtype, moa_fo
     for (int k = 0; k < rankB; ++k)
         if (k != axisB) pb[r] = k, sb[r++] = shapeB[k];
     InnerPlan pl;
-    moa_status st = inner_validate(reduce, combine, dtype, form, rankA, sa, A, rankB, sb, B, out, out_dtype, &pl);
+    moa_status st = inner_validate(reduce, combine, dtype, form, rankA, sa, A, rankB, sb, B, out, out_dtype, &pl, false);
     if (st != MOA_OK) return st;
     const bool moveA = axisA != rankA - 1, moveB = axisB != 0;
-    if (!moveA && !moveB) return inner_run(reduce, combine, dtype, form, A, B, out, out_dtype, pl, (cudaStream_t)stream);
-    if (pl.M == 0 || pl.N == 0 || pl.K == 0)  // nothing to read
+    const bool empty = pl.M == 0 || pl.N == 0 || pl.K == 0;  // nothing to read
+    if (dtype == MOA_B1_U32 && (moveA || moveB) && !empty) return MOA_ERR_UNSUPPORTED;  // bit streams are not transposed
+    if (pl.M * pl.N > 0) {
+        const void *used[3] = {pl.M * pl.K > 0 ? A : nullptr, pl.K * pl.N > 0 ? B : nullptr, out};
+        if ((st = check_device_ptrs(used, 3)) != MOA_OK) return st;
+    }
+    if ((!moveA && !moveB) || empty)
         return inner_run(reduce, combine, dtype, form, A, B, out, out_dtype, pl, (cudaStream_t)stream);
-    if (dtype == MOA_B1_U32) return MOA_ERR_UNSUPPORTED;  // bit streams are not transposed
     // transposed copies in the stream's second workspace slot (the inner
     // product may use the first itself)
     const cudaStream_t s = (cudaStream_t)stream;
@@ -389,6 +422,8 @@ moa_status moa_outer(moa_op op, moa_dtype dtype, int rankA, const int64_t *shape
     if (!aligned_to(A, elem_bytes(dtype)) || !aligned_to(B, elem_bytes(dtype)) ||
         !aligned_to(out, elem_bytes(out_dtype)))
         return MOA_ERR_ALIGNMENT;
+    const void *used[3] = {A, B, out};
+    if ((st = check_device_ptrs(used, 3)) != MOA_OK) return st;
     return from_cuda(launch_outer(op, dtype, out_dtype, A, B, out, M, N, (cudaStream_t)stream));
 }
 
@@ -407,6 +442,7 @@ const char *moa_status_string(moa_status s) {
     case MOA_ERR_ALIGNMENT: return "misaligned pointer";
     case MOA_ERR_INVALID: return "invalid argument";
     case MOA_ERR_SCRATCH_LIMIT: return "problem needs more scratch than the fixed no-allocation buffer holds";
+    case MOA_ERR_NOT_DEVICE: return "pointer is not device memory of the current device";
     }
     return "unknown status";
 }

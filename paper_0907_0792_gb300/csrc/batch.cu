@@ -918,6 +918,18 @@ moa_status moa_batch_plan_create(int count, const moa_problem *problems, moa_bat
             return st;
         }
     }
+    // every problem well formed: then its operands and result must be memory of this device
+    for (int i = 0; i < count; ++i) {
+        const Problem &p = pl->probs[i];
+        if (p.M * p.N == 0) continue;
+        const void *used[3] = {p.type != IT_FILL ? p.A : nullptr, p.type != IT_FILL ? p.B : nullptr, p.D};
+        const moa_status st = check_device_ptrs(used, 3);
+        if (st != MOA_OK) {
+            if (bad_index) *bad_index = i;
+            delete pl;
+            return st;
+        }
+    }
     // descriptors, split planes, tensor maps, items
     std::vector<BInst> inst(count);
     std::vector<SplitJob> jobs;

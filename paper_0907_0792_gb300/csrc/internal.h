@@ -17,6 +17,13 @@ namespace moa {
 // of moa_inner_axes.
 void *workspace_get(cudaStream_t stream, size_t bytes, moa_status *st, int slot = 0);
 
+// MOA_OK when every non-null pointer of ptrs[0..n) lies in device (or
+// managed) memory of the current device; MOA_ERR_NOT_DEVICE otherwise (host
+// memory, another GPU's memory, or an address the CUDA runtime does not
+// know).  The tensor maps and kernels of the library address A, B and out as
+// memory of the device they run on.
+moa_status check_device_ptrs(const void *const *ptrs, int n);
+
 // outer.cu — Eq. (1) over the flattened operands (C is M x N, M = |A|, N = |B|).
 cudaError_t launch_outer(int op, moa_dtype dtype, moa_dtype out_dtype, const void *A, const void *B, void *C,
                          int64_t M, int64_t N, cudaStream_t stream);

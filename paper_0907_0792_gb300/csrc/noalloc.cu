@@ -84,11 +84,13 @@ extern "C" moa_status moa_inner_bf16x3_noalloc(int rankA, const int64_t *shapeA,
     if (!out || (K > 0 && (!A || !B))) return MOA_ERR_NULL;
     if ((uintptr_t)A % 4 || (uintptr_t)B % 4 || (uintptr_t)out % 4) return MOA_ERR_ALIGNMENT;
     cudaStream_t s = (cudaStream_t)stream;
-    if (K == 0) return launch_fill32((uint32_t *)out, 0u, M * N, s) == cudaSuccess ? MOA_OK : MOA_ERR_CUDA;
     // scratch needed: three bf16 planes of A (M x Kp) and of B (K x Np)
     const int64_t lim = (int64_t)MOA_NOALLOC_SCRATCH_BYTES / 6;
     const int64_t Kp = (K + 7) / 8 * 8, Np = (N + 7) / 8 * 8;
-    if (M > lim / Kp || K > lim / Np || M * Kp + K * Np > lim) return MOA_ERR_SCRATCH_LIMIT;
+    if (K > 0 && (M > lim / Kp || K > lim / Np || M * Kp + K * Np > lim)) return MOA_ERR_SCRATCH_LIMIT;
+    const void *used[3] = {K > 0 ? A : nullptr, K > 0 ? B : nullptr, out};
+    if ((st = check_device_ptrs(used, 3)) != MOA_OK) return st;
+    if (K == 0) return launch_fill32((uint32_t *)out, 0u, M * N, s) == cudaSuccess ? MOA_OK : MOA_ERR_CUDA;
     void *scratch = nullptr;
     if ((st = scratch_address(&scratch)) != MOA_OK) return st;
     return tc_inner_bf16x3_scratch(A, B, out, M, N, K, scratch, s);

@@ -16,12 +16,6 @@
 // the main loop of tile t+1.  Tiles are walked in groups of 16 row-tiles so
 // the A and B panels in flight stay resident in L2.
 //
-// Cluster pairs (CL = 2): two CTAs on adjacent row tiles of the same column
-// tile each load half of the B tile and multicast it to both, so the L2 ->
-// SM traffic per k-block drops from A + B to A + B/2.  A stage is refilled
-// only after the MMAs of both CTAs have released it (each MMA warp commits
-// to the stage barrier of both CTAs).
-//
 // Promoted accumulation (PROMOTE): the tensor core's FP32 accumulation is
 // not round-to-nearest (its error grows with the number of MMAs folded into
 // one accumulator), so for the split-BF16x3 form every 64-deep k-block is
@@ -148,7 +142,7 @@ MOA_DEV bool drain_wait(uint32_t bar, uint32_t parity) {
     return true;
 }
 
-template <int BN, int STAGES, int MODE, int CL>
+template <int BN, int STAGES, int MODE>
 __global__ void __launch_bounds__(cta_threads(MODE), 1)
     tc_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const GemmParams p) {
     using C = Cfg<BN, STAGES, MODE>;
@@ -170,7 +164,7 @@ __global__ void __launch_bounds__(cta_threads(MODE), 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             ptx::mbar_init(full(s), 1);
-            ptx::mbar_init(empty(s), CL);  // released by the MMA warp of every CTA sharing the stage
+            ptx::mbar_init(empty(s), 1);  // released by this CTA's MMA warp
         }
         for (int b = 0; b < 2; ++b) {
             ptx::mbar_init(tfull(b), 1);
@@ -189,18 +183,14 @@ __global__ void __launch_bounds__(cta_threads(MODE), 1)
     }
     ptx::tc_fence_before();
     __syncthreads();
-    if constexpr (CL > 1) ptx::cluster_sync();  // peers' barriers exist before any multicast
     ptx::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    // work of this CTA: tile (tmc * CL + crank, tn) for cluster tiles (tmc, tn)
-    const int crank = CL > 1 ? (int)ptx::cluster_ctarank() : 0;
-    const int cfirst = CL > 1 ? (int)ptx::cluster_id_x() : (int)blockIdx.x;
-    const int cstride = CL > 1 ? (int)ptx::nclusters_x() : (int)gridDim.x;
-    const int tiles_mc = (p.tiles_m + CL - 1) / CL;
-    const int num_tiles = tiles_mc * p.tiles_n;
+    // persistent CTAs walk the tiles with a stride of the grid
+    const int cfirst = (int)blockIdx.x;
+    const int cstride = (int)gridDim.x;
+    const int num_tiles = p.tiles_m * p.tiles_n;
     const int kiters = p.kblocks * p.n_terms;
-    constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1u);
 
     if (warp == 0 && lane == 0) {
         // ------------------------------------------------ TMA producer
@@ -209,8 +199,7 @@ __global__ void __launch_bounds__(cta_threads(MODE), 1)
         bool ok = true;
         for (int t = cfirst; t < num_tiles && ok; t += cstride) {
             int tm, tn;
-            tile_of(t, tiles_mc, p.tiles_n, tm, tn);
-            tm = tm * CL + crank;
+            tile_of(t, p.tiles_m, p.tiles_n, tm, tn);
             ozaki::Iter oz;
             oz.start(p.slices, p.chunk, p.kblocks);
             for (int it = 0; it < kiters; ++it) {
@@ -233,16 +222,9 @@ __global__ void __launch_bounds__(cta_threads(MODE), 1)
                 const uint32_t sa = tiles0 + stage * C::STAGE_BYTES, sb = sa + C::A_BYTES;
                 ptx::mbar_arrive_expect_tx(full(stage), C::STAGE_BYTES);
                 ptx::tma_load_3d(sa, &tmA, full(stage), kb * C::BKE, tm * BM, pa);
-                if constexpr (CL > 1) {  // this CTA's share of the B boxes, multicast to the pair
-                    constexpr int NBOX = BN / C::BOXN, PER = (NBOX + CL - 1) / CL;
-                    for (int j = crank * PER; j < (crank + 1) * PER && j < NBOX; ++j)
-                        ptx::tma_load_3d_mc(sb + j * C::BOX_BYTES, &tmB, full(stage), tn * BN + j * C::BOXN, kb * C::BKE,
-                                            pb, kMask);
-                } else {
 #pragma unroll
-                    for (int j = 0; j < BN / C::BOXN; ++j)
-                        ptx::tma_load_3d(sb + j * C::BOX_BYTES, &tmB, full(stage), tn * BN + j * C::BOXN, kb * C::BKE, pb);
-                }
+                for (int j = 0; j < BN / C::BOXN; ++j)
+                    ptx::tma_load_3d(sb + j * C::BOX_BYTES, &tmB, full(stage), tn * BN + j * C::BOXN, kb * C::BKE, pb);
                 issued |= 1u << stage;
                 last_par = (last_par & ~(1u << stage)) | (phase << stage);
                 if (++stage == STAGES) {
@@ -303,10 +285,7 @@ __global__ void __launch_bounds__(cta_threads(MODE), 1)
                     else
                         ptx::mma_bf16(dacc, ad, bd, C::IDESC, (j > 0 || k > 0) ? 1u : 0u);
                 }
-                if constexpr (CL > 1)
-                    ptx::mma_commit_mc(empty(stage), kMask);
-                else
-                    ptx::mma_commit(empty(stage));
+                ptx::mma_commit(empty(stage));
                 if (++stage == STAGES) {
                     stage = 0;
                     phase ^= 1u;
@@ -361,8 +340,7 @@ __global__ void __launch_bounds__(cta_threads(MODE), 1)
         bool ok = true;
         for (int t = cfirst; t < num_tiles && ok; t += cstride) {
             int tm, tn;
-            tile_of(t, tiles_mc, p.tiles_n, tm, tn);
-            tm = tm * CL + crank;
+            tile_of(t, p.tiles_m, p.tiles_n, tm, tn);
             const int64_t row = (int64_t)tm * BM + q * 32 + lane;
             const int64_t colh = (int64_t)tn * BN + half * HC;
             if constexpr (MODE == MODE_OZAKI) {
@@ -489,7 +467,6 @@ __global__ void __launch_bounds__(cta_threads(MODE), 1)
     }
     ptx::tc_fence_before();
     __syncthreads();
-    if constexpr (CL > 1) ptx::cluster_sync();  // no CTA leaves while its peer may still write to it
     if (warp == 1) {
         __syncwarp();
         ptx::tc_fence_after();
@@ -498,15 +475,6 @@ __global__ void __launch_bounds__(cta_threads(MODE), 1)
 }
 
 // ------------------------------------------------------------------ host
-// Cluster pairs with B multicast; MOA_CLUSTER_PAIRS=0 turns them off.
-bool cluster_pairs_enabled() {
-    static const bool on = [] {  // read once, thread-safe
-        const char *e = std::getenv("MOA_CLUSTER_PAIRS");
-        return !(e && e[0] == '0');
-    }();
-    return on;
-}
-
 int num_sms() {
     static const int n = [] {
         int dev = 0, v = 0;
@@ -517,51 +485,28 @@ int num_sms() {
     return n;
 }
 
-template <int BN, int STAGES, int MODE, int CL = 1>
+template <int BN, int STAGES, int MODE>
 cudaError_t launch_tc(const CUtensorMap &ta, const CUtensorMap &tb, GemmParams &p, cudaStream_t s) {
     using C = Cfg<BN, STAGES, MODE>;
-    auto kern = tc_gemm_bf16<BN, STAGES, MODE, CL>;
-    // shared-memory attribute and resident clusters, set up once per process
-    // (under a lock, so concurrent first calls agree; a failure is retried)
+    auto kern = tc_gemm_bf16<BN, STAGES, MODE>;
+    // shared-memory attribute, set up once per process (under a lock, so
+    // concurrent first calls agree; a failure is retried)
     static std::mutex mu;
-    static int cached = 0;
-    int max_clusters;
+    static bool ready = false;
     {
         std::lock_guard<std::mutex> lk(mu);
-        if (!cached) {
+        if (!ready) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
             if (e != cudaSuccess) return e;
-            int mc = num_sms() / CL;
-            if (CL > 1) {
-                cudaLaunchConfig_t cfg = {};
-                cudaLaunchAttribute at[1];
-                at[0].id = cudaLaunchAttributeClusterDimension;
-                at[0].val.clusterDim.x = CL, at[0].val.clusterDim.y = 1, at[0].val.clusterDim.z = 1;
-                cfg.gridDim = dim3(CL * mc), cfg.blockDim = dim3(cta_threads(MODE)), cfg.dynamicSmemBytes = C::SMEM;
-                cfg.attrs = at, cfg.numAttrs = 1;
-                int n = 0;
-                if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n > 0 && n < mc) mc = n;
-                cudaGetLastError();
-            }
-            cached = mc;
+            ready = true;
         }
-        max_clusters = cached;
     }
     p.tiles_m = (p.M + BM - 1) / BM;
     p.tiles_n = (p.N + BN - 1) / BN;
-    const int ctiles = (p.tiles_m + CL - 1) / CL * p.tiles_n;
-    const int clusters = ctiles < max_clusters ? ctiles : max_clusters;
-    if (CL == 1) {
-        kern<<<clusters, cta_threads(MODE), C::SMEM, s>>>(ta, tb, p);
-        return cudaGetLastError();
-    }
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = CL, at[0].val.clusterDim.y = 1, at[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(CL * clusters), cfg.blockDim = dim3(cta_threads(MODE)), cfg.dynamicSmemBytes = C::SMEM, cfg.stream = s;
-    cfg.attrs = at, cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, ta, tb, p);
+    const int tiles = p.tiles_m * p.tiles_n;
+    const int ctas = tiles < num_sms() ? tiles : num_sms();
+    kern<<<ctas, cta_threads(MODE), C::SMEM, s>>>(ta, tb, p);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -628,13 +573,10 @@ moa_status tc_gemm_planes(const __nv_bfloat16 *A, int64_t lda, int planesA, cons
         return e == cudaSuccess ? MOA_OK : MOA_ERR_CUDA;
     }
     if (i32_out) return MOA_ERR_INTERNAL;  // int32 results only from the pair kernel
-    const bool pair = BN == 256 && M > BM && cluster_pairs_enabled();
     if (promote)
-        e = BN == 128 ? launch_tc<128, 6, MODE_PROMOTE>(ta, tb, p, s)
-                      : (pair ? launch_tc<256, 4, MODE_PROMOTE, 2>(ta, tb, p, s) : launch_tc<256, 4, MODE_PROMOTE>(ta, tb, p, s));
+        e = BN == 128 ? launch_tc<128, 6, MODE_PROMOTE>(ta, tb, p, s) : launch_tc<256, 4, MODE_PROMOTE>(ta, tb, p, s);
     else
-        e = BN == 128 ? launch_tc<128, 6, MODE_STORE>(ta, tb, p, s)
-                      : (pair ? launch_tc<256, 4, MODE_STORE, 2>(ta, tb, p, s) : launch_tc<256, 4, MODE_STORE>(ta, tb, p, s));
+        e = BN == 128 ? launch_tc<128, 6, MODE_STORE>(ta, tb, p, s) : launch_tc<256, 4, MODE_STORE>(ta, tb, p, s);
     return e == cudaSuccess ? MOA_OK : MOA_ERR_CUDA;
 }
 
@@ -659,8 +601,7 @@ moa_status tc_gemm_fp8(const uint8_t *A, int64_t lda, const uint8_t *B, int64_t 
     p.D = D, p.ldd = ldd;
     p.vec_store = ((uintptr_t)D % 16 == 0) && (ldd % 4 == 0);
     p.scale_a = scale_a, p.scale_b = scale_b, p.nblk_b = (int)((N + 127) / 128);
-    cudaError_t e = (M > BM && cluster_pairs_enabled()) ? launch_tc<256, 4, MODE_FP8, 2>(ta, tb, p, s)
-                                                        : launch_tc<256, 4, MODE_FP8>(ta, tb, p, s);
+    const cudaError_t e = launch_tc<256, 4, MODE_FP8>(ta, tb, p, s);
     return e == cudaSuccess ? MOA_OK : MOA_ERR_CUDA;
 }
 
@@ -696,8 +637,7 @@ moa_status tc_gemm_ozaki(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat1
     }
     // 192-wide tiles: two accumulators fit TMEM and the int32 class sums of a
     // thread's 96 columns fit its registers
-    cudaError_t e = (M > BM && cluster_pairs_enabled()) ? launch_tc<192, 5, MODE_OZAKI, 2>(ta, tb, p, s)
-                                                        : launch_tc<192, 5, MODE_OZAKI>(ta, tb, p, s);
+    const cudaError_t e = launch_tc<192, 5, MODE_OZAKI>(ta, tb, p, s);
     return e == cudaSuccess ? MOA_OK : MOA_ERR_CUDA;
 }
 

@@ -92,17 +92,6 @@ MOA_DEV void tma_load_3d(uint32_t dst, const CUtensorMap *m, uint32_t bar, int c
         : "memory");
 }
 
-// Same load, delivered to the same shared-memory offset of every CTA in
-// cta_mask (a cluster multicast); each destination CTA's barrier at `bar`'s
-// offset receives the bytes.
-MOA_DEV void tma_load_3d_mc(uint32_t dst, const CUtensorMap *m, uint32_t bar, int c0, int c1, int c2, uint16_t cta_mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster "
-        "[%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(dst),
-        "l"((uint64_t)m), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "h"(cta_mask)
-        : "memory");
-}
-
 // 3-D tiled store shared -> global, tracked by this thread's bulk
 // async-groups; elements outside the tensor are not written.
 MOA_DEV void tma_store_3d(const CUtensorMap *m, uint32_t src, int c0, int c1, int c2) {
@@ -253,14 +242,6 @@ MOA_DEV void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t 
 // Arrive once on `bar` when every tcgen05 op issued so far by this thread is done.
 MOA_DEV void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-// Arrive once on the barrier at `bar`'s offset in every CTA of cta_mask when
-// this thread's tcgen05 ops are done.
-MOA_DEV void mma_commit_mc(uint32_t bar, uint16_t cta_mask) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
-                 "h"(cta_mask)
-                 : "memory");
 }
 
 // 32 lanes x 32 consecutive 32-bit columns: thread t gets lane (base + t).

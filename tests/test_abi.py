@@ -77,6 +77,27 @@ def test_validation_before_launch(L):
     assert _inner_status("add", "mul", "f32", "native", (0, 5), (5, 7), "f32", A=0, out=0) == 0
 
 
+def test_operands_must_be_device_memory(L):
+    """A well-formed call whose A, B or out is not memory of the current
+    device (here: host memory, with no GPU at all) is rejected before any
+    launch with MOA_ERR_NOT_DEVICE, for every entry point that reads caller
+    memory; a call that touches no memory still succeeds."""
+    import numpy as np
+    a = np.zeros((4, 5), np.float32)
+    b = np.zeros((5, 7), np.float32)
+    d = np.zeros((4, 7), np.float32)
+    pa, pb, pd = a.ctypes.data, b.ctypes.data, d.ctypes.data
+    assert _inner_status("add", "mul", "f32", "native", (4, 5), (5, 7), "f32", A=pa, B=pb, out=pd) == 13
+    assert _inner_status("min", "add", "f32", "native", (4, 5), (5, 7), "f32", A=pa, B=pb, out=pd) == 13
+    assert moa.moa_outer("mul", "f32", (4, 5), pa, (5, 7), pb, np.zeros(4 * 5 * 5 * 7, np.float32).ctypes.data,
+                         "f32", stream=0, check=False) == 13
+    assert moa.moa_transpose("f32", (4, 5), pa, (1, 0), pd, stream=0, check=False) == 13
+    assert moa.moa_inner_bf16x3_noalloc((4, 5), pa, (5, 7), pb, pd, stream=0, check=False) == 13
+    # empty contraction on host memory: out is still written, so it is still rejected
+    assert _inner_status("add", "mul", "f32", "native", (4, 0), (0, 7), "f32", A=0, B=0, out=pd) == 13
+    assert moa.moa_status_string(13) == "pointer is not device memory of the current device"
+
+
 def test_axes_and_transpose_validation(L):
     def ax(sa, a, sb, b, dt="f32", A=0x1000, B=0x2000, out=0x3000):
         return moa.moa_inner_axes("add", "mul", dt, "native", sa, A, a, sb, B, b, out, dt, stream=0, check=False)
@@ -125,6 +146,8 @@ def test_batch_plan_validation(L):
     assert create(dict(A=0x1002)) == (10, 2)  # not FP32-aligned
     assert create(dict(kind="outer", shapeA=(4,), shapeB=(3,), out=0x3001)) == (10, 2)
     assert create(dict(shapeA=(4, 5), shapeB=(6, 3)), at=0, n=1) == (3, 0)
+    # every problem well formed, but their pointers are not device memory: the first one is reported
+    assert create(dict()) == (13, 0)
     plan, bad = C.c_void_p(), C.c_int(-1)
     assert moa.lib().moa_batch_plan_create(-1, None, C.byref(plan), C.byref(bad)) == 11
     assert moa.lib().moa_batch_plan_create(2, None, C.byref(plan), C.byref(bad)) == 1
@@ -157,7 +180,7 @@ def test_noalloc_and_selftest_validation(L):
     st = moa.lib().moa_selftest_wait_timeout(0, None)
     assert st == 11
     assert moa.lib().moa_selftest_wait_timeout(2000000, None) == 11
-    for code in range(13):
+    for code in range(14):
         assert moa.moa_status_string(code) != "unknown status"
 
 
