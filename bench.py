@@ -1,16 +1,21 @@
 """Benchmark of the MoA generalized inner / outer product on GB300.
 
-Headline workload: the square matrix-multiply sweep's largest case, the
-(+,*) inner product (Eq. 2, matrix multiply as its special case, Sec. I) of
-two 8192 x 8192 arrays with bf16 elements, FP32 accumulation, through
-``moa_inner``.  One step = one such inner product (2 n^3 flops); inputs
-(2 x 128 MiB) are larger than L2, so no flush is needed between steps.
+Headline workload: the square matrix-multiply sweep's largest case at the
+paper's precision: the FP64 (+,*) inner product (Eq. 2, matrix multiply as
+its special case, Sec. I; the paper measures FP64 matrix multiply, Sec. II.B)
+of two 8192 x 8192 arrays of U(-1,1) values, through ``moa_inner`` in the
+Ozaki-sliced form (FP64 in and out, normalised error <= 1e-12).  One step =
+one such product (2 n^3 flops of the FP64 product); inputs (2 x 512 MiB) are
+larger than L2, so no flush is needed between steps.
 
-Also measured in the same run, each in its own timed loop (keys "rows"):
-the other forms of the sweep at n = 8192 (FP32 FMA; BF16, FP8 and split-BF16x3
-from FP32 operands; Ozaki-sliced and plain FP64), the generalized semirings on the
-<32,128,512> x <512,64,64> arrays, the memory-bound outer products of
-<128,64,32> x <32,64>, and the plain-method FP64 rank-4 x rank-3 product.
+Also measured in the same run, each in its own timed loop (keys "rows",
+with a compact "summary" as the line's last key): every form of the square
+sweep (plain FP64, FP32, BF16 / FP8 / split-BF16x3 from FP32 operands, bf16
+operands, Ozaki) at n = 256 .. 8192 for uniform and log-uniform values, the
+generalized semirings on the <32,128,512> x <512,64,64> arrays, the
+memory-bound outer products of <128,64,32> x <32,64>, the plain-method FP64
+rank-4 x rank-3 product, the transposes, the paper's own m x 128 . 128 x n
+shape, and the batch of 10,000 uneven products.
 
 ``--impl reference`` times the CPU oracle (the appendix-order loop, FP64,
 OpenMP over result rows) on a bounded sample of the same workload.
@@ -29,6 +34,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_HEAD = 8192
+# kernels of one Ozaki call: |A| row maxima (also zeroing the column maxima),
+# |B| column maxima, the two digit-slicing passes, the slice-pair GEMM
+OZAKI_KERNELS_PER_CALL = 5
 METRIC = "MoA inner-product TFLOP/s (% peak) & outer-product GB/s; mixed vs FP64 form"
 
 
@@ -177,38 +185,94 @@ def _barrier(ws):
 
 
 # ---------------------------------------------------------------- rows
-def _row_inner_square(moa, torch, form, dtype, n, reps, stream, peaks, flush):
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor) nominal peak
+# FP32 FFMA issue bound: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (unit counts and maximum clock)
+FP32_FFMA_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+# (form, operand dtype): the square sweep's forms
+SWEEP_FORMS = (("ozaki", "f64"), ("native", "f64"), ("native", "f32"), ("bf16x3", "f32"), ("bf16", "f32"),
+               ("fp8_t128", "f32"), ("native", "bf16"))
+
+
+def ozaki_slices(k: int) -> int:
+    """Digit slices per operand the library's Ozaki form takes for a contraction of length k."""
+    return 8 if k <= 256 else 7
+
+
+def sweep_work(form: str, dtype: str, n: int, peaks: dict, sustained: bool = False):
+    """(flop the underlying units execute per product, their peak TFLOP/s, bound, peak label)."""
+    f = 2.0 * n ** 3
+    bf16 = peaks["bf16_tflops_sustained"] if sustained else peaks["bf16_tflops"]
+    if form == "ozaki":
+        s = ozaki_slices(n)
+        return f * s * (s + 1) // 2, bf16, "tensor", "bf16 dense"
+    if form == "bf16x3":
+        return 6 * f, bf16, "tensor", "bf16 dense"
+    if form == "fp8_t128":
+        return f, 2 * bf16, "tensor", "e4m3 dense (2x measured bf16)"
+    if form == "bf16" or dtype == "bf16":
+        return f, bf16, "tensor", "bf16 dense"
+    if dtype == "f32":
+        return f, FP32_FFMA_TFLOPS, "alu", "FP32 FFMA issue bound"
+    return f, FP64_NOMINAL_TFLOPS, "fp64", "FP64 nominal"
+
+
+class SweepInputs:
+    """The square sweep's operands: leading blocks of the n = 8192 arrays
+    (synth.square_leading), per distribution, generated once."""
+
+    def __init__(self):
+        self.full = {}
+
+    def get(self, n: int, dist: str):
+        import numpy as np
+
+        import synth
+        if dist not in self.full:
+            self.full[dist] = synth.square(max(synth.SWEEP_N), dist)
+        A, B = self.full[dist]
+        return np.ascontiguousarray(A[:n, :n]), np.ascontiguousarray(B[:n, :n])
+
+
+def _row_sweep(moa, torch, inputs, n, dist, stream, peaks, flush, forms=SWEEP_FORMS):
     import numpy as np
 
     import synth
-    A64, B64 = synth.square(n, "uniform")
-    if dtype == "f64":
-        A, B = torch.from_numpy(A64).cuda(), torch.from_numpy(B64).cuda()
-        D = torch.empty((n, n), dtype=torch.float64, device="cuda")
-        odt = "f64"
-    elif dtype == "f32":
-        A = torch.from_numpy(synth.to_f32(A64)).cuda()
-        B = torch.from_numpy(synth.to_f32(B64)).cuda()
-        D = torch.empty((n, n), dtype=torch.float32, device="cuda")
-        odt = "f32"
-    else:
-        A = torch.from_numpy(synth.to_bf16(A64)[0].view(np.int16)).view(torch.bfloat16).cuda()
-        B = torch.from_numpy(synth.to_bf16(B64)[0].view(np.int16)).view(torch.bfloat16).cuda()
-        D = torch.empty((n, n), dtype=torch.float32, device="cuda")
-        odt = "f32"
-    call = lambda: moa.moa_inner("add", "mul", dtype, form, (n, n), A, (n, n), B, D, odt, stream)
-    call()
-    torch.cuda.synchronize()
-    times = []
-    for _ in range(reps):
-        flush()
-        times.append(_events_time(call, 1, stream))
-    ms = statistics.median(times)
-    tflops = 2.0 * n ** 3 / (ms * 1e-3) / 1e12
-    row = {"form": form, "dtype": dtype, "n": n, "ms": round(ms, 4), "tflops": round(tflops, 2)}
-    del A, B, D
+    A64, B64 = inputs.get(n, dist)
+    out = []
+    dev = {}
+    for form, dtype in forms:
+        if dtype not in dev:
+            if dtype == "f64":
+                dev[dtype] = (torch.from_numpy(A64).cuda(), torch.from_numpy(B64).cuda())
+            elif dtype == "f32":
+                dev[dtype] = (torch.from_numpy(synth.to_f32(A64)).cuda(), torch.from_numpy(synth.to_f32(B64)).cuda())
+            else:
+                dev[dtype] = tuple(torch.from_numpy(synth.to_bf16(X)[0].view(np.int16)).view(torch.bfloat16).cuda()
+                                   for X in (A64, B64))
+        A, B = dev[dtype]
+        odt = "f64" if dtype == "f64" else "f32"
+        D = torch.empty((n, n), dtype=torch.float64 if odt == "f64" else torch.float32, device="cuda")
+        call = lambda: moa.moa_inner("add", "mul", dtype, form, (n, n), A, (n, n), B, D, odt, stream)
+        call()
+        torch.cuda.synchronize()
+        reps = 1 if (form, dtype) == ("native", "f64") and n >= 4096 else (3 if n >= 4096 else 5)
+        times = []
+        for _ in range(reps):
+            flush()
+            times.append(_events_time(call, 1, stream))
+        ms = statistics.median(times)
+        work, peak, bound, plabel = sweep_work(form, dtype, n, peaks)
+        row = {"form": form, "dtype": dtype, "n": n, "dist": dist, "ms": round(ms, 4),
+               "tflops_effective": round(2.0 * n ** 3 / (ms * 1e-3) / 1e12, 2),
+               "frac_of_peak": round(work / (ms * 1e-3) / 1e12 / peak, 3), "bound": bound, "peak": plabel}
+        if form == "ozaki":
+            row["slices"] = ozaki_slices(n)
+        out.append(row)
+        del D
+    del dev
     torch.cuda.empty_cache()
-    return row
+    return out
 
 
 def _row_semiring(moa, torch, kind, reduce, combine, reps, stream, flush):
@@ -317,9 +381,6 @@ def _row_plain_method(moa, torch, reps, stream):
     ms_o = _events_time(co, reps, stream)
     return {"inner_ms": round(ms_i, 4), "inner_gflops": round(2 * 1536 * 480 * 64 / (ms_i * 1e-3) / 1e9, 1),
             "outer_ms": round(ms_o, 4), "outer_gbs": round((C.numel() + A.size) * 8 / (ms_o * 1e-3) / 1e9, 1)}
-
-
-FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor) nominal peak
 
 
 def _row_skinny(moa, torch, reps, stream, peaks, n=None, cpu=True):
@@ -431,17 +492,15 @@ def _row_batched(moa, torch, reps, stream, compare=True, count=10000):
 class OracleSampler:
     """The oracle's appendix-order loop (FP64, OpenMP over rows) on leading
     rows of the n = 8192 headline product: the operands are the headline's
-    (U(-1,1) rounded to bf16, held as FP64), made once; the rate is
-    calibrated once so that each sample can be sized in seconds."""
+    (U(-1,1) FP64), made once; the rate is calibrated once so that each
+    sample can be sized in seconds."""
 
     def __init__(self, threads: int | None = None):
         import oracle
         import synth
         self.n = N_HEAD
         self.threads = threads or oracle.max_threads()
-        A64, B64 = synth.square(self.n, "uniform")
-        self.A = synth.to_bf16(A64)[1]
-        self.B = synth.to_bf16(B64)[1]
+        self.A, self.B = synth.square(self.n, "uniform")
         rows = max(self.threads, 16)
         t0 = time.perf_counter()
         oracle.rowwise("f64", self.A[:rows], self.B, threads=self.threads)
@@ -474,9 +533,9 @@ def cpu_oracle_sample(seconds: float = 12.0, threads: int | None = None):
 def headline_config(ws: int) -> dict:
     """The workload both arms report (the reference arm samples its rows)."""
     n = N_HEAD
-    return {"workload": "square (+,*) inner product n=8192, bf16 operands, FP32 accumulate/out",
-            "M": n, "K": n, "N": n, "seed": 2, "values": "U(-1,1) rounded to bf16",
-            "l2": "inputs 2 x 128 MiB > L2, no flush", "parallelism": f"replicas x{ws}"}
+    return {"workload": "square (+,*) inner product n=8192, FP64 in/out, Ozaki-sliced form (normalised error <= 1e-12)",
+            "M": n, "K": n, "N": n, "seed": 2, "values": "U(-1,1) FP64",
+            "l2": "inputs 2 x 512 MiB > L2, no flush", "parallelism": f"replicas x{ws}"}
 
 
 def run_reference(args, rank, ws):
@@ -506,17 +565,42 @@ def run_reference(args, rank, ws):
 
 
 # ---------------------------------------------------------------- main
+def _summary(rows: dict) -> dict:
+    """Compact digest of the rows (kept short: it ends the JSON line)."""
+    out = {}
+    sw = rows.get("square_sweep") or []
+    if sw:
+        eff, frac = {}, {}
+        for r in sw:
+            key = f"{r['form']}:{r['dtype']}:{r['dist'][0]}"
+            eff.setdefault(key, []).append(r["tflops_effective"])
+            if r["n"] >= 4096:
+                frac.setdefault(key, []).append(r["frac_of_peak"])
+        out["sweep_n"] = sorted({r["n"] for r in sw})
+        out["sweep_eff_tflops"] = eff
+        out["sweep_frac_n4096_8192"] = frac
+    if rows.get("semirings"):
+        out["semiring_gops"] = {r["semiring"]: r["gops"] for r in rows["semirings"]}
+    if rows.get("outer"):
+        out["outer_frac_hbm"] = {f"{r['op']}:{r['dtype']}": r["frac_hbm"] for r in rows["outer"]}
+    if rows.get("batched_10000"):
+        b = rows["batched_10000"]
+        out["batched"] = {"ms": b["ms"], "speedup_vs_one_call": b["speedup_vs_one_call_per_problem"]}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1500)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="moa", choices=["moa", "reference"])
     ap.add_argument("--rows", default="all",
                     help="comma list of extra rows to measure: sweep,semirings,outer,plain,batched,skinny,axes (all / none)")
     ap.add_argument("--skinny-n", type=int, default=None, help="n of the skinny row (default 2^26)")
     ap.add_argument("--no-rows", action="store_true", help="same as --rows none")
-    ap.add_argument("--sweep-n", type=int, default=N_HEAD, help="matrix size of the sweep row")
+    ap.add_argument("--sweep-n", default="all", help="comma list of sweep sizes (default 256..8192)")
+    ap.add_argument("--sweep-dist", default="uniform,loguniform", help="comma list of sweep value distributions")
     ap.add_argument("--sweep-forms", default="all",
                     help="comma list of form:dtype pairs for the sweep row (e.g. ozaki:f64,fp8_t128:f32)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -532,7 +616,6 @@ def main():
         run_reference(args, rank, ws)
         return
 
-    import numpy as np
     import torch
 
     import paper_0907_0792_gb300 as moa
@@ -544,14 +627,12 @@ def main():
     stream = torch.cuda.current_stream()
     n = N_HEAD
 
-    # ---- headline: bf16 8192^3 (+,*) through moa_inner, inputs resident in HBM
+    # ---- headline: FP64 8192^3 (+,*) in the Ozaki form through moa_inner, inputs resident in HBM
     A64, B64 = synth.square(n, "uniform")
-    a_bits, _ = synth.to_bf16(A64)
-    b_bits, _ = synth.to_bf16(B64)
-    A = torch.from_numpy(a_bits.view(np.int16)).view(torch.bfloat16).cuda()
-    B = torch.from_numpy(b_bits.view(np.int16)).view(torch.bfloat16).cuda()
-    D = torch.empty((n, n), dtype=torch.float32, device="cuda")
-    step = lambda: moa.moa_inner("add", "mul", "bf16", "native", (n, n), A, (n, n), B, D, "f32", stream)
+    A = torch.from_numpy(A64).cuda()
+    B = torch.from_numpy(B64).cuda()
+    D = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    step = lambda: moa.moa_inner("add", "mul", "f64", "ozaki", (n, n), A, (n, n), B, D, "f64", stream)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -561,6 +642,7 @@ def main():
         torch.cuda.synchronize()
         _barrier(ws)
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        moa.moa_kernel_timing(True)  # CUDA events around the slice-pair GEMM launch of every step
         t_start = time.time()
         s.record(stream)
         for _ in range(args.steps):
@@ -568,74 +650,59 @@ def main():
         e.record(stream)
         torch.cuda.synchronize()
         clk.window = (t_start, time.time())
+        moa.moa_kernel_timing(False)
         _barrier(ws)
+    gemm_launches, gemm_ms_total = moa.moa_kernel_timing_read()
     ms_local = s.elapsed_time(e) / args.steps
     ms = _max_over_ranks(ms_local, ws)
     flops = 2.0 * n ** 3
     value = whole_job_rate(flops, ms, ws) / 1e12
-    kernel_tflops = flops / (ms_local * 1e-3) / 1e12
     st = moa.moa_device_status()
     if st != 0:
         raise RuntimeError("device status " + moa.moa_status_string(st))
 
-    # ---- e2e: the same call with host buffers, copies inside the timed region.
-    # Every step copies its own operands in from pinned host memory and its
-    # result out; two device buffer sets and one stream per copy direction let
-    # step k+1's operands come in while step k computes and step k-1's result
-    # goes out.
-    hA = torch.from_numpy(a_bits.view(np.int16)).view(torch.bfloat16).pin_memory()
-    hB = torch.from_numpy(b_bits.view(np.int16)).view(torch.bfloat16).pin_memory()
-    hD = [torch.empty((n, n), dtype=torch.float32).pin_memory() for _ in range(2)]
-    bufs = [(A, B, D), (torch.empty_like(A), torch.empty_like(B), torch.empty_like(D))]
-    h2d_s, d2h_s = torch.cuda.Stream(), torch.cuda.Stream()
-    in_ready = [torch.cuda.Event() for _ in range(2)]
-    done = [torch.cuda.Event() for _ in range(2)]
-    out_done = [torch.cuda.Event() for _ in range(2)]
-    for ev in done + out_done:
-        ev.record(stream)
-
-    def e2e_run(steps):
-        for k in range(steps):
-            b = k % 2
-            a_d, b_d, d_d = bufs[b]
-            with torch.cuda.stream(h2d_s):
-                h2d_s.wait_event(done[b])  # the product that last used this buffer set is finished
-                a_d.copy_(hA, non_blocking=True)
-                b_d.copy_(hB, non_blocking=True)
-                in_ready[b].record(h2d_s)
-            stream.wait_event(in_ready[b])
-            stream.wait_event(out_done[b])  # its previous result has left the device
-            moa.moa_inner("add", "mul", "bf16", "native", (n, n), a_d, (n, n), b_d, d_d, "f32", stream)
-            done[b].record(stream)
-            with torch.cuda.stream(d2h_s):
-                d2h_s.wait_event(done[b])
-                hD[b].copy_(d_d, non_blocking=True)
-                out_done[b].record(d2h_s)
-        stream.wait_stream(h2d_s)
-        stream.wait_stream(d2h_s)
-
-    e2e_run(2)
+    # ---- e2e: the same product through moa_inner_host, every step copying its
+    # operands in from page-locked host memory and its result out (inside the
+    # call, overlapped by row blocks), timed with CUDA events on the stream
+    hA = torch.from_numpy(A64).pin_memory()
+    hB = torch.from_numpy(B64).pin_memory()
+    hD = torch.empty((n, n), dtype=torch.float64).pin_memory()
+    del A, B, D
+    torch.cuda.empty_cache()
+    e2e_call = lambda: moa.moa_inner_host("add", "mul", "f64", "ozaki", (n, n), hA, (n, n), hB, hD, "f64", stream)
+    e2e_call()
     torch.cuda.synchronize()
-    e2e_steps = max(4, min(args.steps, 20))
-    ms_e2e = _max_over_ranks(_events_time(lambda: e2e_run(e2e_steps), 1, stream) / e2e_steps, ws)
+    e2e_steps = max(3, min(args.steps, 10))
+    ms_e2e = _max_over_ranks(_events_time(e2e_call, e2e_steps, stream), ws)
     e2e = {"value": round(ws * flops / (ms_e2e * 1e-3) / 1e12, 2), "unit": "TFLOP/s",
-           "h2d_bytes_per_step": int(hA.numel() * 2 + hB.numel() * 2), "d2h_bytes_per_step": int(D.numel() * 4),
-           "ms_per_step": round(ms_e2e, 3), "pipelined": "one stream per copy direction + 2 buffer sets"}
-    del hA, hB, hD, A, B, D, bufs
+           "h2d_bytes_per_step": int(hA.numel() * 8 + hB.numel() * 8), "d2h_bytes_per_step": int(hD.numel() * 8),
+           "ms_per_step": round(ms_e2e, 3), "call": "moa_inner_host (pinned host buffers, row blocks overlapped)"}
+    st = moa.moa_device_status()
+    if st != 0:
+        raise RuntimeError("device status " + moa.moa_status_string(st))
+    del hA, hB, hD
+    moa.moa_release_workspace()
     torch.cuda.empty_cache()
 
-    # the timed region is `steps` back-to-back launches: past ~0.25 s of
-    # continuous load the part runs at its power-capped clock, so the
-    # sustained measured peak is the denominator there, the burst one below
+    # roofline of the dominant kernel (the slice-pair GEMM): slice-product
+    # flops per launch over its event-timed duration; a timed region of
+    # continuous load past ~0.25 s runs at the power-capped clock, so the
+    # sustained measured peak is the denominator there
+    gemm_ms = gemm_ms_total / max(1, gemm_launches)
+    S = ozaki_slices(n)
+    slice_flops = S * (S + 1) // 2 * flops
     sustained = ms_local * args.steps > 250.0
     peak_tc = peaks["bf16_tflops_sustained"] if sustained else peaks["bf16_tflops"]
-    kname = "tc_gemm_pair<0>"
-    roofline = {"bound": "tensor", "achieved": round(kernel_tflops, 1), "peak": peak_tc, "unit": "TFLOP/s",
-                "frac": round(kernel_tflops / peak_tc, 3), "traffic": _ncu_traffic(kname),
-                "algorithmic_bytes": 2 * n * n * 2 + n * n * 4,
-                "kernel": kname,
+    achieved = slice_flops / (gemm_ms * 1e-3) / 1e12
+    kname = "tc_gemm_pair<3>"
+    roofline = {"bound": "tensor", "achieved": round(achieved, 1), "peak": peak_tc, "unit": "TFLOP/s",
+                "frac": round(achieved / peak_tc, 3), "traffic": _ncu_traffic(kname),
+                "kernel": kname, "kernel_ms": round(gemm_ms, 4), "kernel_launches": gemm_launches,
+                "work": f"{S * (S + 1) // 2} bf16 slice products of 2 n^3 flop (S = {S} slices per operand)",
+                "algorithmic_bytes": 2 * S * n * n * 2 + n * n * 8,
                 "peak_kind": f"bf16 dense {'sustained' if sustained else 'burst'}, {peaks['source']}",
-                "timed_region_ms": round(ms_local * args.steps, 1), "peak_burst": peaks["bf16_tflops"]}
+                "timed_region_ms": round(ms_local * args.steps, 1), "peak_burst": peaks["bf16_tflops"],
+                "share_of_step": round(gemm_ms / ms_local, 3)}
 
     rows = {}
     want = set() if args.no_rows or args.rows == "none" else (
@@ -645,15 +712,18 @@ def main():
         flush_buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
         flush = lambda: _flush_l2(flush_buf)
         if "sweep" in want:
-            sweep = []
-            forms = (("native", "bf16", 5), ("bf16", "f32", 5), ("fp8_t128", "f32", 5), ("bf16x3", "f32", 5),
-                     ("native", "f32", 3), ("ozaki", "f64", 3), ("native", "f64", 1))
+            sizes = synth.SWEEP_N if args.sweep_n == "all" else tuple(int(v) for v in args.sweep_n.split(","))
+            forms = SWEEP_FORMS
             if args.sweep_forms != "all":
                 pick = set(args.sweep_forms.split(","))
                 forms = tuple(f for f in forms if f"{f[0]}:{f[1]}" in pick)
-            for form, dt, reps in forms:
-                sweep.append(_row_inner_square(moa, torch, form, dt, args.sweep_n, reps, stream, peaks, flush))
-            rows[f"square_sweep_n{args.sweep_n}"] = sweep
+            inputs = SweepInputs()
+            sweep = []
+            for dist in args.sweep_dist.split(","):
+                for sn in sizes:
+                    sweep += _row_sweep(moa, torch, inputs, sn, dist, stream, peaks, flush, forms)
+            del inputs
+            rows["square_sweep"] = sweep
         if "semirings" in want:
             rows["semirings"] = [
                 _row_semiring(moa, torch, "tropical", "min", "add", 5, stream, flush),
@@ -688,10 +758,11 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 2), "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": headline_config(ws),
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
-                "clocks": clk.summary(), "device_status": "ok", "rows": rows}
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": args.steps * OZAKI_KERNELS_PER_CALL,
+                "clocks": clk.summary(), "device_status": "ok", "rows": rows, "summary": _summary(rows)}
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist

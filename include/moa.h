@@ -160,6 +160,25 @@ moa_status moa_inner(moa_op reduce, moa_op combine, moa_dtype dtype, moa_form fo
                      void *out, moa_dtype out_dtype, moa_stream stream);
 
 /*
+ * moa_inner_host — moa_inner for arrays held in host memory: the same
+ * Eq. (2), tuples, forms, exactness and errors, with A, B and out host
+ * pointers (page-locked memory, e.g. from cudaHostAlloc, lets the copies
+ * run asynchronously; pageable memory works but the copies then wait for
+ * the host).  The call enqueues on `stream` the copy of B and A to the
+ * device, the inner product, and the copy of D back into out; when D has
+ * more than 1024 rows (psi-flattened M), its rows are computed in up to four
+ * blocks so that the copies of one block overlap the computation of
+ * another (library-owned copy streams, ordered with `stream` by events).
+ * The host buffers must stay valid and unchanged until `stream` reaches the
+ * end of the call.  Device copies live in a library workspace kept per
+ * (device, stream) (MOA_ERR_WORKSPACE when it cannot be had).  A device
+ * pointer for A, B or out returns MOA_ERR_INVALID.
+ */
+moa_status moa_inner_host(moa_op reduce, moa_op combine, moa_dtype dtype, moa_form form, int rankA,
+                          const int64_t *shapeA, const void *A, int rankB, const int64_t *shapeB, const void *B,
+                          void *out, moa_dtype out_dtype, moa_stream stream);
+
+/*
  * moa_inner_axes — Eq. (2) contracting axis `axisA` of A with axis `axisB`
  * of B (equal lengths) instead of A's last and B's first:
  *   D[i.., j..] = reduce_p ( A[.., p at axisA, ..] combine B[.., p at axisB, ..] ),
@@ -287,6 +306,19 @@ moa_status moa_device_status(moa_stream stream);
  * context stays usable.  Diagnostic only (no counterpart in the paper).
  */
 moa_status moa_selftest_wait_timeout(uint32_t limit_us, moa_stream stream);
+
+/*
+ * moa_kernel_timing — diagnostic timing of the library's tensor-core GEMM
+ * launches (no counterpart in the paper): with enable = 1 every such launch
+ * on the current device is bracketed by a pair of CUDA events recorded on
+ * its stream (and the record of an earlier start is cleared); enable = 0
+ * stops recording.  moa_kernel_timing_read waits for the recorded events and
+ * returns how many launches were recorded and their summed device time in
+ * milliseconds.  Other kernels (pre-passes, CUDA-core kernels) are not
+ * recorded.
+ */
+moa_status moa_kernel_timing(int enable);
+moa_status moa_kernel_timing_read(int64_t *launches, double *total_ms);
 
 /* Free the scratch workspace held for every stream of the current device (synchronises). */
 moa_status moa_release_workspace(void);

@@ -22,6 +22,7 @@ __all__ = [
     "moa_device_status", "moa_release_workspace", "moa_version", "inner", "outer", "OPS", "DTYPES", "FORMS",
     "moa_batch_plan_create", "moa_batch_execute", "moa_batch_plan_destroy", "moa_batch_plan_info", "MoaProblem",
     "moa_inner_bf16x3_noalloc", "NOALLOC_SCRATCH_BYTES", "make_problems", "moa_selftest_wait_timeout",
+    "moa_inner_host", "moa_kernel_timing", "moa_kernel_timing_read",
 ]
 
 # size of the fixed device buffer behind moa_inner_bf16x3_noalloc (MOA_NOALLOC_SCRATCH_BYTES)
@@ -68,6 +69,9 @@ def lib():
         L.moa_inner.argtypes = [I, I, I, I, I, _I64P, P, I, _I64P, P, P, I, V]
         L.moa_outer.argtypes = [I, I, I, _I64P, P, I, _I64P, P, P, I, V]
         L.moa_inner_axes.argtypes = [I, I, I, I, I, _I64P, P, I, I, _I64P, P, I, P, I, V]
+        L.moa_inner_host.argtypes = [I, I, I, I, I, _I64P, P, I, _I64P, P, P, I, V]
+        L.moa_kernel_timing.argtypes = [I]
+        L.moa_kernel_timing_read.argtypes = [C.POINTER(I64), C.POINTER(C.c_double)]
         L.moa_transpose.argtypes = [I, I, _I64P, C.POINTER(C.c_int), P, P, V]
         L.moa_inner_shape.argtypes = [I, _I64P, I, _I64P, C.POINTER(C.c_int), _I64P]
         L.moa_outer_shape.argtypes = [I, _I64P, I, _I64P, C.POINTER(C.c_int), _I64P]
@@ -105,6 +109,15 @@ def _ptr(x):
     return x.data_ptr()
 
 
+def _hptr(x):
+    """Host address of a CPU tensor, a numpy array or an int."""
+    if x is None or isinstance(x, int):
+        return x
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
 def _stream(stream):
     if stream is None:
         import torch
@@ -134,6 +147,32 @@ def moa_inner(reduce, combine, dtype, form, shapeA, A, shapeB, B, out, out_dtype
     if check:
         _check(st, "moa_inner")
     return st
+
+
+def moa_inner_host(reduce, combine, dtype, form, shapeA, A, shapeB, B, out, out_dtype, stream=None, check=True):
+    """C ABI moa_inner_host: Eq. (2) on arrays in host memory (copies in and
+    out inside the call, ordered on `stream`).  A, B, out: host addresses or
+    CPU tensors / numpy arrays (page-locked memory keeps the copies async)."""
+    sa, _ka = _shape(shapeA)
+    sb, _kb = _shape(shapeB)
+    st = lib().moa_inner_host(_enum(OPS, reduce), _enum(OPS, combine), _enum(DTYPES, dtype), _enum(FORMS, form),
+                              len(shapeA), sa, _hptr(A), len(shapeB), sb, _hptr(B), _hptr(out),
+                              _enum(DTYPES, out_dtype), _stream(stream))
+    if check:
+        _check(st, "moa_inner_host")
+    return st
+
+
+def moa_kernel_timing(enable: bool):
+    """Start (True) or stop (False) CUDA-event timing of the library's GEMM launches."""
+    _check(lib().moa_kernel_timing(1 if enable else 0), "moa_kernel_timing")
+
+
+def moa_kernel_timing_read():
+    """(launches, total device milliseconds) of the GEMM launches recorded since the last start."""
+    n, ms = C.c_int64(0), C.c_double(0.0)
+    _check(lib().moa_kernel_timing_read(C.byref(n), C.byref(ms)), "moa_kernel_timing_read")
+    return int(n.value), float(ms.value)
 
 
 def moa_inner_axes(reduce, combine, dtype, form, shapeA, A, axisA, shapeB, B, axisB, out, out_dtype, stream=None,

@@ -160,7 +160,8 @@ struct InnerPlan {
 
 static moa_status inner_validate(moa_op reduce, moa_op combine, moa_dtype dtype, moa_form form, int rankA,
                                  const int64_t *shapeA, const void *A, int rankB, const int64_t *shapeB, const void *B,
-                                 const void *out, moa_dtype out_dtype, InnerPlan *pl, bool check_ptrs = true) {
+                                 const void *out, moa_dtype out_dtype, InnerPlan *pl, int ptr_checks = 2) {
+    // ptr_checks: 0 shapes and types only, 1 also null and alignment, 2 also device memory
     if (rankA < 1 || rankB < 1 || rankA > kMaxRank || rankB > kMaxRank) return MOA_ERR_RANK;
     if (!shapeA || !shapeB) return MOA_ERR_NULL;
     if ((unsigned)reduce > MOA_OP_AND || (unsigned)combine > MOA_OP_AND || (unsigned)dtype > MOA_B1_U32 ||
@@ -196,6 +197,8 @@ static moa_status inner_validate(moa_op reduce, moa_op combine, moa_dtype dtype,
     }
     if (!ok) return MOA_ERR_UNSUPPORTED;
 
+    pl->M = M, pl->K = K, pl->N = N;
+    if (ptr_checks == 0) return MOA_OK;
     if (M * N > 0) {
         if (!out) return MOA_ERR_NULL;
         if (M * K > 0 && !A) return MOA_ERR_NULL;
@@ -204,11 +207,10 @@ static moa_status inner_validate(moa_op reduce, moa_op combine, moa_dtype dtype,
     if (!aligned_to(A, elem_bytes(dtype)) || !aligned_to(B, elem_bytes(dtype)) ||
         !aligned_to(out, elem_bytes(out_dtype)))
         return MOA_ERR_ALIGNMENT;
-    if (check_ptrs && M * N > 0) {  // only operands the call reads, and the result it writes
+    if (ptr_checks >= 2 && M * N > 0) {  // only operands the call reads, and the result it writes
         const void *used[3] = {M * K > 0 ? A : nullptr, K * N > 0 ? B : nullptr, out};
         if ((st = check_device_ptrs(used, 3)) != MOA_OK) return st;
     }
-    pl->M = M, pl->K = K, pl->N = N;
     return MOA_OK;
 }
 
@@ -276,6 +278,23 @@ static moa_status inner_run(moa_op reduce, moa_op combine, moa_dtype dtype, moa_
     default: break;
     }
     return MOA_ERR_UNSUPPORTED;
+}
+
+size_t dtype_bytes(moa_dtype t) { return elem_bytes(t); }
+
+// Validation of moa_inner (all pointer checks when `launch`, none
+// otherwise: moa_inner_host validates its host pointers itself) and, with
+// `launch`, the run on `stream`; the psi-flattened extents are returned.
+moa_status inner_checked(moa_op reduce, moa_op combine, moa_dtype dtype, moa_form form, int rankA,
+                         const int64_t *shapeA, const void *A, int rankB, const int64_t *shapeB, const void *B,
+                         void *out, moa_dtype out_dtype, cudaStream_t stream, int64_t *M, int64_t *K, int64_t *N,
+                         bool launch) {
+    InnerPlan pl;
+    moa_status st = inner_validate(reduce, combine, dtype, form, rankA, shapeA, A, rankB, shapeB, B, out, out_dtype, &pl,
+                                   launch ? 2 : 0);
+    if (st != MOA_OK) return st;
+    *M = pl.M, *K = pl.K, *N = pl.N;
+    return launch ? inner_run(reduce, combine, dtype, form, A, B, out, out_dtype, pl, stream) : MOA_OK;
 }
 
 }  // namespace moa
@@ -367,7 +386,7 @@ moa_status moa_inner_axes(moa_op reduce, moa_op combine, moa_dtype dtype, moa_fo
     for (int k = 0; k < rankB; ++k)
         if (k != axisB) pb[r] = k, sb[r++] = shapeB[k];
     InnerPlan pl;
-    moa_status st = inner_validate(reduce, combine, dtype, form, rankA, sa, A, rankB, sb, B, out, out_dtype, &pl, false);
+    moa_status st = inner_validate(reduce, combine, dtype, form, rankA, sa, A, rankB, sb, B, out, out_dtype, &pl, 1);
     if (st != MOA_OK) return st;
     const bool moveA = axisA != rankA - 1, moveB = axisB != 0;
     const bool empty = pl.M == 0 || pl.N == 0 || pl.K == 0;  // nothing to read

@@ -1,0 +1,153 @@
+// moa_inner_host: the generalized inner product (Eq. 2) of arrays held in
+// host memory.  The call copies A and B to the device, runs the same path as
+// moa_inner there and copies D back, all ordered on the caller's stream.
+//
+// For a result of many rows the copies overlap the computation: the
+// psi-flattened rows of A and D (Fig. 1: row i of D needs row i of A and all
+// of B) are cut into up to four blocks; B and the first block of A go in
+// first, then block b computes while block b+1 of A comes in on an upload
+// stream and block b-1 of D goes out on a download stream.  Two device
+// buffers per operand block alternate.  The two copy streams belong to the
+// library (one pair per device and caller stream) and wait on, and are
+// waited on by, the caller's stream through events, so the whole call is
+// ordered on `stream` like every other call.
+#include <cstring>
+#include <map>
+#include <mutex>
+
+#include "internal.h"
+
+namespace moa {
+
+moa_status inner_checked(moa_op reduce, moa_op combine, moa_dtype dtype, moa_form form, int rankA,
+                         const int64_t *shapeA, const void *A, int rankB, const int64_t *shapeB, const void *B,
+                         void *out, moa_dtype out_dtype, cudaStream_t stream, int64_t *M, int64_t *K, int64_t *N,
+                         bool launch);
+size_t dtype_bytes(moa_dtype t);
+
+namespace {
+
+constexpr int kBufs = 2;
+constexpr int kMaxBlocks = 4;
+
+struct CopyStreams {
+    cudaStream_t up = nullptr, down = nullptr;
+    cudaEvent_t start = nullptr, b_in = nullptr, finished = nullptr;
+    cudaEvent_t a_in[kBufs] = {}, computed[kBufs] = {}, d_out[kBufs] = {};
+};
+
+std::mutex g_mu;
+std::map<std::pair<int, cudaStream_t>, CopyStreams> g_streams;
+
+moa_status copy_streams(cudaStream_t s, CopyStreams **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return MOA_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_streams.find({dev, s});
+    if (it == g_streams.end()) {
+        CopyStreams c;
+        bool ok = cudaStreamCreateWithFlags(&c.up, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&c.down, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&c.start, cudaEventDisableTiming) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&c.b_in, cudaEventDisableTiming) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&c.finished, cudaEventDisableTiming) == cudaSuccess;
+        for (int i = 0; i < kBufs && ok; ++i)
+            ok = cudaEventCreateWithFlags(&c.a_in[i], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&c.computed[i], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&c.d_out[i], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            return MOA_ERR_CUDA;
+        }
+        it = g_streams.emplace(std::make_pair(dev, s), c).first;
+    }
+    *out = &it->second;
+    return MOA_OK;
+}
+
+bool host_memory(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+}  // namespace
+}  // namespace moa
+
+using namespace moa;
+
+extern "C" moa_status moa_inner_host(moa_op reduce, moa_op combine, moa_dtype dtype, moa_form form, int rankA,
+                                     const int64_t *shapeA, const void *A, int rankB, const int64_t *shapeB,
+                                     const void *B, void *out, moa_dtype out_dtype, moa_stream stream) {
+    int64_t M = 0, K = 0, N = 0;
+    // validation of everything but where the memory lives
+    moa_status st = inner_checked(reduce, combine, dtype, form, rankA, shapeA, nullptr, rankB, shapeB, nullptr,
+                                  nullptr, out_dtype, nullptr, &M, &K, &N, false);
+    if (st != MOA_OK) return st;
+    if (M == 0 || N == 0) return MOA_OK;
+    if (!out || (M * K > 0 && !A) || (K * N > 0 && !B)) return MOA_ERR_NULL;
+    if (!host_memory(out) || (M * K > 0 && !host_memory(A)) || (K * N > 0 && !host_memory(B))) return MOA_ERR_INVALID;
+    const cudaStream_t s = (cudaStream_t)stream;
+    const size_t ea = dtype_bytes(dtype), ed = dtype_bytes(out_dtype);
+    // blocks of rows (whole result for packed bits, whose rows need not start on a word)
+    int nb = 1;
+    if (dtype != MOA_B1_U32) {
+        nb = (int)(M / 512);
+        nb = nb < 1 ? 1 : (nb > kMaxBlocks ? kMaxBlocks : nb);
+    }
+    const int64_t rows = (M + nb - 1) / nb;
+    const size_t bytesB = dtype == MOA_B1_U32 ? (size_t)((K * N + 31) / 32) * 4 : (size_t)(K * N) * ea;
+    const size_t bytesA = dtype == MOA_B1_U32 ? (size_t)((M * K + 31) / 32) * 4 : (size_t)(rows * K) * ea;
+    const size_t bytesD = out_dtype == MOA_B1_U32 ? (size_t)((M * N + 31) / 32) * 4 : (size_t)(rows * N) * ed;
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t offA = up(bytesB), offD = offA + kBufs * up(bytesA), total = offD + kBufs * up(bytesD);
+    uint8_t *ws = (uint8_t *)workspace_get(s, total, &st, 2);
+    if (st != MOA_OK) return st;
+    CopyStreams *c = nullptr;
+    if ((st = copy_streams(s, &c)) != MOA_OK) return st;
+    auto ok = [](cudaError_t e) { return e == cudaSuccess; };
+    // the copy streams start after the work already queued on `stream` (which
+    // may still read the buffers of an earlier call)
+    if (!ok(cudaEventRecord(c->start, s)) || !ok(cudaStreamWaitEvent(c->up, c->start, 0)) ||
+        !ok(cudaStreamWaitEvent(c->down, c->start, 0)))
+        return MOA_ERR_CUDA;
+    uint8_t *dB = ws, *dA[kBufs], *dD[kBufs];
+    for (int i = 0; i < kBufs; ++i) dA[i] = ws + offA + i * up(bytesA), dD[i] = ws + offD + i * up(bytesD);
+    if (bytesB && !ok(cudaMemcpyAsync(dB, B, bytesB, cudaMemcpyHostToDevice, c->up))) return MOA_ERR_CUDA;
+    if (!ok(cudaEventRecord(c->b_in, c->up))) return MOA_ERR_CUDA;
+    auto upload = [&](int b) -> bool {
+        const int64_t r0 = b * rows, r1 = (r0 + rows < M) ? r0 + rows : M;
+        const size_t n = dtype == MOA_B1_U32 ? bytesA : (size_t)((r1 - r0) * K) * ea;
+        const uint8_t *src = (const uint8_t *)A + (dtype == MOA_B1_U32 ? 0 : (size_t)(r0 * K) * ea);
+        if (b >= kBufs && !ok(cudaStreamWaitEvent(c->up, c->computed[b % kBufs], 0))) return false;  // buffer free
+        if (n && !ok(cudaMemcpyAsync(dA[b % kBufs], src, n, cudaMemcpyHostToDevice, c->up))) return false;
+        return ok(cudaEventRecord(c->a_in[b % kBufs], c->up));
+    };
+    if (!upload(0)) return MOA_ERR_CUDA;
+    if (!ok(cudaStreamWaitEvent(s, c->b_in, 0))) return MOA_ERR_CUDA;
+    for (int b = 0; b < nb; ++b) {
+        const int64_t r0 = b * rows, r1 = (r0 + rows < M) ? r0 + rows : M;
+        if (b + 1 < nb && !upload(b + 1)) return MOA_ERR_CUDA;
+        if (!ok(cudaStreamWaitEvent(s, c->a_in[b % kBufs], 0))) return MOA_ERR_CUDA;
+        if (b >= kBufs && !ok(cudaStreamWaitEvent(s, c->d_out[b % kBufs], 0))) return MOA_ERR_CUDA;  // D buffer free
+        // the block as its own inner product: rho A = <rows, K>, rho B = <K, N>
+        const int64_t sa[2] = {r1 - r0, K}, sb[2] = {K, N};
+        int64_t m, k, n;
+        st = inner_checked(reduce, combine, dtype, form, 2, sa, dA[b % kBufs], 2, sb, dB, dD[b % kBufs], out_dtype, s,
+                           &m, &k, &n, true);
+        if (st != MOA_OK) return st;
+        if (!ok(cudaEventRecord(c->computed[b % kBufs], s)) || !ok(cudaStreamWaitEvent(c->down, c->computed[b % kBufs], 0)))
+            return MOA_ERR_CUDA;
+        const size_t nd = out_dtype == MOA_B1_U32 ? bytesD : (size_t)((r1 - r0) * N) * ed;
+        uint8_t *dst = (uint8_t *)out + (out_dtype == MOA_B1_U32 ? 0 : (size_t)(r0 * N) * ed);
+        if (nd && !ok(cudaMemcpyAsync(dst, dD[b % kBufs], nd, cudaMemcpyDeviceToHost, c->down))) return MOA_ERR_CUDA;
+        if (!ok(cudaEventRecord(c->d_out[b % kBufs], c->down))) return MOA_ERR_CUDA;
+    }
+    // `stream` is done with the call once the last result has left the device
+    if (!ok(cudaEventRecord(c->finished, c->down)) || !ok(cudaStreamWaitEvent(s, c->finished, 0))) return MOA_ERR_CUDA;
+    if (!ok(cudaStreamWaitEvent(s, c->a_in[(nb - 1) % kBufs], 0))) return MOA_ERR_CUDA;
+    return MOA_OK;
+}

@@ -14,7 +14,7 @@ namespace moa {
 // Workspace: scratch device memory owned by the library, one buffer per
 // (device, stream, slot), grown with stream-ordered allocation (api.cu).
 // Slot 0 serves the inner and outer products, slot 1 the transposed operands
-// of moa_inner_axes.
+// of moa_inner_axes, slot 2 the device copies of moa_inner_host's operands.
 void *workspace_get(cudaStream_t stream, size_t bytes, moa_status *st, int slot = 0);
 
 // MOA_OK when every non-null pointer of ptrs[0..n) lies in device (or
@@ -23,6 +23,19 @@ void *workspace_get(cudaStream_t stream, size_t bytes, moa_status *st, int slot 
 // know).  The tensor maps and kernels of the library address A, B and out as
 // memory of the device they run on.
 moa_status check_device_ptrs(const void *const *ptrs, int n);
+
+// timing.cu — while moa_kernel_timing is on, a GemmTimer around a GEMM
+// launch records a CUDA event pair on the launch stream (nothing otherwise).
+class GemmTimer {
+  public:
+    explicit GemmTimer(cudaStream_t s);
+    void done();  // call right after the launch
+    ~GemmTimer();
+
+  private:
+    cudaStream_t stream_;
+    cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
 
 // outer.cu — Eq. (1) over the flattened operands (C is M x N, M = |A|, N = |B|).
 cudaError_t launch_outer(int op, moa_dtype dtype, moa_dtype out_dtype, const void *A, const void *B, void *C,

@@ -5,19 +5,24 @@
 // multiplication and its applications", Numer. Algorithms 59, 2012), with
 // power-of-two scales per row of A and per column of B.
 //
-//   row i of A:    e_i with max_k |A[i,k]| < 2^e_i,  A[i,k] = 2^e_i * a'  (|a'| < 1)
-//   column j of B: f_j with max_k |B[k,j]| < 2^f_j,  B[k,j] = 2^f_j * b'
-//   a' ~ sum_{s<S} d_s 2^-(s+1)beta, d_s integers in [-(2^beta - 1), 2^beta - 1]
-//   (the digits of |a'| truncated to S*beta fractional bits, signed like a')
+//   row i of A:    e_i with max_k |A[i,k]| < 2^(e_i - 1),  A[i,k] = 2^e_i * a'
+//                  (|a'| < 1/2)
+//   column j of B: f_j likewise,  B[k,j] = 2^f_j * b'
+//   a' ~ sum_{s<S} d_s 2^-(s+1)beta, the S * beta fractional bits of |a'|
+//        (truncated) written in balanced base 2^beta: d_s in [-2^(beta-1),
+//        2^(beta-1) - 1] for s > 0 and d_0 in [0, 2^(beta-1)], signed like a'
 //   D[i,j] ~ 2^(e_i + f_j) * sum_{s+u<S} 2^-(s+u+2)beta * (A_s . B_u)[i,j]
 //
-// With beta = 7 every digit is an integer of magnitude <= 127, exact in bf16,
-// and a 1024-long partial sum of digit products stays below 2^24, so each
-// chunk the tensor cores accumulate in FP32 is exact.  The pairs with
-// s + u >= S are dropped (their weight is below 2^-(S+1)beta).  S slices keep
-// S * 7 bits of every operand relative to its row / column maximum; S grows
-// as the contraction shortens (a short sum can be dominated by entries far
-// below their row or column maximum, and it costs little to slice deeper).
+// With beta = 8 every digit is an integer of magnitude <= 128, exact in bf16,
+// every digit product is at most 2^14, and a 1024-long partial sum stays at
+// or below 2^24, so each chunk the tensor cores accumulate in FP32 is exact.
+// The balanced digits carry 8 bits each where unsigned 7-bit digits carried
+// 7 at the same product bound, so 7 slices keep 55 bits of every operand
+// relative to its row / column maximum (28 slice products) where 8 slices of
+// 7 bits needed 36 products for 56 bits.  The pairs with s + u >= S are
+// dropped (their weight is at most 2^-(S+2)beta * 2^14).  S grows as the
+// contraction shortens (a short sum can be dominated by entries far below
+// their row or column maximum, and it costs little to slice deeper).
 //
 // Pre-pass (this file, memory bound): |A| row maxima and |B| column maxima as
 // FP64 bit patterns (integer max of the magnitude bits; finite inputs), then
@@ -28,6 +33,7 @@
 #include "common.cuh"
 #include "internal.h"
 #include "tc.h"
+#include "ozaki_epi.cuh"
 
 namespace moa {
 
@@ -38,16 +44,20 @@ moa_status tc_gemm_ozaki(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat1
 namespace {
 
 constexpr int kMaxSlices = 10;
-constexpr int kBeta = 7;
-constexpr int kChunkKBlocks = 16;  // 16 x 64 = 1024 products per exact FP32 chunk
+constexpr int kBeta = 8;
+constexpr int kChunkKBlocks = 16;  // 16 x 64 = 1024 products (each at most 2^14) per exact FP32 chunk
 
 MOA_DEV uint64_t mag_bits(double x) { return (uint64_t)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull; }
 
-// one warp per row: max |A[i, :]| as magnitude bits
-__global__ void row_max_kernel(const double *__restrict__ A, int64_t M, int64_t K, uint64_t *__restrict__ out) {
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+// one warp per row: max |A[i, :]| as magnitude bits; the grid also zeroes
+// the N column maxima that col_max_kernel, launched next, combines into
+__global__ void row_max_kernel(const double *__restrict__ A, int64_t M, int64_t K, uint64_t *__restrict__ out,
+                               uint64_t *__restrict__ col_zero, int64_t N) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nthreads = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = tid; j < N; j += nthreads) col_zero[j] = 0;
+    const int64_t warp = tid / 32;
     const int lane = threadIdx.x % 32;
-    const int64_t nwarps = (int64_t)gridDim.x * blockDim.x / 32;
+    const int64_t nwarps = nthreads / 32;
     for (int64_t i = warp; i < M; i += nwarps) {
         uint64_t m = 0;
         for (int64_t k = lane; k < K; k += 32) m = max(m, mag_bits(__ldg(A + i * K + k)));
@@ -69,53 +79,93 @@ __global__ void col_max_kernel(const double *__restrict__ B, int64_t K, int64_t 
     if (m) atomicMax((unsigned long long *)(out + j), (unsigned long long)m);
 }
 
-MOA_DEV int scale_exp(uint64_t maxbits) {
-    const int be = (int)((maxbits >> 52) & 0x7FF);
-    if (be == 0) return maxbits == 0 ? 0 : -1022;
-    return be - 1022;
-}
-
-// Digit s of |x| * 2^-e (|x| < 2^e): floor(|x| 2^(-e + (s+1) beta)) mod 2^beta,
-// from the FP64 fields (|x| = mant * 2^ex).
-MOA_DEV int digit(uint64_t mant, int ex, int e, int s) {
-    const int t = ex - e + (s + 1) * kBeta;  // |x| 2^(-e + (s+1) beta) = mant * 2^t
-    uint64_t v;
-    if (t >= 0) v = t >= 64 ? 0 : (mant << t);
-    else v = (-t) >= 64 ? 0 : (mant >> (-t));
-    return (int)(v & ((1u << kBeta) - 1u));
+// The S balanced digits of one element, signed like it: |x| = mant 2^ex,
+// scaled by 2^-e (|x| < 2^(e-1)).  The unsigned base-2^beta digits u_s of
+// the truncated |x| 2^-e (u_s = floor(|x| 2^(-e + (s+1) beta)) mod 2^beta,
+// u_0 < 2^(beta-1)) are rewritten from the lowest up: a digit of 2^(beta-1)
+// or more becomes u - 2^beta with a carry of one into the next higher digit.
+MOA_DEV void balanced_digits(uint64_t mant, int ex, int e, bool neg, int S, int (&d)[kMaxSlices]) {
+    int carry = 0;
+#pragma unroll
+    for (int s = kMaxSlices - 1; s >= 0; --s) {
+        if (s >= S) {
+            d[s] = 0;
+            continue;
+        }
+        const int t = ex - e + (s + 1) * kBeta;  // |x| 2^(-e + (s+1) beta) = mant * 2^t
+        uint64_t v;
+        if (t >= 0) v = t >= 64 ? 0 : (mant << t);
+        else v = (-t) >= 64 ? 0 : (mant >> (-t));
+        int u = (int)(v & ((1u << kBeta) - 1u)) + carry;
+        carry = 0;
+        if (s > 0 && u >= (1 << (kBeta - 1))) {
+            u -= 1 << kBeta;
+            carry = 1;
+        }
+        d[s] = neg ? -u : u;
+    }
 }
 
 // X rows x cols (row stride cols) -> S digit planes [S][rows][colsp];
 // row_scale: the exponent comes from maxbits[row], else from maxbits[col].
-template <bool ROW_SCALE>
+// Four consecutive columns per thread (colsp is a multiple of 8): one or two
+// 16-byte loads when the row allows (VEC), one 8-byte store per plane.
+template <bool ROW_SCALE, bool VEC>
 __global__ void __launch_bounds__(256) slice_kernel(const double *__restrict__ X, int64_t rows, int64_t cols,
                                                      int64_t colsp, const uint64_t *__restrict__ maxbits, int S,
                                                      __nv_bfloat16 *__restrict__ out) {
-    const int64_t plane = rows * colsp;
+    const int64_t plane = rows * colsp, groups = colsp / 4;
     for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
-        const int er = ROW_SCALE ? scale_exp(maxbits[r]) : 0;
-        for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < colsp; c += (int64_t)gridDim.x * blockDim.x) {
-            uint64_t mant = 0;
-            int ex = 0, e = 0;
-            bool neg = false;
-            if (c < cols) {
-                const double x = __ldg(X + r * cols + c);
-                const uint64_t b = (uint64_t)__double_as_longlong(x);
-                const int be = (int)((b >> 52) & 0x7FF);
-                mant = be ? ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) : (b & 0xFFFFFFFFFFFFFull);
-                ex = (be ? be : 1) - 1075;
-                e = ROW_SCALE ? er : scale_exp(maxbits[c]);
-                neg = (b >> 63) != 0;
-            }
-            __nv_bfloat16 *dst = out + r * colsp + c;
+        const int er = ROW_SCALE ? ozaki::scale_exponent(maxbits[r]) : 0;
+        const double *src = X + r * cols;
+        for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t c0 = 4 * g;
+            double x[4];
+            if constexpr (VEC) {  // cols % 4 == 0 and 16-byte aligned rows: the group is all in or all out
+                if (c0 < cols) {
+                    const double2 v0 = __ldg(reinterpret_cast<const double2 *>(src + c0));
+                    const double2 v1 = __ldg(reinterpret_cast<const double2 *>(src + c0 + 2));
+                    x[0] = v0.x, x[1] = v0.y, x[2] = v1.x, x[3] = v1.y;
+                } else {
+                    x[0] = x[1] = x[2] = x[3] = 0.0;
+                }
+            } else {
 #pragma unroll
-            for (int s = 0; s < kMaxSlices; ++s) {
-                if (s >= S) break;
-                const int d = mant ? digit(mant, ex, e, s) : 0;
-                dst[s * plane] = __int2bfloat16_rn(neg ? -d : d);
+                for (int t = 0; t < 4; ++t) x[t] = c0 + t < cols ? __ldg(src + c0 + t) : 0.0;
+            }
+            __align__(8) __nv_bfloat16 pl[kMaxSlices][4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const uint64_t b = (uint64_t)__double_as_longlong(x[t]);
+                const int be = (int)((b >> 52) & 0x7FF);
+                const uint64_t mant = be ? ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) : (b & 0xFFFFFFFFFFFFFull);
+                const int ex = (be ? be : 1) - 1075;
+                const int e = ROW_SCALE ? er : (c0 + t < cols ? ozaki::scale_exponent(maxbits[c0 + t]) : 0);
+                int d[kMaxSlices];
+                balanced_digits(mant, ex, e, (b >> 63) != 0, S, d);
+#pragma unroll
+                for (int q = 0; q < kMaxSlices; ++q) pl[q][t] = __int2bfloat16_rn(d[q]);
+            }
+            __nv_bfloat16 *dst = out + r * colsp + c0;
+#pragma unroll
+            for (int q = 0; q < kMaxSlices; ++q) {
+                if (q >= S) break;
+                *reinterpret_cast<uint2 *>(dst + q * plane) = *reinterpret_cast<const uint2 *>(pl[q]);
             }
         }
     }
+}
+
+template <bool ROW_SCALE>
+void run_slices(const double *X, int64_t rows, int64_t cols, int64_t colsp, const uint64_t *maxbits, int S,
+                __nv_bfloat16 *out, cudaStream_t s) {
+    const int64_t groups = colsp / 4;
+    const int64_t gx = groups >= 256 * 4 ? 4 : (groups + 255) / 256;
+    const dim3 grid((unsigned)gx, (unsigned)(rows < 4096 ? rows : 4096));
+    if (cols % 4 == 0 && (uintptr_t)X % 16 == 0)
+        slice_kernel<ROW_SCALE, true><<<grid, 256, 0, s>>>(X, rows, cols, colsp, maxbits, S, out);
+    else
+        slice_kernel<ROW_SCALE, false><<<grid, 256, 0, s>>>(X, rows, cols, colsp, maxbits, S, out);
 }
 
 int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
@@ -130,7 +180,7 @@ int ozaki_slices(int64_t K) {
         return (v < 4 || v > kMaxSlices) ? 0 : v;
     }();
     if (forced) return forced;
-    return K <= 256 ? 10 : (K <= 2048 ? 9 : 8);
+    return K <= 256 ? 8 : 7;
 }
 
 size_t ozaki_workspace_bytes(int64_t M, int64_t N, int64_t K) {
@@ -141,8 +191,8 @@ size_t ozaki_workspace_bytes(int64_t M, int64_t N, int64_t K) {
 moa_status tc_inner_ozaki(const double *A, const double *B, double *D, int64_t M, int64_t N, int64_t K,
                           cudaStream_t s) {
     // the int32 sum of one weight class (at most S pairs of K digit products
-    // below 127^2) must stay below 2^31
-    if ((double)ozaki_slices(K) * (double)K * 127.0 * 127.0 >= 2147483648.0) return MOA_ERR_UNSUPPORTED;
+    // of magnitude at most 2^14) must stay below 2^31
+    if ((double)ozaki_slices(K) * (double)K * 16384.0 >= 2147483648.0) return MOA_ERR_UNSUPPORTED;
     const int64_t Kp = round8(K), Np = round8(N);
     moa_status st;
     uint8_t *ws = (uint8_t *)workspace_get(s, ozaki_workspace_bytes(M, N, K), &st);
@@ -156,8 +206,7 @@ moa_status tc_inner_ozaki(const double *A, const double *B, double *D, int64_t M
     // scales
     {
         int64_t warps = M < 152 * 32 ? M : 152 * 32;
-        row_max_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(A, M, K, rmax);
-        if (cudaMemsetAsync(cmax, 0, (size_t)N * 8, s) != cudaSuccess) return MOA_ERR_CUDA;
+        row_max_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(A, M, K, rmax, cmax, N);
         const int64_t gx = (N + 255) / 256;
         int64_t gy = (152 * 8 + gx - 1) / gx;
         if (gy > K) gy = K;
@@ -166,13 +215,9 @@ moa_status tc_inner_ozaki(const double *A, const double *B, double *D, int64_t M
         col_max_kernel<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, s>>>(B, K, N, rpb, cmax);
     }
     // digit planes
-    {
-        const int64_t gxa = Kp >= 1024 ? 4 : (Kp + 255) / 256;
-        slice_kernel<true><<<dim3((unsigned)gxa, (unsigned)(M < 4096 ? M : 4096)), 256, 0, s>>>(A, M, K, Kp, rmax, S, a);
-        const int64_t gxb = Np >= 1024 ? 4 : (Np + 255) / 256;
-        slice_kernel<false><<<dim3((unsigned)gxb, (unsigned)(K < 4096 ? K : 4096)), 256, 0, s>>>(B, K, N, Np, cmax, S, b);
-        if (cudaGetLastError() != cudaSuccess) return MOA_ERR_CUDA;
-    }
+    run_slices<true>(A, M, K, Kp, rmax, S, a, s);
+    run_slices<false>(B, K, N, Np, cmax, S, b, s);
+    if (cudaGetLastError() != cudaSuccess) return MOA_ERR_CUDA;
     // accumulator units 2^-lsb with lsb = (S + 1) beta: every kept pair weight 2^(lsb - (s+u+2) beta) >= 1
     const int lsb = (S + 1) * kBeta;
     return tc_gemm_ozaki(a, Kp, b, Np, S, kBeta, lsb, kChunkKBlocks, rmax, cmax, D, N, M, N, K, rs, s);

@@ -4,7 +4,7 @@
 // double-float running sum, and the final conversion to FP64.
 //
 // Slices: A = sum_s 2^(e_row - (s+1) beta) A_s and B likewise with digit
-// planes A_s, B_u of beta-bit integers; the product keeps the pairs
+// planes A_s, B_u of balanced beta-bit integers; the product keeps the pairs
 // s + u < S, grouped by weight class g = s + u.  Accumulators count units of
 // 2^(e_row + e_col - lsb).
 #pragma once
@@ -44,12 +44,13 @@ struct Iter {
     }
 };
 
-// Exponent e with |x| < 2^e for the largest |x| of a row / column, from its
-// FP64 bit pattern (0 for an all-zero row).
+// Exponent e with |x| < 2^(e-1) for the largest |x| of a row / column, from
+// its FP64 bit pattern (0 for an all-zero row): the scaled values lie below
+// 1/2, which leaves the balanced top digit its carry.
 MOA_DEV int scale_exponent(uint64_t maxbits) {
     const int be = (int)((maxbits >> 52) & 0x7FF);
-    if (be == 0) return maxbits == 0 ? 0 : -1022;
-    return be - 1022;
+    if (be == 0) return maxbits == 0 ? 0 : -1021;
+    return be - 1021;
 }
 
 // The power-of-two weight of class g in accumulator units, exact in FP32.

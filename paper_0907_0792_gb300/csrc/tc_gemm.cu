@@ -505,8 +505,11 @@ cudaError_t launch_tc(const CUtensorMap &ta, const CUtensorMap &tb, GemmParams &
     p.tiles_n = (p.N + BN - 1) / BN;
     const int tiles = p.tiles_m * p.tiles_n;
     const int ctas = tiles < num_sms() ? tiles : num_sms();
+    GemmTimer timer(s);
     kern<<<ctas, cta_threads(MODE), C::SMEM, s>>>(ta, tb, p);
-    return cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
+    timer.done();
+    return e;
 }
 
 }  // namespace
@@ -614,9 +617,10 @@ moa_status tc_gemm_ozaki(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat1
                          int64_t ldd, int64_t M, int64_t N, int64_t K, void *scratch, cudaStream_t s) {
     if (M >= (1ll << 31) || N >= (1ll << 31) || K >= (1ll << 31)) return MOA_ERR_OVERFLOW;
     // weights 2^(lsb - (g+2) beta) must be exact FP32 powers of two >= 1, and a
-    // class sum (g+1 <= S pairs of K * (2^beta-1)^2) must stay below 2^31
+    // class sum (g+1 <= S pairs of K balanced digit products, each at most
+    // 2^(2 beta - 2) in magnitude) must stay below 2^31
     if (S < 1 || S > 10 || chunk_kblocks < 1 || lsb - 2 * beta > 100 || lsb - (S + 1) * beta < 0 ||
-        (double)S * (double)K * ((1 << beta) - 1) * ((1 << beta) - 1) >= 2147483648.0)
+        (double)S * (double)K * (double)(1 << (2 * beta - 2)) >= 2147483648.0)
         return MOA_ERR_INTERNAL;
     if ((uintptr_t)A % 16 || (uintptr_t)B % 16 || lda % 8 || ldb % 8) return MOA_ERR_INTERNAL;
     CUtensorMap ta, tb;

@@ -573,7 +573,10 @@ cudaError_t launch_pair(const CUtensorMap &ta, const CUtensorMap &tb, const CUte
     const int clusters = tiles < max_clusters ? tiles : max_clusters;
     cfg.gridDim = dim3(2 * clusters);
     cfg.stream = s;
-    return cudaLaunchKernelEx(&cfg, kern, ta, tb, td, tsa, tsb, p);
+    GemmTimer timer(s);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, ta, tb, td, tsa, tsb, p);
+    timer.done();
+    return e;
 }
 
 }  // namespace

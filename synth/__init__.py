@@ -70,6 +70,14 @@ def uniform_at(seed: int, stream: int, idx, lo: float, hi: float) -> np.ndarray:
     return lo + (hi - lo) * ((z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53))
 
 
+def u64_at(seed: int, stream: int, idx) -> np.ndarray:
+    """The elements of ``u64(seed, stream, n)`` at the given positions."""
+    key = _key(seed, stream)
+    i = np.asarray(idx, dtype=np.uint64) + np.uint64(1)
+    with np.errstate(over="ignore"):
+        return _mix(key + i * GAMMA)
+
+
 def _i64(u: int) -> int:
     """A 64-bit pattern as the signed integer torch stores it as."""
     u &= 0xFFFFFFFFFFFFFFFF
@@ -115,6 +123,18 @@ def bernoulli(seed: int, stream: int, shape, p: float) -> np.ndarray:
     return uniform01(seed, stream, int(np.prod(shape, dtype=np.int64))).reshape(shape) < p
 
 
+def _log_uniform_from(r: np.ndarray, lo_exp2: int, hi_exp2: int) -> np.ndarray:
+    e = (r % np.uint64(hi_exp2 - lo_exp2)).astype(np.int64) + lo_exp2
+    f = 1.0 + ((r >> np.uint64(11)) & np.uint64((1 << 52) - 1)).astype(np.float64) * (2.0 ** -52)
+    s = np.where((r >> np.uint64(10)) & np.uint64(1), -1.0, 1.0)
+    return s * np.ldexp(f, e)
+
+
+def log_uniform_at(seed: int, stream: int, idx, lo_exp2: int = -13, hi_exp2: int = 13) -> np.ndarray:
+    """The elements of ``log_uniform_signed`` at the given flat positions."""
+    return _log_uniform_from(u64_at(seed, stream, idx), lo_exp2, hi_exp2)
+
+
 def log_uniform_signed(seed: int, stream: int, shape, lo_exp2: int = -13, hi_exp2: int = 13) -> np.ndarray:
     """Random sign times a magnitude spread evenly over octaves.
 
@@ -124,11 +144,7 @@ def log_uniform_signed(seed: int, stream: int, shape, lo_exp2: int = -13, hi_exp
     likely.  Built with ``ldexp`` only, so it is bit-identical across hosts.
     """
     n = int(np.prod(shape, dtype=np.int64))
-    r = u64(seed, stream, n)
-    e = (r % np.uint64(hi_exp2 - lo_exp2)).astype(np.int64) + lo_exp2
-    f = 1.0 + ((r >> np.uint64(11)) & np.uint64((1 << 52) - 1)).astype(np.float64) * (2.0 ** -52)
-    s = np.where((r >> np.uint64(10)) & np.uint64(1), -1.0, 1.0)
-    return (s * np.ldexp(f, e)).reshape(shape)
+    return _log_uniform_from(u64(seed, stream, n), lo_exp2, hi_exp2).reshape(shape)
 
 
 # ---------------------------------------------------------------- rounding
@@ -219,6 +235,26 @@ def square(n: int, dist: str = "uniform", seed: int = 2, m: int | None = None, k
     if dist == "loguniform":
         return log_uniform_signed(seed, tag, (m, k)), log_uniform_signed(seed, tag + 1, (k, n))
     raise ValueError(dist)
+
+
+SWEEP_N = (256, 512, 1024, 2048, 4096, 8192)
+
+
+def square_leading(n: int, dist: str = "uniform", n_full: int = 8192, seed: int = 2):
+    """The leading n x n blocks of the operands ``square(n_full, dist)``,
+    drawn positionally (the square sweep's smaller sizes are sub-blocks of
+    its largest case; n = n_full gives ``square(n_full, dist)`` itself)."""
+    if n == n_full:
+        return square(n_full, dist, seed)
+    idx = (np.arange(n, dtype=np.int64)[:, None] * n_full + np.arange(n, dtype=np.int64)[None, :]).reshape(-1)
+    tag = 0 if dist == "uniform" else 10
+    if dist == "uniform":
+        A, B = uniform_at(seed, tag, idx, -1.0, 1.0), uniform_at(seed, tag + 1, idx, -1.0, 1.0)
+    elif dist == "loguniform":
+        A, B = log_uniform_at(seed, tag, idx), log_uniform_at(seed, tag + 1, idx)
+    else:
+        raise ValueError(dist)
+    return A.reshape(n, n), B.reshape(n, n)
 
 
 def skinny_shapes(m: int, n: int, k: int = SKINNY_K):

@@ -204,6 +204,19 @@ def test_problem_struct_layout_matches_header(tmp_path):
     assert got[1:] == [getattr(moa.MoaProblem, f).offset for f in fields]
 
 
+def test_host_entry_and_timing_validation(L):
+    """moa_inner_host validates shapes, types and null pointers before any
+    copy; the timing read rejects null outputs."""
+    def h(sa, sb, dt="f32", form="native", A=0x1000, B=0x2000, out=0x3000, odt="f32"):
+        return moa.moa_inner_host("add", "mul", dt, form, sa, A, sb, B, out, odt, stream=0, check=False)
+    assert h((4, 5), (6, 7)) == 3
+    assert h((), (5, 7)) == 2
+    assert h((4, 5), (5, 7), dt="f64", form="bf16x3", odt="f64") == 5
+    assert h((4, 5), (5, 7), out=0) == 1
+    assert h((0, 5), (5, 7), A=0, out=0) == 0
+    assert moa.lib().moa_kernel_timing_read(None, None) == 1
+
+
 def test_status_strings(L):
     assert moa.moa_status_string(0) == "ok"
     assert "shape" in moa.moa_status_string(3)

@@ -3,14 +3,19 @@
 operands.
 
 Tolerance: 6e-2 (the stated FP8 bound) for the square sweep's shapes, with
-uniform and log-uniform operands, and for any shape with uniform operands
-and a contraction of 256 or more.  Shorter contractions of uniform operands
-get the bound of the arithmetic alone: each product carries at most two
-e4m3 roundings (unit roundoff u = 2^-4), so |error| <= (2u + u^2) sum|a||b|
-= 0.129.  Log-uniform operands spanning 26 binades exceed e4m3's range
-inside one scale block (entries far below the block maximum round to
-subnormals or zero), so short, single-product-dominated contractions of
-such data are outside this form's accuracy; the square sweep keeps them."""
+uniform and log-uniform operands, for any shape with uniform operands and a
+contraction of 256 or more, and for log-uniform operands with a contraction
+of 512 or more.  Shorter contractions of uniform operands get the bound of
+the arithmetic alone: each product carries at most two e4m3 roundings (unit
+roundoff u = 2^-4), so |error| <= (2u + u^2) sum|a||b| = 0.129.
+
+Log-uniform operands with a contraction of 256 to 511 exceed 6e-2: their
+sums are dominated by a few products whose e4m3 rounding errors (up to
+2^-4 relative per operand) do not average out.  Measured (GPU, and the
+same quantisation modelled in FP64 on the CPU): 0.066-0.068 at K = 256 and
+K = 300 (130 x K . K x 131, seeds 51-53), 0.052-0.055 at K = 512, 0.036-0.047
+at K = 1000, 0.029-0.031 at K = 2048.  Those shapes are held to 7e-2, the
+measured maximum with a margin, and listed here rather than left out."""
 import pytest
 
 import paper_0907_0792_gb300 as moa
@@ -37,6 +42,20 @@ def test_fp8_small(shA, shB):
     A = synth.to_f32(synth.uniform(51, 0, shA, -1, 1))
     B = synth.to_f32(synth.uniform(51, 1, shB, -1, 1))
     tol = 6e-2 if shA[-1] >= 256 else SMALL_K_TOL
+    assert_norm_err(_fp8(A, B).cpu().numpy(), A, B, tol)
+    check_status()
+
+
+LOG_SHAPES = [((130, 256), (256, 131)), ((130, 300), (300, 131)), ((300, 512), (512, 200)),
+              ((130, 1000), (1000, 131)), ((520, 1000), (1000, 700)), ((256, 2048), (2048, 256))]
+
+
+@pytest.mark.parametrize("shA,shB", LOG_SHAPES)
+def test_fp8_loguniform_shapes(shA, shB):
+    """Log-uniform operands (26 binades) at contractions of 256 and more."""
+    A = synth.to_f32(synth.log_uniform_signed(51, 0, shA))
+    B = synth.to_f32(synth.log_uniform_signed(51, 1, shB))
+    tol = 6e-2 if shA[-1] >= 512 else 7e-2
     assert_norm_err(_fp8(A, B).cpu().numpy(), A, B, tol)
     check_status()
 

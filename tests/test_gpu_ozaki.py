@@ -11,8 +11,10 @@ from gpu_helpers import assert_norm_err, check_status, empty, sample_idx, to_dev
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-12
+# contractions on both sides of the slice-count change (8 slices up to K = 256, 7 above)
 SHAPES = [((300, 136), (136, 200)), ((2, 64, 72), (72, 5, 80)), ((129, 8), (8, 257)), ((1, 1), (1, 1)),
-          ((37, 61), (61, 45)), ((130, 1500), (1500, 131)), ((16, 12, 8, 64), (64, 24, 20))]
+          ((37, 61), (61, 45)), ((130, 1500), (1500, 131)), ((16, 12, 8, 64), (64, 24, 20)),
+          ((140, 256), (256, 150)), ((140, 257), (257, 150)), ((260, 3000), (3000, 270))]
 
 
 def _ozaki(A, B):
@@ -42,6 +44,11 @@ def test_ozaki_zero_rows_columns_and_wide_range():
     A[5] *= 1e200
     B[:, 9] *= 1e-200
     A[6, 4] = 5e-310  # subnormal entry
+    # entries just below a power of two: every lower digit of the scaled value is all ones, so the
+    # balanced digits carry into the top one (which becomes 2^(beta-1))
+    A[8] = np.nextafter(1.0, 0.0) * np.where(np.arange(90) % 2, 1.0, -1.0)
+    B[:, 11] = np.nextafter(0.5, 0.0)
+    A[9, :] = np.nextafter(np.ldexp(1.0, -3), 0.0)
     D = _ozaki(A, B).cpu().numpy()
     assert np.all(D[3] == 0) and np.all(D[:, 7] == 0)
     assert_norm_err(D, A, B, TOL)
@@ -52,6 +59,19 @@ def test_ozaki_square_whole(n):
     for dist in ("uniform", "loguniform"):
         A, B = synth.square(n, dist)
         assert_norm_err(_ozaki(A, B).cpu().numpy(), A, B, TOL)
+    check_status()
+
+
+def test_ozaki_longest_contraction_sampled():
+    """K = 16384, the longest contraction the form takes (a class sum of 7
+    slice pairs stays below 2^31)."""
+    import torch
+    for dist in ("uniform", "loguniform"):
+        A, B = synth.square(300, dist, m=300, k=16384)
+        D = _ozaki(A, B)
+        idx = sample_idx(300 * 300, 2000)
+        got = D.view(-1)[torch.from_numpy(idx).to(D.device)].cpu().numpy()
+        assert_norm_err(got, A, B, TOL, out_idx=idx)
     check_status()
 
 

@@ -1,0 +1,58 @@
+"""GPU parity of every configuration of the square matrix-multiply sweep that
+bench.py times: each form of the (+,*) inner product (Eq. 2, matrix multiply
+as its special case, Sec. I) at n = 256 .. 8192 with uniform and log-uniform
+values, on the sweep's own operands (leading blocks of the n = 8192 arrays,
+synth.square_leading), in the launch configuration the benchmark times.
+Whole results at n <= 512, 1,500 sampled outputs above, against the
+oracle's Dot2 reference of the operands as the form receives them.
+
+Bars (normalised error |D - D_exact| / sum_p |A||B|): Ozaki and plain FP64
+1e-12; FP32 native, split-BF16x3 and bf16 operands as given 2e-6; BF16 form
+1e-2; FP8 form 6e-2."""
+import numpy as np
+import pytest
+
+import paper_0907_0792_gb300 as moa
+import synth
+from gpu_helpers import assert_norm_err, bf16_dev, check_status, empty, sample_idx, to_dev
+
+pytestmark = pytest.mark.gpu
+
+FORMS = [("ozaki", "f64", 1e-12), ("native", "f64", 1e-12), ("native", "f32", 2e-6), ("bf16x3", "f32", 2e-6),
+         ("bf16", "f32", 1e-2), ("fp8_t128", "f32", 6e-2), ("native", "bf16", 2e-6)]
+_FULL = {}
+
+
+def _operands(n, dist):
+    if dist not in _FULL:
+        _FULL[dist] = synth.square(max(synth.SWEEP_N), dist)
+    A, B = _FULL[dist]
+    return np.ascontiguousarray(A[:n, :n]), np.ascontiguousarray(B[:n, :n])
+
+
+@pytest.mark.parametrize("dist", ["uniform", "loguniform"])
+@pytest.mark.parametrize("n", list(synth.SWEEP_N))
+def test_sweep_configuration(n, dist):
+    import torch
+    A64, B64 = _operands(n, dist)
+    assert np.array_equal(A64[:64, :64], synth.square_leading(64, dist)[0])  # the sweep's own operands
+    idx = None if n <= 512 else sample_idx(n * n, 1500, seed=n)
+    for form, dtype, tol in FORMS:
+        if dtype == "f64":
+            a, b, A, B = A64, B64, to_dev(A64), to_dev(B64)
+        elif dtype == "f32":
+            a, b = synth.to_f32(A64), synth.to_f32(B64)
+            A, B = to_dev(a), to_dev(b)
+        else:
+            (abits, a), (bbits, b) = synth.to_bf16(A64), synth.to_bf16(B64)
+            A, B = bf16_dev(abits), bf16_dev(bbits)
+        D = empty((n, n), torch.float64 if dtype == "f64" else torch.float32)
+        moa.moa_inner("add", "mul", dtype, form, (n, n), A, (n, n), B, D, "f64" if dtype == "f64" else "f32")
+        got = D.cpu().numpy() if idx is None else D.view(-1)[torch.from_numpy(idx).to(D.device)].cpu().numpy()
+        try:
+            assert_norm_err(got, a, b, tol, out_idx=idx)
+        except AssertionError as e:
+            raise AssertionError(f"{form}:{dtype} n={n} {dist}: {e}") from None
+        del A, B, D
+    check_status()
+    torch.cuda.empty_cache()

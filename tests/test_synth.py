@@ -102,3 +102,14 @@ def test_batched_workload_matches_its_recipe():
     # about 1/11 per octave; rounding 2^0 (1 + f) sends half of the first octave to M = 2
     assert 0.07 < share[1:].min() and share[1:].max() < 0.13 and 0.02 < share[0] < 0.08
 
+
+
+def test_square_leading_is_the_leading_block():
+    """The sweep's smaller sizes are the leading blocks of the largest case's
+    operands, drawn positionally."""
+    for dist in ("uniform", "loguniform"):
+        A, B = synth.square(512, dist)
+        a, b = synth.square_leading(64, dist, n_full=512)
+        assert np.array_equal(a, A[:64, :64]) and np.array_equal(b, B[:64, :64])
+        a, b = synth.square_leading(512, dist, n_full=512)
+        assert np.array_equal(a, A) and np.array_equal(b, B)
