@@ -196,7 +196,7 @@ SWEEP_FORMS = (("ozaki", "f64"), ("native", "f64"), ("native", "f32"), ("bf16x3"
 
 def ozaki_slices(k: int) -> int:
     """Digit slices per operand the library's Ozaki form takes for a contraction of length k."""
-    return 8 if k <= 256 else 7
+    return 10 if k <= 64 else (8 if k <= 256 else 7)
 
 
 def sweep_work(form: str, dtype: str, n: int, peaks: dict, sustained: bool = False):
@@ -565,24 +565,32 @@ def run_reference(args, rank, ws):
 
 
 # ---------------------------------------------------------------- main
+SHORT_FORM = {("ozaki", "f64"): "oz", ("native", "f64"): "f64", ("native", "f32"): "f32", ("bf16x3", "f32"): "x3",
+              ("bf16", "f32"): "bf16", ("fp8_t128", "f32"): "fp8", ("native", "bf16"): "bf16in"}
+
+
 def _summary(rows: dict) -> dict:
-    """Compact digest of the rows (kept short: it ends the JSON line)."""
+    """Compact digest of the rows (kept short: it ends the JSON line).  Sweep
+    keys: form (oz Ozaki, f64 / f32 native, x3 split-BF16x3, bf16 / fp8 forms
+    from FP32, bf16in bf16 operands) : distribution (u uniform, l log-uniform);
+    values per sweep size."""
     out = {}
     sw = rows.get("square_sweep") or []
     if sw:
         eff, frac = {}, {}
         for r in sw:
-            key = f"{r['form']}:{r['dtype']}:{r['dist'][0]}"
-            eff.setdefault(key, []).append(r["tflops_effective"])
+            key = f"{SHORT_FORM.get((r['form'], r['dtype']), r['form'])}:{r['dist'][0]}"
+            v = r["tflops_effective"]
+            eff.setdefault(key, []).append(round(v) if v >= 100 else (round(v, 1) if v >= 10 else round(v, 2)))
             if r["n"] >= 4096:
-                frac.setdefault(key, []).append(r["frac_of_peak"])
+                frac.setdefault(key, []).append(round(r["frac_of_peak"], 2))
         out["sweep_n"] = sorted({r["n"] for r in sw})
         out["sweep_eff_tflops"] = eff
         out["sweep_frac_n4096_8192"] = frac
     if rows.get("semirings"):
-        out["semiring_gops"] = {r["semiring"]: r["gops"] for r in rows["semirings"]}
+        out["semiring_gops"] = {r["semiring"]: round(r["gops"]) for r in rows["semirings"]}
     if rows.get("outer"):
-        out["outer_frac_hbm"] = {f"{r['op']}:{r['dtype']}": r["frac_hbm"] for r in rows["outer"]}
+        out["outer_frac_hbm"] = {f"{r['op']}:{r['dtype']}": round(r["frac_hbm"], 2) for r in rows["outer"]}
     if rows.get("batched_10000"):
         b = rows["batched_10000"]
         out["batched"] = {"ms": b["ms"], "speedup_vs_one_call": b["speedup_vs_one_call_per_problem"]}

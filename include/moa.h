@@ -19,8 +19,10 @@
  * Conventions shared by every call
  * --------------------------------
  *  Layout     Element vectors are row-major (C order) ravels of the array,
- *             as the appendix's addressing RES(i*restride+j),
- *             L(l+i*lstride), R(l*rstride+j) implies.  MOA_B1_U32 arrays are
+ *             as the appendix's addressing implies (element (i, p) of the
+ *             flattened left operand at i*K + p, element (p, j) of the right
+ *             operand and (i, j) of the result at p*N + j and i*N + j).
+ *             MOA_B1_U32 arrays are
  *             the row-major ravel packed as a bit stream: element e is bit
  *             (e % 32) (LSB first) of 32-bit word e / 32; the last word's
  *             unused bits are zero on input and written as zero on output.

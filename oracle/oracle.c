@@ -15,8 +15,9 @@
  *
  * Conventions (the paper's statement of the problem, Sec. I):
  *  - an array is a shape vector (rho A) plus an element vector;
- *  - elements are stored contiguously in row-major order (the appendix's
- *    RES(i*restride+j), L(l+i*lstride), R(l*rstride+j) addressing);
+ *  - elements are stored contiguously in row-major order (the appendix
+ *    addresses row i of the left operand, row p of the right operand and
+ *    row i of the result at multiples of their row lengths);
  *  - psi-indexing: a full index vector idx selects the element at
  *    offset sum_k idx[k] * prod_{m>k} rho[m].
  *
@@ -356,15 +357,16 @@ int oracle_outer_i32(int op, int rankA, const int64_t *shA, const int32_t *A, in
 /* ------------------------------------------- appendix-order formulation */
 
 /*
- * The paper's own organisation (Fig. 1 and the appendix's MoA fragment):
- * one result row at a time; for each position l of the contraction, row l of
- * the right operand, scaled by the element (i, l) of the left operand, is
- * accumulated into row i of the result; rows are dealt to threads cyclically
- * (thread t takes rows t, t+T, ...).  The arrays are addressed through the
- * flattening the appendix uses: noproc = prod(rho A without its last axis)
- * rows, rowsinred = the contracted length, elsinop = prod(rho B without its
- * first axis) elements per row, lstride = rowsinred, rstride = restride =
- * elsinop.
+ * Row-at-a-time organisation of the inner product (Fig. 1; the appendix's
+ * MoA routine is organised this way): the arrays are psi-flattened to an
+ * M x K left operand, a K x N right operand and an M x N result (M = prod of
+ * rho A without its last axis, K the contracted length, N = prod of rho B
+ * without its first axis).  Result row i starts at the identity of the
+ * reduce; then for every contraction position p, row p of the right operand
+ * is combined with the single element A[i][p] and reduced into row i, one
+ * element at a time along the row.  Result rows are shared among threads
+ * round-robin (thread t owns rows t, t + T, t + 2T, ...), the thread
+ * organisation of Sec. II.
  *
  * Plain recursive summation in the working type (no compensation).  This is
  * the second formulation the definition loops are cross-checked against, and
@@ -378,10 +380,9 @@ int oracle_rowwise(int kind, int reduce, int combine, int rankA, const int64_t *
     int64_t nD;
     int st = inner_check(rankA, shA, rankB, shB, &nD);
     if (st) return st;
-    const int64_t rowsinred = shA[rankA - 1];
-    const int64_t noproc = tau(rankA - 1, shA);
-    const int64_t elsinop = tau(rankB - 1, shB + 1);
-    const int64_t lstride = rowsinred, rstride = elsinop, restride = elsinop;
+    const int64_t M = tau(rankA - 1, shA);      /* result rows */
+    const int64_t K = shA[rankA - 1];           /* contracted length */
+    const int64_t N = tau(rankB - 1, shB + 1);  /* elements of a result row */
     if (nthreads < 1) nthreads = 1;
     if (kind == 1 && !((reduce == OP_ADD && combine == OP_MUL) ||
                        ((reduce == OP_MIN || reduce == OP_MAX) &&
@@ -391,35 +392,44 @@ int oracle_rowwise(int kind, int reduce, int combine, int rankA, const int64_t *
 #ifdef _OPENMP
 #pragma omp parallel for schedule(static, 1) num_threads(nthreads)
 #endif
-    for (int64_t i = 0; i < noproc; ++i) {
+    for (int64_t i = 0; i < M; ++i) {
         if (kind == 0) {
-            double *res = (double *)D + i * restride;
-            const double *l_ = (const double *)A, *r_ = (const double *)B;
-            for (int64_t j = 0; j < elsinop; ++j) res[j] = 0.0;
-            for (int64_t l = 0; l < rowsinred; ++l)
-                for (int64_t j = 0; j < elsinop; ++j) res[j] = res[j] + l_[l + i * lstride] * r_[l * rstride + j];
+            const double *a_row = (const double *)A + i * K;
+            double *d_row = (double *)D + i * N;
+            for (int64_t j = 0; j < N; ++j) d_row[j] = 0.0;
+            for (int64_t p = 0; p < K; ++p) {
+                const double alpha = a_row[p];
+                const double *b_row = (const double *)B + p * N;
+                for (int64_t j = 0; j < N; ++j) d_row[j] = d_row[j] + alpha * b_row[j];
+            }
         } else if (kind == 1) {
-            float *res = (float *)D + i * restride;
-            const float *l_ = (const float *)A, *r_ = (const float *)B;
-            for (int64_t j = 0; j < elsinop; ++j) res[j] = reduce == OP_ADD ? 0.0f : f32_identity(reduce);
-            for (int64_t l = 0; l < rowsinred; ++l)
-                for (int64_t j = 0; j < elsinop; ++j) {
-                    const float t = f32_combine(combine, l_[l + i * lstride], r_[l * rstride + j]);
-                    res[j] = f32_combine(reduce, res[j], t);
-                }
+            const float *a_row = (const float *)A + i * K;
+            float *d_row = (float *)D + i * N;
+            const float start = reduce == OP_ADD ? 0.0f : f32_identity(reduce);
+            for (int64_t j = 0; j < N; ++j) d_row[j] = start;
+            for (int64_t p = 0; p < K; ++p) {
+                const float alpha = a_row[p];
+                const float *b_row = (const float *)B + p * N;
+                for (int64_t j = 0; j < N; ++j) d_row[j] = f32_combine(reduce, d_row[j], f32_combine(combine, alpha, b_row[j]));
+            }
         } else if (kind == 2) {
-            uint32_t *res = (uint32_t *)D + i * restride;
-            const int32_t *l_ = (const int32_t *)A, *r_ = (const int32_t *)B;
-            for (int64_t j = 0; j < elsinop; ++j) res[j] = 0u;
-            for (int64_t l = 0; l < rowsinred; ++l)
-                for (int64_t j = 0; j < elsinop; ++j)
-                    res[j] = res[j] + (uint32_t)l_[l + i * lstride] * (uint32_t)r_[l * rstride + j];
+            const int32_t *a_row = (const int32_t *)A + i * K;
+            uint32_t *d_row = (uint32_t *)D + i * N;
+            for (int64_t j = 0; j < N; ++j) d_row[j] = 0u;
+            for (int64_t p = 0; p < K; ++p) {
+                const uint32_t alpha = (uint32_t)a_row[p];
+                const int32_t *b_row = (const int32_t *)B + p * N;
+                for (int64_t j = 0; j < N; ++j) d_row[j] = d_row[j] + alpha * (uint32_t)b_row[j];
+            }
         } else {
-            uint8_t *res = (uint8_t *)D + i * restride;
-            const uint8_t *l_ = (const uint8_t *)A, *r_ = (const uint8_t *)B;
-            for (int64_t j = 0; j < elsinop; ++j) res[j] = 0;
-            for (int64_t l = 0; l < rowsinred; ++l)
-                for (int64_t j = 0; j < elsinop; ++j) res[j] = res[j] | (l_[l + i * lstride] & r_[l * rstride + j]);
+            const uint8_t *a_row = (const uint8_t *)A + i * K;
+            uint8_t *d_row = (uint8_t *)D + i * N;
+            for (int64_t j = 0; j < N; ++j) d_row[j] = 0;
+            for (int64_t p = 0; p < K; ++p) {
+                const uint8_t alpha = a_row[p];
+                const uint8_t *b_row = (const uint8_t *)B + p * N;
+                for (int64_t j = 0; j < N; ++j) d_row[j] = d_row[j] | (alpha & b_row[j]);
+            }
         }
     }
     return ORC_OK;

@@ -2,8 +2,8 @@
 // dispatch of the generalized inner product (Eq. 2) and outer product
 // (Eq. 1), plus the per-stream scratch workspace.
 //
-// psi-flattening (Fig. 1; the appendix addresses A as L(l + i*lstride), B as
-// R(l*rstride + j) and the result as RES(i*restride + j)): for rho A =
+// psi-flattening (Fig. 1; the appendix addresses element (i, p) of A at
+// i*K + p, (p, j) of B at p*N + j and (i, j) of the result at i*N + j): for rho A =
 // <a_0 .. a_{r-2}, p> and rho B = <p, b_1 .. b_{s-1}>, the row-major element
 // vectors already are an M x K and a K x N row-major matrix with
 // M = prod a, K = p, N = prod b, and D's element vector is the M x N

@@ -117,19 +117,26 @@ def test_full_size_sampled(op, dt):
         idx = sample_idx(C.numel(), 200000)
         got = C.view(-1)[torch.from_numpy(idx).to(C.device)].cpu().numpy()
         assert np.array_equal(got, oracle.outer_i32(op, A, B, out_idx=idx))
+        slab = C.view(-1)[: 8 * B.size].cpu().numpy()
+        want = oracle.outer_i32(op, A.ravel()[:8], B.ravel())
     elif dt == "f32":
         A, B = synth.outer_inputs(op, "f32")
         C = _run(op, "f32", to_dev(A), to_dev(B), "f32", shA, shB)
         idx = sample_idx(C.numel(), 200000)
         got = C.view(-1)[torch.from_numpy(idx).to(C.device)].cpu().numpy()
         assert np.array_equal(got, oracle.outer_f(op, A, B, out="f32", out_idx=idx))
+        slab = C.view(-1)[: 8 * B.size].cpu().numpy()
+        want = oracle.outer_f(op, A.ravel()[:8], B.ravel(), out="f32")
     else:
         (ab, av), (bb, bv) = synth.outer_inputs(op, "bf16")
         C = _run(op, "bf16", bf16_dev(ab), bf16_dev(bb), "bf16", shA, shB)
         idx = sample_idx(C.numel(), 200000)
         got = C.view(torch.int16).view(-1)[torch.from_numpy(idx).to(C.device)].cpu().numpy().view(np.uint16)
         assert np.array_equal(got, oracle.outer_f(op, av, bv, out="bf16", out_idx=idx))
-    # every row of the result must be A[i] op B (property on a whole slab)
+        slab = C.view(torch.int16).view(-1)[: 8 * bv.size].cpu().numpy().view(np.uint16)
+        want = oracle.outer_f(op, av.ravel()[:8], bv.ravel(), out="bf16")
+    # the first eight rows of the flattened result whole: row i is A[i] op B
+    assert np.array_equal(slab.ravel(), np.asarray(want).ravel())
     check_status()
     del C
     torch.cuda.empty_cache()

@@ -308,13 +308,28 @@ def test_outer_matches_numpy_ufunc_outer(op, uf):
     assert np.array_equal(gb.view(np.int16), ref)
 
 
-def test_outer_i32_and_rank0():
+def _wrap32(x):
+    """int64 values reduced to int32 two's complement (modulo 2^32)."""
+    x = np.asarray(x, dtype=np.int64) % 2 ** 32
+    return np.where(x >= 2 ** 31, x - 2 ** 32, x).astype(np.int32)
+
+
+@pytest.mark.parametrize("op,uf", [("add", np.add), ("sub", np.subtract), ("mul", np.multiply)])
+def test_outer_i32_and_rank0(op, uf):
+    """Eq. (1) over int32 for every operator: numpy's ufunc.outer in int64,
+    reduced modulo 2^32, on ordinary and on wrapping operands (sub is
+    A - B, not B - A)."""
     A, B = synth.outer_inputs("mul", "i32", shape_a=(4, 3), shape_b=(5,))
-    assert np.array_equal(oracle.outer_i32("mul", A, B), np.multiply.outer(A.astype(np.int64), B).astype(np.int32))
-    big = np.array([2 ** 31 - 1, -(2 ** 31)], dtype=np.int32)
-    want = (np.multiply.outer(big.astype(np.int64), big.astype(np.int64)) % 2 ** 32)
-    want = np.where(want >= 2 ** 31, want - 2 ** 32, want).astype(np.int32)
-    assert np.array_equal(oracle.outer_i32("mul", big, big), want)
+    assert np.array_equal(oracle.outer_i32(op, A, B), _wrap32(uf.outer(A.astype(np.int64), B.astype(np.int64))))
+    big = np.array([2 ** 31 - 1, -(2 ** 31), -1, 7], dtype=np.int32)
+    small = np.array([1, -2, 2 ** 30], dtype=np.int32)
+    assert np.array_equal(oracle.outer_i32(op, big, small),
+                          _wrap32(uf.outer(big.astype(np.int64), small.astype(np.int64))))
+    assert np.array_equal(oracle.outer_i32(op, big, big), _wrap32(uf.outer(big.astype(np.int64), big.astype(np.int64))))
+    # one element by hand: 2^31 - 1 + 1 wraps to -2^31; -2^31 - 1 wraps to 2^31 - 1; 3 - 5 = -2
+    assert oracle.outer_i32("add", big[:1], small[:1])[0, 0] == -(2 ** 31)
+    assert oracle.outer_i32("sub", big[1:2], small[:1])[0, 0] == 2 ** 31 - 1
+    assert oracle.outer_i32("sub", np.array([3], np.int32), np.array([5], np.int32))[0, 0] == -2
     # rank 0 operand: rho C = rho B
     s = np.array(3.0)
     assert np.array_equal(oracle.outer_f("mul", s, np.arange(4.0)), 3.0 * np.arange(4.0))
