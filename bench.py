@@ -191,7 +191,7 @@ FP32_FFMA_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 # (form, operand dtype): the square sweep's forms
 SWEEP_FORMS = (("ozaki", "f64"), ("native", "f64"), ("native", "f32"), ("bf16x3", "f32"), ("bf16", "f32"),
-               ("fp8_t128", "f32"), ("native", "bf16"))
+               ("f16", "f32"), ("fp8_t128", "f32"), ("native", "bf16"))
 
 
 def ozaki_slices(k: int) -> int:
@@ -210,8 +210,8 @@ def sweep_work(form: str, dtype: str, n: int, peaks: dict, sustained: bool = Fal
         return 6 * f, bf16, "tensor", "bf16 dense"
     if form == "fp8_t128":
         return f, 2 * bf16, "tensor", "e4m3 dense (2x measured bf16)"
-    if form == "bf16" or dtype == "bf16":
-        return f, bf16, "tensor", "bf16 dense"
+    if form in ("bf16", "f16") or dtype == "bf16":
+        return f, bf16, "tensor", "bf16 dense" if form != "f16" else "fp16 dense (= bf16 measured)"
     if dtype == "f32":
         return f, FP32_FFMA_TFLOPS, "alu", "FP32 FFMA issue bound"
     return f, FP64_NOMINAL_TFLOPS, "fp64", "FP64 nominal"
@@ -566,13 +566,14 @@ def run_reference(args, rank, ws):
 
 # ---------------------------------------------------------------- main
 SHORT_FORM = {("ozaki", "f64"): "oz", ("native", "f64"): "f64", ("native", "f32"): "f32", ("bf16x3", "f32"): "x3",
-              ("bf16", "f32"): "bf16", ("fp8_t128", "f32"): "fp8", ("native", "bf16"): "bf16in"}
+              ("bf16", "f32"): "bf16", ("f16", "f32"): "f16", ("fp8_t128", "f32"): "fp8", ("native", "bf16"): "bf16in"}
 
 
 def _summary(rows: dict) -> dict:
     """Compact digest of the rows (kept short: it ends the JSON line).  Sweep
-    keys: form (oz Ozaki, f64 / f32 native, x3 split-BF16x3, bf16 / fp8 forms
-    from FP32, bf16in bf16 operands) : distribution (u uniform, l log-uniform);
+    keys: form (oz Ozaki, f64 / f32 native, x3 split-BF16x3, bf16 / f16 / fp8
+    forms from FP32, bf16in bf16 operands) : distribution (u uniform, l
+    log-uniform);
     values per sweep size."""
     out = {}
     sw = rows.get("square_sweep") or []

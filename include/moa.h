@@ -99,9 +99,10 @@ typedef enum {
     MOA_F64 = 0,
     MOA_F32 = 1,
     MOA_BF16 = 2,
-    MOA_FP8E4M3 = 3, /* reserved for storage; FP8 is used internally by MOA_FORM_FP8_T128 */
+    MOA_FP8E4M3 = 3, /* OCP FP8 E4M3 (1 sign, 4 exponent bits with bias 7, 3 mantissa bits; no infinities) */
     MOA_I32 = 4,
-    MOA_B1_U32 = 5   /* packed bits, see "Layout" above */
+    MOA_B1_U32 = 5,  /* packed bits, see "Layout" above */
+    MOA_F16 = 6      /* IEEE binary16 */
 } moa_dtype;
 
 /*
@@ -112,7 +113,15 @@ typedef enum {
  *             bf16 (inputs already bf16, FP32 out): tensor cores, FP32
  *             accumulation, <= 2e-6 relative to the bf16 operands.
  *             i32: exact modulo 2^32.
+ *             f16 (inputs already fp16, FP32 out): tensor cores, FP32
+ *             accumulation, <= 2e-6 relative to the fp16 operands.
+ *             fp8e4m3 (inputs already e4m3, unit scales, FP32 out): tensor
+ *             cores, FP32 accumulation, <= 2e-6 relative to the e4m3
+ *             operands.
  *   BF16      f32 in/out: operands rounded to bf16, tensor cores, <= 1e-2.
+ *   F16       f32 in/out: operands rounded to fp16 (RNE; magnitudes above
+ *             65504 held at 65504), tensor cores, <= 2e-3 for operands
+ *             whose magnitudes lie in fp16's normal range.
  *   FP8_T128  f32 in/out: operands scaled by powers of two per 1x128 block
  *             along the contraction and rounded to e4m3; tensor cores with
  *             the scale applied per block in FP32, <= 6e-2.
@@ -129,7 +138,8 @@ typedef enum {
     MOA_FORM_BF16 = 1,
     MOA_FORM_FP8_T128 = 2,
     MOA_FORM_BF16X3 = 3,
-    MOA_FORM_OZAKI = 4
+    MOA_FORM_OZAKI = 4,
+    MOA_FORM_F16 = 5
 } moa_form;
 
 /*
@@ -144,8 +154,10 @@ typedef enum {
  *
  * Supported (reduce, combine, dtype -> out_dtype, form):
  *   (add, mul) F64 -> F64      NATIVE | OZAKI
- *   (add, mul) F32 -> F32      NATIVE | BF16 | FP8_T128 | BF16X3
+ *   (add, mul) F32 -> F32      NATIVE | BF16 | F16 | FP8_T128 | BF16X3
  *   (add, mul) BF16 -> F32     NATIVE
+ *   (add, mul) F16 -> F32      NATIVE
+ *   (add, mul) FP8E4M3 -> F32  NATIVE (no NaN inputs)
  *   (add, mul) I32 -> I32      NATIVE (wraps modulo 2^32; when every value lies in
  *                              [-128, 127] and K <= 1024 it runs on tensor cores,
  *                              with the same bits)

@@ -29,8 +29,8 @@ __all__ = [
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 OPS = {"add": 0, "sub": 1, "mul": 2, "div": 3, "min": 4, "max": 5, "or": 6, "and": 7}
-DTYPES = {"f64": 0, "f32": 1, "bf16": 2, "fp8e4m3": 3, "i32": 4, "b1": 5}
-FORMS = {"native": 0, "bf16": 1, "fp8_t128": 2, "bf16x3": 3, "ozaki": 4}
+DTYPES = {"f64": 0, "f32": 1, "bf16": 2, "fp8e4m3": 3, "i32": 4, "b1": 5, "f16": 6}
+FORMS = {"native": 0, "bf16": 1, "fp8_t128": 2, "bf16x3": 3, "ozaki": 4, "f16": 5}
 STATUS = {0: "MOA_OK", 1: "MOA_ERR_NULL", 2: "MOA_ERR_RANK", 3: "MOA_ERR_SHAPE_MISMATCH", 4: "MOA_ERR_OVERFLOW",
           5: "MOA_ERR_UNSUPPORTED", 6: "MOA_ERR_WORKSPACE", 7: "MOA_ERR_CUDA", 8: "MOA_ERR_TIMEOUT",
           9: "MOA_ERR_INTERNAL", 10: "MOA_ERR_ALIGNMENT", 11: "MOA_ERR_INVALID", 12: "MOA_ERR_SCRATCH_LIMIT",
@@ -312,7 +312,11 @@ def moa_batch_plan_destroy(plan):
 # ------------------------------------------------------------ conveniences
 def _dtype_of(t):
     import torch
-    return {torch.float64: "f64", torch.float32: "f32", torch.bfloat16: "bf16", torch.int32: "i32"}[t.dtype]
+    table = {torch.float64: "f64", torch.float32: "f32", torch.bfloat16: "bf16", torch.float16: "f16",
+             torch.int32: "i32"}
+    if hasattr(torch, "float8_e4m3fn"):
+        table[torch.float8_e4m3fn] = "fp8e4m3"
+    return table[t.dtype]
 
 
 def inner(A, B, reduce="add", combine="mul", form="native", out=None, out_dtype=None, stream=None):
@@ -320,7 +324,7 @@ def inner(A, B, reduce="add", combine="mul", form="native", out=None, out_dtype=
     import torch
     dt = _dtype_of(A)
     if out_dtype is None:
-        out_dtype = "f32" if dt == "bf16" else dt
+        out_dtype = "f32" if dt in ("bf16", "f16", "fp8e4m3") else dt
     shD = tuple(A.shape[:-1]) + tuple(B.shape[1:])
     if out is None:
         tdt = {"f64": torch.float64, "f32": torch.float32, "i32": torch.int32}[out_dtype]

@@ -21,6 +21,7 @@
 namespace moa {
 
 static constexpr int kMaxRank = 8;
+static constexpr unsigned kMaxDtype = MOA_F16;  // largest moa_dtype code
 
 // ------------------------------------------------------------- validation
 static moa_status count_elems(int rank, const int64_t *shape, int64_t *count) {
@@ -43,6 +44,7 @@ static size_t elem_bytes(moa_dtype t) {
     case MOA_FP8E4M3: return 1;
     case MOA_I32: return 4;
     case MOA_B1_U32: return 4;
+    case MOA_F16: return 2;
     }
     return 0;
 }
@@ -164,8 +166,8 @@ static moa_status inner_validate(moa_op reduce, moa_op combine, moa_dtype dtype,
     // ptr_checks: 0 shapes and types only, 1 also null and alignment, 2 also device memory
     if (rankA < 1 || rankB < 1 || rankA > kMaxRank || rankB > kMaxRank) return MOA_ERR_RANK;
     if (!shapeA || !shapeB) return MOA_ERR_NULL;
-    if ((unsigned)reduce > MOA_OP_AND || (unsigned)combine > MOA_OP_AND || (unsigned)dtype > MOA_B1_U32 ||
-        (unsigned)out_dtype > MOA_B1_U32 || (unsigned)form > MOA_FORM_OZAKI)
+    if ((unsigned)reduce > MOA_OP_AND || (unsigned)combine > MOA_OP_AND || (unsigned)dtype > kMaxDtype ||
+        (unsigned)out_dtype > kMaxDtype || (unsigned)form > MOA_FORM_F16)
         return MOA_ERR_INVALID;
     int64_t nA, nB;
     moa_status st;
@@ -184,9 +186,10 @@ static moa_status inner_validate(moa_op reduce, moa_op combine, moa_dtype dtype,
     if (reduce == MOA_OP_ADD && combine == MOA_OP_MUL) {
         ok = (dtype == MOA_F64 && out_dtype == MOA_F64 && (form == MOA_FORM_NATIVE || form == MOA_FORM_OZAKI)) ||
              (dtype == MOA_F32 && out_dtype == MOA_F32 &&
-              (form == MOA_FORM_NATIVE || form == MOA_FORM_BF16 || form == MOA_FORM_BF16X3 ||
+              (form == MOA_FORM_NATIVE || form == MOA_FORM_BF16 || form == MOA_FORM_F16 || form == MOA_FORM_BF16X3 ||
                form == MOA_FORM_FP8_T128)) ||
-             (dtype == MOA_BF16 && out_dtype == MOA_F32 && form == MOA_FORM_NATIVE) ||
+             ((dtype == MOA_BF16 || dtype == MOA_F16 || dtype == MOA_FP8E4M3) && out_dtype == MOA_F32 &&
+              form == MOA_FORM_NATIVE) ||
              (dtype == MOA_I32 && out_dtype == MOA_I32 && form == MOA_FORM_NATIVE);
     } else if ((reduce == MOA_OP_MIN || reduce == MOA_OP_MAX) &&
                (combine == MOA_OP_ADD || combine == MOA_OP_SUB || combine == MOA_OP_MUL || combine == MOA_OP_MIN ||
@@ -275,6 +278,8 @@ static moa_status inner_run(moa_op reduce, moa_op combine, moa_dtype dtype, moa_
         }
         return tc_inner_f32(form, (const float *)A, (const float *)B, (float *)out, M, N, K, s);
     case MOA_BF16: return tc_inner_bf16((const __nv_bfloat16 *)A, (const __nv_bfloat16 *)B, (float *)out, M, N, K, s);
+    case MOA_F16: return tc_inner_f16((const __half *)A, (const __half *)B, (float *)out, M, N, K, s);
+    case MOA_FP8E4M3: return tc_inner_e4m3((const uint8_t *)A, (const uint8_t *)B, (float *)out, M, N, K, s);
     default: break;
     }
     return MOA_ERR_UNSUPPORTED;
@@ -349,7 +354,7 @@ moa_status moa_transpose(moa_dtype dtype, int rank, const int64_t *shape, const 
                          moa_stream stream) {
     if (rank < 0 || rank > kMaxRank) return MOA_ERR_RANK;
     if (rank > 0 && (!shape || !perm)) return MOA_ERR_NULL;
-    if ((unsigned)dtype > MOA_B1_U32) return MOA_ERR_INVALID;
+    if ((unsigned)dtype > kMaxDtype) return MOA_ERR_INVALID;
     if (dtype == MOA_B1_U32) return MOA_ERR_UNSUPPORTED;  // a packed bit stream has no per-element address
     bool seen[kMaxRank] = {};
     for (int k = 0; k < rank; ++k) {
@@ -422,7 +427,7 @@ moa_status moa_outer(moa_op op, moa_dtype dtype, int rankA, const int64_t *shape
                      const int64_t *shapeB, const void *B, void *out, moa_dtype out_dtype, moa_stream stream) {
     if (rankA < 0 || rankB < 0 || rankA > kMaxRank || rankB > kMaxRank) return MOA_ERR_RANK;
     if ((rankA > 0 && !shapeA) || (rankB > 0 && !shapeB)) return MOA_ERR_NULL;
-    if ((unsigned)op > MOA_OP_AND || (unsigned)dtype > MOA_B1_U32 || (unsigned)out_dtype > MOA_B1_U32)
+    if ((unsigned)op > MOA_OP_AND || (unsigned)dtype > kMaxDtype || (unsigned)out_dtype > kMaxDtype)
         return MOA_ERR_INVALID;
     int64_t M, N;
     moa_status st;

@@ -193,7 +193,85 @@ __global__ void __launch_bounds__(256) quant_bt_kernel(const float *__restrict__
     }
 }
 
+// Byte rows X (rows x cols, row stride cols) -> rows x colsp (colsp a
+// multiple of 16, zero past cols): one 16-byte store per thread.
+__global__ void __launch_bounds__(256) pad_rows_u8(const uint8_t *__restrict__ X, int64_t rows, int64_t cols,
+                                                   int64_t colsp, uint8_t *__restrict__ out) {
+    const int64_t groups = colsp / 16, total = rows * groups;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = idx / groups, c = (idx - r * groups) * 16;
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int b = 0; b < 16; ++b)
+            if (c + b < cols) w[b / 4] |= (uint32_t)__ldg(X + r * cols + c + b) << (8 * (b % 4));
+        *reinterpret_cast<uint4 *>(out + r * colsp + c) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// Bt [N][Kp] = B [K][N] transposed (bytes; zero for k >= K): 64 x 64 tiles
+// through shared memory, reads along B's rows, writes along Bt's rows.
+__global__ void __launch_bounds__(256) transpose_u8(const uint8_t *__restrict__ B, int64_t K, int64_t N, int64_t Kp,
+                                                    uint8_t *__restrict__ Bt) {
+    __shared__ uint8_t tile[64][65];
+    const int64_t k0 = (int64_t)blockIdx.y * 64, n0 = (int64_t)blockIdx.x * 64;
+    const int tx = threadIdx.x % 64, ty = threadIdx.x / 64;  // 64 x 4
+    for (int i = ty; i < 64; i += 4) {
+        const int64_t k = k0 + i, n = n0 + tx;
+        tile[i][tx] = (k < K && n < N) ? __ldg(B + k * N + n) : (uint8_t)0;
+    }
+    __syncthreads();
+    for (int i = ty; i < 64; i += 4) {
+        const int64_t n = n0 + i, k = k0 + tx;
+        if (n < N && k < Kp) Bt[n * Kp + k] = tile[tx][i];
+    }
+}
+
 }  // namespace
+
+// e4m3 operands as given (unit scales): A [M][K] and B [K][N] bytes.  The
+// block-scaled pair GEMM takes A K-major (padded rows when K % 16 != 0) and B
+// transposed, with every scale word 2^0; the single-CTA FP8 kernel takes B
+// as given (padded rows) with unit scale tables.
+moa_status tc_inner_e4m3(const uint8_t *A, const uint8_t *B, float *D, int64_t M, int64_t N, int64_t K, cudaStream_t s) {
+    const int64_t Kp = (K + 15) / 16 * 16, Np = (N + 15) / 16 * 16, KB = (K + 127) / 128, NB = (N + 127) / 128;
+    if (KB > 65535) return MOA_ERR_OVERFLOW;
+    const bool pair = M > 128 && N > 128 && M < (1ll << 31) && N < (1ll << 31) && K < (1ll << 31) && pair_mma_enabled();
+    const bool a_direct = K % 16 == 0 && (uintptr_t)A % 16 == 0;
+    const bool b_direct = !pair && N % 16 == 0 && (uintptr_t)B % 16 == 0;
+    const int64_t T = pair_fp8_tile_n(), MB = (M + 127) / 128, TN = (N + T - 1) / T;
+    const size_t abytes = a_direct ? 0 : (size_t)(M * Kp), bbytes = b_direct ? 0 : (size_t)(pair ? N * Kp : K * Np);
+    const size_t words = pair ? (size_t)(MB * KB * 128 + TN * KB * 256) : (size_t)(M * KB + KB * NB);
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    moa_status st;
+    uint8_t *ws = (uint8_t *)workspace_get(s, up(abytes) + up(bbytes) + words * 4 + 256, &st);
+    if (st != MOA_OK) return st;
+    const uint8_t *a8 = a_direct ? A : ws;
+    uint8_t *b8 = ws + up(abytes);
+    uint32_t *scales = (uint32_t *)(ws + up(abytes) + up(bbytes));
+    if (!a_direct) {
+        const int64_t total = M * (Kp / 16);
+        pad_rows_u8<<<(unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16), 256, 0, s>>>(A, M, K, Kp, ws);
+    }
+    if (pair) {
+        transpose_u8<<<dim3((unsigned)((N + 63) / 64), (unsigned)((Kp + 63) / 64)), 256, 0, s>>>(B, K, N, Kp, b8);
+        if (cudaGetLastError() != cudaSuccess) return MOA_ERR_CUDA;
+        if (cudaMemsetAsync(scales, 0x7f, words * 4, s) != cudaSuccess) return MOA_ERR_CUDA;  // UE8M0 127 = 2^0
+        const uint32_t *sfa = scales, *sfb = scales + MB * KB * 128;
+        return tc_gemm_pair_fp8_launch(a8, Kp, b8, Kp, (int)M, (int)N, (int)K, sfa, sfb, D, N, s) == cudaSuccess
+                   ? MOA_OK
+                   : MOA_ERR_CUDA;
+    }
+    const uint8_t *bb = B;
+    if (!b_direct) {
+        const int64_t total = K * (Np / 16);
+        pad_rows_u8<<<(unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16), 256, 0, s>>>(B, K, N, Np, b8);
+        bb = b8;
+    }
+    if (cudaGetLastError() != cudaSuccess) return MOA_ERR_CUDA;
+    if (launch_fill32(scales, 0x3f800000u, (int64_t)words, s) != cudaSuccess) return MOA_ERR_CUDA;  // FP32 1.0
+    const float *sa = (const float *)scales, *sb = sa + M * KB;
+    return tc_gemm_fp8(a8, Kp, bb, Np, sa, sb, D, N, M, N, K, s);
+}
 
 size_t fp8_workspace_bytes(int64_t M, int64_t N, int64_t K) {
     const int64_t Kp = (K + 15) / 16 * 16, Np = (N + 15) / 16 * 16, KB = (K + 127) / 128, NB = (N + 127) / 128;

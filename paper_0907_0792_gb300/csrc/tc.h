@@ -5,6 +5,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -25,7 +26,13 @@ bool make_tmap(CUtensorMap *m, const void *base, uint64_t inner, uint64_t rows, 
 // bf16 operands as given, FP32 out.
 moa_status tc_inner_bf16(const __nv_bfloat16 *A, const __nv_bfloat16 *B, float *D, int64_t M, int64_t N, int64_t K,
                          cudaStream_t stream);
-// FP32 operands, FP32 out: MOA_FORM_BF16, MOA_FORM_BF16X3 or MOA_FORM_FP8_T128.
+// fp16 operands as given, FP32 out (the same kernels with fp16 operand formats).
+moa_status tc_inner_f16(const __half *A, const __half *B, float *D, int64_t M, int64_t N, int64_t K,
+                        cudaStream_t stream);
+// e4m3 operands as given (unit scales), FP32 out.
+moa_status tc_inner_e4m3(const uint8_t *A, const uint8_t *B, float *D, int64_t M, int64_t N, int64_t K,
+                         cudaStream_t stream);
+// FP32 operands, FP32 out: MOA_FORM_BF16, MOA_FORM_F16, MOA_FORM_BF16X3 or MOA_FORM_FP8_T128.
 moa_status tc_inner_f32(moa_form form, const float *A, const float *B, float *D, int64_t M, int64_t N, int64_t K,
                         cudaStream_t stream);
 // FP32 operands, FP32 out, e4m3 with per-128 power-of-two block scales.
@@ -52,7 +59,7 @@ moa_status tc_inner_bf16x3_scratch(const float *A, const float *B, float *D, int
 bool pair_mma_enabled();
 cudaError_t tc_gemm_pair_launch(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, int K, int n_terms,
                                 uint32_t term_a, uint32_t term_b, float *D, int64_t ldd, bool promote,
-                                cudaStream_t stream, bool i32_out = false);
+                                cudaStream_t stream, bool i32_out = false, bool fp16 = false);
 // FP8 (e4m3) pair GEMM with block-scaled MMAs: A8 [M][lda] and B
 // transposed, Bt8 [N][ldb] (both K-major, lda and ldb multiples of 16,
 // 16-byte aligned).  Scale factors as UE8M0 bytes, each repeated in the four

@@ -2,6 +2,10 @@
 // multiply special case of Sec. I) built on the tcgen05 GEMM of tc_gemm.cu:
 //   bf16 operands as given          -> one term, no pre-pass when aligned;
 //   FP32 operands, MOA_FORM_BF16     -> round each operand to bf16 (RNE);
+//   fp16 operands as given           -> the same kernels with fp16 operand
+//       formats (one MMA takes one type for both operands);
+//   FP32 operands, MOA_FORM_F16      -> round each operand to fp16 (RNE,
+//       magnitudes beyond fp16's largest finite value 65504 held at it);
 //   FP32 operands, MOA_FORM_BF16X3   -> split each operand exactly-ish into
 //       x = hi + mid + lo (three bf16 values, each the RNE rounding of what
 //       the previous ones left), then accumulate the six cross products of
@@ -27,7 +31,8 @@ namespace moa {
 
 moa_status tc_gemm_planes(const __nv_bfloat16 *A, int64_t lda, int planesA, const __nv_bfloat16 *B, int64_t ldb,
                           int planesB, int n_terms, const int *term_a, const int *term_b, float *D, int64_t ldd,
-                          int64_t M, int64_t N, int64_t K, bool promote, cudaStream_t s, bool i32_out = false);
+                          int64_t M, int64_t N, int64_t K, bool promote, cudaStream_t s, bool i32_out = false,
+                          bool fp16 = false);
 
 namespace {
 
@@ -136,7 +141,58 @@ cudaError_t run_split(const Tin *X, int64_t rows, int64_t cols, int64_t colsp, _
     return cudaGetLastError();
 }
 
+// X (rows x cols, float or fp16) -> fp16 rows x colsp (zero columns past
+// cols): RNE rounding of FP32 values with the magnitude held at 65504, or a
+// copy of fp16 values.  Four consecutive columns per thread.
+template <typename Tin>
+__global__ void __launch_bounds__(256) to_f16_rows(const Tin *__restrict__ X, int64_t rows, int64_t cols, int64_t colsp,
+                                                    __half *__restrict__ out) {
+    const int64_t groups = colsp / 4;
+    for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
+        const Tin *src = X + r * cols;
+        for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t c = 4 * g;
+            __align__(8) __half y[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if constexpr (std::is_same<Tin, float>::value) {
+                    const float x = c + t < cols ? src[c + t] : 0.0f;
+                    y[t] = __float2half_rn(fminf(fmaxf(x, -65504.0f), 65504.0f));
+                } else {
+                    y[t] = c + t < cols ? src[c + t] : __ushort_as_half((unsigned short)0);
+                }
+            }
+            *reinterpret_cast<uint2 *>(out + r * colsp + c) = *reinterpret_cast<const uint2 *>(y);
+        }
+    }
+}
+
+template <typename Tin>
+cudaError_t run_to_f16(const Tin *X, int64_t rows, int64_t cols, int64_t colsp, __half *out, cudaStream_t s) {
+    if (rows == 0 || colsp == 0) return cudaSuccess;
+    const int64_t groups = colsp / 4;
+    const int64_t gx = groups >= 256 * 4 ? 4 : (groups + 255) / 256;
+    const dim3 grid((unsigned)gx, (unsigned)(rows < 2048 ? rows : 2048));
+    to_f16_rows<Tin><<<grid, 256, 0, s>>>(X, rows, cols, colsp, out);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+moa_status tc_inner_f16(const __half *A, const __half *B, float *D, int64_t M, int64_t N, int64_t K, cudaStream_t s) {
+    const int ta[1] = {0}, tb[1] = {0};
+    auto bf = [](const __half *p) { return reinterpret_cast<const __nv_bfloat16 *>(p); };  // 2-byte planes, fp16 bits
+    if ((uintptr_t)A % 16 == 0 && (uintptr_t)B % 16 == 0 && K % 8 == 0 && N % 8 == 0)
+        return tc_gemm_planes(bf(A), K, 1, bf(B), N, 1, 1, ta, tb, D, N, M, N, K, false, s, false, true);
+    // copy into 16-byte-aligned, padded rows first
+    const int64_t Kp = round8(K), Np = round8(N);
+    moa_status st;
+    __half *ws = (__half *)workspace_get(s, (size_t)(M * Kp + K * Np) * 2, &st);
+    if (st != MOA_OK) return st;
+    __half *a = ws, *b = ws + M * Kp;
+    if (run_to_f16(A, M, K, Kp, a, s) != cudaSuccess || run_to_f16(B, K, N, Np, b, s) != cudaSuccess) return MOA_ERR_CUDA;
+    return tc_gemm_planes(bf(a), Kp, 1, bf(b), Np, 1, 1, ta, tb, D, N, M, N, K, false, s, false, true);
+}
 
 moa_status tc_inner_bf16(const __nv_bfloat16 *A, const __nv_bfloat16 *B, float *D, int64_t M, int64_t N, int64_t K,
                          cudaStream_t s) {
@@ -157,6 +213,18 @@ moa_status tc_inner_bf16(const __nv_bfloat16 *A, const __nv_bfloat16 *B, float *
 moa_status tc_inner_f32(moa_form form, const float *A, const float *B, float *D, int64_t M, int64_t N, int64_t K,
                         cudaStream_t s) {
     if (form == MOA_FORM_FP8_T128) return tc_inner_fp8(A, B, D, M, N, K, s);
+    if (form == MOA_FORM_F16) {
+        const int64_t Kp = round8(K), Np = round8(N);
+        moa_status st;
+        __half *ws = (__half *)workspace_get(s, (size_t)(M * Kp + K * Np) * 2, &st);
+        if (st != MOA_OK) return st;
+        __half *a = ws, *b = ws + M * Kp;
+        if (run_to_f16(A, M, K, Kp, a, s) != cudaSuccess || run_to_f16(B, K, N, Np, b, s) != cudaSuccess)
+            return MOA_ERR_CUDA;
+        const int ta[1] = {0}, tb[1] = {0};
+        return tc_gemm_planes(reinterpret_cast<const __nv_bfloat16 *>(a), Kp, 1, reinterpret_cast<const __nv_bfloat16 *>(b),
+                              Np, 1, 1, ta, tb, D, N, M, N, K, false, s, false, true);
+    }
     if (form != MOA_FORM_BF16 && form != MOA_FORM_BF16X3) return MOA_ERR_UNSUPPORTED;
     const int npl = form == MOA_FORM_BF16 ? 1 : 3;
     const int64_t Kp = round8(K), Np = round8(N);

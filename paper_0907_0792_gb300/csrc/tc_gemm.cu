@@ -89,6 +89,7 @@ struct GemmParams {
     float *D;
     int64_t ldd;
     int vec_store;  // D rows 16-byte aligned and ldd % 4 == 0
+    uint32_t ab_fmt;  // kind::f16 operand format bits (bf16 or fp16 planes)
     // Ozaki mode
     int slices;      // S: digit planes per operand
     int beta;        // bits per digit
@@ -239,6 +240,7 @@ __global__ void __launch_bounds__(cta_threads(MODE), 1)
         }
     } else if (warp == 1 && lane == 0) {
         // ------------------------------------------------ MMA issuer
+        const uint32_t idesc = (C::IDESC & ~ptx::kIdescAbMask) | p.ab_fmt;  // kind::f16: bf16 or fp16 planes
         int stage = 0, abuf = 0;
         uint32_t phase = 0, aphase = 0;
         bool ok = true;
@@ -283,7 +285,7 @@ __global__ void __launch_bounds__(cta_threads(MODE), 1)
                     if constexpr (MODE == MODE_FP8)
                         ptx::mma_e4m3(dacc, ad, bd, C::IDESC, (j > 0 || k > 0) ? 1u : 0u);
                     else
-                        ptx::mma_bf16(dacc, ad, bd, C::IDESC, (j > 0 || k > 0) ? 1u : 0u);
+                        ptx::mma_bf16(dacc, ad, bd, idesc, (j > 0 || k > 0) ? 1u : 0u);
                 }
                 ptx::mma_commit(empty(stage));
                 if (++stage == STAGES) {
@@ -548,7 +550,7 @@ bool make_tmap(CUtensorMap *m, const void *base, uint64_t inner, uint64_t rows, 
 // lda, ldb multiples of 8 and the bases 16-byte aligned (TMA rules).
 moa_status tc_gemm_planes(const __nv_bfloat16 *A, int64_t lda, int planesA, const __nv_bfloat16 *B, int64_t ldb,
                           int planesB, int n_terms, const int *term_a, const int *term_b, float *D, int64_t ldd,
-                          int64_t M, int64_t N, int64_t K, bool promote, cudaStream_t s, bool i32_out) {
+                          int64_t M, int64_t N, int64_t K, bool promote, cudaStream_t s, bool i32_out, bool fp16) {
     if (M >= (1ll << 31) || N >= (1ll << 31) || K >= (1ll << 31)) return MOA_ERR_OVERFLOW;
     if (n_terms < 1 || n_terms > kMaxTerms) return MOA_ERR_INTERNAL;
     if ((uintptr_t)A % 16 || (uintptr_t)B % 16 || lda % 8 || ldb % 8) return MOA_ERR_INTERNAL;
@@ -570,9 +572,10 @@ moa_status tc_gemm_planes(const __nv_bfloat16 *A, int64_t lda, int planesA, cons
     p.D = D;
     p.ldd = ldd;
     p.vec_store = ((uintptr_t)D % 16 == 0) && (ldd % 4 == 0);
+    p.ab_fmt = ptx::idesc_ab_f16(fp16);
     cudaError_t e;
     if (BN == 256 && M > BM && pair_mma_enabled()) {
-        e = tc_gemm_pair_launch(ta, tb, p.M, p.N, p.K, n_terms, p.term_a, p.term_b, D, ldd, promote, s, i32_out);
+        e = tc_gemm_pair_launch(ta, tb, p.M, p.N, p.K, n_terms, p.term_a, p.term_b, D, ldd, promote, s, i32_out, fp16);
         return e == cudaSuccess ? MOA_OK : MOA_ERR_CUDA;
     }
     if (i32_out) return MOA_ERR_INTERNAL;  // int32 results only from the pair kernel
@@ -634,6 +637,7 @@ moa_status tc_gemm_ozaki(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat1
     p.n_terms = S * (S + 1) / 2;
     p.slices = S, p.beta = beta, p.lsb = lsb, p.chunk = chunk_kblocks;
     p.D64 = D, p.ldd = ldd, p.row_max = row_max, p.col_max = col_max;
+    p.ab_fmt = ptx::idesc_ab_f16(false);
     if (M > BM && N > 128 && pair_mma_enabled() && scratch) {  // 256 x 256 tiles on CTA pairs
         const cudaError_t e = tc_gemm_pair_ozaki_launch(ta, tb, p.M, p.N, p.K, S, beta, lsb, chunk_kblocks, row_max, col_max,
                                                         D, ldd, scratch, s);

@@ -123,6 +123,7 @@ struct PairParams {
     float *D;
     int64_t ldd;
     int vec_store;
+    uint32_t ab_fmt;  // kind::f16 operand format bits (bf16 or fp16 planes)
     int tma_store;  // D written through per-warp staging tiles and TMA stores
     int d_evict_first;  // those stores under an evict-first L2 policy (D is not re-read)
     uint32_t *bits_out;  // store mode: write [D > 0] as the packed bit stream (N % 32 == 0) instead of D
@@ -277,6 +278,7 @@ __global__ void __launch_bounds__(threads(MODE), 1)
         int stage = 0, abuf = 0, sfb = 0;
         uint32_t phase = 0, aphase = 0;
         bool ok = true, any = false;
+        const uint32_t id16 = (idesc(MODE) & ~ptx::kIdescAbMask) | p.ab_fmt;  // kind::f16: bf16 or fp16 planes
         // descriptors of stage 0, k-step 0; A steps +32 B along the swizzled
         // K row, B (MN-major) +uk rows of 128 B or (K-major, FP8) +32 B, a
         // stage +STAGE_BYTES (offsets >> 4)
@@ -336,7 +338,7 @@ __global__ void __launch_bounds__(threads(MODE), 1)
                             ptx::mma_mxf8_pair_h(dacc, alo, a0.hi, blo, b0.hi, idesc(MODE) | ((uint32_t)k << 4) | ((uint32_t)k << 29),
                                                  sfa, sfa + 4, (j > 0 || k > 0) ? 1u : 0u);
                         } else {
-                            ptx::mma_bf16_pair_h(dacc, alo, a0.hi, blo, b0.hi, idesc(MODE), (j > 0 || k > 0) ? 1u : 0u);
+                            ptx::mma_bf16_pair_h(dacc, alo, a0.hi, blo, b0.hi, id16, (j > 0 || k > 0) ? 1u : 0u);
                         }
                     }
                     ptx::mma_commit_pair_mc(empty(stage), kPair);
@@ -653,9 +655,10 @@ cudaError_t tc_gemm_pair_fp8_launch(const uint8_t *A8, int64_t lda, const uint8_
 
 cudaError_t tc_gemm_pair_launch(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, int K, int n_terms,
                                 uint32_t term_a, uint32_t term_b, float *D, int64_t ldd, bool promote, cudaStream_t s,
-                                bool i32_out) {
+                                bool i32_out, bool fp16) {
     if (promote && i32_out) return cudaErrorInvalidValue;
     PairParams p{};
+    p.ab_fmt = ptx::idesc_ab_f16(fp16);
     p.i32_out = i32_out ? 1 : 0;
     p.M = M, p.N = N, p.K = K;
     p.kblocks = (K + bk(MODE_STORE) - 1) / bk(MODE_STORE);
@@ -673,6 +676,7 @@ cudaError_t tc_gemm_pair_ozaki_launch(const CUtensorMap &ta, const CUtensorMap &
                                       int lsb, int chunk_kblocks, const uint64_t *row_max, const uint64_t *col_max,
                                       double *D, int64_t ldd, void *scratch, cudaStream_t s) {
     PairParams p{};
+    p.ab_fmt = ptx::idesc_ab_f16(false);
     p.rs = (float2 *)scratch;
     p.M = M, p.N = N, p.K = K;
     p.kblocks = (K + bk(MODE_OZAKI) - 1) / bk(MODE_OZAKI);

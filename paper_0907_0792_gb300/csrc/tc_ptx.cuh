@@ -213,6 +213,12 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N, int b_mn) {
            ((uint32_t)(M >> 4) << 24);
 }
 
+// kind::f16 operand format bits of an instruction descriptor: A (bits 7-9)
+// and B (bits 10-12) both bf16 (code 1) or both fp16 (code 0); one MMA
+// takes one type for both operands.
+constexpr uint32_t kIdescAbMask = (7u << 7) | (7u << 10);
+__host__ __device__ constexpr uint32_t idesc_ab_f16(bool fp16) { return fp16 ? 0u : ((1u << 7) | (1u << 10)); }
+
 // Instruction descriptor, kind::f8f6f4 with e4m3 A and B (format code 0),
 // D f32, A K-major, B MN-major (b_mn = 1) or K-major, shape M x N.
 __host__ __device__ constexpr uint32_t idesc_e4m3_f32(int M, int N, int b_mn) {

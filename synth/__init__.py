@@ -174,6 +174,45 @@ def to_bf16(x: np.ndarray):
     return b, bf16_bits_to_f64(b)
 
 
+def to_f16(x: np.ndarray):
+    """Round to IEEE binary16 (RNE, numpy's conversion from float64).
+
+    Returns (bits as uint16, the exact values as float64)."""
+    h = np.asarray(x, dtype=np.float64).astype(np.float16)
+    return h.view(np.uint16), h.astype(np.float64)
+
+
+def e4m3_decode_table() -> np.ndarray:
+    """The value of every FP8 E4M3 code (OCP 8-bit floating point, E4M3):
+    bit 7 sign, bits 3-6 exponent with bias 7, bits 0-2 mantissa; exponent
+    field 0 encodes subnormals m/8 * 2^-6; codes 0x7F and 0xFF are NaN; no
+    infinities (the all-ones exponent with mantissa < 7 is a normal number)."""
+    out = np.empty(256, dtype=np.float64)
+    for c in range(256):
+        sgn = -1.0 if c & 0x80 else 1.0
+        e, m = (c >> 3) & 0xF, c & 0x7
+        if e == 0xF and m == 0x7:
+            out[c] = np.nan
+        elif e == 0:
+            out[c] = sgn * (m / 8.0) * 2.0 ** -6
+        else:
+            out[c] = sgn * (1.0 + m / 8.0) * 2.0 ** (e - 7)
+    return out
+
+
+def e4m3_codes(seed: int, stream: int, shape, max_exp: int = 15):
+    """FP8 E4M3 operands as stored: codes drawn uniformly over the finite
+    codes whose exponent field is at most max_exp (NaN never drawn).
+
+    Returns (codes as uint8, the exact values as float64)."""
+    table = e4m3_decode_table()
+    finite = np.array([c for c in range(256) if not np.isnan(table[c]) and ((c >> 3) & 0xF) <= max_exp],
+                      dtype=np.uint8)
+    n = int(np.prod(shape, dtype=np.int64))
+    codes = finite[(u64(seed, stream, n) % np.uint64(len(finite))).astype(np.int64)].reshape(shape)
+    return codes, table[codes]
+
+
 # ---------------------------------------------------------------- bit packing
 def pack_bits(x: np.ndarray) -> np.ndarray:
     """Row-major ravel packed as a bit stream: element e -> word e//32, bit e%32

@@ -113,3 +113,24 @@ def test_square_leading_is_the_leading_block():
         assert np.array_equal(a, A[:64, :64]) and np.array_equal(b, B[:64, :64])
         a, b = synth.square_leading(512, dist, n_full=512)
         assert np.array_equal(a, A) and np.array_equal(b, B)
+
+
+def test_f16_rounding_and_e4m3_table():
+    """fp16 rounding is numpy's binary16 conversion (a library routine) and
+    keeps its range ends; the E4M3 decode table written from the format's
+    definition agrees with torch's float8_e4m3fn for every code, and with
+    values worked by hand."""
+    bits, vals = synth.to_f16(np.array([1.0, 65504.0, 2.0 ** -24, 1.0 + 2.0 ** -11, -0.1]))
+    assert list(bits[:3]) == [0x3C00, 0x7BFF, 0x0001] and vals[3] == 1.0  # a tie rounds to even
+    assert vals[4] == np.float64(np.float16(-0.1))
+    t = synth.e4m3_decode_table()
+    assert t[0x00] == 0.0 and t[0x38] == 1.0 and t[0xB8] == -1.0 and t[0x7E] == 448.0 and t[0x01] == 2.0 ** -9
+    assert t[0x08] == 2.0 ** -6 and np.isnan(t[0x7F]) and np.isnan(t[0xFF]) and t[0x77] == 240.0
+    torch = pytest.importorskip("torch")
+    if not hasattr(torch, "float8_e4m3fn"):
+        pytest.skip("no float8 in this torch")
+    ref = torch.arange(256, dtype=torch.uint8).view(torch.float8_e4m3fn).to(torch.float64).numpy()
+    assert np.array_equal(t, ref, equal_nan=True)
+    codes, vals = synth.e4m3_codes(3, 0, (1000,), max_exp=9)
+    assert not np.isnan(vals).any() and np.abs(vals).max() <= 2.0 ** 3 * 1.875
+    assert np.array_equal(vals, t[codes])
