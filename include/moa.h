@@ -110,14 +110,12 @@ typedef enum {
  * MOA_FORM_NATIVE only.  Normalised error bounds (max over elements of
  * |D - D_exact| / sum_p |A||B|, D_exact from the operands as given):
  *   NATIVE    f64: FP64 FMA, <= 1e-12.  f32: FP32 FMA, <= 2e-6.
- *             bf16 (inputs already bf16, FP32 out): tensor cores, FP32
- *             accumulation, <= 2e-6 relative to the bf16 operands.
  *             i32: exact modulo 2^32.
- *             f16 (inputs already fp16, FP32 out): tensor cores, FP32
- *             accumulation, <= 2e-6 relative to the fp16 operands.
- *             fp8e4m3 (inputs already e4m3, unit scales, FP32 out): tensor
- *             cores, FP32 accumulation, <= 2e-6 relative to the e4m3
- *             operands.
+ *             bf16, f16, fp8e4m3 (inputs already in that type; e4m3 with
+ *             unit scales; FP32 out): tensor cores, one FP32 accumulator
+ *             over the whole contraction (exact products, the running sum
+ *             truncated at most once per 16-deep step), <= max(2e-6,
+ *             (K/16) 2^-23) relative to the operands as given.
  *   BF16      f32 in/out: operands rounded to bf16, tensor cores, <= 1e-2.
  *   F16       f32 in/out: operands rounded to fp16 (RNE; magnitudes above
  *             65504 held at 65504), tensor cores, <= 2e-3 for operands
