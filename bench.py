@@ -530,10 +530,9 @@ def cpu_oracle_sample(seconds: float = 12.0, threads: int | None = None):
     return r
 
 
-def headline_config(ws: int) -> dict:
+def headline_config(ws: int, n: int = N_HEAD) -> dict:
     """The workload both arms report (the reference arm samples its rows)."""
-    n = N_HEAD
-    return {"workload": "square (+,*) inner product n=8192, FP64 in/out, Ozaki-sliced form (normalised error <= 1e-12)",
+    return {"workload": f"square (+,*) inner product n={n}, FP64 in/out, Ozaki-sliced form (normalised error <= 1e-12)",
             "M": n, "K": n, "N": n, "seed": 2, "values": "U(-1,1) FP64",
             "l2": "inputs 2 x 512 MiB > L2, no flush", "parallelism": f"replicas x{ws}"}
 
@@ -613,6 +612,9 @@ def main():
     ap.add_argument("--sweep-forms", default="all",
                     help="comma list of form:dtype pairs for the sweep row (e.g. ozaki:f64,fp8_t128:f32)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--headline-n", type=int, default=N_HEAD,
+                    help="matrix size of the headline product (smaller sizes for profiling captures only)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer (end-to-end) leg")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--batched-count", type=int, default=10000, help="problems in the batched row")
     ap.add_argument("--batched-no-compare", action="store_true",
@@ -634,7 +636,7 @@ def main():
     moa.lib()
     peaks = _peaks()
     stream = torch.cuda.current_stream()
-    n = N_HEAD
+    n = args.headline_n
 
     # ---- headline: FP64 8192^3 (+,*) in the Ozaki form through moa_inner, inputs resident in HBM
     A64, B64 = synth.square(n, "uniform")
@@ -673,23 +675,25 @@ def main():
     # ---- e2e: the same product through moa_inner_host, every step copying its
     # operands in from page-locked host memory and its result out (inside the
     # call, overlapped by row blocks), timed with CUDA events on the stream
-    hA = torch.from_numpy(A64).pin_memory()
-    hB = torch.from_numpy(B64).pin_memory()
-    hD = torch.empty((n, n), dtype=torch.float64).pin_memory()
     del A, B, D
     torch.cuda.empty_cache()
-    e2e_call = lambda: moa.moa_inner_host("add", "mul", "f64", "ozaki", (n, n), hA, (n, n), hB, hD, "f64", stream)
-    e2e_call()
-    torch.cuda.synchronize()
-    e2e_steps = max(3, min(args.steps, 10))
-    ms_e2e = _max_over_ranks(_events_time(e2e_call, e2e_steps, stream), ws)
-    e2e = {"value": round(ws * flops / (ms_e2e * 1e-3) / 1e12, 2), "unit": "TFLOP/s",
-           "h2d_bytes_per_step": int(hA.numel() * 8 + hB.numel() * 8), "d2h_bytes_per_step": int(hD.numel() * 8),
-           "ms_per_step": round(ms_e2e, 3), "call": "moa_inner_host (pinned host buffers, row blocks overlapped)"}
-    st = moa.moa_device_status()
-    if st != 0:
-        raise RuntimeError("device status " + moa.moa_status_string(st))
-    del hA, hB, hD
+    e2e = None
+    if not args.no_e2e:
+        hA = torch.from_numpy(A64).pin_memory()
+        hB = torch.from_numpy(B64).pin_memory()
+        hD = torch.empty((n, n), dtype=torch.float64).pin_memory()
+        e2e_call = lambda: moa.moa_inner_host("add", "mul", "f64", "ozaki", (n, n), hA, (n, n), hB, hD, "f64", stream)
+        e2e_call()
+        torch.cuda.synchronize()
+        e2e_steps = max(3, min(args.steps, 10))
+        ms_e2e = _max_over_ranks(_events_time(e2e_call, e2e_steps, stream), ws)
+        e2e = {"value": round(ws * flops / (ms_e2e * 1e-3) / 1e12, 2), "unit": "TFLOP/s",
+               "h2d_bytes_per_step": int(hA.numel() * 8 + hB.numel() * 8), "d2h_bytes_per_step": int(hD.numel() * 8),
+               "ms_per_step": round(ms_e2e, 3), "call": "moa_inner_host (pinned host buffers, row blocks overlapped)"}
+        st = moa.moa_device_status()
+        if st != 0:
+            raise RuntimeError("device status " + moa.moa_status_string(st))
+        del hA, hB, hD
     moa.moa_release_workspace()
     torch.cuda.empty_cache()
 
@@ -768,7 +772,7 @@ def main():
         line = {"metric": METRIC, "value": round(value, 2), "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": headline_config(ws),
+                "config": headline_config(ws, n),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": args.steps * OZAKI_KERNELS_PER_CALL,
                 "clocks": clk.summary(), "device_status": "ok", "rows": rows, "summary": _summary(rows)}
