@@ -534,7 +534,8 @@ def headline_config(ws: int, n: int = N_HEAD) -> dict:
     """The workload both arms report (the reference arm samples its rows)."""
     return {"workload": f"square (+,*) inner product n={n}, FP64 in/out, Ozaki-sliced form (normalised error <= 1e-12)",
             "M": n, "K": n, "N": n, "seed": 2, "values": "U(-1,1) FP64",
-            "l2": "inputs 2 x 512 MiB > L2, no flush", "parallelism": f"replicas x{ws}"}
+            "l2": "inputs 2 x 512 MiB > L2, no flush",
+            "parallelism": "single GPU" if ws == 1 else f"row partition x{ws} (B broadcast once, {ws} x {n} rows)"}
 
 
 def run_reference(args, rank, ws):
@@ -638,10 +639,19 @@ def main():
     stream = torch.cuda.current_stream()
     n = args.headline_n
 
-    # ---- headline: FP64 8192^3 (+,*) in the Ozaki form through moa_inner, inputs resident in HBM
+    # ---- headline: FP64 8192^3 (+,*) in the Ozaki form through moa_inner, inputs resident in HBM.
+    # With N ranks the problem is the (N n) x n . n x n product partitioned by rows of A and D
+    # (rowpart): rank r holds its n rows of A (stream 100 + r of the seed for r > 0), rank 0 holds B and
+    # broadcasts it once; no exchange inside a step.
+    from paper_0907_0792_gb300 import rowpart
     A64, B64 = synth.square(n, "uniform")
+    if rank > 0:
+        A64 = synth.uniform(2, 100 + rank, (n, n), -1.0, 1.0)
     A = torch.from_numpy(A64).cuda()
-    B = torch.from_numpy(B64).cuda()
+    B = torch.from_numpy(B64).cuda() if rank == 0 else torch.empty((n, n), dtype=torch.float64, device="cuda")
+    if ws > 1:
+        rowpart.broadcast_operand(B, src=0)
+        torch.cuda.synchronize()
     D = torch.empty((n, n), dtype=torch.float64, device="cuda")
     step = lambda: moa.moa_inner("add", "mul", "f64", "ozaki", (n, n), A, (n, n), B, D, "f64", stream)
     for _ in range(args.warmup):
