@@ -85,14 +85,11 @@ __global__ void col_max_kernel(const double *__restrict__ B, int64_t K, int64_t 
 // the truncated |x| 2^-e (u_s = floor(|x| 2^(-e + (s+1) beta)) mod 2^beta,
 // u_0 < 2^(beta-1)) are rewritten from the lowest up: a digit of 2^(beta-1)
 // or more becomes u - 2^beta with a carry of one into the next higher digit.
-MOA_DEV void balanced_digits(uint64_t mant, int ex, int e, bool neg, int S, int (&d)[kMaxSlices]) {
+template <int S>
+MOA_DEV void balanced_digits(uint64_t mant, int ex, int e, bool neg, int (&d)[S]) {
     int carry = 0;
 #pragma unroll
-    for (int s = kMaxSlices - 1; s >= 0; --s) {
-        if (s >= S) {
-            d[s] = 0;
-            continue;
-        }
+    for (int s = S - 1; s >= 0; --s) {
         const int t = ex - e + (s + 1) * kBeta;  // |x| 2^(-e + (s+1) beta) = mant * 2^t
         uint64_t v;
         if (t >= 0) v = t >= 64 ? 0 : (mant << t);
@@ -111,9 +108,9 @@ MOA_DEV void balanced_digits(uint64_t mant, int ex, int e, bool neg, int S, int 
 // row_scale: the exponent comes from maxbits[row], else from maxbits[col].
 // Four consecutive columns per thread (colsp is a multiple of 8): one or two
 // 16-byte loads when the row allows (VEC), one 8-byte store per plane.
-template <bool ROW_SCALE, bool VEC>
+template <bool ROW_SCALE, bool VEC, int S>
 __global__ void __launch_bounds__(256) slice_kernel(const double *__restrict__ X, int64_t rows, int64_t cols,
-                                                     int64_t colsp, const uint64_t *__restrict__ maxbits, int S,
+                                                     int64_t colsp, const uint64_t *__restrict__ maxbits,
                                                      __nv_bfloat16 *__restrict__ out) {
     const int64_t plane = rows * colsp, groups = colsp / 4;
     for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
@@ -134,44 +131,71 @@ __global__ void __launch_bounds__(256) slice_kernel(const double *__restrict__ X
 #pragma unroll
                 for (int t = 0; t < 4; ++t) x[t] = c0 + t < cols ? __ldg(src + c0 + t) : 0.0;
             }
-            __align__(8) __nv_bfloat16 pl[kMaxSlices][4];
+            uint32_t pk[S][2];  // four bf16 digits per plane, packed in two words
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 const uint64_t b = (uint64_t)__double_as_longlong(x[t]);
                 const int be = (int)((b >> 52) & 0x7FF);
                 const uint64_t mant = be ? ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) : (b & 0xFFFFFFFFFFFFFull);
                 const int ex = (be ? be : 1) - 1075;
-                const int e = ROW_SCALE ? er : (c0 + t < cols ? ozaki::scale_exponent(maxbits[c0 + t]) : 0);
-                int d[kMaxSlices];
-                balanced_digits(mant, ex, e, (b >> 63) != 0, S, d);
+                const int e = ROW_SCALE ? er : (c0 + t < cols ? ozaki::scale_exponent(__ldg(maxbits + c0 + t)) : 0);
+                int d[S];
+                balanced_digits<S>(mant, ex, e, (b >> 63) != 0, d);
 #pragma unroll
-                for (int q = 0; q < kMaxSlices; ++q) pl[q][t] = __int2bfloat16_rn(d[q]);
+                for (int q = 0; q < S; ++q) {
+                    const uint32_t h = (uint32_t)__bfloat16_as_ushort(__int2bfloat16_rn(d[q]));
+                    if (t % 2 == 0) pk[q][t / 2] = h;
+                    else pk[q][t / 2] |= h << 16;
+                }
             }
             __nv_bfloat16 *dst = out + r * colsp + c0;
 #pragma unroll
-            for (int q = 0; q < kMaxSlices; ++q) {
-                if (q >= S) break;
-                *reinterpret_cast<uint2 *>(dst + q * plane) = *reinterpret_cast<const uint2 *>(pl[q]);
-            }
+            for (int q = 0; q < S; ++q) *reinterpret_cast<uint2 *>(dst + q * plane) = make_uint2(pk[q][0], pk[q][1]);
         }
     }
 }
 
-template <bool ROW_SCALE>
-void run_slices(const double *X, int64_t rows, int64_t cols, int64_t colsp, const uint64_t *maxbits, int S,
-                __nv_bfloat16 *out, cudaStream_t s) {
+template <bool ROW_SCALE, int S>
+void run_slices_s(const double *X, int64_t rows, int64_t cols, int64_t colsp, const uint64_t *maxbits,
+                  __nv_bfloat16 *out, cudaStream_t s) {
     const int64_t groups = colsp / 4;
     const int64_t gx = groups >= 256 * 4 ? 4 : (groups + 255) / 256;
     const dim3 grid((unsigned)gx, (unsigned)(rows < 4096 ? rows : 4096));
     if (cols % 4 == 0 && (uintptr_t)X % 16 == 0)
-        slice_kernel<ROW_SCALE, true><<<grid, 256, 0, s>>>(X, rows, cols, colsp, maxbits, S, out);
+        slice_kernel<ROW_SCALE, true, S><<<grid, 256, 0, s>>>(X, rows, cols, colsp, maxbits, out);
     else
-        slice_kernel<ROW_SCALE, false><<<grid, 256, 0, s>>>(X, rows, cols, colsp, maxbits, S, out);
+        slice_kernel<ROW_SCALE, false, S><<<grid, 256, 0, s>>>(X, rows, cols, colsp, maxbits, out);
+}
+
+template <bool ROW_SCALE>
+bool run_slices(const double *X, int64_t rows, int64_t cols, int64_t colsp, const uint64_t *maxbits, int S,
+                __nv_bfloat16 *out, cudaStream_t s) {
+    switch (S) {
+    case 4: run_slices_s<ROW_SCALE, 4>(X, rows, cols, colsp, maxbits, out, s); return true;
+    case 5: run_slices_s<ROW_SCALE, 5>(X, rows, cols, colsp, maxbits, out, s); return true;
+    case 6: run_slices_s<ROW_SCALE, 6>(X, rows, cols, colsp, maxbits, out, s); return true;
+    case 7: run_slices_s<ROW_SCALE, 7>(X, rows, cols, colsp, maxbits, out, s); return true;
+    case 8: run_slices_s<ROW_SCALE, 8>(X, rows, cols, colsp, maxbits, out, s); return true;
+    case 9: run_slices_s<ROW_SCALE, 9>(X, rows, cols, colsp, maxbits, out, s); return true;
+    case 10: run_slices_s<ROW_SCALE, 10>(X, rows, cols, colsp, maxbits, out, s); return true;
+    }
+    return false;
 }
 
 int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
 
 }  // namespace
+
+// k-blocks of 64 per exact FP32 chunk (MOA_OZAKI_CHUNK overrides, 1..16):
+// a chunk's slice-pair accumulator holds at most 64 * chunk products of 2^14.
+int ozaki_chunk() {
+    static const int forced = [] {
+        const char *e = std::getenv("MOA_OZAKI_CHUNK");
+        const int v = e ? std::atoi(e) : 0;
+        return (v < 1 || v > kChunkKBlocks) ? 0 : v;
+    }();
+    return forced ? forced : kChunkKBlocks;
+}
 
 // Slices per operand for a contraction of length K (MOA_OZAKI_SLICES overrides, 4..10).
 int ozaki_slices(int64_t K) {
@@ -216,12 +240,12 @@ moa_status tc_inner_ozaki(const double *A, const double *B, double *D, int64_t M
         col_max_kernel<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, s>>>(B, K, N, rpb, cmax);
     }
     // digit planes
-    run_slices<true>(A, M, K, Kp, rmax, S, a, s);
-    run_slices<false>(B, K, N, Np, cmax, S, b, s);
+    if (!run_slices<true>(A, M, K, Kp, rmax, S, a, s) || !run_slices<false>(B, K, N, Np, cmax, S, b, s))
+        return MOA_ERR_INTERNAL;
     if (cudaGetLastError() != cudaSuccess) return MOA_ERR_CUDA;
     // accumulator units 2^-lsb with lsb = (S + 1) beta: every kept pair weight 2^(lsb - (s+u+2) beta) >= 1
     const int lsb = (S + 1) * kBeta;
-    return tc_gemm_ozaki(a, Kp, b, Np, S, kBeta, lsb, kChunkKBlocks, rmax, cmax, D, N, M, N, K, rs, s);
+    return tc_gemm_ozaki(a, Kp, b, Np, S, kBeta, lsb, ozaki_chunk(), rmax, cmax, D, N, M, N, K, rs, s);
 }
 
 }  // namespace moa

@@ -118,6 +118,7 @@ static_assert(smem_bytes(MODE_STORE) <= 227 * 1024 && smem_bytes(MODE_FP8) <= 22
 struct PairParams {
     int M, N, K;
     int tiles_m, tiles_n;  // pair tiles: ceil(M / 256) x ceil(N / 256)
+    int group_m;           // row tiles per raster group
     int kblocks, n_terms;
     uint32_t term_a, term_b;  // plane of A / B for term i in bits 4i..4i+3
     float *D;
@@ -135,10 +136,9 @@ struct PairParams {
     float2 *rs;  // running-sum scratch: per CTA, per epilogue warp, 64 columns x 32 lanes
 };
 
-// Groups of 16 row tiles, column tiles within a group: the A and B panels
+// Groups of GM row tiles, column tiles within a group: the A and B panels
 // in flight stay resident in L2.
-MOA_DEV void pair_tile_of(int t, int tiles_m, int tiles_n, int &tm, int &tn) {
-    constexpr int GM = 16;
+MOA_DEV void pair_tile_of(int t, int tiles_m, int tiles_n, int GM, int &tm, int &tn) {
     const int group = t / (GM * tiles_n);
     const int first = group * GM;
     const int gsz = min(tiles_m - first, GM);
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(threads(MODE), 1)
         bool ok = true;
         for (int t = cfirst; t < num_tiles && ok; t += cstride) {
             int tm, tn;
-            pair_tile_of(t, p.tiles_m, p.tiles_n, tm, tn);
+            pair_tile_of(t, p.tiles_m, p.tiles_n, p.group_m, tm, tn);
             const int row0 = tm * 2 * BM + crank * BM;
             const int col0 = tn * BN + crank * (BN / 2);
             ozaki::Iter oz;
@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(threads(MODE), 1)
         bool ok = true;
         for (int t = cfirst; t < num_tiles && ok; t += cstride) {
             int tm, tn;
-            pair_tile_of(t, p.tiles_m, p.tiles_n, tm, tn);
+            pair_tile_of(t, p.tiles_m, p.tiles_n, p.group_m, tm, tn);
             const int64_t row = (int64_t)tm * 2 * BM + crank * BM + q * 32 + lane;
             const int64_t colh = (int64_t)tn * BN + half * HC;
             const uint32_t lanes = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * HC);
@@ -530,6 +530,19 @@ __global__ void __launch_bounds__(threads(MODE), 1)
     }
 }
 
+// Row tiles per raster group: 16 (MOA_PAIR_GROUP_M overrides for all
+// modes, MOA_OZAKI_GROUP_M for the Ozaki slice-pair mode alone; 1..64).
+int group_env(const char *name) {
+    const char *e = std::getenv(name);
+    const int v = e ? std::atoi(e) : 0;
+    return (v >= 1 && v <= 64) ? v : 0;
+}
+int pair_group_m(int mode) {
+    static const int all = group_env("MOA_PAIR_GROUP_M"), oz = group_env("MOA_OZAKI_GROUP_M");
+    if (mode == MODE_OZAKI && oz) return oz;
+    return all ? all : 16;
+}
+
 int pair_sms() {
     static const int n = [] {  // read once, thread-safe
         int dev = 0, v = 0;
@@ -571,6 +584,7 @@ cudaError_t launch_pair(const CUtensorMap &ta, const CUtensorMap &tb, const CUte
     }
     p.tiles_m = (p.M + 2 * BM - 1) / (2 * BM);
     p.tiles_n = (p.N + bn(MODE) - 1) / bn(MODE);
+    p.group_m = pair_group_m(MODE);
     const int tiles = p.tiles_m * p.tiles_n;
     const int clusters = tiles < max_clusters ? tiles : max_clusters;
     cfg.gridDim = dim3(2 * clusters);
