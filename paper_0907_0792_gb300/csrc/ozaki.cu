@@ -39,8 +39,8 @@
 namespace moa {
 
 moa_status tc_gemm_ozaki(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb, int S, int beta,
-                         int lsb, int chunk_kblocks, const uint64_t *row_max, const uint64_t *col_max, double *D,
-                         int64_t ldd, int64_t M, int64_t N, int64_t K, void *scratch, cudaStream_t s);
+                         int lsb, int chunk_kblocks, int acc_pairs, const uint64_t *row_max, const uint64_t *col_max,
+                         double *D, int64_t ldd, int64_t M, int64_t N, int64_t K, void *scratch, cudaStream_t s);
 
 namespace {
 
@@ -186,8 +186,9 @@ int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
 
 }  // namespace
 
-// k-blocks of 64 per exact FP32 chunk (MOA_OZAKI_CHUNK overrides, 1..16):
-// a chunk's slice-pair accumulator holds at most 64 * chunk products of 2^14.
+// k-blocks of 64 per chunk of the contraction (MOA_OZAKI_CHUNK overrides,
+// 1..16); an accumulator takes 16 / chunk slice pairs of a chunk, so it
+// holds at most 1024 products of 2^14.
 int ozaki_chunk() {
     static const int forced = [] {
         const char *e = std::getenv("MOA_OZAKI_CHUNK");
@@ -245,7 +246,8 @@ moa_status tc_inner_ozaki(const double *A, const double *B, double *D, int64_t M
     if (cudaGetLastError() != cudaSuccess) return MOA_ERR_CUDA;
     // accumulator units 2^-lsb with lsb = (S + 1) beta: every kept pair weight 2^(lsb - (s+u+2) beta) >= 1
     const int lsb = (S + 1) * kBeta;
-    return tc_gemm_ozaki(a, Kp, b, Np, S, kBeta, lsb, ozaki_chunk(), rmax, cmax, D, N, M, N, K, rs, s);
+    const int chunk = ozaki_chunk();
+    return tc_gemm_ozaki(a, Kp, b, Np, S, kBeta, lsb, chunk, kChunkKBlocks / chunk, rmax, cmax, D, N, M, N, K, rs, s);
 }
 
 }  // namespace moa

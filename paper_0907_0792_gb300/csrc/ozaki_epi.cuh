@@ -17,18 +17,26 @@ namespace ozaki {
 // Iteration order: weight class g from S-1 (lightest) down to 0, then
 // chunk c of the contraction (`chunk` k-blocks, the last one shorter), then
 // the class's slice pairs (s, g - s), s = 0..g, then the k-blocks of the
-// chunk.  Each (class, chunk, pair) is one exact FP32 accumulator; a class's
-// sum is complete, and folded once, after its last chunk.  Running the
-// class's pairs chunk by chunk keeps the slice panels of one chunk in L2
-// while every tile of a wave uses them.
+// chunk.  One exact FP32 accumulator takes `ap` consecutive pairs of a
+// (class, chunk) (fewer for the class's last group), so it sums at most
+// ap * chunk k-blocks of digit products; a class's sum is complete, and
+// folded once, after its last chunk.  Running the class's pairs chunk by
+// chunk keeps the slice panels of one chunk in L2 while every tile of a
+// wave uses them; a short chunk makes that working set small, and grouping
+// its pairs keeps the accumulators (one epilogue pass each) few.
 struct Iter {
-    int g = 0, c = 0, s = 0, kk = 0, clen = 0;
-    MOA_DEV void start(int S, int chunk, int kblocks) {
+    int g = 0, c = 0, s = 0, kk = 0, clen = 0, ap = 1;
+    MOA_DEV void start(int S, int chunk, int kblocks, int pairs_per_acc = 1) {
         g = S - 1;
         c = s = kk = 0;
         clen = min(chunk, kblocks);
+        ap = pairs_per_acc;
     }
     MOA_DEV int kb(int chunk) const { return c * chunk + kk; }
+    // position of the current k-block inside its accumulator, and whether it
+    // is the accumulator's last (both before next())
+    MOA_DEV int acc_pos() const { return (s % ap) * clen + kk; }
+    MOA_DEV bool acc_last() const { return kk == clen - 1 && (s % ap == ap - 1 || s == g); }
     MOA_DEV void next(int chunk, int kblocks) {
         if (++kk < clen) return;
         kk = 0;
@@ -43,6 +51,10 @@ struct Iter {
         --g;
     }
 };
+
+// Accumulators the epilogue receives for class g: per chunk, its g + 1 pairs
+// in groups of ap.
+MOA_DEV int accs_in_class(int g, int chunks, int ap) { return chunks * ((g + ap) / ap); }
 
 // Exponent e with |x| < 2^(e-1) for the largest |x| of a row / column, from
 // its FP64 bit pattern (0 for an all-zero row): the scaled values lie below

@@ -79,8 +79,9 @@ cudaError_t tc_gemm_pair_fp8_launch(const uint8_t *A8, int64_t lda, const uint8_
 // sums (16-byte aligned).
 size_t pair_ozaki_scratch_bytes();
 cudaError_t tc_gemm_pair_ozaki_launch(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, int K, int S, int beta,
-                                      int lsb, int chunk_kblocks, const uint64_t *row_max, const uint64_t *col_max,
-                                      double *D, int64_t ldd, void *scratch, cudaStream_t stream);
+                                      int lsb, int chunk_kblocks, int acc_pairs, const uint64_t *row_max,
+                                      const uint64_t *col_max, double *D, int64_t ldd, void *scratch,
+                                      cudaStream_t stream);
 cudaError_t pair_read_and_clear_status(uint32_t *flags);
 // Launch the bounded-wait self-test (a wait that can only time out).
 cudaError_t tc_wait_probe(uint64_t limit_ns, cudaStream_t stream);

@@ -94,7 +94,8 @@ struct GemmParams {
     int slices;      // S: digit planes per operand
     int beta;        // bits per digit
     int lsb;         // the accumulator counts units of 2^-lsb of 2^(e_row + e_col)
-    int chunk;       // k-blocks per exact FP32 chunk
+    int chunk;       // k-blocks per chunk of the contraction
+    int acc_pairs;   // slice pairs of a (class, chunk) per exact FP32 accumulator
     double *D64;
     const uint64_t *row_max;  // |A| row maxima as FP64 bit patterns
     const uint64_t *col_max;  // |B| column maxima as FP64 bit patterns
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(cta_threads(MODE), 1)
             int tm, tn;
             tile_of(t, p.tiles_m, p.tiles_n, tm, tn);
             ozaki::Iter oz;
-            oz.start(p.slices, p.chunk, p.kblocks);
+            oz.start(p.slices, p.chunk, p.kblocks, p.acc_pairs);
             for (int it = 0; it < kiters; ++it) {
                 int kb, pa, pb;
                 if constexpr (MODE == MODE_OZAKI) {  // class, chunk, pair, k-block (ozaki::Iter)
@@ -249,7 +250,7 @@ __global__ void __launch_bounds__(cta_threads(MODE), 1)
         // a slice pair (Ozaki)
         for (int t = cfirst; t < num_tiles && ok; t += cstride) {
             ozaki::Iter oz;
-            oz.start(p.slices, p.chunk, p.kblocks);
+            oz.start(p.slices, p.chunk, p.kblocks, p.acc_pairs);
             for (int it = 0; it < kiters; ++it) {
                 int j, last;  // position inside the current accumulator; whether it is its last step
                 if constexpr (MODE == MODE_STORE) {
@@ -259,8 +260,8 @@ __global__ void __launch_bounds__(cta_threads(MODE), 1)
                     j = it % p.n_terms;
                     last = j == p.n_terms - 1;
                 } else {  // one accumulator per (class, chunk, pair)
-                    j = oz.kk;
-                    last = oz.kk == oz.clen - 1;
+                    j = oz.acc_pos();
+                    last = oz.acc_last();
                     oz.next(p.chunk, p.kblocks);
                 }
                 if (j == 0) {
@@ -358,7 +359,7 @@ __global__ void __launch_bounds__(cta_threads(MODE), 1)
                     const bool class_ends = true;  // the loops below consume the whole class
                     // the class's power-of-two weight in accumulator units, exact in FP32
                     const float w = ozaki::class_weight(cls, p.lsb, p.beta);
-                    for (int c = 0; c < chunks * (cls + 1); ++c) {  // (chunk, pair) accumulators of the class
+                    for (int c = 0; c < ozaki::accs_in_class(cls, chunks, p.acc_pairs); ++c) {  // the class's accumulators
                         if (!wait_acc()) {
                             ok = false;
                             break;
@@ -616,12 +617,16 @@ moa_status tc_gemm_fp8(const uint8_t *A, int64_t lda, const uint8_t *B, int64_t 
 // 2^(e_row + e_col - (s + u + 2) * beta) * (A_s . B_u); lsb is chosen so
 // every pair weight 2^(lsb - (s + u + 2) beta) is within FP32's range.
 moa_status tc_gemm_ozaki(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb, int S, int beta,
-                         int lsb, int chunk_kblocks, const uint64_t *row_max, const uint64_t *col_max, double *D,
-                         int64_t ldd, int64_t M, int64_t N, int64_t K, void *scratch, cudaStream_t s) {
+                         int lsb, int chunk_kblocks, int acc_pairs, const uint64_t *row_max, const uint64_t *col_max,
+                         double *D, int64_t ldd, int64_t M, int64_t N, int64_t K, void *scratch, cudaStream_t s) {
     if (M >= (1ll << 31) || N >= (1ll << 31) || K >= (1ll << 31)) return MOA_ERR_OVERFLOW;
     // weights 2^(lsb - (g+2) beta) must be exact FP32 powers of two >= 1, and a
     // class sum (g+1 <= S pairs of K balanced digit products, each at most
     // 2^(2 beta - 2) in magnitude) must stay below 2^31
+    // an accumulator (acc_pairs pairs of a chunk of chunk_kblocks k-blocks of 64 products of at most
+    // 2^(2 beta - 2)) must stay at or below 2^24 to be exact in FP32
+    if (acc_pairs < 1 || (double)acc_pairs * chunk_kblocks * 64.0 * (double)(1 << (2 * beta - 2)) > 16777216.0)
+        return MOA_ERR_INTERNAL;
     if (S < 1 || S > 10 || chunk_kblocks < 1 || lsb - 2 * beta > 100 || lsb - (S + 1) * beta < 0 ||
         (double)S * (double)K * (double)(1 << (2 * beta - 2)) >= 2147483648.0)
         return MOA_ERR_INTERNAL;
@@ -635,12 +640,12 @@ moa_status tc_gemm_ozaki(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat1
     p.M = (int)M, p.N = (int)N, p.K = (int)K;
     p.kblocks = (int)((K + BK - 1) / BK);
     p.n_terms = S * (S + 1) / 2;
-    p.slices = S, p.beta = beta, p.lsb = lsb, p.chunk = chunk_kblocks;
+    p.slices = S, p.beta = beta, p.lsb = lsb, p.chunk = chunk_kblocks, p.acc_pairs = acc_pairs;
     p.D64 = D, p.ldd = ldd, p.row_max = row_max, p.col_max = col_max;
     p.ab_fmt = ptx::idesc_ab_f16(false);
     if (M > BM && N > 128 && pair_mma_enabled() && scratch) {  // 256 x 256 tiles on CTA pairs
-        const cudaError_t e = tc_gemm_pair_ozaki_launch(ta, tb, p.M, p.N, p.K, S, beta, lsb, chunk_kblocks, row_max, col_max,
-                                                        D, ldd, scratch, s);
+        const cudaError_t e = tc_gemm_pair_ozaki_launch(ta, tb, p.M, p.N, p.K, S, beta, lsb, chunk_kblocks, acc_pairs,
+                                                        row_max, col_max, D, ldd, scratch, s);
         return e == cudaSuccess ? MOA_OK : MOA_ERR_CUDA;
     }
     // 192-wide tiles: two accumulators fit TMEM and the int32 class sums of a

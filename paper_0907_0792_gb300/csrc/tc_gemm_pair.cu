@@ -131,6 +131,7 @@ struct PairParams {
     int i32_out;  // store mode: D holds int32 (every accumulator an exact integer, |x| <= 2^24)
     // Ozaki mode (ozaki_epi.cuh)
     int slices, beta, lsb, chunk;  // S, bits per digit, accumulator LSB, k-blocks per exact chunk
+    int acc_pairs;                 // slice pairs of a (class, chunk) per accumulator
     double *D64;
     const uint64_t *row_max, *col_max;  // |A| row / |B| column maxima as FP64 bit patterns
     float2 *rs;  // running-sum scratch: per CTA, per epilogue warp, 64 columns x 32 lanes
@@ -225,7 +226,7 @@ __global__ void __launch_bounds__(threads(MODE), 1)
             const int row0 = tm * 2 * BM + crank * BM;
             const int col0 = tn * BN + crank * (BN / 2);
             ozaki::Iter oz;
-            oz.start(p.slices, p.chunk, p.kblocks);
+            oz.start(p.slices, p.chunk, p.kblocks, p.acc_pairs);
             for (int it = 0; it < kiters; ++it) {
                 int kb, pa, pb;
                 if constexpr (MODE == MODE_OZAKI) {  // class, chunk, pair, k-block
@@ -291,15 +292,15 @@ __global__ void __launch_bounds__(threads(MODE), 1)
         const ptx::DescHalves s0 = ptx::desc_halves(ptx::smem_desc_plain(tiles0 + sf_off(MODE), 128));
         for (int t = cfirst; t < num_tiles && ok; t += cstride) {
             ozaki::Iter oz;
-            oz.start(p.slices, p.chunk, p.kblocks);
+            oz.start(p.slices, p.chunk, p.kblocks, p.acc_pairs);
             for (int it = 0; it < kiters; ++it) {
                 int j, last;  // position inside the current accumulator; whether it is its last step
                 if constexpr (MODE == MODE_STORE || MODE == MODE_FP8) {
                     j = it;
                     last = it == kiters - 1;
                 } else if constexpr (MODE == MODE_OZAKI) {  // one accumulator per (class, chunk, pair)
-                    j = oz.kk;
-                    last = oz.kk == oz.clen - 1;
+                    j = oz.acc_pos();
+                    last = oz.acc_last();
                     oz.next(p.chunk, p.kblocks);
                 } else {  // a fresh accumulator per k-block (all its terms)
                     j = it % p.n_terms;
@@ -440,7 +441,7 @@ __global__ void __launch_bounds__(threads(MODE), 1)
                 for (int j = 0; j < HC; ++j) qacc[j] = 0;
                 const int chunks = (p.kblocks + p.chunk - 1) / p.chunk;
                 for (int cls = p.slices - 1; cls >= 0 && ok; --cls) {
-                    for (int a = 0; a < chunks * (cls + 1); ++a) {
+                    for (int a = 0; a < ozaki::accs_in_class(cls, chunks, p.acc_pairs); ++a) {
                         if (!wait_acc()) {
                             ok = false;
                             break;
@@ -452,7 +453,7 @@ __global__ void __launch_bounds__(threads(MODE), 1)
                             ptx::tmem_ld16(tb + c0, r);
                             ptx::tmem_ld_wait();
 #pragma unroll
-                            for (int j = 0; j < 16; ++j)  // exact: chunk sums are integers below 2^24
+                            for (int j = 0; j < 16; ++j)  // exact: accumulator sums are integers of at most 2^24
                                 qacc[c0 + j] += __float2int_rz(__uint_as_float(r[j]));
                         }
                         release_acc();  // the MMA may refill the accumulator during the fold
@@ -687,9 +688,10 @@ cudaError_t tc_gemm_pair_launch(const CUtensorMap &ta, const CUtensorMap &tb, in
 }
 
 cudaError_t tc_gemm_pair_ozaki_launch(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, int K, int S, int beta,
-                                      int lsb, int chunk_kblocks, const uint64_t *row_max, const uint64_t *col_max,
-                                      double *D, int64_t ldd, void *scratch, cudaStream_t s) {
+                                      int lsb, int chunk_kblocks, int acc_pairs, const uint64_t *row_max,
+                                      const uint64_t *col_max, double *D, int64_t ldd, void *scratch, cudaStream_t s) {
     PairParams p{};
+    p.acc_pairs = acc_pairs;
     p.ab_fmt = ptx::idesc_ab_f16(false);
     p.rs = (float2 *)scratch;
     p.M = M, p.N = N, p.K = K;
