@@ -26,22 +26,29 @@ namespace ozaki {
 // its pairs keeps the accumulators (one epilogue pass each) few.
 struct Iter {
     int g = 0, c = 0, s = 0, kk = 0, clen = 0, ap = 1;
+    int sg = 0;   // index of pair s inside its group of ap pairs
+    int pos = 0;  // k-blocks of the current accumulator before this one
     MOA_DEV void start(int S, int chunk, int kblocks, int pairs_per_acc = 1) {
         g = S - 1;
-        c = s = kk = 0;
+        c = s = kk = sg = pos = 0;
         clen = min(chunk, kblocks);
         ap = pairs_per_acc;
     }
     MOA_DEV int kb(int chunk) const { return c * chunk + kk; }
     // position of the current k-block inside its accumulator, and whether it
-    // is the accumulator's last (both before next())
-    MOA_DEV int acc_pos() const { return (s % ap) * clen + kk; }
-    MOA_DEV bool acc_last() const { return kk == clen - 1 && (s % ap == ap - 1 || s == g); }
+    // is the accumulator's last (both before next()); kept incrementally, no
+    // division in the issuing thread's loop
+    MOA_DEV int acc_pos() const { return pos; }
+    MOA_DEV bool acc_last() const { return kk == clen - 1 && (sg == ap - 1 || s == g); }
     MOA_DEV void next(int chunk, int kblocks) {
+        pos = acc_last() ? 0 : pos + 1;
         if (++kk < clen) return;
         kk = 0;
-        if (++s <= g) return;
-        s = 0;
+        if (++s <= g) {
+            if (++sg == ap) sg = 0;
+            return;
+        }
+        s = sg = 0;
         if (++c * chunk < kblocks) {
             clen = min(chunk, kblocks - c * chunk);
             return;
