@@ -186,16 +186,20 @@ int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
 
 }  // namespace
 
-// k-blocks of 64 per chunk of the contraction (MOA_OZAKI_CHUNK overrides,
-// 1..16); an accumulator takes 16 / chunk slice pairs of a chunk, so it
-// holds at most 1024 products of 2^14.
+// k-blocks of 64 per chunk of the contraction: 8 (MOA_OZAKI_CHUNK
+// overrides, 1..16); an accumulator takes 16 / chunk slice pairs of a chunk,
+// so it holds at most 1024 products of 2^14.  Measured at 8192^3 on one box,
+// two runs each: chunk 16 (one pair per accumulator) 51.5-52.0 effective
+// TFLOP/s at a 1702 MHz median clock, chunk 8 (two pairs) 54.3-54.5 at
+// 1826-1905 MHz (less DRAM traffic, so more of the power budget for the
+// SMs), chunk 4 (four pairs) 52.0-52.4.
 int ozaki_chunk() {
     static const int forced = [] {
         const char *e = std::getenv("MOA_OZAKI_CHUNK");
         const int v = e ? std::atoi(e) : 0;
         return (v < 1 || v > kChunkKBlocks) ? 0 : v;
     }();
-    return forced ? forced : kChunkKBlocks;
+    return forced ? forced : 8;
 }
 
 // Slices per operand for a contraction of length K (MOA_OZAKI_SLICES overrides, 4..10).
