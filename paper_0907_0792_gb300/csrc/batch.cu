@@ -13,22 +13,20 @@
 // split planes and the item list are uploaded once.
 //
 // Execute (moa_batch_execute): a CUDA graph, captured on the first execute
-// and replayed after.  Under the default schedules it holds (1) persistent
-// CUDA-core kernels, one per (operator, occupied tile halves) present, two
-// 256-thread CTAs per SM, each pulling its CC items from its own queue
-// counter; (2) the grouped split pre-pass (FP32 -> three bf16 planes for
-// every BF16x3 problem); (3) one persistent grouped kernel (one CTA per SM)
-// for the TC / OUT / FILL items.  In that kernel the TMA warp pulls item
-// indices from a device-side queue (one atomic counter) and hands each to
-// the MMA warp and the 8 epilogue warps through a 4-slot ring of
-// shared-memory slots guarded by mbarriers.  TC items run the tcgen05
-// pipeline of tc_gemm.cu in its promoted form (per-k-block FP32 promotion);
-// OUT / FILL items are computed by the 8 epilogue warps.  The third schedule
-// instead runs the CC items inside the grouped kernel too, on its epilogue
-// warps (the FP32 promotion of TC items keeps those warps busy, so there the
-// two kinds of work mostly serialise); the autotuner times the schedules on
-// the first execute.  Every wait is bounded and reports through the batch
-// status word.
+// and replayed after.  It holds (1) persistent CUDA-core kernels, one per
+// (operator, occupied tile halves) present, two 256-thread CTAs per SM, each
+// pulling its CC items from its own queue counter; (2) the grouped split
+// pre-pass (FP32 -> three bf16 planes for every BF16x3 problem); (3) one
+// persistent grouped kernel (one CTA per SM) for the TC / OUT / FILL items.
+// In that kernel the TMA warp pulls item indices from a device-side queue
+// (one atomic counter) and hands each to the MMA warp and the 16 epilogue
+// warps through a 4-slot ring of shared-memory slots guarded by mbarriers.
+// TC items run the tcgen05 pipeline of tc_gemm.cu in its promoted form
+// (per-k-block FP32 promotion) with four TMEM accumulators in turn; OUT /
+// FILL items are computed by the epilogue warps.  The two schedules differ
+// in the grouped queue's order (longest first over all items, or tensor-core
+// tiles first); the autotuner times them on the first execute.  Every wait
+// is bounded and reports through the batch status word.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <sys/stat.h>
@@ -81,15 +79,19 @@ struct SplitJob {
 };
 
 constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4, RING = 4, TERMS = 6;
-constexpr int kThreads = 320, kEpiWarps = 8;
+// 16 epilogue warps (four per TMEM lane quarter, 32 columns each) and four
+// TMEM accumulators, so the promotion and stores of short tiles keep up with
+// the MMA warp
+constexpr int kEpiWarps = 16, kThreads = 64 + 32 * kEpiWarps, kEpiThreads = 32 * kEpiWarps, NACC = 4;
 constexpr int A_BYTES = BM * BK * 2, B_BYTES = BK * BN * 2, STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int CC_BK = 16, CC_PAD = 4, CC_LD = 128 + CC_PAD;
 constexpr int CC_BYTES = 2 * 2 * CC_BK * CC_LD * 4;  // As[2][16][132] + Bs[2][16][132]
-constexpr int NBARS = 2 * STAGES + 5 + 2 * RING;
+constexpr int NBARS = 2 * STAGES + 2 * NACC + 1 + 2 * RING;
 constexpr int TC_STG_FLOATS = 32 * 33;                  // an epilogue warp's 32 x 32 staging slice (padded rows)
 constexpr int TC_STG_BYTES = kEpiWarps * TC_STG_FLOATS * 4;
-constexpr int SMEM = STAGES * STAGE_BYTES + CC_BYTES + 1024 + TC_STG_BYTES + 1024;
-constexpr int TMEM_COLS = 2 * BN;
+constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + TC_STG_BYTES + 1024;
+constexpr int TMEM_COLS = NACC * BN;
+static_assert(TMEM_COLS <= 512 && NBARS * 8 + 16 <= 1024 && SMEM <= 227 * 1024, "grouped kernel resources");
 constexpr uint32_t IDESC = ptx::idesc_bf16_f32(BM, BN, 1);
 // split-BF16x3 terms (plane of A, plane of B): small products first, hi*hi last
 __constant__ int kTermA[TERMS] = {1, 0, 2, 0, 1, 0};
@@ -210,39 +212,12 @@ __device__ __forceinline__ void cc_tile_body(const BInst &in, int tm, int tn, fl
     }
 }
 
-// Out of line in the grouped kernel (its register budget is set by the
-// tensor-core roles); inlined in the CUDA-core kernel.
-template <class Op, bool RH, bool CH>
-__device__ __noinline__ void cc_tile_q(const BInst &in, int tm, int tn, float *As, float *Bs, int tid) {
-    cc_tile_body<Op, RH, CH>(in, tm, tn, As, Bs, tid);
-}
-
-template <class Op>
-MOA_DEV void cc_tile_inline(const BInst &in, int tm, int tn, float *As, float *Bs, int tid) {
-    const bool rh = (int64_t)tm * 128 + 64 < in.M, ch = (int64_t)tn * 128 + 64 < in.N;
-    if (rh && ch) cc_tile_body<Op, true, true>(in, tm, tn, As, Bs, tid);
-    else if (rh) cc_tile_body<Op, true, false>(in, tm, tn, As, Bs, tid);
-    else if (ch) cc_tile_body<Op, false, true>(in, tm, tn, As, Bs, tid);
-    else cc_tile_body<Op, false, false>(in, tm, tn, As, Bs, tid);
-}
-
-template <class Op>
-MOA_DEV void cc_tile(const BInst &in, int tm, int tn, float *As, float *Bs, int tid) {
-    const bool rh = (int64_t)tm * 128 + 64 < in.M, ch = (int64_t)tn * 128 + 64 < in.N;
-    if (rh && ch) cc_tile_q<Op, true, true>(in, tm, tn, As, Bs, tid);
-    else if (rh) cc_tile_q<Op, true, false>(in, tm, tn, As, Bs, tid);
-    else if (ch) cc_tile_q<Op, false, true>(in, tm, tn, As, Bs, tid);
-    else cc_tile_q<Op, false, false>(in, tm, tn, As, Bs, tid);
-}
-
 __global__ void __launch_bounds__(kThreads, 1)
     batch_grouped_kernel(const __grid_constant__ BatchParams p) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    float *ccA = (float *)(smem + STAGES * STAGE_BYTES);
-    float *ccB = ccA + 2 * CC_BK * CC_LD;
-    uint64_t *bars = (uint64_t *)(smem + STAGES * STAGE_BYTES + CC_BYTES);
-    float *tcstg = (float *)(smem + STAGES * STAGE_BYTES + CC_BYTES + 1024);  // TC epilogue staging, per warp
+    uint64_t *bars = (uint64_t *)(smem + STAGES * STAGE_BYTES);
+    float *tcstg = (float *)(smem + STAGES * STAGE_BYTES + 1024);  // TC epilogue staging, per warp
     uint32_t *tmem_slot = (uint32_t *)(bars + NBARS);
     volatile uint32_t *abort_flag = tmem_slot + 1;
     volatile int *ring = (volatile int *)(tmem_slot + 2);
@@ -253,15 +228,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     auto full = [&](int s) { return bar0 + 8u * s; };
     auto empty = [&](int s) { return bar0 + 8u * (STAGES + s); };
     auto tfull = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
-    auto tempty = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 + b); };
-    const uint32_t drain = bar0 + 8u * (2 * STAGES + 4);
-    auto rfull = [&](int s) { return bar0 + 8u * (2 * STAGES + 5 + s); };
-    auto rempty = [&](int s) { return bar0 + 8u * (2 * STAGES + 5 + RING + s); };
+    auto tempty = [&](int b) { return bar0 + 8u * (2 * STAGES + NACC + b); };
+    const uint32_t drain = bar0 + 8u * (2 * STAGES + 2 * NACC);
+    auto rfull = [&](int s) { return bar0 + 8u * (2 * STAGES + 2 * NACC + 1 + s); };
+    auto rempty = [&](int s) { return bar0 + 8u * (2 * STAGES + 2 * NACC + 1 + RING + s); };
     uint32_t *status = &g_batch_status;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) ptx::mbar_init(full(s), 1), ptx::mbar_init(empty(s), 1);
-        for (int b = 0; b < 2; ++b) ptx::mbar_init(tfull(b), 1), ptx::mbar_init(tempty(b), kEpiWarps);
+        for (int b = 0; b < NACC; ++b) ptx::mbar_init(tfull(b), 1), ptx::mbar_init(tempty(b), kEpiWarps);
         ptx::mbar_init(drain, 1);
         for (int s = 0; s < RING; ++s) ptx::mbar_init(rfull(s), 1), ptx::mbar_init(rempty(s), 1 + kEpiWarps);
         *abort_flag = 0u;
@@ -369,8 +344,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (++stage == STAGES) stage = 0, phase ^= 1u;
                 if (j == TERMS - 1) {
                     ptx::mma_commit(tfull(abuf));
-                    abuf ^= 1;
-                    if (!abuf) aphase ^= 1u;
+                    if (++abuf == NACC) abuf = 0, aphase ^= 1u;
                 }
             }
             if (!ok) break;
@@ -383,8 +357,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else if (warp >= 2) {
         // ------------------------------------------------ epilogue / CUDA-core warps
-        const int q = warp & 3, half = (warp - 2) / 4, etid = threadIdx.x - 64;
-        constexpr int HC = BN / 2;
+        const int q = warp & 3, part = (warp - 2) / 4, etid = threadIdx.x - 64;
+        constexpr int HC = BN / (kEpiWarps / 4);  // columns of the tile per epilogue warp
         int abuf = 0, slot = 0;
         uint32_t aphase = 0, rphase = 0;
         bool ok = true;
@@ -415,7 +389,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                     ptx::tc_fence_after();
-                    const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(abuf * BN + half * HC);
+                    const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(abuf * BN + part * HC);
 #pragma unroll
                     for (int c = 0; c < HC; c += 32) {
                         uint32_t r[32];
@@ -427,15 +401,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                     ptx::tc_fence_before();
                     __syncwarp();
                     if (lane == 0) ptx::mbar_arrive(tempty(abuf));
-                    abuf ^= 1;
-                    if (!abuf) aphase ^= 1u;
+                    if (++abuf == NACC) abuf = 0, aphase ^= 1u;
                 }
                 if (!ok) break;
                 // the warp's 32 rows x HC columns leave through its own shared-memory
                 // slice, 32 columns at a time, so that every store instruction writes
                 // 32 consecutive columns of one row (128 contiguous bytes)
                 const int64_t row0 = (int64_t)it.a * BM + q * 32;
-                const int64_t col0 = (int64_t)it.b * BN + half * HC;
+                const int64_t col0 = (int64_t)it.b * BN + part * HC;
                 const int rows_here = (int)min((int64_t)32, in.M - row0);
                 float *sl = tcstg + (warp - 2) * TC_STG_FLOATS;
                 if (rows_here > 0) {
@@ -452,24 +425,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                         __syncwarp();
                     }
                 }
-            } else if (it.type == IT_CC) {
-                switch (in.op) {
-                case CC_MIN_PLUS: cc_tile<sr::F32MinPlus>(in, it.a, it.b, ccA, ccB, etid); break;
-                case CC_MAX_PLUS: cc_tile<sr::F32MaxPlus>(in, it.a, it.b, ccA, ccB, etid); break;
-                case CC_MIN_TIMES: cc_tile<sr::F32MinTimes>(in, it.a, it.b, ccA, ccB, etid); break;
-                case CC_MAX_TIMES: cc_tile<sr::F32MaxTimes>(in, it.a, it.b, ccA, ccB, etid); break;
-                default: cc_tile<sr::F32PlusTimes>(in, it.a, it.b, ccA, ccB, etid); break;
-                }
             } else if (it.type == IT_OUT) {
                 const int64_t N = in.N, e0 = (int64_t)it.a * N, e1 = (int64_t)(it.a + it.b) * N;
-                for (int64_t e = e0 + etid; e < e1; e += 256) {
+                for (int64_t e = e0 + etid; e < e1; e += kEpiThreads) {
                     const int64_t i = e / N;
                     in.D[e] = op_apply(in.op, __ldg(in.A + i), __ldg(in.B + (e - i * N)));
                 }
             } else {  // IT_FILL
                 const int64_t e0 = (int64_t)it.a * in.N, e1 = (int64_t)(it.a + it.b) * in.N;
                 const float v = __int_as_float(in.op);
-                for (int64_t e = e0 + etid; e < e1; e += 256) in.D[e] = v;
+                for (int64_t e = e0 + etid; e < e1; e += kEpiThreads) in.D[e] = v;
             }
         }
         (void)ok;
@@ -693,7 +658,7 @@ int tune_mode() {  // 0 off, 1 cached, 2 force
 // (before the split pass), the grouped queue longest first; 1 the same with
 // tensor-core items first in the grouped queue; 2 every item in the grouped
 // kernel, tensor-core and CUDA-core items interleaved.
-constexpr int kPolicies = 3;
+constexpr int kPolicies = 2;
 
 }  // namespace
 }  // namespace moa
@@ -747,17 +712,9 @@ void order_items(const moa_batch_plan &pl, int policy, std::vector<BItem> &group
     if (policy == 0) {
         for (int i : idx)
             if (pl.items[i].type != IT_CC) grouped.push_back(pl.items[i]);
-    } else if (policy == 1) {
+    } else {
         for (int i : tc) grouped.push_back(pl.items[i]);
         for (int i : other) grouped.push_back(pl.items[i]);
-    } else {  // interleave tensor-core and CUDA-core items so both kinds of unit stay busy
-        size_t a = 0, b = 0;
-        while (a < tc.size() || b < ccs.size()) {
-            if (a < tc.size()) grouped.push_back(pl.items[tc[a++]]);
-            if (b < ccs.size()) grouped.push_back(pl.items[ccs[b++]]);
-        }
-        for (int i : other) grouped.push_back(pl.items[i]);
-        return;
     }
     for (int g = 0; g < kCcGroups; ++g)  // by kernel (operator, tile halves), longest first within each
         for (int i : ccs)
@@ -832,7 +789,7 @@ moa_status autotune(moa_batch_plan *pl, cudaStream_t s) {
         return upload_order(pl, pl->policy, s);
     }
     const int mode = tune_mode();
-    const std::string key = gpu_signature() + "|s2|" + pl->signature;  // s2: the schedules listed at kPolicies
+    const std::string key = gpu_signature() + "|s3|" + pl->signature;  // s3: the schedules listed at kPolicies
     if (mode == 0) {
         pl->policy = 0;
         return upload_order(pl, 0, s);

@@ -96,7 +96,7 @@ def test_batch_full_10000_sampled():
     check_status()
 
 
-@pytest.mark.parametrize("schedule", ["0", "1", "2"])
+@pytest.mark.parametrize("schedule", ["0", "1"])
 def test_batch_every_cuda_core_operator_and_schedule(schedule, monkeypatch):
     """Every CUDA-core (reduce, combine) of the batch, tiles with one, two or
     four occupied halves and several tiles per problem, under each schedule
