@@ -10,12 +10,14 @@
 // buffers per operand block alternate.  The two copy streams belong to the
 // library (one pair per device and caller stream) and wait on, and are
 // waited on by, the caller's stream through events, so the whole call is
-// ordered on `stream` like every other call.
+// ordered on `stream` like every other call.  In the Ozaki form B's column
+// maxima and digit planes are made once, not once per block.
 #include <cstring>
 #include <map>
 #include <mutex>
 
 #include "internal.h"
+#include "tc.h"
 
 namespace moa {
 
@@ -128,6 +130,19 @@ extern "C" moa_status moa_inner_host(moa_op reduce, moa_op combine, moa_dtype dt
     };
     if (!upload(0)) return MOA_ERR_CUDA;
     if (!ok(cudaStreamWaitEvent(s, c->b_in, 0))) return MOA_ERR_CUDA;
+    // The Ozaki form prepares B (column maxima, digit planes) once for all
+    // row blocks, while the first block of A is still coming in.
+    const bool ozaki_blocks = reduce == MOA_OP_ADD && combine == MOA_OP_MUL && dtype == MOA_F64 &&
+                              form == MOA_FORM_OZAKI && K > 0;
+    OzakiB ob{};
+    void *oz_rows_ws = nullptr;
+    if (ozaki_blocks) {
+        void *oz_b_ws = workspace_get(s, ozaki_b_bytes(K, N), &st, 3);
+        if (st != MOA_OK) return st;
+        oz_rows_ws = workspace_get(s, ozaki_rows_bytes(rows, K), &st, 0);
+        if (st != MOA_OK) return st;
+        if ((st = ozaki_prepare_b((const double *)dB, K, N, oz_b_ws, &ob, s)) != MOA_OK) return st;
+    }
     for (int b = 0; b < nb; ++b) {
         const int64_t r0 = b * rows, r1 = (r0 + rows < M) ? r0 + rows : M;
         if (b + 1 < nb && !upload(b + 1)) return MOA_ERR_CUDA;
@@ -136,8 +151,11 @@ extern "C" moa_status moa_inner_host(moa_op reduce, moa_op combine, moa_dtype dt
         // the block as its own inner product: rho A = <rows, K>, rho B = <K, N>
         const int64_t sa[2] = {r1 - r0, K}, sb[2] = {K, N};
         int64_t m, k, n;
-        st = inner_checked(reduce, combine, dtype, form, 2, sa, dA[b % kBufs], 2, sb, dB, dD[b % kBufs], out_dtype, s,
-                           &m, &k, &n, true);
+        if (ozaki_blocks)
+            st = ozaki_rows((const double *)dA[b % kBufs], r1 - r0, ob, (double *)dD[b % kBufs], oz_rows_ws, s);
+        else
+            st = inner_checked(reduce, combine, dtype, form, 2, sa, dA[b % kBufs], 2, sb, dB, dD[b % kBufs], out_dtype,
+                               s, &m, &k, &n, true);
         if (st != MOA_OK) return st;
         if (!ok(cudaEventRecord(c->computed[b % kBufs], s)) || !ok(cudaStreamWaitEvent(c->down, c->computed[b % kBufs], 0)))
             return MOA_ERR_CUDA;

@@ -14,7 +14,8 @@ namespace moa {
 // Workspace: scratch device memory owned by the library, one buffer per
 // (device, stream, slot), grown with stream-ordered allocation (api.cu).
 // Slot 0 serves the inner and outer products, slot 1 the transposed operands
-// of moa_inner_axes, slot 2 the device copies of moa_inner_host's operands.
+// of moa_inner_axes, slot 2 the device copies of moa_inner_host's operands,
+// slot 3 the digit planes of B that moa_inner_host's Ozaki row blocks share.
 void *workspace_get(cudaStream_t stream, size_t bytes, moa_status *st, int slot = 0);
 
 // MOA_OK when every non-null pointer of ptrs[0..n) lies in device (or

@@ -254,4 +254,49 @@ moa_status tc_inner_ozaki(const double *A, const double *B, double *D, int64_t M
     return tc_gemm_ozaki(a, Kp, b, Np, S, kBeta, lsb, chunk, kChunkKBlocks / chunk, rmax, cmax, D, N, M, N, K, rs, s);
 }
 
+// The same product in two steps, for a caller that runs several blocks of
+// result rows against one B (moa_inner_host): B's column maxima and digit
+// planes once, then per block of rows A's maxima, planes and the GEMM.
+size_t ozaki_b_bytes(int64_t K, int64_t N) {
+    return (size_t)ozaki_slices(K) * (size_t)(K * round8(N)) * 2 + (size_t)N * 8 + 256;
+}
+size_t ozaki_rows_bytes(int64_t M, int64_t K) {
+    return (size_t)ozaki_slices(K) * (size_t)(M * round8(K)) * 2 + (size_t)M * 8 + pair_ozaki_scratch_bytes() + 256;
+}
+
+moa_status ozaki_prepare_b(const double *B, int64_t K, int64_t N, void *ws, OzakiB *ob, cudaStream_t s) {
+    if ((double)ozaki_slices(K) * (double)K * 16384.0 >= 2147483648.0) return MOA_ERR_UNSUPPORTED;
+    const int S = ozaki_slices(K);
+    const int64_t Np = round8(N);
+    __nv_bfloat16 *b = (__nv_bfloat16 *)ws;
+    uint64_t *cmax = (uint64_t *)(((uintptr_t)(b + (int64_t)S * K * Np) + 15) & ~(uintptr_t)15);
+    if (launch_fill64(cmax, 0ull, N, s) != cudaSuccess) return MOA_ERR_CUDA;
+    const int64_t gx = (N + 255) / 256;
+    int64_t gy = (152 * 8 + gx - 1) / gx;
+    if (gy > K) gy = K;
+    const int64_t rpb = (K + gy - 1) / gy;
+    gy = (K + rpb - 1) / rpb;
+    col_max_kernel<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, s>>>(B, K, N, rpb, cmax);
+    if (!run_slices<false>(B, K, N, Np, cmax, S, b, s)) return MOA_ERR_INTERNAL;
+    if (cudaGetLastError() != cudaSuccess) return MOA_ERR_CUDA;
+    *ob = OzakiB{b, cmax, S, K, N};
+    return MOA_OK;
+}
+
+moa_status ozaki_rows(const double *A, int64_t M, const OzakiB &ob, double *D, void *ws, cudaStream_t s) {
+    const int64_t K = ob.K, N = ob.N, Kp = round8(K);
+    const int S = ob.S;
+    __nv_bfloat16 *a = (__nv_bfloat16 *)ws;
+    uint64_t *rmax = (uint64_t *)(((uintptr_t)(a + (int64_t)S * M * Kp) + 15) & ~(uintptr_t)15);
+    void *rs = (void *)(((uintptr_t)(rmax + M) + 15) & ~(uintptr_t)15);
+    const int64_t warps = M < 152 * 32 ? M : 152 * 32;
+    row_max_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(A, M, K, rmax, nullptr, 0);
+    if (!run_slices<true>(A, M, K, Kp, rmax, S, a, s)) return MOA_ERR_INTERNAL;
+    if (cudaGetLastError() != cudaSuccess) return MOA_ERR_CUDA;
+    const int lsb = (S + 1) * kBeta;
+    const int chunk = ozaki_chunk();
+    return tc_gemm_ozaki(a, Kp, ob.planes, round8(N), S, kBeta, lsb, chunk, kChunkKBlocks / chunk, rmax, ob.cmax, D, N,
+                         M, N, K, rs, s);
+}
+
 }  // namespace moa

@@ -40,6 +40,19 @@ moa_status tc_inner_fp8(const float *A, const float *B, float *D, int64_t M, int
 // FP64 operands, FP64 out, Ozaki-sliced on bf16 tensor cores.
 moa_status tc_inner_ozaki(const double *A, const double *B, double *D, int64_t M, int64_t N, int64_t K,
                           cudaStream_t stream);
+// The Ozaki form in two steps (several blocks of result rows against one B):
+// B's column maxima and digit planes into ws (ozaki_b_bytes), then per block
+// of rows A's maxima, planes and the GEMM with scratch ws (ozaki_rows_bytes).
+struct OzakiB {
+    const __nv_bfloat16 *planes;
+    const uint64_t *cmax;
+    int S;
+    int64_t K, N;
+};
+size_t ozaki_b_bytes(int64_t K, int64_t N);
+size_t ozaki_rows_bytes(int64_t M, int64_t K);
+moa_status ozaki_prepare_b(const double *B, int64_t K, int64_t N, void *ws, OzakiB *ob, cudaStream_t stream);
+moa_status ozaki_rows(const double *A, int64_t M, const OzakiB &ob, double *D, void *ws, cudaStream_t stream);
 // int32 operands, int32 out, on bf16 tensor cores when every operand value
 // lies in [-128, 127] (else on CUDA cores): see tc_forms.cu.
 bool i32_tc_applies(int64_t M, int64_t N, int64_t K);

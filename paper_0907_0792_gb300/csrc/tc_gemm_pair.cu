@@ -448,12 +448,12 @@ __global__ void __launch_bounds__(threads(MODE), 1)
                         }
                         const uint32_t tb = lanes + (uint32_t)(abuf * ACC_STRIDE);
 #pragma unroll
-                        for (int c0 = 0; c0 < HC; c0 += 16) {
-                            uint32_t r[16];
-                            ptx::tmem_ld16(tb + c0, r);
+                        for (int c0 = 0; c0 < HC; c0 += 8) {  // 8 columns a load: the 64 class sums leave few registers
+                            uint32_t r[8];
+                            ptx::tmem_ld8(tb + c0, r);
                             ptx::tmem_ld_wait();
 #pragma unroll
-                            for (int j = 0; j < 16; ++j)  // exact: accumulator sums are integers of at most 2^24
+                            for (int j = 0; j < 8; ++j)  // exact: accumulator sums are integers of at most 2^24
                                 qacc[c0 + j] += __float2int_rz(__uint_as_float(r[j]));
                         }
                         release_acc();  // the MMA may refill the accumulator during the fold
