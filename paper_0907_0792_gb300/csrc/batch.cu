@@ -687,6 +687,8 @@ struct moa_batch_plan {
     void *d_ws = nullptr;
     // graph
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t side = nullptr;  // the split pre-pass runs here, beside the CUDA-core kernels
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::mutex mu;
 };
@@ -754,6 +756,18 @@ cudaError_t enqueue(moa_batch_plan *pl, cudaStream_t s) {
         cudaError_t e = cudaMemsetAsync(pl->d_queue, 0, (1 + kCcGroups) * sizeof(int), s);
         if (e != cudaSuccess) return e;
     }
+    // the split pre-pass (memory bound) on the plan's side stream, beside the
+    // CUDA-core kernels (ALU bound); the grouped kernel waits for both
+    const bool fork = pl->n_jobs > 0 && pl->n_cc > 0;
+    if (fork) {
+        cudaError_t e = cudaEventRecord(pl->ev_fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(pl->side, pl->ev_fork, 0);
+        if (e != cudaSuccess) return e;
+        const int blocks = std::min(pl->n_jobs, sm_count_dev() * 8);
+        batch_split_kernel<<<blocks, 256, 0, pl->side>>>(pl->d_jobs, pl->n_jobs);
+        e = cudaEventRecord(pl->ev_join, pl->side);
+        if (e != cudaSuccess) return e;
+    }
     // one persistent kernel per (operator, occupied tile halves) present, each with its own queue
     for (int g = 0; g < kCcGroups; ++g) {
         const int cnt = pl->cc_cnt[g];
@@ -770,7 +784,10 @@ cudaError_t enqueue(moa_batch_plan *pl, cudaStream_t s) {
         default: launch_cc_quad<sr::F32PlusTimes>(q, grid, pl->d_inst, items, cnt, queue, s); break;
         }
     }
-    if (pl->n_jobs > 0) {
+    if (fork) {
+        const cudaError_t e = cudaStreamWaitEvent(s, pl->ev_join, 0);
+        if (e != cudaSuccess) return e;
+    } else if (pl->n_jobs > 0) {
         const int blocks = std::min(pl->n_jobs, sm_count_dev() * 8);
         batch_split_kernel<<<blocks, 256, 0, s>>>(pl->d_jobs, pl->n_jobs);
     }
@@ -843,6 +860,9 @@ void plan_free(moa_batch_plan *pl) {
     cudaDeviceSynchronize();
     if (pl->exec) cudaGraphExecDestroy(pl->exec);
     if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+    if (pl->side) cudaStreamDestroy(pl->side);
+    if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
+    if (pl->ev_join) cudaEventDestroy(pl->ev_join);
     cudaFree(pl->d_inst);
     cudaFree(pl->d_items);
     cudaFree(pl->d_cc_items);
@@ -981,7 +1001,10 @@ moa_status moa_batch_plan_create(int count, const moa_problem *problems, moa_bat
     ok = (inst.empty() || cudaMemcpy(pl->d_inst, inst.data(), inst.size() * sizeof(BInst), cudaMemcpyHostToDevice) == cudaSuccess) &&
          (tmaps.empty() || cudaMemcpy(pl->d_tmaps, tmaps.data(), tmaps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice) == cudaSuccess) &&
          (jobs.empty() || cudaMemcpy(pl->d_jobs, jobs.data(), jobs.size() * sizeof(SplitJob), cudaMemcpyHostToDevice) == cudaSuccess);
-    if (!ok || cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    if (!ok || cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&pl->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         plan_free(pl);
         return MOA_ERR_CUDA;
     }
@@ -1024,14 +1047,13 @@ moa_status moa_batch_plan_info(const moa_batch_plan *plan, int64_t *n_problems, 
     if (n_launches) {  // before the first execute: the default schedule (CUDA-core items in their own kernel)
         int64_t cc = 0;
         for (const BItem &it : plan->items) cc += it.type == IT_CC;
-        const bool sep = plan->policy != 2;
-        const int64_t grouped = sep ? plan->n_items - cc : plan->n_items;
+        const int64_t grouped = plan->n_items - cc;
         bool used[kCcGroups] = {};  // one CUDA-core kernel per (operator, tile halves) present
         for (const BItem &it : plan->items)
             if (it.type == IT_CC) used[cc_group(*plan, it)] = true;
         int ops = 0;
         for (bool u : used) ops += u;
-        *n_launches = (plan->n_jobs > 0 ? 1 : 0) + (grouped > 0 ? 1 : 0) + (sep ? ops : 0);
+        *n_launches = (plan->n_jobs > 0 ? 1 : 0) + (grouped > 0 ? 1 : 0) + ops;
     }
     if (n_tiles) *n_tiles = plan->n_items;
     if (work_flops) *work_flops = plan->work;
