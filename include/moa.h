@@ -191,6 +191,25 @@ moa_status moa_inner_host(moa_op reduce, moa_op combine, moa_dtype dtype, moa_fo
                           void *out, moa_dtype out_dtype, moa_stream stream);
 
 /*
+ * moa_inner_e4m3_scaled — the (add, mul) inner product, Eq. (2) in its
+ * matrix-multiply case (Sec. I), of FP8 E4M3 arrays stored with per-block
+ * power-of-two scales, the layout of MOA_FORM_FP8_T128:
+ *   A[i.., p] = a8[i.., p] * scale_a[i][p / 128],
+ *   B[p, j..] = b8[p, j..] * scale_b[p / 128][j / 128]   (psi-flattened i, j),
+ *   D = A . B in FP32 (tensor cores, one FP32 accumulator over the whole
+ *   contraction; normalised error <= max(2e-6, (K/16) 2^-23) relative to the
+ *   scaled operands).
+ * scale_a: M x ceil(K/128) FP32, scale_b: ceil(K/128) x ceil(N/128) FP32,
+ * row-major device memory of the current device.  Each scale is used as the
+ * power of two of its exponent field (2^floor(log2 |s|)); scales should be
+ * finite normal powers of two.  Shapes, errors and streams as for moa_inner
+ * with dtype MOA_FP8E4M3; a NULL scale array returns MOA_ERR_NULL.
+ */
+moa_status moa_inner_e4m3_scaled(int rankA, const int64_t *shapeA, const void *A, const float *scale_a, int rankB,
+                                 const int64_t *shapeB, const void *B, const float *scale_b, float *out,
+                                 moa_stream stream);
+
+/*
  * moa_inner_axes — Eq. (2) contracting axis `axisA` of A with axis `axisB`
  * of B (equal lengths) instead of A's last and B's first:
  *   D[i.., j..] = reduce_p ( A[.., p at axisA, ..] combine B[.., p at axisB, ..] ),

@@ -22,7 +22,7 @@ __all__ = [
     "moa_device_status", "moa_release_workspace", "moa_version", "inner", "outer", "OPS", "DTYPES", "FORMS",
     "moa_batch_plan_create", "moa_batch_execute", "moa_batch_plan_destroy", "moa_batch_plan_info", "MoaProblem",
     "moa_inner_bf16x3_noalloc", "NOALLOC_SCRATCH_BYTES", "make_problems", "moa_selftest_wait_timeout",
-    "moa_inner_host", "moa_kernel_timing", "moa_kernel_timing_read",
+    "moa_inner_host", "moa_kernel_timing", "moa_kernel_timing_read", "moa_inner_e4m3_scaled",
 ]
 
 # size of the fixed device buffer behind moa_inner_bf16x3_noalloc (MOA_NOALLOC_SCRATCH_BYTES)
@@ -70,6 +70,7 @@ def lib():
         L.moa_outer.argtypes = [I, I, I, _I64P, P, I, _I64P, P, P, I, V]
         L.moa_inner_axes.argtypes = [I, I, I, I, I, _I64P, P, I, I, _I64P, P, I, P, I, V]
         L.moa_inner_host.argtypes = [I, I, I, I, I, _I64P, P, I, _I64P, P, P, I, V]
+        L.moa_inner_e4m3_scaled.argtypes = [I, _I64P, P, P, I, _I64P, P, P, P, V]
         L.moa_kernel_timing.argtypes = [I]
         L.moa_kernel_timing_read.argtypes = [C.POINTER(I64), C.POINTER(C.c_double)]
         L.moa_transpose.argtypes = [I, I, _I64P, C.POINTER(C.c_int), P, P, V]
@@ -160,6 +161,17 @@ def moa_inner_host(reduce, combine, dtype, form, shapeA, A, shapeB, B, out, out_
                               _enum(DTYPES, out_dtype), _stream(stream))
     if check:
         _check(st, "moa_inner_host")
+    return st
+
+
+def moa_inner_e4m3_scaled(shapeA, A, scale_a, shapeB, B, scale_b, out, stream=None, check=True):
+    """C ABI moa_inner_e4m3_scaled: Eq. (2) (+,*) on E4M3 arrays with per-128 power-of-two block scales."""
+    sa, _ka = _shape(shapeA)
+    sb, _kb = _shape(shapeB)
+    st = lib().moa_inner_e4m3_scaled(len(shapeA), sa, _ptr(A), _ptr(scale_a), len(shapeB), sb, _ptr(B), _ptr(scale_b),
+                                     _ptr(out), _stream(stream))
+    if check:
+        _check(st, "moa_inner_e4m3_scaled")
     return st
 
 

@@ -350,6 +350,24 @@ moa_status moa_inner(moa_op reduce, moa_op combine, moa_dtype dtype, moa_form fo
     return inner_run(reduce, combine, dtype, form, A, B, out, out_dtype, pl, (cudaStream_t)stream);
 }
 
+moa_status moa_inner_e4m3_scaled(int rankA, const int64_t *shapeA, const void *A, const float *scale_a, int rankB,
+                                 const int64_t *shapeB, const void *B, const float *scale_b, float *out,
+                                 moa_stream stream) {
+    InnerPlan pl;
+    moa_status st = inner_validate(MOA_OP_ADD, MOA_OP_MUL, MOA_FP8E4M3, MOA_FORM_NATIVE, rankA, shapeA, A, rankB, shapeB,
+                                   B, out, MOA_F32, &pl);
+    if (st != MOA_OK) return st;
+    const int64_t M = pl.M, K = pl.K, N = pl.N;
+    if (M == 0 || N == 0) return MOA_OK;
+    const cudaStream_t s = (cudaStream_t)stream;
+    if (K == 0) return inner_identity_fill(MOA_OP_ADD, MOA_F32, out, M, N, s);
+    if (!scale_a || !scale_b) return MOA_ERR_NULL;
+    if (!aligned_to(scale_a, 4) || !aligned_to(scale_b, 4)) return MOA_ERR_ALIGNMENT;
+    const void *used[2] = {scale_a, scale_b};
+    if ((st = check_device_ptrs(used, 2)) != MOA_OK) return st;
+    return tc_inner_e4m3((const uint8_t *)A, (const uint8_t *)B, out, M, N, K, s, scale_a, scale_b);
+}
+
 moa_status moa_transpose(moa_dtype dtype, int rank, const int64_t *shape, const int *perm, const void *A, void *out,
                          moa_stream stream) {
     if (rank < 0 || rank > kMaxRank) return MOA_ERR_RANK;

@@ -226,13 +226,44 @@ __global__ void __launch_bounds__(256) transpose_u8(const uint8_t *__restrict__ 
     }
 }
 
+// Caller scales (FP32, taken as the power of two of their exponent field)
+// -> the pair GEMM's UE8M0 words: A's [row][k-block] and B's [k-block][column
+// block of 128], in the word order of tc_gemm_pair_fp8_launch (tc.h).
+__global__ void scale_words_kernel(const float *__restrict__ scale_a, const float *__restrict__ scale_b, int64_t M,
+                                   int64_t N, int64_t KB, int64_t NB, int T, uint32_t *__restrict__ sfa,
+                                   uint32_t *__restrict__ sfb) {
+    const int64_t na = M * KB, nb = N * KB;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < na + nb; i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < na) {
+            const int64_t row = i / KB, kb = i - row * KB;
+            sfa[((row / 128) * KB + kb) * 128 + (row % 32) * 4 + (row % 128) / 32] = ue8m0_word(scale_a[i]);
+        } else {
+            const int64_t e = i - na, n = e / KB, kb = e - n * KB;
+            const int64_t tn = n / T;
+            const int j = (int)(n - tn * T) / 32, l = (int)(n % 32);
+            sfb[(tn * KB + kb) * 256 + (j / 4) * 128 + l * 4 + j % 4] = ue8m0_word(scale_b[kb * NB + n / 128]);
+        }
+    }
+}
+
+// The same scales as FP32 powers of two (exponent field kept, sign and
+// mantissa dropped) for the single-CTA kernel, so both kernels apply the same
+// factors.
+__global__ void pow2_scales_kernel(const float *__restrict__ src, int64_t n, float *__restrict__ dst) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = __uint_as_float(__float_as_uint(src[i]) & 0x7F800000u);
+}
+
 }  // namespace
 
-// e4m3 operands as given (unit scales): A [M][K] and B [K][N] bytes.  The
-// block-scaled pair GEMM takes A K-major (padded rows when K % 16 != 0) and B
-// transposed, with every scale word 2^0; the single-CTA FP8 kernel takes B
-// as given (padded rows) with unit scale tables.
-moa_status tc_inner_e4m3(const uint8_t *A, const uint8_t *B, float *D, int64_t M, int64_t N, int64_t K, cudaStream_t s) {
+// e4m3 operands as given: A [M][K] and B [K][N] bytes, with unit scales, or
+// with the caller's scales scale_a [M][ceil(K/128)] and scale_b
+// [ceil(K/128)][ceil(N/128)] (FP32 device arrays).  The block-scaled pair GEMM
+// takes A K-major (padded rows when K % 16 != 0) and B transposed, with the
+// scale words 2^0 or built from the caller's scales; the single-CTA FP8
+// kernel takes B as given (padded rows) with scale tables.
+moa_status tc_inner_e4m3(const uint8_t *A, const uint8_t *B, float *D, int64_t M, int64_t N, int64_t K, cudaStream_t s,
+                         const float *scale_a, const float *scale_b) {
     const int64_t Kp = (K + 15) / 16 * 16, Np = (N + 15) / 16 * 16, KB = (K + 127) / 128, NB = (N + 127) / 128;
     if (KB > 65535) return MOA_ERR_OVERFLOW;
     const bool pair = M > 128 && N > 128 && M < (1ll << 31) && N < (1ll << 31) && K < (1ll << 31) && pair_mma_enabled();
@@ -256,7 +287,13 @@ moa_status tc_inner_e4m3(const uint8_t *A, const uint8_t *B, float *D, int64_t M
         transpose_u8<<<dim3((unsigned)((N + 63) / 64), (unsigned)((Kp + 63) / 64)), 256, 0, s>>>(B, K, N, Kp, b8);
         if (cudaGetLastError() != cudaSuccess) return MOA_ERR_CUDA;
         if (cudaMemsetAsync(scales, 0x7f, words * 4, s) != cudaSuccess) return MOA_ERR_CUDA;  // UE8M0 127 = 2^0
-        const uint32_t *sfa = scales, *sfb = scales + MB * KB * 128;
+        uint32_t *sfa = scales, *sfb = scales + MB * KB * 128;
+        if (scale_a) {
+            const int64_t n = (M + N) * KB;
+            scale_words_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, s>>>(
+                scale_a, scale_b, M, N, KB, NB, (int)T, sfa, sfb);
+            if (cudaGetLastError() != cudaSuccess) return MOA_ERR_CUDA;
+        }
         return tc_gemm_pair_fp8_launch(a8, Kp, b8, Kp, (int)M, (int)N, (int)K, sfa, sfb, D, N, s) == cudaSuccess
                    ? MOA_OK
                    : MOA_ERR_CUDA;
@@ -268,8 +305,14 @@ moa_status tc_inner_e4m3(const uint8_t *A, const uint8_t *B, float *D, int64_t M
         bb = b8;
     }
     if (cudaGetLastError() != cudaSuccess) return MOA_ERR_CUDA;
-    if (launch_fill32(scales, 0x3f800000u, (int64_t)words, s) != cudaSuccess) return MOA_ERR_CUDA;  // FP32 1.0
-    const float *sa = (const float *)scales, *sb = sa + M * KB;
+    float *sa = (float *)scales, *sb = sa + M * KB;
+    if (scale_a) {
+        pow2_scales_kernel<<<(unsigned)std::min<int64_t>((M * KB + 255) / 256, 152 * 16), 256, 0, s>>>(scale_a, M * KB, sa);
+        pow2_scales_kernel<<<(unsigned)std::min<int64_t>((KB * NB + 255) / 256, 152 * 16), 256, 0, s>>>(scale_b, KB * NB, sb);
+        if (cudaGetLastError() != cudaSuccess) return MOA_ERR_CUDA;
+    } else if (launch_fill32(scales, 0x3f800000u, (int64_t)words, s) != cudaSuccess) {  // FP32 1.0
+        return MOA_ERR_CUDA;
+    }
     return tc_gemm_fp8(a8, Kp, bb, Np, sa, sb, D, N, M, N, K, s);
 }
 

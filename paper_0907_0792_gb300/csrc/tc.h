@@ -29,9 +29,10 @@ moa_status tc_inner_bf16(const __nv_bfloat16 *A, const __nv_bfloat16 *B, float *
 // fp16 operands as given, FP32 out (the same kernels with fp16 operand formats).
 moa_status tc_inner_f16(const __half *A, const __half *B, float *D, int64_t M, int64_t N, int64_t K,
                         cudaStream_t stream);
-// e4m3 operands as given (unit scales), FP32 out.
+// e4m3 operands as given, FP32 out: unit scales, or the caller's
+// power-of-two scales scale_a [M][ceil(K/128)], scale_b [ceil(K/128)][ceil(N/128)].
 moa_status tc_inner_e4m3(const uint8_t *A, const uint8_t *B, float *D, int64_t M, int64_t N, int64_t K,
-                         cudaStream_t stream);
+                         cudaStream_t stream, const float *scale_a = nullptr, const float *scale_b = nullptr);
 // FP32 operands, FP32 out: MOA_FORM_BF16, MOA_FORM_F16, MOA_FORM_BF16X3 or MOA_FORM_FP8_T128.
 moa_status tc_inner_f32(moa_form form, const float *A, const float *B, float *D, int64_t M, int64_t N, int64_t K,
                         cudaStream_t stream);

@@ -215,6 +215,12 @@ def test_host_entry_and_timing_validation(L):
     assert h((4, 5), (5, 7), out=0) == 1
     assert h((0, 5), (5, 7), A=0, out=0) == 0
     assert moa.lib().moa_kernel_timing_read(None, None) == 1
+    # the scaled e4m3 call: shape and null checks before any device work
+    def e4(sa, sb, A=0x1000, B=0x2000, out=0x3000, scA=0x4000, scB=0x5000):
+        return moa.moa_inner_e4m3_scaled(sa, A, scA, sb, B, scB, out, stream=0, check=False)
+    assert e4((4, 5), (6, 7)) == 3
+    assert e4((4, 5), (5, 7), out=0) == 1
+    assert e4((0, 5), (5, 7), A=0, out=0) == 0
 
 
 def test_status_strings(L):

@@ -103,3 +103,29 @@ def test_f16_and_e4m3_square_sampled(n):
     check_status()
     del D
     torch.cuda.empty_cache()
+
+
+def _pow2_scales(seed, stream, shape, lo=-20, hi=20):
+    return np.ldexp(1.0, synth.int_uniform(seed, stream, shape, lo, hi)).astype(np.float32)
+
+
+@pytest.mark.parametrize("shA,shB", [((300, 136), (136, 200)), ((2, 64, 300), (300, 5, 80)), ((260, 700), (700, 390)),
+                                     ((37, 61), (61, 45)), ((129, 8), (8, 257))])
+def test_e4m3_with_block_scales(shA, shB):
+    """moa_inner_e4m3_scaled: e4m3 codes times per-block powers of two (A per
+    row and 128-block of the contraction, B per 128 x 128 block) against the
+    oracle's Dot2 of the scaled operands (exact in FP64)."""
+    import torch
+    M, K = int(np.prod(shA[:-1])), shA[-1]
+    N = int(np.prod(shB[1:]))
+    KB, NB = (K + 127) // 128, (N + 127) // 128
+    (ac, a), (bc, b) = synth.e4m3_codes(77, 0, shA, 12), synth.e4m3_codes(77, 1, shB, 12)
+    sa, sb = _pow2_scales(77, 2, (M, KB)), _pow2_scales(77, 3, (KB, NB))
+    kb = np.arange(K) // 128
+    As = a.reshape(M, K) * sa.astype(np.float64)[:, kb]
+    Bs = b.reshape(K, N) * sb.astype(np.float64)[kb][:, np.arange(N) // 128]
+    D = empty(shA[:-1] + shB[1:], torch.float32)
+    moa.moa_inner_e4m3_scaled(shA, torch.from_numpy(np.ascontiguousarray(ac)).to("cuda:0"), to_dev(sa), shB,
+                              torch.from_numpy(np.ascontiguousarray(bc)).to("cuda:0"), to_dev(sb), D)
+    assert_norm_err(D.cpu().numpy().reshape(M, N), As, Bs, _acc_tol(K))
+    check_status()
