@@ -12,6 +12,10 @@
 // from 48 KB to 32 KB (six stages in flight).  Each k-block's MMAs are
 // issued by one elected lane of a converged warp.
 //
+// The tiles that would make up a last, at most half-full wave run as two
+// units of half their columns each (an MMA of N = 128 on each half), so that
+// wave takes half as long.
+//
 // Roles (both CTAs run the same code; rank 0 of the cluster leads):
 //   warp 0     TMA producer in both CTAs: this CTA's 128 x 64 slice of A
 //              and its 64 x 128 slice of B per stage, into its own shared
@@ -119,6 +123,7 @@ struct PairParams {
     int M, N, K;
     int tiles_m, tiles_n;  // pair tiles: ceil(M / 256) x ceil(N / 256)
     int group_m;           // row tiles per raster group
+    int full_units;        // tiles run whole; each later tile runs as two halves of its columns
     int kblocks, n_terms;
     uint32_t term_a, term_b;  // plane of A / B for term i in bits 4i..4i+3
     float *D;
@@ -212,7 +217,19 @@ __global__ void __launch_bounds__(threads(MODE), 1)
     const bool leader = crank == 0;
     const int cfirst = (int)ptx::cluster_id_x();
     const int cstride = (int)ptx::nclusters_x();
+    // Work units: tiles [0, full_units) whole, then each remaining tile as two
+    // units of half its columns (coff = 0 or BN / 2), so the last, partly
+    // filled wave of whole tiles becomes half as long.
     const int num_tiles = p.tiles_m * p.tiles_n;
+    const int num_units = p.full_units + 2 * (num_tiles - p.full_units);
+    auto unit_of = [&](int u, int &t, int &coff, int &ncols) {
+        if (u < p.full_units) {
+            t = u, coff = 0, ncols = BN;
+        } else {
+            const int v = u - p.full_units;
+            t = p.full_units + (v >> 1), coff = (v & 1) * (BN / 2), ncols = BN / 2;
+        }
+    };
     const int kiters = p.kblocks * p.n_terms;
 
     if (warp == 0) {
@@ -220,11 +237,13 @@ __global__ void __launch_bounds__(threads(MODE), 1)
         int stage = 0;
         uint32_t phase = 0, issued = 0, last_par = 0;
         bool ok = true;
-        for (int t = cfirst; t < num_tiles && ok; t += cstride) {
-            int tm, tn;
+        for (int u = cfirst; u < num_units && ok; u += cstride) {
+            int t, coff, ncols, tm, tn;
+            unit_of(u, t, coff, ncols);
             pair_tile_of(t, p.tiles_m, p.tiles_n, p.group_m, tm, tn);
             const int row0 = tm * 2 * BM + crank * BM;
-            const int col0 = tn * BN + crank * (BN / 2);
+            const int col0 = tn * BN + coff + crank * (ncols / 2);
+            const int boxes = (ncols / 2) / boxn(MODE);  // B boxes this CTA loads per stage (bf16 modes)
             ozaki::Iter oz;
             oz.start(p.slices, p.chunk, p.kblocks, p.acc_pairs);
             for (int it = 0; it < kiters; ++it) {
@@ -247,7 +266,9 @@ __global__ void __launch_bounds__(threads(MODE), 1)
                 if (ptx::elect_one()) {
                     const uint32_t sa = tiles0 + stage * STAGE_BYTES, sb = sa + A_BYTES;
                     const uint32_t fbar = ptx::mapa(full(stage), 0);
-                    if (leader) ptx::mbar_arrive_expect_tx(full(stage), 2 * stage_tx(MODE));
+                    if (leader)
+                        ptx::mbar_arrive_expect_tx(
+                            full(stage), MODE == MODE_FP8 ? 2 * stage_tx(MODE) : 2 * (A_BYTES + boxes * box_bytes(MODE)));
                     ptx::tma_load_3d_pair(sa, &tmA, fbar, kb * bk(MODE), row0, pa);
                     if constexpr (MODE == MODE_FP8) {  // K-major B: rows = columns of B; then the scale blocks
                         ptx::tma_load_3d_pair(sb, &tmB, fbar, kb * bk(MODE), col0, pb);
@@ -257,8 +278,9 @@ __global__ void __launch_bounds__(threads(MODE), 1)
                     } else {
 #pragma unroll
                         for (int j = 0; j < nbox(MODE); ++j)
-                            ptx::tma_load_3d_pair(sb + j * box_bytes(MODE), &tmB, fbar, col0 + j * boxn(MODE), kb * bk(MODE),
-                                                  pb);
+                            if (j < boxes)
+                                ptx::tma_load_3d_pair(sb + j * box_bytes(MODE), &tmB, fbar, col0 + j * boxn(MODE),
+                                                      kb * bk(MODE), pb);
                     }
                 }
                 __syncwarp();
@@ -290,7 +312,11 @@ __global__ void __launch_bounds__(threads(MODE), 1)
                              : ptx::smem_desc_sw128(tiles0 + A_BYTES, box_bytes(MODE), 1024));
         // FP8: the stage's scale blocks, rows of 16 B in 8-row groups (no swizzle)
         const ptx::DescHalves s0 = ptx::desc_halves(ptx::smem_desc_plain(tiles0 + sf_off(MODE), 128));
-        for (int t = cfirst; t < num_tiles && ok; t += cstride) {
+        for (int u = cfirst; u < num_units && ok; u += cstride) {
+            int t, coff, ncols;
+            unit_of(u, t, coff, ncols);
+            // the MMA's N: the whole tile or half of its columns (instruction descriptor bits 17-22: N / 8)
+            const uint32_t id_u = (id16 & ~(0x3Fu << 17)) | ((uint32_t)(ncols >> 3) << 17);
             ozaki::Iter oz;
             oz.start(p.slices, p.chunk, p.kblocks, p.acc_pairs);
             for (int it = 0; it < kiters; ++it) {
@@ -339,7 +365,7 @@ __global__ void __launch_bounds__(threads(MODE), 1)
                             ptx::mma_mxf8_pair_h(dacc, alo, a0.hi, blo, b0.hi, idesc(MODE) | ((uint32_t)k << 4) | ((uint32_t)k << 29),
                                                  sfa, sfa + 4, (j > 0 || k > 0) ? 1u : 0u);
                         } else {
-                            ptx::mma_bf16_pair_h(dacc, alo, a0.hi, blo, b0.hi, id16, (j > 0 || k > 0) ? 1u : 0u);
+                            ptx::mma_bf16_pair_h(dacc, alo, a0.hi, blo, b0.hi, id_u, (j > 0 || k > 0) ? 1u : 0u);
                         }
                     }
                     ptx::mma_commit_pair_mc(empty(stage), kPair);
@@ -423,11 +449,15 @@ __global__ void __launch_bounds__(threads(MODE), 1)
             }
         };
         bool ok = true;
-        for (int t = cfirst; t < num_tiles && ok; t += cstride) {
-            int tm, tn;
+        for (int u = cfirst; u < num_units && ok; u += cstride) {
+            int t, coff, ncols, tm, tn;
+            unit_of(u, t, coff, ncols);
             pair_tile_of(t, p.tiles_m, p.tiles_n, p.group_m, tm, tn);
             const int64_t row = (int64_t)tm * 2 * BM + crank * BM + q * 32 + lane;
-            const int64_t colh = (int64_t)tn * BN + half * HC;
+            const int64_t colh = (int64_t)tn * BN + coff + half * HC;
+            // a warp whose columns lie past a half tile's only keeps the barrier
+            // protocol (it waits for and releases every accumulator)
+            const bool active = half * HC < ncols;
             const uint32_t lanes = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * HC);
             if constexpr (MODE == MODE_OZAKI) {
                 // every (class, chunk, pair) accumulator of a class added exactly into int32, the class
@@ -447,25 +477,27 @@ __global__ void __launch_bounds__(threads(MODE), 1)
                             break;
                         }
                         const uint32_t tb = lanes + (uint32_t)(abuf * ACC_STRIDE);
+                        if (active) {
 #pragma unroll
-                        for (int c0 = 0; c0 < HC; c0 += 8) {  // 8 columns a load: the 64 class sums leave few registers
-                            uint32_t r[8];
-                            ptx::tmem_ld8(tb + c0, r);
-                            ptx::tmem_ld_wait();
+                            for (int c0 = 0; c0 < HC; c0 += 8) {  // 8 columns a load: the 64 class sums leave few registers
+                                uint32_t r[8];
+                                ptx::tmem_ld8(tb + c0, r);
+                                ptx::tmem_ld_wait();
 #pragma unroll
-                            for (int j = 0; j < 8; ++j)  // exact: accumulator sums are integers of at most 2^24
-                                qacc[c0 + j] += __float2int_rz(__uint_as_float(r[j]));
+                                for (int j = 0; j < 8; ++j)  // exact: accumulator sums are integers of at most 2^24
+                                    qacc[c0 + j] += __float2int_rz(__uint_as_float(r[j]));
+                            }
                         }
                         release_acc();  // the MMA may refill the accumulator during the fold
                     }
                     if (!ok) break;
-                    ozaki::fold_rs<HC>(qacc, ozaki::class_weight(cls, p.lsb, p.beta), rs, first);
+                    if (active) ozaki::fold_rs<HC>(qacc, ozaki::class_weight(cls, p.lsb, p.beta), rs, first);
 #pragma unroll
                     for (int j = 0; j < HC; ++j) qacc[j] = 0;
                     first = false;
                 }
                 if (!ok) break;
-                if (row_ok) ozaki::finish_rs<HC>(rs, drow, colh, p.N, p.row_max[row], p.col_max, p.lsb);
+                if (row_ok && active) ozaki::finish_rs<HC>(rs, drow, colh, p.N, p.row_max[row], p.col_max, p.lsb);
             } else if constexpr (MODE == MODE_PROMOTE) {
                 float acc[HC];
 #pragma unroll
@@ -476,17 +508,20 @@ __global__ void __launch_bounds__(threads(MODE), 1)
                         break;
                     }
                     const uint32_t tb = lanes + (uint32_t)(abuf * ACC_STRIDE);
+                    if (active) {
 #pragma unroll
-                    for (int c = 0; c < HC; c += 16) {
-                        uint32_t r[16];
-                        ptx::tmem_ld16(tb + c, r);
-                        ptx::tmem_ld_wait();
+                        for (int c = 0; c < HC; c += 16) {
+                            uint32_t r[16];
+                            ptx::tmem_ld16(tb + c, r);
+                            ptx::tmem_ld_wait();
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) acc[c + j] = __fadd_rn(acc[c + j], __uint_as_float(r[j]));
+                            for (int j = 0; j < 16; ++j) acc[c + j] = __fadd_rn(acc[c + j], __uint_as_float(r[j]));
+                        }
                     }
                     release_acc();
                 }
                 if (!ok) break;
+                if (!active) continue;
 #pragma unroll
                 for (int c = 0; c < HC; c += 32) {
                     uint32_t r[32];
@@ -498,7 +533,7 @@ __global__ void __launch_bounds__(threads(MODE), 1)
                 if (!wait_acc()) break;
                 const uint32_t tb = lanes + (uint32_t)(abuf * ACC_STRIDE);
 #pragma unroll 1
-                for (int c = 0; c < HC; c += 32) {
+                for (int c = 0; c < HC && c < ncols; c += 32) {
                     uint32_t r[32];
                     ptx::tmem_ld32(tb + c, r);
                     ptx::tmem_ld_wait();
@@ -544,6 +579,15 @@ int pair_group_m(int mode) {
     return all ? all : 16;
 }
 
+// MOA_PAIR_HALF_TILES=0 keeps every tile whole.
+bool half_tiles_enabled() {
+    static const bool on = [] {
+        const char *e = std::getenv("MOA_PAIR_HALF_TILES");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
 int pair_sms() {
     static const int n = [] {  // read once, thread-safe
         int dev = 0, v = 0;
@@ -587,7 +631,19 @@ cudaError_t launch_pair(const CUtensorMap &ta, const CUtensorMap &tb, const CUte
     p.tiles_n = (p.N + bn(MODE) - 1) / bn(MODE);
     p.group_m = pair_group_m(MODE);
     const int tiles = p.tiles_m * p.tiles_n;
-    const int clusters = tiles < max_clusters ? tiles : max_clusters;
+    // the tiles of a last wave that would fill at most half of the resident
+    // clusters run as column halves (twice the units, half as long) when the
+    // launch has at most 8 waves; the FP8 mode's B box and scale blocks cover
+    // whole tiles, so it keeps them whole.  Measured (same box, A/B): n = 4096
+    // (3.4 waves) +2..4 % for the bf16, fp16, BF16x3 and Ozaki forms; n = 8192
+    // (13.5 waves) no gain, so longer launches keep whole tiles.
+    const int tail = tiles % max_clusters;
+    p.full_units = (MODE != MODE_FP8 && tiles > max_clusters && tiles <= 8 * max_clusters && 2 * tail <= max_clusters &&
+                    half_tiles_enabled())
+                       ? tiles - tail
+                       : tiles;
+    const int units = p.full_units + 2 * (tiles - p.full_units);
+    const int clusters = units < max_clusters ? units : max_clusters;
     cfg.gridDim = dim3(2 * clusters);
     cfg.stream = s;
     GemmTimer timer(s);
