@@ -135,6 +135,30 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- helpers
+def _bind_near_gpu(index: int):
+    """Run the host side on the CPUs of the GPU's own NUMA node (from sysfs),
+    so the page-locked buffers of the end-to-end leg are allocated in the
+    memory nearest to the GPU's host link.  Returns the CPU list used, or None
+    when the node is unknown (the affinity is then left alone)."""
+    try:
+        import torch
+        pr = torch.cuda.get_device_properties(index)
+        dev = f"{pr.pci_domain_id:04x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+        with open(f"/sys/bus/pci/devices/{dev}/local_cpulist") as f:
+            spec = f.read().strip()
+        cpus = set()
+        for part in spec.split(","):
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        if cpus:
+            os.sched_setaffinity(0, cpus)
+            return spec
+    except Exception:
+        return None
+    return None
+
+
+
 def _events_time(fn, iters, stream):
     """Average ms per call of fn over `iters` calls, CUDA events on `stream`."""
     import torch
@@ -634,6 +658,8 @@ def main():
     import synth
 
     torch.cuda.set_device(local)
+    all_cpus = os.sched_getaffinity(0)
+    near_cpus = _bind_near_gpu(local)
     moa.lib()
     peaks = _peaks()
     stream = torch.cuda.current_stream()
@@ -699,11 +725,13 @@ def main():
         ms_e2e = _max_over_ranks(_events_time(e2e_call, e2e_steps, stream), ws)
         e2e = {"value": round(ws * flops / (ms_e2e * 1e-3) / 1e12, 2), "unit": "TFLOP/s",
                "h2d_bytes_per_step": int(hA.numel() * 8 + hB.numel() * 8), "d2h_bytes_per_step": int(hD.numel() * 8),
-               "ms_per_step": round(ms_e2e, 3), "call": "moa_inner_host (pinned host buffers, row blocks overlapped)"}
+               "ms_per_step": round(ms_e2e, 3), "call": "moa_inner_host (pinned host buffers, row blocks overlapped)",
+               "host_cpus": near_cpus}
         st = moa.moa_device_status()
         if st != 0:
             raise RuntimeError("device status " + moa.moa_status_string(st))
         del hA, hB, hD
+    os.sched_setaffinity(0, all_cpus)  # the CPU baseline and the rows use every host core again
     moa.moa_release_workspace()
     torch.cuda.empty_cache()
 
