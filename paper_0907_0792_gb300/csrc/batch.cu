@@ -18,9 +18,11 @@
 // pulling its CC items from its own queue counter; (2) the grouped split
 // pre-pass (FP32 -> three bf16 planes for every BF16x3 problem); (3) one
 // persistent grouped kernel (one CTA per SM) for the TC / OUT / FILL items.
-// In that kernel the TMA warp pulls item indices from a device-side queue
-// (one atomic counter) and hands each to the MMA warp and the 16 epilogue
-// warps through a 4-slot ring of shared-memory slots guarded by mbarriers.
+// In that kernel a scheduler warp pulls item indices from a device-side
+// queue (one atomic counter), copies each item and its problem descriptor
+// into an 8-slot shared-memory ring guarded by mbarriers (prefetching the
+// tensor maps of tensor-core items), and the TMA warp, the MMA warp and the
+// 16 epilogue warps take their work from that ring.
 // TC items run the tcgen05 pipeline of tc_gemm.cu in its promoted form
 // (per-k-block FP32 promotion) with four TMEM accumulators in turn; OUT /
 // FILL items are computed by the epilogue warps.  The two schedules differ
@@ -72,30 +74,50 @@ struct alignas(16) BItem {
     int32_t inst, type, a, b;  // TC / CC: tile (a = row tile, b = column tile); OUT / FILL: rows [a, a + b)
 };
 
+// One slot of the grouped kernel's item ring: the scheduler copies the item
+// and its problem descriptor here ahead of use, so the other roles read them
+// from shared memory.
+struct alignas(16) RingSlot {
+    BItem it;
+    BInst in;
+    int32_t item, pad[3];
+};
+
 struct SplitJob {
     const float *src;
     __nv_bfloat16 *dst;
     int64_t cols, colsp, plane, r0, r1;
 };
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4, RING = 4, TERMS = 6;
+// A stage is one 32-deep slice of K holding all three bf16 planes of the A
+// tile and of the B tile (one 3-plane TMA box each), so each plane tile is
+// loaded once for the six products it takes part in; the FP32 promotion is
+// per 64-deep block (two stages).
+constexpr int BM = 128, BN = 128, BK = 32, KB = 64, STAGES = 3, RING = 8, TERMS = 6, PLANES = 3;
+// warp 0 the scheduler, warp 1 the TMA producer, warp 2 the MMA issuer, then
 // 16 epilogue warps (four per TMEM lane quarter, 32 columns each) and four
 // TMEM accumulators, so the promotion and stores of short tiles keep up with
 // the MMA warp
-constexpr int kEpiWarps = 16, kThreads = 64 + 32 * kEpiWarps, kEpiThreads = 32 * kEpiWarps, NACC = 4;
-constexpr int A_BYTES = BM * BK * 2, B_BYTES = BK * BN * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int kCtlWarps = 3, kEpiWarps = 16, kThreads = 32 * (kCtlWarps + kEpiWarps), kEpiThreads = 32 * kEpiWarps,
+              NACC = 4;
+constexpr int A_PLANE = BM * BK * 2;        // 128 rows x 64 B, 64-B swizzle
+constexpr int B_PLANE = BK * 64 * 2;        // one 64-column half: 32 rows x 128 B, 128-B swizzle
+constexpr int B_HALF = PLANES * B_PLANE;    // a half's three planes
+constexpr int A_BYTES = PLANES * A_PLANE, B_BYTES = 2 * B_HALF, STAGE_BYTES = A_BYTES + B_BYTES;
+static_assert(STAGE_BYTES % 1024 == 0 && A_PLANE % 1024 == 0 && B_PLANE % 1024 == 0, "swizzle atoms stay aligned");
 constexpr int CC_BK = 16, CC_PAD = 4, CC_LD = 128 + CC_PAD;
 constexpr int CC_BYTES = 2 * 2 * CC_BK * CC_LD * 4;  // As[2][16][132] + Bs[2][16][132]
 constexpr int NBARS = 2 * STAGES + 2 * NACC + 1 + 2 * RING;
 constexpr int TC_STG_FLOATS = 32 * 33;                  // an epilogue warp's 32 x 32 staging slice (padded rows)
 constexpr int TC_STG_BYTES = kEpiWarps * TC_STG_FLOATS * 4;
-constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + TC_STG_BYTES + 1024;
+constexpr int RING_BYTES = RING * (int)sizeof(RingSlot);
+constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + TC_STG_BYTES + RING_BYTES + 1024;
 constexpr int TMEM_COLS = NACC * BN;
 static_assert(TMEM_COLS <= 512 && NBARS * 8 + 16 <= 1024 && SMEM <= 227 * 1024, "grouped kernel resources");
 constexpr uint32_t IDESC = ptx::idesc_bf16_f32(BM, BN, 1);
 // split-BF16x3 terms (plane of A, plane of B): small products first, hi*hi last
-__constant__ int kTermA[TERMS] = {1, 0, 2, 0, 1, 0};
-__constant__ int kTermB[TERMS] = {1, 2, 0, 1, 0, 0};
+MOA_DEV constexpr int term_a(int t) { return t == 0 ? 1 : t == 2 ? 2 : t == 4 ? 1 : 0; }  // 1, 0, 2, 0, 1, 0
+MOA_DEV constexpr int term_b(int t) { return t == 0 ? 1 : t == 1 ? 2 : t == 3 ? 1 : 0; }  // 1, 2, 0, 1, 0, 0
 
 struct BatchParams {
     const BInst *inst;
@@ -218,9 +240,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *bars = (uint64_t *)(smem + STAGES * STAGE_BYTES);
     float *tcstg = (float *)(smem + STAGES * STAGE_BYTES + 1024);  // TC epilogue staging, per warp
+    RingSlot *rs = (RingSlot *)(smem + STAGES * STAGE_BYTES + 1024 + TC_STG_BYTES);
     uint32_t *tmem_slot = (uint32_t *)(bars + NBARS);
     volatile uint32_t *abort_flag = tmem_slot + 1;
-    volatile int *ring = (volatile int *)(tmem_slot + 2);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const uint32_t tiles0 = ptx::smem_u32(smem);
@@ -238,12 +260,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int s = 0; s < STAGES; ++s) ptx::mbar_init(full(s), 1), ptx::mbar_init(empty(s), 1);
         for (int b = 0; b < NACC; ++b) ptx::mbar_init(tfull(b), 1), ptx::mbar_init(tempty(b), kEpiWarps);
         ptx::mbar_init(drain, 1);
-        for (int s = 0; s < RING; ++s) ptx::mbar_init(rfull(s), 1), ptx::mbar_init(rempty(s), 1 + kEpiWarps);
+        // a slot is released by the producer, the MMA issuer and every epilogue warp
+        for (int s = 0; s < RING; ++s) ptx::mbar_init(rfull(s), 1), ptx::mbar_init(rempty(s), 2 + kEpiWarps);
         *abort_flag = 0u;
         ptx::fence_mbar_init();
         ptx::fence_proxy_async_smem();
     }
-    if (warp == 1) {
+    if (warp == 2) {
         ptx::tmem_alloc(ptx::smem_u32(tmem_slot), TMEM_COLS);
         ptx::tmem_relinquish();
     }
@@ -253,40 +276,64 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0 && lane == 0) {
-        // ------------------------------------------------ queue + TMA producer
+        // ------------------------------------------------ scheduler: queue -> ring
+        // Items are claimed and their descriptors copied up to RING slots ahead of
+        // the roles that run them; the tensor maps of tensor-core items are
+        // prefetched so the producer's first copy of a tile does not wait on them.
+        int slot = 0;
+        uint32_t rphase = 0;
+        for (;;) {
+            int item = atomicAdd(p.queue, 1);
+            if (item >= p.n_items) item = -1;
+            BItem it{};
+            BInst in{};
+            if (item >= 0) {
+                it = p.items[item];
+                in = p.inst[it.inst];
+                if (it.type == IT_TC) {
+                    ptx::prefetch_tmap(p.tmaps + in.tmap);
+                    ptx::prefetch_tmap(p.tmaps + in.tmap + 1);
+                }
+            }
+            if (!ptx::mbar_wait(rempty(slot), rphase ^ 1u, abort_flag, status)) break;
+            rs[slot].it = it;
+            rs[slot].in = in;
+            rs[slot].item = item;
+            ptx::mbar_arrive(rfull(slot));  // release: the slot's contents before the arrival
+            if (++slot == RING) slot = 0, rphase ^= 1u;
+            if (item < 0) break;
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ------------------------------------------------ TMA producer
         int stage = 0, slot = 0;
         uint32_t phase = 0, rphase = 0, issued = 0, last_par = 0;
         bool ok = true;
         for (;;) {
-            int item = atomicAdd(p.queue, 1);
-            if (item >= p.n_items) item = -1;
-            if (!ptx::mbar_wait(rempty(slot), rphase ^ 1u, abort_flag, status)) {
+            if (!ptx::mbar_wait(rfull(slot), rphase, abort_flag, status)) {
                 ok = false;
                 break;
             }
-            ring[slot] = item;
-            ptx::mbar_arrive(rfull(slot));
+            const int item = rs[slot].item;
+            const BItem it = rs[slot].it;
+            const int tmap = rs[slot].in.tmap, kslices = (rs[slot].in.K + BK - 1) / BK;
+            ptx::mbar_arrive(rempty(slot));
             if (++slot == RING) slot = 0, rphase ^= 1u;
             if (item < 0) break;
-            const BItem it = p.items[item];
             if (it.type != IT_TC) continue;
-            const BInst in = p.inst[it.inst];
-            const CUtensorMap *ta = p.tmaps + in.tmap, *tb = ta + 1;
+            const CUtensorMap *ta = p.tmaps + tmap, *tb = ta + 1;
             ptx::fence_tensormap(ta);
             ptx::fence_tensormap(tb);
-            const int kiters = in.kblocks * TERMS;
-            for (int i = 0; i < kiters; ++i) {
-                const int kb = i / TERMS, term = i - kb * TERMS;
+            for (int i = 0; i < kslices; ++i) {
                 if (!ptx::mbar_wait(empty(stage), phase ^ 1u, abort_flag, status)) {
                     ok = false;
                     break;
                 }
                 const uint32_t sa = tiles0 + stage * STAGE_BYTES, sb = sa + A_BYTES;
                 ptx::mbar_arrive_expect_tx(full(stage), STAGE_BYTES);
-                ptx::tma_load_3d(sa, ta, full(stage), kb * BK, it.a * BM, kTermA[term]);
+                ptx::tma_load_3d(sa, ta, full(stage), i * BK, it.a * BM, 0);  // three planes in one box
 #pragma unroll
                 for (int j = 0; j < BN / 64; ++j)
-                    ptx::tma_load_3d(sb + j * (BK * 128), tb, full(stage), it.b * BN + j * 64, kb * BK, kTermB[term]);
+                    ptx::tma_load_3d(sb + j * B_HALF, tb, full(stage), it.b * BN + j * 64, i * BK, 0);
                 issued |= 1u << stage;
                 last_par = (last_par & ~(1u << stage)) | (phase << stage);
                 if (++stage == STAGES) stage = 0, phase ^= 1u;
@@ -301,7 +348,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 }
         }
-    } else if (warp == 1 && lane == 0) {
+    } else if (warp == 2 && lane == 0) {
         // ------------------------------------------------ MMA issuer
         int stage = 0, abuf = 0, slot = 0;
         uint32_t phase = 0, aphase = 0, rphase = 0;
@@ -311,15 +358,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 ok = false;
                 break;
             }
-            const int item = ring[slot];
+            const int item = rs[slot].item, type = rs[slot].it.type, kslices = (rs[slot].in.K + BK - 1) / BK;
             ptx::mbar_arrive(rempty(slot));
             if (++slot == RING) slot = 0, rphase ^= 1u;
             if (item < 0) break;
-            const BItem it = p.items[item];
-            if (it.type != IT_TC) continue;
-            const int kiters = p.inst[it.inst].kblocks * TERMS;
-            for (int i = 0; i < kiters; ++i) {
-                const int j = i % TERMS;
+            if (type != IT_TC) continue;
+            constexpr int SPB = KB / BK;  // stages per promotion block
+            for (int i = 0; i < kslices; ++i) {
+                const int j = i % SPB;
                 if (j == 0) {
                     if (!ptx::mbar_wait(tempty(abuf), aphase ^ 1u, abort_flag, status)) {
                         ok = false;
@@ -335,14 +381,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t sa = tiles0 + stage * STAGE_BYTES, sb = sa + A_BYTES;
                 const uint32_t dacc = tmem + (uint32_t)(abuf * BN);
 #pragma unroll
-                for (int k = 0; k < BK / 16; ++k) {
-                    const uint64_t ad = ptx::smem_desc_sw128(sa + k * 32, 16, 1024);
-                    const uint64_t bd = ptx::smem_desc_sw128(sb + k * 2048, BK * 128, 1024);
-                    ptx::mma_bf16(dacc, ad, bd, IDESC, (j > 0 || k > 0) ? 1u : 0u);
+                for (int t = 0; t < TERMS; ++t) {
+#pragma unroll
+                    for (int k = 0; k < BK / 16; ++k) {
+                        // A: K-major rows of 64 B (8-row atoms 512 B apart), 32 B per k-step;
+                        // B: the two 64-column halves B_HALF apart, 16 rows of 128 B per k-step
+                        const uint64_t ad = ptx::smem_desc_sw64(sa + term_a(t) * A_PLANE + k * 32, 512);
+                        const uint64_t bd = ptx::smem_desc_sw128(sb + term_b(t) * B_PLANE + k * 2048, B_HALF, 1024);
+                        ptx::mma_bf16(dacc, ad, bd, IDESC, (j > 0 || t > 0 || k > 0) ? 1u : 0u);
+                    }
                 }
                 ptx::mma_commit(empty(stage));
                 if (++stage == STAGES) stage = 0, phase ^= 1u;
-                if (j == TERMS - 1) {
+                if (j == SPB - 1 || i == kslices - 1) {
                     ptx::mma_commit(tfull(abuf));
                     if (++abuf == NACC) abuf = 0, aphase ^= 1u;
                 }
@@ -355,27 +406,27 @@ __global__ void __launch_bounds__(kThreads, 1)
             while (!ptx::mbar_try_wait(drain, 0) && globaltimer() - t0 < kWaitLimitNs) {
             }
         }
-    } else if (warp >= 2) {
-        // ------------------------------------------------ epilogue / CUDA-core warps
-        const int q = warp & 3, part = (warp - 2) / 4, etid = threadIdx.x - 64;
+    } else if (warp >= kCtlWarps) {
+        // ------------------------------------------------ epilogue warps
+        // warp % 4 is the TMEM lane quarter the warp may read; `part` picks its 32 columns
+        const int ew = warp - kCtlWarps, q = warp & 3, part = ew / 4, etid = threadIdx.x - 32 * kCtlWarps;
         constexpr int HC = BN / (kEpiWarps / 4);  // columns of the tile per epilogue warp
         int abuf = 0, slot = 0;
         uint32_t aphase = 0, rphase = 0;
         bool ok = true;
         for (;;) {
-            int item = 0, okw = 1;
-            if (lane == 0) {
-                okw = ptx::mbar_wait(rfull(slot), rphase, abort_flag, status) ? 1 : 0;
-                if (okw) item = ring[slot];
-            }
+            int okw = 1;
+            if (lane == 0) okw = ptx::mbar_wait(rfull(slot), rphase, abort_flag, status) ? 1 : 0;
             okw = __shfl_sync(0xffffffffu, okw, 0);
-            item = __shfl_sync(0xffffffffu, item, 0);
             if (!okw) break;
+            __syncwarp();  // lane 0's acquire of the slot orders the other lanes' reads too
+            const int item = rs[slot].item;
+            const BItem it = rs[slot].it;
+            const BInst in = rs[slot].in;
+            __syncwarp();  // every lane has read the slot before it is released
             if (lane == 0) ptx::mbar_arrive(rempty(slot));
             if (++slot == RING) slot = 0, rphase ^= 1u;
             if (item < 0) break;
-            const BItem it = p.items[item];
-            const BInst in = p.inst[it.inst];
             if (it.type == IT_TC) {
                 float acc[HC];
 #pragma unroll
@@ -410,7 +461,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int64_t row0 = (int64_t)it.a * BM + q * 32;
                 const int64_t col0 = (int64_t)it.b * BN + part * HC;
                 const int rows_here = (int)min((int64_t)32, in.M - row0);
-                float *sl = tcstg + (warp - 2) * TC_STG_FLOATS;
+                float *sl = tcstg + ew * TC_STG_FLOATS;
                 if (rows_here > 0) {
 #pragma unroll
                     for (int c = 0; c < HC; c += 32) {
@@ -441,7 +492,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     ptx::tc_fence_before();
     __syncthreads();
-    if (warp == 1) {
+    if (warp == 2) {
         __syncwarp();
         ptx::tc_fence_after();
         ptx::tmem_dealloc(tmem, TMEM_COLS);
@@ -619,7 +670,7 @@ moa_status classify(const moa_problem &q, Problem *out) {
 // estimated microseconds of one item on one SM (orders the queue)
 double item_cost(const Problem &p, const BItem &it) {
     switch (it.type) {
-    case IT_TC: return 1.0 + 0.26 * (double)((p.K + BK - 1) / BK) * TERMS;
+    case IT_TC: return 1.0 + 0.26 * (double)((p.K + KB - 1) / KB) * TERMS;
     case IT_CC: return 1.0 + 128.0 * 128.0 * (double)p.K / 79000.0;
     default: return 0.5 + (double)it.b * (double)p.N * 4.0 / 43000.0;
     }
@@ -934,7 +985,7 @@ moa_status moa_batch_plan_create(int count, const moa_problem *problems, moa_bat
         const Problem &p = pl->probs[i];
         BInst &b = inst[i];
         b.type = p.type, b.op = p.op, b.M = (int)p.M, b.N = (int)p.N, b.K = (int)p.K;
-        b.kblocks = (int)((p.K + BK - 1) / BK);
+        b.kblocks = (int)((p.K + KB - 1) / KB);  // promotion blocks
         b.A = p.A, b.B = p.B, b.D = p.D, b.tmap = -1;
         b.vec = ((uintptr_t)p.D % 16 == 0) && (p.N % 4 == 0);
         if (p.M * p.N == 0) continue;
@@ -943,9 +994,10 @@ moa_status moa_batch_plan_create(int count, const moa_problem *problems, moa_bat
             __nv_bfloat16 *pa = (__nv_bfloat16 *)((uint8_t *)pl->d_ws + ws_off[i]);
             __nv_bfloat16 *pb = pa + 3 * p.M * Kp;
             if (!make_tmap(&tmaps[2 * t], pa, (uint64_t)p.K, (uint64_t)p.M, 3, (uint64_t)Kp * 2, (uint64_t)(Kp * p.M * 2),
-                           BK, BM) ||
+                           BK, BM, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, CU_TENSOR_MAP_SWIZZLE_64B, PLANES) ||
                 !make_tmap(&tmaps[2 * t + 1], pb, (uint64_t)p.N, (uint64_t)p.K, 3, (uint64_t)Np * 2,
-                           (uint64_t)(Np * p.K * 2), 64, BK)) {
+                           (uint64_t)(Np * p.K * 2), 64, BK, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, CU_TENSOR_MAP_SWIZZLE_128B,
+                           PLANES)) {
                 if (bad_index) *bad_index = i;
                 plan_free(pl);
                 return MOA_ERR_CUDA;

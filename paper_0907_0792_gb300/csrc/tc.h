@@ -15,13 +15,13 @@
 
 namespace moa {
 
-// 3-D tensor map [planes][rows][inner] with the given byte strides, 128-B
-// swizzled boxes of box_inner x box_rows x 1 (TMA rules: base 16-byte
+// 3-D tensor map [planes][rows][inner] with the given byte strides, swizzled
+// boxes of box_inner x box_rows x box_planes (TMA rules: base 16-byte
 // aligned, strides multiples of 16 bytes).  False if encoding failed.
 bool make_tmap(CUtensorMap *m, const void *base, uint64_t inner, uint64_t rows, uint64_t planes, uint64_t row_bytes,
                uint64_t plane_bytes, uint32_t box_inner, uint32_t box_rows,
                CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
-               CUtensorMapSwizzle swizzle = CU_TENSOR_MAP_SWIZZLE_128B);
+               CUtensorMapSwizzle swizzle = CU_TENSOR_MAP_SWIZZLE_128B, uint32_t box_planes = 1);
 
 // bf16 operands as given, FP32 out.
 moa_status tc_inner_bf16(const __nv_bfloat16 *A, const __nv_bfloat16 *B, float *D, int64_t M, int64_t N, int64_t K,

@@ -535,12 +535,12 @@ PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
 // boxes of box_inner x box_rows (128-B swizzled unless `swizzle` says otherwise).
 bool make_tmap(CUtensorMap *m, const void *base, uint64_t inner, uint64_t rows, uint64_t planes, uint64_t row_bytes,
                uint64_t plane_bytes, uint32_t box_inner, uint32_t box_rows, CUtensorMapDataType dt,
-               CUtensorMapSwizzle swizzle) {
+               CUtensorMapSwizzle swizzle, uint32_t box_planes) {
     auto enc = tmap_encoder();
     if (!enc) return false;
     cuuint64_t dims[3] = {inner, rows, planes};
     cuuint64_t strides[2] = {row_bytes, plane_bytes};
-    cuuint32_t box[3] = {box_inner, box_rows, 1};
+    cuuint32_t box[3] = {box_inner, box_rows, box_planes};
     cuuint32_t estr[3] = {1, 1, 1};
     return enc(m, dt, 3, const_cast<void *>(base), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,

@@ -127,6 +127,11 @@ MOA_DEV void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uin
 MOA_DEV void cp_async4(void *smem_dst, const void *gsrc) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
 }
+// The same copy with zero fill: `valid` false reads nothing and writes 0.
+MOA_DEV void cp_async4_zfill(void *smem_dst, const void *gsrc, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(smem_dst)), "l"(gsrc), "r"(valid ? 4 : 0)
+                 : "memory");
+}
 MOA_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N> MOA_DEV void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
@@ -167,7 +172,7 @@ MOA_DEV void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;"
 //   bits  0-13 start address >> 4     bits 16-29 leading byte offset >> 4
 //   bits 32-45 stride byte offset >> 4  bits 46-47 version (1)
 //   bits 49-51 base offset (0: atoms 1024-byte aligned)  bits 61-63 swizzle
-// Swizzle code 2 = 128-byte swizzle.
+// Swizzle code 2 = 128-byte swizzle, 4 = 64-byte swizzle.
 //  K-major operand, 128B swizzle: rows of 64 bf16 (128 B), 8-row atoms of
 //    1024 B; SBO = 1024 (atom to atom along M/N), LBO unused (1).
 //  MN-major operand, 128B swizzle: 64 contiguous MN elements per 128-B row,
@@ -180,6 +185,18 @@ MOA_DEV uint64_t smem_desc_sw128(uint32_t addr, uint32_t lbo, uint32_t sbo) {
     d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
     d |= (uint64_t)1 << 46;
     d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Shared-memory descriptor of a K-major matrix in 64-B swizzled rows (8-row
+// atoms of 512 B, `sbo` bytes apart; the leading offset is unused there).
+MOA_DEV uint64_t smem_desc_sw64(uint32_t addr, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;
     return d;
 }
 
