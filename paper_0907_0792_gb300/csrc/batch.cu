@@ -105,8 +105,10 @@ constexpr int B_PLANE = BK * 64 * 2;        // one 64-column half: 32 rows x 128
 constexpr int B_HALF = PLANES * B_PLANE;    // a half's three planes
 constexpr int A_BYTES = PLANES * A_PLANE, B_BYTES = 2 * B_HALF, STAGE_BYTES = A_BYTES + B_BYTES;
 static_assert(STAGE_BYTES % 1024 == 0 && A_PLANE % 1024 == 0 && B_PLANE % 1024 == 0, "swizzle atoms stay aligned");
-constexpr int CC_BK = 16, CC_PAD = 4, CC_LD = 128 + CC_PAD;
-constexpr int CC_BYTES = 2 * 2 * CC_BK * CC_LD * 4;  // As[2][16][132] + Bs[2][16][132]
+// CUDA-core tiles: panels of 16 k, four stages in flight (cp.async)
+constexpr int CC_BK = 16, CC_PAD = 4, CC_LD = 128 + CC_PAD, CC_STAGES = 4;
+constexpr int CC_PANEL = CC_BK * CC_LD;                 // floats of one operand's panel
+constexpr int CC_BYTES = CC_STAGES * 2 * CC_PANEL * 4;  // As[4][16][132] + Bs[4][16][132]
 constexpr int NBARS = 2 * STAGES + 2 * NACC + 1 + 2 * RING;
 constexpr int TC_STG_FLOATS = 32 * 33;                  // an epilogue warp's 32 x 32 staging slice (padded rows)
 constexpr int TC_STG_BYTES = kEpiWarps * TC_STG_FLOATS * 4;
@@ -129,8 +131,13 @@ struct BatchParams {
 
 MOA_DEV void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
-// One 128 x 128 CUDA-core tile of D = reduce_p(A combine B), 256 threads
-// (the epilogue warps), panels in shared memory, tail of K by a short loop.
+// One 128 x 128 CUDA-core tile of D = reduce_p(A combine B), 256 threads.
+// The panels of A (transposed to [k][m]) and B ([k][n]) stream through four
+// shared-memory stages by 4-byte cp.async copies, three panels ahead of the
+// one being reduced, so short contractions wait for one load latency rather
+// than one per panel.  Elements outside the problem are zero-filled: rows and
+// columns past M / N give results that are never stored, and k past K is
+// never read (the last panel is reduced over its K % 16 valid k only).
 // RH / CH: whether the tile's second 64 rows / columns hold any output; the
 // halves a thread would compute outside the problem are skipped (the flags
 // are the same for every thread of the tile, so no warp diverges).
@@ -142,44 +149,45 @@ __device__ __forceinline__ void cc_tile_body(const BInst &in, int tm, int tn, fl
     const int64_t m0 = (int64_t)tm * 128, n0 = (int64_t)tn * 128;
     const int a_k = tid % CC_BK, a_m = tid / CC_BK;  // 16 rows per pass
     const int b_n = tid % 128, b_k = tid / 128;      // 2 rows per pass
-    float ra[8], rb[8];
-    auto load = [&](int64_t k0) {
+    const int64_t full = K / CC_BK;
+    const int tail = (int)(K - full * CC_BK);
+    const int64_t panels = full + (tail ? 1 : 0);
+    auto issue = [&](int64_t p) {
+        float *as = As + (int)(p & (CC_STAGES - 1)) * CC_PANEL, *bs = Bs + (int)(p & (CC_STAGES - 1)) * CC_PANEL;
+        const int64_t k0 = p * CC_BK;
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
+        for (int r = 0; r < (RH ? 8 : 4); ++r) {
             const int64_t m = m0 + a_m + r * 16, k = k0 + a_k;
-            ra[r] = (m < M && k < K) ? __ldg(A + m * K + k) : Op::identity();
+            const bool ok = m < M && k < K;
+            ptx::cp_async4_zfill(as + a_k * CC_LD + a_m + r * 16, ok ? A + m * K + k : A, ok);
         }
+        if (CH || b_n < 64) {  // warp-uniform: a warp's 32 columns lie in one half
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            const int64_t k = k0 + b_k + r * 2, n = n0 + b_n;
-            rb[r] = (k < K && n < N) ? __ldg(B + k * N + n) : Op::identity();
+            for (int r = 0; r < 8; ++r) {
+                const int64_t k = k0 + b_k + r * 2, n = n0 + b_n;
+                const bool ok = k < K && n < N;
+                ptx::cp_async4_zfill(bs + (b_k + r * 2) * CC_LD + b_n, ok ? B + k * N + n : B, ok);
+            }
         }
-    };
-    auto stash = [&](int buf) {
-        float *as = As + buf * CC_BK * CC_LD, *bs = Bs + buf * CC_BK * CC_LD;
-#pragma unroll
-        for (int r = 0; r < 8; ++r) as[a_k * CC_LD + a_m + r * 16] = ra[r];
-#pragma unroll
-        for (int r = 0; r < 8; ++r) bs[(b_k + r * 2) * CC_LD + b_n] = rb[r];
     };
     float acc[8][8];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] = Op::identity();
-    const int64_t full = K / CC_BK;
-    const int tail = (int)(K - full * CC_BK);
-    const int64_t panels = full + (tail ? 1 : 0);
-    if (panels > 0) {
-        load(0);
-        stash(0);
+#pragma unroll
+    for (int s = 0; s < CC_STAGES - 1; ++s) {
+        if (s < panels) issue(s);
+        ptx::cp_async_commit();  // empty groups keep the count of groups per panel fixed
     }
-    epi_bar();
     for (int64_t p = 0; p < panels; ++p) {
-        const int buf = (int)(p & 1);
-        if (p + 1 < panels) load((p + 1) * CC_BK);
+        ptx::cp_async_wait<CC_STAGES - 2>();  // this thread's copies of panel p have landed
+        epi_bar();  // everyone's copies of panel p are visible; panel p - 1's stage is free again
+        if (p + CC_STAGES - 1 < panels) issue(p + CC_STAGES - 1);
+        ptx::cp_async_commit();
+        const int buf = (int)(p & (CC_STAGES - 1));
         // two groups of 4 rows / columns half a tile apart: conflict-free 16-byte reads
-        const float *as = As + buf * CC_BK * CC_LD + ty * 4, *bs = Bs + buf * CC_BK * CC_LD + tx * 4;
+        const float *as = As + buf * CC_PANEL + ty * 4, *bs = Bs + buf * CC_PANEL + tx * 4;
         if (p < full) {
 #pragma unroll
             for (int kk = 0; kk < CC_BK; kk += 2) {
@@ -219,17 +227,25 @@ __device__ __forceinline__ void cc_tile_body(const BInst &in, int tm, int tn, fl
                     for (int j = 0; j < (CH ? 8 : 4); ++j) acc[i][j] = Op::step(acc[i][j], a0[i], b0[j]);
             }
         }
-        if (p + 1 < panels) stash(buf ^ 1);
-        epi_bar();
     }
+    ptx::cp_async_wait<0>();  // no copy of this tile outlives it (the last groups are empty)
+    // four consecutive columns per store where the rows allow 16-byte stores
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int64_t m = m0 + ty * 4 + (i & 3) + (i >> 2) * 64;
         if (m >= M) continue;
+        float *row = in.D + m * N;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int64_t n = n0 + tx * 4 + (j & 3) + (j >> 2) * 64;
-            if (n < N) in.D[m * N + n] = acc[i][j];
+        for (int h = 0; h < 2; ++h) {
+            const int64_t n = n0 + tx * 4 + h * 64;
+            if (in.vec && n + 3 < N) {
+                *reinterpret_cast<float4 *>(row + n) = make_float4(acc[i][4 * h], acc[i][4 * h + 1], acc[i][4 * h + 2],
+                                                                   acc[i][4 * h + 3]);
+            } else {
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (n + t < N) row[n + t] = acc[i][4 * h + t];
+            }
         }
     }
 }
@@ -554,9 +570,9 @@ __global__ void __launch_bounds__(256) batch_split_kernel(const SplitJob *__rest
 template <class Op, bool RH, bool CH>
 __global__ void __launch_bounds__(256, 2)
     batch_cc_kernel(const BInst *__restrict__ inst, const BItem *__restrict__ items, int n_items, int *queue) {
-    __shared__ __align__(16) float cc_smem[CC_BYTES / 4];
+    extern __shared__ __align__(16) float cc_smem[];  // CC_BYTES
     __shared__ int s_next;
-    float *ccA = cc_smem, *ccB = cc_smem + 2 * CC_BK * CC_LD;
+    float *ccA = cc_smem, *ccB = cc_smem + CC_STAGES * CC_PANEL;
     for (;;) {
         if (threadIdx.x == 0) s_next = atomicAdd(queue, 1);
         __syncthreads();
@@ -601,13 +617,26 @@ int cc_quadrants(const Problem &p, const BItem &it) {
     return ((int64_t)it.a * 128 + 64 < p.M ? 2 : 0) | ((int64_t)it.b * 128 + 64 < p.N ? 1 : 0);
 }
 
+template <class Op, bool RH, bool CH>
+cudaError_t launch_cc(int grid, const BInst *inst, const BItem *items, int cnt, int *queue, cudaStream_t s) {
+    static std::once_flag once;  // the dynamic shared-memory limit of this instance, raised once
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(batch_cc_kernel<Op, RH, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, CC_BYTES);
+    });
+    if (attr != cudaSuccess) return attr;
+    batch_cc_kernel<Op, RH, CH><<<grid, 256, CC_BYTES, s>>>(inst, items, cnt, queue);
+    return cudaSuccess;
+}
+
 template <class Op>
-void launch_cc_quad(int q, int grid, const BInst *inst, const BItem *items, int cnt, int *queue, cudaStream_t s) {
+cudaError_t launch_cc_quad(int q, int grid, const BInst *inst, const BItem *items, int cnt, int *queue,
+                           cudaStream_t s) {
     switch (q) {
-    case 3: batch_cc_kernel<Op, true, true><<<grid, 256, 0, s>>>(inst, items, cnt, queue); break;
-    case 2: batch_cc_kernel<Op, true, false><<<grid, 256, 0, s>>>(inst, items, cnt, queue); break;
-    case 1: batch_cc_kernel<Op, false, true><<<grid, 256, 0, s>>>(inst, items, cnt, queue); break;
-    default: batch_cc_kernel<Op, false, false><<<grid, 256, 0, s>>>(inst, items, cnt, queue); break;
+    case 3: return launch_cc<Op, true, true>(grid, inst, items, cnt, queue, s);
+    case 2: return launch_cc<Op, true, false>(grid, inst, items, cnt, queue, s);
+    case 1: return launch_cc<Op, false, true>(grid, inst, items, cnt, queue, s);
+    default: return launch_cc<Op, false, false>(grid, inst, items, cnt, queue, s);
     }
 }
 
@@ -827,13 +856,15 @@ cudaError_t enqueue(moa_batch_plan *pl, cudaStream_t s) {
         const BItem *items = pl->d_cc_items + pl->cc_off[g];
         int *queue = pl->d_queue + 1 + g;
         const int q = g % 4;
+        cudaError_t e;
         switch (g / 4) {
-        case CC_MIN_PLUS: launch_cc_quad<sr::F32MinPlus>(q, grid, pl->d_inst, items, cnt, queue, s); break;
-        case CC_MAX_PLUS: launch_cc_quad<sr::F32MaxPlus>(q, grid, pl->d_inst, items, cnt, queue, s); break;
-        case CC_MIN_TIMES: launch_cc_quad<sr::F32MinTimes>(q, grid, pl->d_inst, items, cnt, queue, s); break;
-        case CC_MAX_TIMES: launch_cc_quad<sr::F32MaxTimes>(q, grid, pl->d_inst, items, cnt, queue, s); break;
-        default: launch_cc_quad<sr::F32PlusTimes>(q, grid, pl->d_inst, items, cnt, queue, s); break;
+        case CC_MIN_PLUS: e = launch_cc_quad<sr::F32MinPlus>(q, grid, pl->d_inst, items, cnt, queue, s); break;
+        case CC_MAX_PLUS: e = launch_cc_quad<sr::F32MaxPlus>(q, grid, pl->d_inst, items, cnt, queue, s); break;
+        case CC_MIN_TIMES: e = launch_cc_quad<sr::F32MinTimes>(q, grid, pl->d_inst, items, cnt, queue, s); break;
+        case CC_MAX_TIMES: e = launch_cc_quad<sr::F32MaxTimes>(q, grid, pl->d_inst, items, cnt, queue, s); break;
+        default: e = launch_cc_quad<sr::F32PlusTimes>(q, grid, pl->d_inst, items, cnt, queue, s); break;
         }
+        if (e != cudaSuccess) return e;
     }
     if (fork) {
         const cudaError_t e = cudaStreamWaitEvent(s, pl->ev_join, 0);
