@@ -72,7 +72,12 @@ struct alignas(16) BInst {
 
 struct alignas(16) BItem {
     int32_t inst, type, a, b;  // TC / CC: tile (a = row tile, b = column tile); OUT / FILL: rows [a, a + b)
+    // TC tile shape: bit 0 a 128 x 64 tile (b counts 64-column tiles; one B half,
+    // N = 64 MMAs), bit 1 a 64-row A box (problems with M <= 64; the MMA rows
+    // 64..127 read stale planes and are never stored)
+    int32_t shape, pad0, pad1, pad2;
 };
+constexpr int SH_NARROW = 1, SH_SHORT = 2;
 
 // One slot of the grouped kernel's item ring: the scheduler copies the item
 // and its problem descriptor here ahead of use, so the other roles read them
@@ -117,6 +122,7 @@ constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + TC_STG_BYTES + RING_BYTES + 1
 constexpr int TMEM_COLS = NACC * BN;
 static_assert(TMEM_COLS <= 512 && NBARS * 8 + 16 <= 1024 && SMEM <= 227 * 1024, "grouped kernel resources");
 constexpr uint32_t IDESC = ptx::idesc_bf16_f32(BM, BN, 1);
+constexpr uint32_t IDESC_N64 = ptx::idesc_bf16_f32(BM, 64, 1);
 // split-BF16x3 terms (plane of A, plane of B): small products first, hi*hi last
 MOA_DEV constexpr int term_a(int t) { return t == 0 ? 1 : t == 2 ? 2 : t == 4 ? 1 : 0; }  // 1, 0, 2, 0, 1, 0
 MOA_DEV constexpr int term_b(int t) { return t == 0 ? 1 : t == 1 ? 2 : t == 3 ? 1 : 0; }  // 1, 2, 0, 1, 0, 0
@@ -307,7 +313,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 it = p.items[item];
                 in = p.inst[it.inst];
                 if (it.type == IT_TC) {
-                    ptx::prefetch_tmap(p.tmaps + in.tmap);
+                    ptx::prefetch_tmap(p.tmaps + in.tmap + ((it.shape & SH_SHORT) ? 2 : 0));
                     ptx::prefetch_tmap(p.tmaps + in.tmap + 1);
                 }
             }
@@ -336,7 +342,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (++slot == RING) slot = 0, rphase ^= 1u;
             if (item < 0) break;
             if (it.type != IT_TC) continue;
-            const CUtensorMap *ta = p.tmaps + tmap, *tb = ta + 1;
+            const bool narrow = it.shape & SH_NARROW, short_a = it.shape & SH_SHORT;
+            // A's maps: [tmap] 128-row boxes, [tmap + 2] 64-row boxes; B's at [tmap + 1]
+            const CUtensorMap *ta = p.tmaps + tmap + (short_a ? 2 : 0), *tb = p.tmaps + tmap + 1;
+            const uint32_t bytes = (short_a ? A_BYTES / 2 : A_BYTES) + (narrow ? B_HALF : 2 * B_HALF);
+            const int b_col = narrow ? it.b * 64 : it.b * BN;
             ptx::fence_tensormap(ta);
             ptx::fence_tensormap(tb);
             for (int i = 0; i < kslices; ++i) {
@@ -345,11 +355,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     break;
                 }
                 const uint32_t sa = tiles0 + stage * STAGE_BYTES, sb = sa + A_BYTES;
-                ptx::mbar_arrive_expect_tx(full(stage), STAGE_BYTES);
+                ptx::mbar_arrive_expect_tx(full(stage), bytes);
                 ptx::tma_load_3d(sa, ta, full(stage), i * BK, it.a * BM, 0);  // three planes in one box
-#pragma unroll
-                for (int j = 0; j < BN / 64; ++j)
-                    ptx::tma_load_3d(sb + j * B_HALF, tb, full(stage), it.b * BN + j * 64, i * BK, 0);
+                for (int j = 0; j < (narrow ? 1 : BN / 64); ++j)
+                    ptx::tma_load_3d(sb + j * B_HALF, tb, full(stage), b_col + j * 64, i * BK, 0);
                 issued |= 1u << stage;
                 last_par = (last_par & ~(1u << stage)) | (phase << stage);
                 if (++stage == STAGES) stage = 0, phase ^= 1u;
@@ -375,11 +384,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 break;
             }
             const int item = rs[slot].item, type = rs[slot].it.type, kslices = (rs[slot].in.K + BK - 1) / BK;
+            const int shape = rs[slot].it.shape;
             ptx::mbar_arrive(rempty(slot));
             if (++slot == RING) slot = 0, rphase ^= 1u;
             if (item < 0) break;
             if (type != IT_TC) continue;
             constexpr int SPB = KB / BK;  // stages per promotion block
+            const uint32_t idesc = (shape & SH_NARROW) ? IDESC_N64 : IDESC;
+            const int a_plane = (shape & SH_SHORT) ? A_PLANE / 2 : A_PLANE;  // a 64-row box packs its planes
             for (int i = 0; i < kslices; ++i) {
                 const int j = i % SPB;
                 if (j == 0) {
@@ -402,9 +414,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int k = 0; k < BK / 16; ++k) {
                         // A: K-major rows of 64 B (8-row atoms 512 B apart), 32 B per k-step;
                         // B: the two 64-column halves B_HALF apart, 16 rows of 128 B per k-step
-                        const uint64_t ad = ptx::smem_desc_sw64(sa + term_a(t) * A_PLANE + k * 32, 512);
+                        const uint64_t ad = ptx::smem_desc_sw64(sa + term_a(t) * a_plane + k * 32, 512);
                         const uint64_t bd = ptx::smem_desc_sw128(sb + term_b(t) * B_PLANE + k * 2048, B_HALF, 1024);
-                        ptx::mma_bf16(dacc, ad, bd, IDESC, (j > 0 || t > 0 || k > 0) ? 1u : 0u);
+                        ptx::mma_bf16(dacc, ad, bd, idesc, (j > 0 || t > 0 || k > 0) ? 1u : 0u);
                     }
                 }
                 ptx::mma_commit(empty(stage));
@@ -444,6 +456,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (++slot == RING) slot = 0, rphase ^= 1u;
             if (item < 0) break;
             if (it.type == IT_TC) {
+                const bool narrow = it.shape & SH_NARROW;
+                const bool active = !narrow || part * HC < 64;  // a 128 x 64 tile leaves columns 64..127 unwritten
                 float acc[HC];
 #pragma unroll
                 for (int j = 0; j < HC; ++j) acc[j] = 0.0f;
@@ -457,13 +471,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     ptx::tc_fence_after();
                     const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(abuf * BN + part * HC);
+                    if (active) {
 #pragma unroll
-                    for (int c = 0; c < HC; c += 32) {
-                        uint32_t r[32];
-                        ptx::tmem_ld32(tb + c, r);
-                        ptx::tmem_ld_wait();
+                        for (int c = 0; c < HC; c += 32) {
+                            uint32_t r[32];
+                            ptx::tmem_ld32(tb + c, r);
+                            ptx::tmem_ld_wait();
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) acc[c + j] = __fadd_rn(acc[c + j], __uint_as_float(r[j]));
+                            for (int j = 0; j < 32; ++j) acc[c + j] = __fadd_rn(acc[c + j], __uint_as_float(r[j]));
+                        }
                     }
                     ptx::tc_fence_before();
                     __syncwarp();
@@ -475,10 +491,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // slice, 32 columns at a time, so that every store instruction writes
                 // 32 consecutive columns of one row (128 contiguous bytes)
                 const int64_t row0 = (int64_t)it.a * BM + q * 32;
-                const int64_t col0 = (int64_t)it.b * BN + part * HC;
+                const int64_t col0 = (narrow ? (int64_t)it.b * 64 : (int64_t)it.b * BN) + part * HC;
                 const int rows_here = (int)min((int64_t)32, in.M - row0);
                 float *sl = tcstg + ew * TC_STG_FLOATS;
-                if (rows_here > 0) {
+                if (active && rows_here > 0) {
 #pragma unroll
                     for (int c = 0; c < HC; c += 32) {
 #pragma unroll
@@ -699,7 +715,10 @@ moa_status classify(const moa_problem &q, Problem *out) {
 // estimated microseconds of one item on one SM (orders the queue)
 double item_cost(const Problem &p, const BItem &it) {
     switch (it.type) {
-    case IT_TC: return 1.0 + 0.26 * (double)((p.K + KB - 1) / KB) * TERMS;
+    case IT_TC: {  // by the bytes a stage loads: A's share and B's share
+        const double f = (((it.shape & SH_SHORT) ? 0.5 : 1.0) + ((it.shape & SH_NARROW) ? 0.5 : 1.0)) / 2.0;
+        return 1.0 + 0.26 * (double)((p.K + KB - 1) / KB) * TERMS * f;
+    }
     case IT_CC: return 1.0 + 128.0 * 128.0 * (double)p.K / 79000.0;
     default: return 0.5 + (double)it.b * (double)p.N * 4.0 / 43000.0;
     }
@@ -734,11 +753,13 @@ int tune_mode() {  // 0 off, 1 cached, 2 force
     return 1;
 }
 
-// Schedules the autotuner picks from: 0 CUDA-core items in their own kernel
-// (before the split pass), the grouped queue longest first; 1 the same with
-// tensor-core items first in the grouped queue; 2 every item in the grouped
-// kernel, tensor-core and CUDA-core items interleaved.
-constexpr int kPolicies = 2;
+// Schedules the autotuner picks from, two bits: bit 0 the grouped queue's
+// order (0 longest first over all its items, 1 tensor-core tiles first);
+// bit 1 the tensor-core tile shapes (0 every tile 128 x 128; 1 a 64-row A
+// box for problems with M <= 64 and a 128 x 64 last column tile where at most
+// 64 columns remain).  Schedules with bit 1 exist only for plans where a
+// tile changes shape.
+constexpr int kPolicies = 4;
 
 }  // namespace
 }  // namespace moa
@@ -749,8 +770,9 @@ struct moa_batch_plan {
     int device = 0;
     int count = 0;
     std::vector<Problem> probs;
-    std::vector<BItem> items;  // unordered
-    std::vector<double> cost;
+    std::vector<BItem> items;      // unordered, tensor-core tiles 128 x 128
+    std::vector<BItem> tc_shaped;  // the tensor-core tiles of the shaped schedules
+    bool shapes_differ = false;    // some tile of tc_shaped is not 128 x 128
     int n_items = 0, n_jobs = 0;
     int n_grouped = 0, n_cc = 0;  // items in the grouped kernel / the CUDA-core kernels (set by the policy)
     int cc_off[kCcGroups] = {}, cc_cnt[kCcGroups] = {};  // CUDA-core items of each kernel in d_cc_items
@@ -783,24 +805,31 @@ int cc_group(const moa_batch_plan &pl, const BItem &it) {
 
 // The grouped kernel's queue and the CUDA-core kernels' queues for a policy.
 void order_items(const moa_batch_plan &pl, int policy, std::vector<BItem> &grouped, std::vector<BItem> &cc) {
-    std::vector<int> idx(pl.items.size());
+    const bool shaped = (policy & 2) != 0;
+    std::vector<BItem> all;
+    all.reserve(pl.items.size());
+    for (const BItem &it : pl.items)
+        if (!(shaped && it.type == IT_TC)) all.push_back(it);
+    if (shaped) all.insert(all.end(), pl.tc_shaped.begin(), pl.tc_shaped.end());
+    std::vector<double> cost(all.size());
+    for (size_t i = 0; i < all.size(); ++i) cost[i] = item_cost(pl.probs[all[i].inst], all[i]);
+    std::vector<int> idx(all.size());
     for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
-    auto by_cost = [&](int a, int b) { return pl.cost[a] > pl.cost[b]; };
-    std::stable_sort(idx.begin(), idx.end(), by_cost);
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost[a] > cost[b]; });
     grouped.clear();
     cc.clear();
     std::vector<int> tc, ccs, other;
-    for (int i : idx) (pl.items[i].type == IT_TC ? tc : pl.items[i].type == IT_CC ? ccs : other).push_back(i);
-    if (policy == 0) {
+    for (int i : idx) (all[i].type == IT_TC ? tc : all[i].type == IT_CC ? ccs : other).push_back(i);
+    if ((policy & 1) == 0) {
         for (int i : idx)
-            if (pl.items[i].type != IT_CC) grouped.push_back(pl.items[i]);
+            if (all[i].type != IT_CC) grouped.push_back(all[i]);
     } else {
-        for (int i : tc) grouped.push_back(pl.items[i]);
-        for (int i : other) grouped.push_back(pl.items[i]);
+        for (int i : tc) grouped.push_back(all[i]);
+        for (int i : other) grouped.push_back(all[i]);
     }
     for (int g = 0; g < kCcGroups; ++g)  // by kernel (operator, tile halves), longest first within each
         for (int i : ccs)
-            if (cc_group(pl, pl.items[i]) == g) cc.push_back(pl.items[i]);
+            if (cc_group(pl, all[i]) == g) cc.push_back(all[i]);
 }
 
 moa_status upload_order(moa_batch_plan *pl, int policy, cudaStream_t s) {
@@ -888,7 +917,7 @@ moa_status autotune(moa_batch_plan *pl, cudaStream_t s) {
         return upload_order(pl, pl->policy, s);
     }
     const int mode = tune_mode();
-    const std::string key = gpu_signature() + "|s3|" + pl->signature;  // s3: the schedules listed at kPolicies
+    const std::string key = gpu_signature() + "|s5|" + pl->signature;  // s5: the schedules listed at kPolicies
     if (mode == 0) {
         pl->policy = 0;
         return upload_order(pl, 0, s);
@@ -909,6 +938,7 @@ moa_status autotune(moa_batch_plan *pl, cudaStream_t s) {
     double best = 1e30;
     int best_pol = 0;
     for (int pol = 0; pol < kPolicies; ++pol) {
+        if ((pol & 2) && !pl->shapes_differ) continue;  // the same tiles as pol & 1
         moa_status st = upload_order(pl, pol, s);
         if (st != MOA_OK) return st;
         float best_ms = 1e30f;
@@ -1004,7 +1034,7 @@ moa_status moa_batch_plan_create(int count, const moa_problem *problems, moa_bat
             ++n_tc;
         }
     }
-    std::vector<CUtensorMap> tmaps((size_t)2 * n_tc);
+    std::vector<CUtensorMap> tmaps((size_t)3 * n_tc);  // per problem: A (128-row boxes), B, A (64-row boxes)
     if (ws_bytes && cudaMalloc(&pl->d_ws, ws_bytes) != cudaSuccess) {
         cudaGetLastError();
         plan_free(pl);
@@ -1024,24 +1054,35 @@ moa_status moa_batch_plan_create(int count, const moa_problem *problems, moa_bat
             const int64_t Kp = round8(p.K), Np = round8(p.N);
             __nv_bfloat16 *pa = (__nv_bfloat16 *)((uint8_t *)pl->d_ws + ws_off[i]);
             __nv_bfloat16 *pb = pa + 3 * p.M * Kp;
-            if (!make_tmap(&tmaps[2 * t], pa, (uint64_t)p.K, (uint64_t)p.M, 3, (uint64_t)Kp * 2, (uint64_t)(Kp * p.M * 2),
+            if (!make_tmap(&tmaps[3 * t], pa, (uint64_t)p.K, (uint64_t)p.M, 3, (uint64_t)Kp * 2, (uint64_t)(Kp * p.M * 2),
                            BK, BM, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, CU_TENSOR_MAP_SWIZZLE_64B, PLANES) ||
-                !make_tmap(&tmaps[2 * t + 1], pb, (uint64_t)p.N, (uint64_t)p.K, 3, (uint64_t)Np * 2,
+                !make_tmap(&tmaps[3 * t + 1], pb, (uint64_t)p.N, (uint64_t)p.K, 3, (uint64_t)Np * 2,
                            (uint64_t)(Np * p.K * 2), 64, BK, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, CU_TENSOR_MAP_SWIZZLE_128B,
-                           PLANES)) {
+                           PLANES) ||
+                !make_tmap(&tmaps[3 * t + 2], pa, (uint64_t)p.K, (uint64_t)p.M, 3, (uint64_t)Kp * 2,
+                           (uint64_t)(Kp * p.M * 2), BK, BM / 2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                           CU_TENSOR_MAP_SWIZZLE_64B, PLANES)) {
                 if (bad_index) *bad_index = i;
                 plan_free(pl);
                 return MOA_ERR_CUDA;
             }
-            b.tmap = 2 * t++;
+            b.tmap = 3 * t++;
             // split jobs: blocks of rows of about 64K elements
             const int64_t ra = std::max<int64_t>(1, 65536 / Kp), rb = std::max<int64_t>(1, 65536 / Np);
             for (int64_t r = 0; r < p.M; r += ra)
                 jobs.push_back(SplitJob{p.A, pa, p.K, Kp, p.M * Kp, r, std::min(p.M, r + ra)});
             for (int64_t r = 0; r < p.K; r += rb)
                 jobs.push_back(SplitJob{p.B, pb, p.N, Np, p.K * Np, r, std::min(p.K, r + rb)});
+            const int nt = (int)((p.N + BN - 1) / BN);
+            const bool short_a = p.M <= BM / 2, narrow_last = p.N - (int64_t)(nt - 1) * BN <= 64;
             for (int tm = 0; tm < (p.M + BM - 1) / BM; ++tm)
-                for (int tn = 0; tn < (p.N + BN - 1) / BN; ++tn) pl->items.push_back(BItem{i, IT_TC, tm, tn});
+                for (int tn = 0; tn < nt; ++tn) {
+                    pl->items.push_back(BItem{i, IT_TC, tm, tn});
+                    const bool narrow = narrow_last && tn == nt - 1;  // the last tile: a 64-column tile
+                    const int shape = (narrow ? SH_NARROW : 0) | (short_a ? SH_SHORT : 0);
+                    pl->tc_shaped.push_back(BItem{i, IT_TC, tm, narrow ? 2 * tn : tn, shape});
+                    pl->shapes_differ |= shape != 0;
+                }
             pl->work += 2.0 * p.M * p.N * p.K;
             sig_tc += (uint64_t)p.M * p.N * p.K;
         } else if (p.type == IT_CC) {
@@ -1057,7 +1098,6 @@ moa_status moa_batch_plan_create(int count, const moa_problem *problems, moa_bat
             sig_out += (uint64_t)p.M * p.N;
         }
     }
-    for (const BItem &it : pl->items) pl->cost.push_back(item_cost(pl->probs[it.inst], it));
     pl->n_items = (int)pl->items.size();
     pl->n_jobs = (int)jobs.size();
     {
@@ -1095,6 +1135,12 @@ moa_status moa_batch_plan_create(int count, const moa_problem *problems, moa_bat
     return MOA_OK;
 }
 
+// A failed CUDA call of an execute; with MOA_DEBUG set its error is printed.
+static moa_status batch_cuda_failed(cudaError_t e, const char *where) {
+    if (std::getenv("MOA_DEBUG")) std::fprintf(stderr, "moa batch: %s: %s\n", where, cudaGetErrorString(e));
+    return MOA_ERR_CUDA;
+}
+
 moa_status moa_batch_execute(moa_batch_plan *plan, moa_stream stream) {
     if (!plan) return MOA_ERR_NULL;
     std::lock_guard<std::mutex> lk(plan->mu);
@@ -1111,16 +1157,17 @@ moa_status moa_batch_execute(moa_batch_plan *plan, moa_stream stream) {
         if (e != cudaSuccess || e2 != cudaSuccess || !g) {
             if (g) cudaGraphDestroy(g);
             cudaGetLastError();
-            return MOA_ERR_CUDA;
+            return batch_cuda_failed(e != cudaSuccess ? e : e2, "capture");
         }
         e = cudaGraphInstantiate(&plan->exec, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) {
             plan->exec = nullptr;
-            return MOA_ERR_CUDA;
+            return batch_cuda_failed(e, "instantiate");
         }
     }
-    return cudaGraphLaunch(plan->exec, s) == cudaSuccess ? MOA_OK : MOA_ERR_CUDA;
+    const cudaError_t e = cudaGraphLaunch(plan->exec, s);
+    return e == cudaSuccess ? MOA_OK : batch_cuda_failed(e, "launch");
 }
 
 moa_status moa_batch_plan_info(const moa_batch_plan *plan, int64_t *n_problems, int64_t *n_launches, int64_t *n_tiles,

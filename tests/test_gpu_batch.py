@@ -96,11 +96,35 @@ def test_batch_full_10000_sampled():
     check_status()
 
 
-@pytest.mark.parametrize("schedule", ["0", "1"])
+@pytest.mark.parametrize("schedule", ["0", "1", "2", "3"])
+def test_batch_tensor_core_tiles_every_schedule(schedule, monkeypatch):
+    """Split-BF16x3 tiles under each schedule: ragged M, N and K (K % 32 != 0,
+    K < 32, K = 1), M = 1 and N = 1 problems, narrow last column tiles, K past
+    one promotion block; every output checked."""
+    import torch
+    monkeypatch.setenv("MOA_BATCH_SCHEDULE", schedule)
+    shapes = [(1, 1, 1), (1, 37, 200), (130, 8, 1), (129, 45, 64), (257, 300, 190), (64, 129, 65), (200, 97, 33),
+              (3, 513, 7), (140, 31, 250), (128, 128, 128)]
+    probs = []
+    for M, K, N in shapes:
+        probs.append({"kind": "bf16x3", "shapeA": (M, K), "shapeB": (K, N), "M": M, "K": K, "N": N})
+    probs += [p for p in synth.batched_problems(120, seed=9, mn_octaves=8) if p["kind"] != "outer"][:60]
+    pool, oa, ob, od, dpool, dout, specs = _build(probs, seed=9)
+    arr, keep = moa.make_problems(specs)
+    plan = moa.moa_batch_plan_create(arr)
+    try:
+        moa.moa_batch_execute(plan)
+        torch.cuda.synchronize()
+        _check(probs, pool, oa, ob, od, dout.cpu().numpy(), range(len(probs)), max_out=1 << 30)
+    finally:
+        moa.moa_batch_plan_destroy(plan)
+    check_status()
+
+
+@pytest.mark.parametrize("schedule", ["0", "1", "2", "3"])
 def test_batch_every_cuda_core_operator_and_schedule(schedule, monkeypatch):
     """Every CUDA-core (reduce, combine) of the batch, tiles with one, two or
-    four occupied halves and several tiles per problem, under each schedule
-    (CUDA-core items in their own kernels, or inside the grouped kernel)."""
+    four occupied halves and several tiles per problem, under each schedule."""
     import torch
     monkeypatch.setenv("MOA_BATCH_SCHEDULE", schedule)
     ops = [("min", "add", "tropical"), ("max", "add", "tropical"), ("min", "mul", "maxmul"), ("max", "mul", "maxmul"),
