@@ -180,9 +180,14 @@ def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws <= 1:
         return 0, 1, 0
+    import torch
     import torch.distributed as dist
-    dist.init_process_group("nccl" if os.environ.get("MOA_BENCH_BACKEND", "nccl") == "nccl" else "gloo")
-    return dist.get_rank(), ws, int(os.environ.get("LOCAL_RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    backend = "nccl" if os.environ.get("MOA_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+    if backend == "nccl":
+        torch.cuda.set_device(local)  # before the process group, so its communicator lands on this rank's GPU
+    dist.init_process_group(backend)
+    return dist.get_rank(), ws, local
 
 
 def _max_over_ranks(x, ws, device="cuda"):
@@ -756,7 +761,8 @@ def main():
                 "share_of_step": round(gemm_ms / ms_local, 3)}
 
     rows = {}
-    want = set() if args.no_rows or args.rows == "none" else (
+    # the extra rows are single-GPU measurements: with N ranks only the headline runs
+    want = set() if args.no_rows or args.rows == "none" or ws > 1 else (
         {"sweep", "semirings", "outer", "plain", "batched", "skinny", "axes"} if args.rows == "all"
         else set(args.rows.split(",")))
     if want:
@@ -803,7 +809,7 @@ def main():
             raise RuntimeError("device status " + moa.moa_status_string(st))
 
     cpu = None
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and ws == 1 and not args.no_cpu:  # the CPU baseline belongs to the single-GPU line
         cpu = cpu_oracle_sample(args.cpu_seconds)
 
     if rank == 0:
