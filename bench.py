@@ -51,10 +51,11 @@ def _peaks():
 
 
 def kernel_source_hash() -> str:
-    """SHA-256 over the sources the headline kernel (tc_gemm_pair.cu) is compiled from."""
+    """SHA-256 over the sources the headline kernel (tc_gemm_pair.cu) is compiled from and over
+    ozaki.cu, which sets the slice count and so the work of each of its launches."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("tc_gemm_pair.cu", "tc_ptx.cuh", "common.cuh", "ozaki_epi.cuh"):
+    for f in ("tc_gemm_pair.cu", "tc_ptx.cuh", "common.cuh", "ozaki_epi.cuh", "ozaki.cu"):
         with open(os.path.join(ROOT, "paper_0907_0792_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -225,7 +226,7 @@ SWEEP_FORMS = (("ozaki", "f64"), ("native", "f64"), ("native", "f32"), ("bf16x3"
 
 def ozaki_slices(k: int) -> int:
     """Digit slices per operand the library's Ozaki form takes for a contraction of length k."""
-    return 10 if k <= 64 else (8 if k <= 256 else 7)
+    return 10 if k <= 64 else (8 if k <= 256 else (7 if k < 4096 else 6))
 
 
 def sweep_work(form: str, dtype: str, n: int, peaks: dict, sustained: bool = False):

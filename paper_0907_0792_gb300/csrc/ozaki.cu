@@ -22,8 +22,10 @@
 // 7 bits needed 36 products for 56 bits.  The pairs with s + u >= S are
 // dropped (their weight is at most 2^-(S+2)beta * 2^14).  S grows as the
 // contraction shortens (a short sum can be dominated by entries far below
-// their row or column maximum, and it costs little to slice deeper): 10
-// slices up to K = 64, 8 up to K = 256, 7 above.
+// their row or column maximum, and it costs little to slice deeper; the
+// truncation errors of a long sum partly cancel): 10 slices up to K = 64, 8
+// up to K = 256, 7 below K = 4096, 6 from K = 4096 (21 slice products; 47
+// bits of every operand).
 //
 // Pre-pass (this file, memory bound): |A| row maxima and |B| column maxima as
 // FP64 bit patterns (integer max of the magnitude bits; finite inputs), then
@@ -210,7 +212,7 @@ int ozaki_slices(int64_t K) {
         return (v < 4 || v > kMaxSlices) ? 0 : v;
     }();
     if (forced) return forced;
-    return K <= 64 ? 10 : (K <= 256 ? 8 : 7);
+    return K <= 64 ? 10 : (K <= 256 ? 8 : (K < 4096 ? 7 : 6));
 }
 
 size_t ozaki_workspace_bytes(int64_t M, int64_t N, int64_t K) {

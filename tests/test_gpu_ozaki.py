@@ -11,10 +11,12 @@ from gpu_helpers import assert_norm_err, check_status, empty, sample_idx, to_dev
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-12
-# contractions on both sides of the slice-count change (8 slices up to K = 256, 7 above)
+# contractions on both sides of each slice-count change (10 slices up to K = 64, 8 up to K = 256, 7 below
+# K = 4096, 6 from there)
 SHAPES = [((300, 136), (136, 200)), ((2, 64, 72), (72, 5, 80)), ((129, 8), (8, 257)), ((1, 1), (1, 1)),
           ((37, 61), (61, 45)), ((130, 1500), (1500, 131)), ((16, 12, 8, 64), (64, 24, 20)),
-          ((140, 256), (256, 150)), ((140, 257), (257, 150)), ((260, 3000), (3000, 270))]
+          ((140, 256), (256, 150)), ((140, 257), (257, 150)), ((260, 3000), (3000, 270)),
+          ((96, 4095), (4095, 70)), ((96, 4096), (4096, 70))]
 
 
 def _ozaki(A, B):
@@ -63,15 +65,26 @@ def test_ozaki_square_whole(n):
 
 
 def test_ozaki_longest_contraction_sampled():
-    """K = 16384, the longest contraction the form takes (a class sum of 7
-    slice pairs stays below 2^31)."""
+    """K = 21845, the longest contraction the form takes (6 slices: a class
+    sum of 6 slice pairs of K products of at most 2^14 stays below 2^31)."""
     import torch
     for dist in ("uniform", "loguniform"):
-        A, B = synth.square(300, dist, m=300, k=16384)
+        A, B = synth.square(300, dist, m=300, k=21845)
         D = _ozaki(A, B)
         idx = sample_idx(300 * 300, 2000)
         got = D.view(-1)[torch.from_numpy(idx).to(D.device)].cpu().numpy()
         assert_norm_err(got, A, B, TOL, out_idx=idx)
+    check_status()
+
+
+def test_ozaki_contraction_past_the_limit_is_refused():
+    """K = 21846: a class sum could reach 2^31, so the call is refused before any launch."""
+    A, B = synth.uniform(43, 0, (4, 21846), -1, 1), synth.uniform(43, 1, (21846, 3), -1, 1)
+    import torch
+    D = empty((4, 3), torch.float64)
+    with pytest.raises(moa.MoaError) as e:
+        moa.moa_inner("add", "mul", "f64", "ozaki", A.shape, to_dev(A), B.shape, to_dev(B), D, "f64")
+    assert moa.STATUS[e.value.status] == "MOA_ERR_UNSUPPORTED"
     check_status()
 
 
