@@ -5,13 +5,15 @@
 // For a result of many rows the copies overlap the computation: the
 // psi-flattened rows of A and D (Fig. 1: row i of D needs row i of A and all
 // of B) are cut into up to four blocks; B and the first block of A go in
-// first, then block b computes while block b+1 of A comes in on an upload
-// stream and block b-1 of D goes out on a download stream.  Two device
-// buffers per operand block alternate.  The two copy streams belong to the
-// library (one pair per device and caller stream) and wait on, and are
-// waited on by, the caller's stream through events, so the whole call is
-// ordered on `stream` like every other call.  In the Ozaki form B's column
-// maxima and digit planes are made once, not once per block.
+// first, then block b computes while block b+1 of A comes in on the upload
+// streams and block b-1 of D goes out on the download streams.  Two device
+// buffers per operand block alternate.  Every copy is split in two halves on
+// two streams of its direction, so two copy engines share it (one engine
+// alone reaches about half of the host link).  The copy streams belong to the
+// library (one set per device and caller stream) and wait on, and are waited
+// on by, the caller's stream through events, so the whole call is ordered on
+// `stream` like every other call.  In the Ozaki form B's column maxima and
+// digit planes are made once, not once per block.
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -31,11 +33,13 @@ namespace {
 
 constexpr int kBufs = 2;
 constexpr int kMaxBlocks = 4;
+constexpr int kLanes = 2;  // copy streams per direction
 
 struct CopyStreams {
-    cudaStream_t up = nullptr, down = nullptr;
-    cudaEvent_t start = nullptr, b_in = nullptr, finished = nullptr;
-    cudaEvent_t a_in[kBufs] = {}, computed[kBufs] = {}, d_out[kBufs] = {};
+    cudaStream_t up[kLanes] = {}, down[kLanes] = {};
+    cudaEvent_t start = nullptr;
+    cudaEvent_t b_in[kLanes] = {}, finished[kLanes] = {};
+    cudaEvent_t a_in[kBufs][kLanes] = {}, computed[kBufs] = {}, d_out[kBufs][kLanes] = {};
 };
 
 std::mutex g_mu;
@@ -48,15 +52,16 @@ moa_status copy_streams(cudaStream_t s, CopyStreams **out) {
     auto it = g_streams.find({dev, s});
     if (it == g_streams.end()) {
         CopyStreams c;
-        bool ok = cudaStreamCreateWithFlags(&c.up, cudaStreamNonBlocking) == cudaSuccess &&
-                  cudaStreamCreateWithFlags(&c.down, cudaStreamNonBlocking) == cudaSuccess &&
-                  cudaEventCreateWithFlags(&c.start, cudaEventDisableTiming) == cudaSuccess &&
-                  cudaEventCreateWithFlags(&c.b_in, cudaEventDisableTiming) == cudaSuccess &&
-                  cudaEventCreateWithFlags(&c.finished, cudaEventDisableTiming) == cudaSuccess;
-        for (int i = 0; i < kBufs && ok; ++i)
-            ok = cudaEventCreateWithFlags(&c.a_in[i], cudaEventDisableTiming) == cudaSuccess &&
-                 cudaEventCreateWithFlags(&c.computed[i], cudaEventDisableTiming) == cudaSuccess &&
-                 cudaEventCreateWithFlags(&c.d_out[i], cudaEventDisableTiming) == cudaSuccess;
+        auto ev = [](cudaEvent_t *e) { return cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess; };
+        bool ok = ev(&c.start);
+        for (int l = 0; l < kLanes && ok; ++l)
+            ok = cudaStreamCreateWithFlags(&c.up[l], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaStreamCreateWithFlags(&c.down[l], cudaStreamNonBlocking) == cudaSuccess && ev(&c.b_in[l]) &&
+                 ev(&c.finished[l]);
+        for (int i = 0; i < kBufs && ok; ++i) {
+            ok = ev(&c.computed[i]);
+            for (int l = 0; l < kLanes && ok; ++l) ok = ev(&c.a_in[i][l]) && ev(&c.d_out[i][l]);
+        }
         if (!ok) {
             cudaGetLastError();
             return MOA_ERR_CUDA;
@@ -111,25 +116,37 @@ extern "C" moa_status moa_inner_host(moa_op reduce, moa_op combine, moa_dtype dt
     CopyStreams *c = nullptr;
     if ((st = copy_streams(s, &c)) != MOA_OK) return st;
     auto ok = [](cudaError_t e) { return e == cudaSuccess; };
+    // one copy as two halves (split on a 256-byte boundary), one per stream of `lanes`
+    auto copy2 = [&](void *dst, const void *src, size_t n, cudaMemcpyKind kind, cudaStream_t *lanes) -> bool {
+        const size_t h = n < 512 ? n : (n / 2 + 255) & ~(size_t)255;
+        if (h && !ok(cudaMemcpyAsync(dst, src, h, kind, lanes[0]))) return false;
+        return n == h || ok(cudaMemcpyAsync((uint8_t *)dst + h, (const uint8_t *)src + h, n - h, kind, lanes[1]));
+    };
     // the copy streams start after the work already queued on `stream` (which
     // may still read the buffers of an earlier call)
-    if (!ok(cudaEventRecord(c->start, s)) || !ok(cudaStreamWaitEvent(c->up, c->start, 0)) ||
-        !ok(cudaStreamWaitEvent(c->down, c->start, 0)))
-        return MOA_ERR_CUDA;
+    if (!ok(cudaEventRecord(c->start, s))) return MOA_ERR_CUDA;
+    for (int l = 0; l < kLanes; ++l)
+        if (!ok(cudaStreamWaitEvent(c->up[l], c->start, 0)) || !ok(cudaStreamWaitEvent(c->down[l], c->start, 0)))
+            return MOA_ERR_CUDA;
     uint8_t *dB = ws, *dA[kBufs], *dD[kBufs];
     for (int i = 0; i < kBufs; ++i) dA[i] = ws + offA + i * up(bytesA), dD[i] = ws + offD + i * up(bytesD);
-    if (bytesB && !ok(cudaMemcpyAsync(dB, B, bytesB, cudaMemcpyHostToDevice, c->up))) return MOA_ERR_CUDA;
-    if (!ok(cudaEventRecord(c->b_in, c->up))) return MOA_ERR_CUDA;
+    if (bytesB && !copy2(dB, B, bytesB, cudaMemcpyHostToDevice, c->up)) return MOA_ERR_CUDA;
+    for (int l = 0; l < kLanes; ++l)
+        if (!ok(cudaEventRecord(c->b_in[l], c->up[l]))) return MOA_ERR_CUDA;
     auto upload = [&](int b) -> bool {
         const int64_t r0 = b * rows, r1 = (r0 + rows < M) ? r0 + rows : M;
         const size_t n = dtype == MOA_B1_U32 ? bytesA : (size_t)((r1 - r0) * K) * ea;
         const uint8_t *src = (const uint8_t *)A + (dtype == MOA_B1_U32 ? 0 : (size_t)(r0 * K) * ea);
-        if (b >= kBufs && !ok(cudaStreamWaitEvent(c->up, c->computed[b % kBufs], 0))) return false;  // buffer free
-        if (n && !ok(cudaMemcpyAsync(dA[b % kBufs], src, n, cudaMemcpyHostToDevice, c->up))) return false;
-        return ok(cudaEventRecord(c->a_in[b % kBufs], c->up));
+        for (int l = 0; l < kLanes; ++l)  // the buffer is free once block b - kBufs is computed
+            if (b >= kBufs && !ok(cudaStreamWaitEvent(c->up[l], c->computed[b % kBufs], 0))) return false;
+        if (n && !copy2(dA[b % kBufs], src, n, cudaMemcpyHostToDevice, c->up)) return false;
+        for (int l = 0; l < kLanes; ++l)
+            if (!ok(cudaEventRecord(c->a_in[b % kBufs][l], c->up[l]))) return false;
+        return true;
     };
     if (!upload(0)) return MOA_ERR_CUDA;
-    if (!ok(cudaStreamWaitEvent(s, c->b_in, 0))) return MOA_ERR_CUDA;
+    for (int l = 0; l < kLanes; ++l)
+        if (!ok(cudaStreamWaitEvent(s, c->b_in[l], 0))) return MOA_ERR_CUDA;
     // The Ozaki form prepares B (column maxima, digit planes) once for all
     // row blocks, while the first block of A is still coming in.
     const bool ozaki_blocks = reduce == MOA_OP_ADD && combine == MOA_OP_MUL && dtype == MOA_F64 &&
@@ -146,8 +163,10 @@ extern "C" moa_status moa_inner_host(moa_op reduce, moa_op combine, moa_dtype dt
     for (int b = 0; b < nb; ++b) {
         const int64_t r0 = b * rows, r1 = (r0 + rows < M) ? r0 + rows : M;
         if (b + 1 < nb && !upload(b + 1)) return MOA_ERR_CUDA;
-        if (!ok(cudaStreamWaitEvent(s, c->a_in[b % kBufs], 0))) return MOA_ERR_CUDA;
-        if (b >= kBufs && !ok(cudaStreamWaitEvent(s, c->d_out[b % kBufs], 0))) return MOA_ERR_CUDA;  // D buffer free
+        for (int l = 0; l < kLanes; ++l) {
+            if (!ok(cudaStreamWaitEvent(s, c->a_in[b % kBufs][l], 0))) return MOA_ERR_CUDA;
+            if (b >= kBufs && !ok(cudaStreamWaitEvent(s, c->d_out[b % kBufs][l], 0))) return MOA_ERR_CUDA;  // D free
+        }
         // the block as its own inner product: rho A = <rows, K>, rho B = <K, N>
         const int64_t sa[2] = {r1 - r0, K}, sb[2] = {K, N};
         int64_t m, k, n;
@@ -157,15 +176,19 @@ extern "C" moa_status moa_inner_host(moa_op reduce, moa_op combine, moa_dtype dt
             st = inner_checked(reduce, combine, dtype, form, 2, sa, dA[b % kBufs], 2, sb, dB, dD[b % kBufs], out_dtype,
                                s, &m, &k, &n, true);
         if (st != MOA_OK) return st;
-        if (!ok(cudaEventRecord(c->computed[b % kBufs], s)) || !ok(cudaStreamWaitEvent(c->down, c->computed[b % kBufs], 0)))
-            return MOA_ERR_CUDA;
+        if (!ok(cudaEventRecord(c->computed[b % kBufs], s))) return MOA_ERR_CUDA;
+        for (int l = 0; l < kLanes; ++l)
+            if (!ok(cudaStreamWaitEvent(c->down[l], c->computed[b % kBufs], 0))) return MOA_ERR_CUDA;
         const size_t nd = out_dtype == MOA_B1_U32 ? bytesD : (size_t)((r1 - r0) * N) * ed;
         uint8_t *dst = (uint8_t *)out + (out_dtype == MOA_B1_U32 ? 0 : (size_t)(r0 * N) * ed);
-        if (nd && !ok(cudaMemcpyAsync(dst, dD[b % kBufs], nd, cudaMemcpyDeviceToHost, c->down))) return MOA_ERR_CUDA;
-        if (!ok(cudaEventRecord(c->d_out[b % kBufs], c->down))) return MOA_ERR_CUDA;
+        if (nd && !copy2(dst, dD[b % kBufs], nd, cudaMemcpyDeviceToHost, c->down)) return MOA_ERR_CUDA;
+        for (int l = 0; l < kLanes; ++l)
+            if (!ok(cudaEventRecord(c->d_out[b % kBufs][l], c->down[l]))) return MOA_ERR_CUDA;
     }
     // `stream` is done with the call once the last result has left the device
-    if (!ok(cudaEventRecord(c->finished, c->down)) || !ok(cudaStreamWaitEvent(s, c->finished, 0))) return MOA_ERR_CUDA;
-    if (!ok(cudaStreamWaitEvent(s, c->a_in[(nb - 1) % kBufs], 0))) return MOA_ERR_CUDA;
+    for (int l = 0; l < kLanes; ++l)
+        if (!ok(cudaEventRecord(c->finished[l], c->down[l])) || !ok(cudaStreamWaitEvent(s, c->finished[l], 0)) ||
+            !ok(cudaStreamWaitEvent(s, c->a_in[(nb - 1) % kBufs][l], 0)))
+            return MOA_ERR_CUDA;
     return MOA_OK;
 }
