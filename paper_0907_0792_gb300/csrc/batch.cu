@@ -753,13 +753,16 @@ int tune_mode() {  // 0 off, 1 cached, 2 force
     return 1;
 }
 
-// Schedules the autotuner picks from, two bits: bit 0 the grouped queue's
+// Schedules the autotuner picks from, three bits: bit 0 the grouped queue's
 // order (0 longest first over all its items, 1 tensor-core tiles first);
 // bit 1 the tensor-core tile shapes (0 every tile 128 x 128; 1 a 64-row A
 // box for problems with M <= 64 and a 128 x 64 last column tile where at most
-// 64 columns remain).  Schedules with bit 1 exist only for plans where a
-// tile changes shape.
-constexpr int kPolicies = 4;
+// 64 columns remain); bit 2 the CUDA-core kernels one after another on the
+// caller's stream (0) or side by side on streams of their own, the largest
+// first, so one kernel's tail overlaps the next (1).  Schedules with bit 1
+// exist only for plans where a tile changes shape, with bit 2 only for plans
+// with more than one CUDA-core kernel.
+constexpr int kPolicies = 8;
 
 }  // namespace
 }  // namespace moa
@@ -791,6 +794,10 @@ struct moa_batch_plan {
     cudaStream_t cap_stream = nullptr;
     cudaStream_t side = nullptr;  // the split pre-pass runs here, beside the CUDA-core kernels
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // under the schedules that run the CUDA-core kernels side by side: their streams and join events
+    cudaStream_t cc_streams[kCcGroups] = {};
+    cudaEvent_t cc_join[kCcGroups] = {};
+    int policy_now = 0;  // the schedule whose order is uploaded (what enqueue launches)
     cudaGraphExec_t exec = nullptr;
     std::mutex mu;
 };
@@ -835,6 +842,7 @@ void order_items(const moa_batch_plan &pl, int policy, std::vector<BItem> &group
 moa_status upload_order(moa_batch_plan *pl, int policy, cudaStream_t s) {
     std::vector<BItem> grouped, cc;
     order_items(*pl, policy, grouped, cc);
+    pl->policy_now = policy;
     pl->n_grouped = (int)grouped.size();
     pl->n_cc = (int)cc.size();
     for (int g = 0; g < kCcGroups; ++g) pl->cc_cnt[g] = 0;
@@ -868,32 +876,52 @@ cudaError_t enqueue(moa_batch_plan *pl, cudaStream_t s) {
     // the split pre-pass (memory bound) on the plan's side stream, beside the
     // CUDA-core kernels (ALU bound); the grouped kernel waits for both
     const bool fork = pl->n_jobs > 0 && pl->n_cc > 0;
+    const bool cc_side_by_side = (pl->policy_now & 4) != 0;
+    if (fork || cc_side_by_side) {
+        const cudaError_t e = cudaEventRecord(pl->ev_fork, s);
+        if (e != cudaSuccess) return e;
+    }
     if (fork) {
-        cudaError_t e = cudaEventRecord(pl->ev_fork, s);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(pl->side, pl->ev_fork, 0);
+        cudaError_t e = cudaStreamWaitEvent(pl->side, pl->ev_fork, 0);
         if (e != cudaSuccess) return e;
         const int blocks = std::min(pl->n_jobs, sm_count_dev() * 8);
         batch_split_kernel<<<blocks, 256, 0, pl->side>>>(pl->d_jobs, pl->n_jobs);
         e = cudaEventRecord(pl->ev_join, pl->side);
         if (e != cudaSuccess) return e;
     }
-    // one persistent kernel per (operator, occupied tile halves) present, each with its own queue
-    for (int g = 0; g < kCcGroups; ++g) {
-        const int cnt = pl->cc_cnt[g];
-        if (cnt == 0) continue;
+    // one persistent kernel per (operator, occupied tile halves) present, each with its own queue;
+    // side by side: each on a stream of its own, the kernel with the most items launched first
+    int order[kCcGroups], n_used = 0;
+    for (int g = 0; g < kCcGroups; ++g)
+        if (pl->cc_cnt[g] > 0) order[n_used++] = g;
+    if (cc_side_by_side)
+        std::stable_sort(order, order + n_used, [&](int a, int b) { return pl->cc_cnt[a] > pl->cc_cnt[b]; });
+    for (int k = 0; k < n_used; ++k) {
+        const int g = order[k], cnt = pl->cc_cnt[g];
         const int grid = std::min(2 * sm_count_dev(), cnt);
         const BItem *items = pl->d_cc_items + pl->cc_off[g];
         int *queue = pl->d_queue + 1 + g;
         const int q = g % 4;
+        cudaStream_t cs = s;
+        if (cc_side_by_side) {
+            cs = pl->cc_streams[k];
+            const cudaError_t e = cudaStreamWaitEvent(cs, pl->ev_fork, 0);
+            if (e != cudaSuccess) return e;
+        }
         cudaError_t e;
         switch (g / 4) {
-        case CC_MIN_PLUS: e = launch_cc_quad<sr::F32MinPlus>(q, grid, pl->d_inst, items, cnt, queue, s); break;
-        case CC_MAX_PLUS: e = launch_cc_quad<sr::F32MaxPlus>(q, grid, pl->d_inst, items, cnt, queue, s); break;
-        case CC_MIN_TIMES: e = launch_cc_quad<sr::F32MinTimes>(q, grid, pl->d_inst, items, cnt, queue, s); break;
-        case CC_MAX_TIMES: e = launch_cc_quad<sr::F32MaxTimes>(q, grid, pl->d_inst, items, cnt, queue, s); break;
-        default: e = launch_cc_quad<sr::F32PlusTimes>(q, grid, pl->d_inst, items, cnt, queue, s); break;
+        case CC_MIN_PLUS: e = launch_cc_quad<sr::F32MinPlus>(q, grid, pl->d_inst, items, cnt, queue, cs); break;
+        case CC_MAX_PLUS: e = launch_cc_quad<sr::F32MaxPlus>(q, grid, pl->d_inst, items, cnt, queue, cs); break;
+        case CC_MIN_TIMES: e = launch_cc_quad<sr::F32MinTimes>(q, grid, pl->d_inst, items, cnt, queue, cs); break;
+        case CC_MAX_TIMES: e = launch_cc_quad<sr::F32MaxTimes>(q, grid, pl->d_inst, items, cnt, queue, cs); break;
+        default: e = launch_cc_quad<sr::F32PlusTimes>(q, grid, pl->d_inst, items, cnt, queue, cs); break;
         }
         if (e != cudaSuccess) return e;
+        if (cc_side_by_side) {
+            e = cudaEventRecord(pl->cc_join[k], cs);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, pl->cc_join[k], 0);
+            if (e != cudaSuccess) return e;
+        }
     }
     if (fork) {
         const cudaError_t e = cudaStreamWaitEvent(s, pl->ev_join, 0);
@@ -917,7 +945,7 @@ moa_status autotune(moa_batch_plan *pl, cudaStream_t s) {
         return upload_order(pl, pl->policy, s);
     }
     const int mode = tune_mode();
-    const std::string key = gpu_signature() + "|s5|" + pl->signature;  // s5: the schedules listed at kPolicies
+    const std::string key = gpu_signature() + "|s6|" + pl->signature;  // s6: the schedules listed at kPolicies
     if (mode == 0) {
         pl->policy = 0;
         return upload_order(pl, 0, s);
@@ -937,8 +965,16 @@ moa_status autotune(moa_batch_plan *pl, cudaStream_t s) {
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return MOA_ERR_CUDA;
     double best = 1e30;
     int best_pol = 0;
+    int n_cc_kernels = 0;
+    {
+        bool used[kCcGroups] = {};
+        for (const BItem &it : pl->items)
+            if (it.type == IT_CC) used[cc_group(*pl, it)] = true;
+        for (bool u : used) n_cc_kernels += u;
+    }
     for (int pol = 0; pol < kPolicies; ++pol) {
-        if ((pol & 2) && !pl->shapes_differ) continue;  // the same tiles as pol & 1
+        if ((pol & 2) && !pl->shapes_differ) continue;  // the same tiles as pol & ~2
+        if ((pol & 4) && n_cc_kernels < 2) continue;     // nothing to run side by side
         moa_status st = upload_order(pl, pol, s);
         if (st != MOA_OK) return st;
         float best_ms = 1e30f;
@@ -967,12 +1003,32 @@ moa_status autotune(moa_batch_plan *pl, cudaStream_t s) {
     return upload_order(pl, best_pol, s);
 }
 
+// The streams and join events of the side-by-side CUDA-core kernels (one per kernel present).
+bool make_cc_streams(moa_batch_plan *pl) {
+    bool used[kCcGroups] = {};
+    for (const BItem &it : pl->items)
+        if (it.type == IT_CC) used[cc_group(*pl, it)] = true;
+    int k = 0;
+    for (int g = 0; g < kCcGroups; ++g)
+        if (used[g]) {
+            if (cudaStreamCreateWithFlags(&pl->cc_streams[k], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&pl->cc_join[k], cudaEventDisableTiming) != cudaSuccess)
+                return false;
+            ++k;
+        }
+    return true;
+}
+
 void plan_free(moa_batch_plan *pl) {
     if (!pl) return;
     cudaDeviceSynchronize();
     if (pl->exec) cudaGraphExecDestroy(pl->exec);
     if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
     if (pl->side) cudaStreamDestroy(pl->side);
+    for (int g = 0; g < kCcGroups; ++g) {
+        if (pl->cc_streams[g]) cudaStreamDestroy(pl->cc_streams[g]);
+        if (pl->cc_join[g]) cudaEventDestroy(pl->cc_join[g]);
+    }
     if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
     if (pl->ev_join) cudaEventDestroy(pl->ev_join);
     cudaFree(pl->d_inst);
@@ -1127,7 +1183,7 @@ moa_status moa_batch_plan_create(int count, const moa_problem *problems, moa_bat
     if (!ok || cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&pl->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming) != cudaSuccess || !make_cc_streams(pl)) {
         plan_free(pl);
         return MOA_ERR_CUDA;
     }

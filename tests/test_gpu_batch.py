@@ -96,7 +96,7 @@ def test_batch_full_10000_sampled():
     check_status()
 
 
-@pytest.mark.parametrize("schedule", ["0", "1", "2", "3"])
+@pytest.mark.parametrize("schedule", ["0", "1", "2", "3", "4", "7"])
 def test_batch_tensor_core_tiles_every_schedule(schedule, monkeypatch):
     """Split-BF16x3 tiles under each schedule: ragged M, N and K (K % 32 != 0,
     K < 32, K = 1), M = 1 and N = 1 problems, narrow last column tiles, K past
@@ -121,7 +121,7 @@ def test_batch_tensor_core_tiles_every_schedule(schedule, monkeypatch):
     check_status()
 
 
-@pytest.mark.parametrize("schedule", ["0", "1", "2", "3"])
+@pytest.mark.parametrize("schedule", ["0", "1", "2", "3", "4", "7"])
 def test_batch_every_cuda_core_operator_and_schedule(schedule, monkeypatch):
     """Every CUDA-core (reduce, combine) of the batch, tiles with one, two or
     four occupied halves and several tiles per problem, under each schedule."""
