@@ -4,6 +4,9 @@
 // Plan (host, moa_batch_plan_create): every problem is validated as its
 // single call would be and psi-flattened; its work is cut into items —
 //   TC   one 128 x 128 tile of a split-BF16x3 (+,*) problem (tensor cores),
+//   GEMV rows or columns of a split-BF16x3 problem with M = 1 or N = 1, on the
+//        CUDA cores straight from the FP32 operands (a compensated dot
+//        product, more accurate than the split form),
 //   CC   one 128 x 128 tile of a CUDA-core semiring problem ((min|max|+),
 //        (+|*)) — 8 x 8 register micro-tiles, shared-memory panels,
 //   OUT  a block of rows of an outer product,
@@ -55,7 +58,11 @@ __device__ uint32_t g_batch_status;
 
 namespace {
 
-enum ItemType { IT_TC = 0, IT_CC = 1, IT_OUT = 2, IT_FILL = 3 };
+enum ItemType { IT_TC = 0, IT_CC = 1, IT_OUT = 2, IT_FILL = 3, IT_GEMV = 4 };
+// IT_GEMV: a split-BF16x3 (+,*) problem with M = 1 or N = 1, on the CUDA cores
+// (shape GV_ROWS: rows [a, a + b) of an N = 1 product, one warp per row;
+// GV_COLS: columns [a, a + b) of an M = 1 product, one thread per column)
+constexpr int GV_ROWS = 1, GV_COLS = 2;
 enum CcOp { CC_MIN_PLUS = 0, CC_MAX_PLUS = 1, CC_MIN_TIMES = 2, CC_MAX_TIMES = 3, CC_PLUS_TIMES = 4 };
 constexpr int kCcOps = 5, kCcGroups = 4 * kCcOps;  // CUDA-core kernels: operator x occupied tile halves
 
@@ -136,6 +143,29 @@ struct BatchParams {
 };
 
 MOA_DEV void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+// Compensated dot product in FP32 (Ogita, Rump and Oishi's Dot2): the product
+// split exactly into p + e by an FMA, p added to the running sum by TwoSum,
+// both error terms collected in `cmp`; sum + cmp is as accurate as a dot
+// product computed in twice the working precision and then rounded.  Every
+// step is an explicitly rounded operation, so no contraction changes it.
+MOA_DEV void dot2_step(float &sum, float &cmp, float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);
+    const float t = __fadd_rn(sum, p);
+    const float z = __fsub_rn(t, sum);
+    const float err = __fadd_rn(__fsub_rn(sum, __fsub_rn(t, z)), __fsub_rn(p, z));
+    sum = t;
+    cmp = __fadd_rn(cmp, __fadd_rn(err, e));
+}
+// (sum, cmp) += (sum2, cmp2), the two sums added by TwoSum.
+MOA_DEV void dot2_merge(float &sum, float &cmp, float sum2, float cmp2) {
+    const float t = __fadd_rn(sum, sum2);
+    const float z = __fsub_rn(t, sum);
+    const float err = __fadd_rn(__fsub_rn(sum, __fsub_rn(t, z)), __fsub_rn(sum2, z));
+    sum = t;
+    cmp = __fadd_rn(__fadd_rn(cmp, cmp2), err);
+}
 
 // One 128 x 128 CUDA-core tile of D = reduce_p(A combine B), 256 threads.
 // The panels of A (transposed to [k][m]) and B ([k][n]) stream through four
@@ -531,6 +561,60 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+// Matrix-vector items (split-BF16x3 problems with M = 1 or N = 1) on their
+// own: a persistent kernel of 256 threads and at most 32 registers per SM, so
+// that it fits beside the grouped kernel and runs while the tensor cores do.
+// N = 1 items: one warp per row, the lanes striding along the contraction,
+// the warp's partial sums merged by TwoSum.  M = 1 items: four columns per
+// thread (four loads of B in flight each step), A's element read by all.
+__global__ void __launch_bounds__(256, 8)
+    batch_gemv_kernel(const BInst *__restrict__ inst, const BItem *__restrict__ items, int n_items, int *queue) {
+    __shared__ int s_next;
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+    for (;;) {
+        if (threadIdx.x == 0) s_next = atomicAdd(queue, 1);
+        __syncthreads();
+        const int i = s_next;
+        __syncthreads();
+        if (i >= n_items) break;
+        const BItem it = items[i];
+        const BInst in = inst[it.inst];
+        const int64_t K = in.K, N = in.N;
+        if (it.shape == GV_ROWS) {
+            for (int r = it.a + warp; r < it.a + it.b; r += 8) {
+                float sum = 0.0f, cmp = 0.0f;
+                const float *arow = in.A + (int64_t)r * K;
+                for (int64_t k = lane; k < K; k += 32) dot2_step(sum, cmp, __ldg(arow + k), __ldg(in.B + k));
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+                    dot2_merge(sum, cmp, __shfl_xor_sync(0xffffffffu, sum, o), __shfl_xor_sync(0xffffffffu, cmp, o));
+                if (lane == 0) in.D[r] = __fadd_rn(sum, cmp);
+            }
+        } else {
+            // columns n0 + threadIdx.x + 256 j, j < 4 (those below the item's end)
+            const int n0 = it.a, n1 = it.a + it.b;
+            float sum[4] = {0.0f, 0.0f, 0.0f, 0.0f}, cmp[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            for (int64_t k = 0; k < K; ++k) {
+                const float a = __ldg(in.A + k);
+                const float *brow = in.B + k * N;
+                float b[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int n = n0 + (int)threadIdx.x + 256 * j;
+                    b[j] = n < n1 ? __ldg(brow + n) : 0.0f;
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) dot2_step(sum[j], cmp[j], a, b[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int n = n0 + (int)threadIdx.x + 256 * j;
+                if (n < n1) in.D[n] = __fadd_rn(sum[j], cmp[j]);
+            }
+        }
+    }
+}
+
 // Grouped split pre-pass: each job is a block of rows of one operand; the
 // threads of a CTA walk the job's rows as one flat range of 4-column groups
 // (padded rows are a multiple of 8 columns), so short rows still keep every
@@ -720,6 +804,7 @@ double item_cost(const Problem &p, const BItem &it) {
         return 1.0 + 0.26 * (double)((p.K + KB - 1) / KB) * TERMS * f;
     }
     case IT_CC: return 1.0 + 128.0 * 128.0 * (double)p.K / 79000.0;
+    case IT_GEMV: return 0.5 + (double)it.b * (double)p.K / 40000.0;
     default: return 0.5 + (double)it.b * (double)p.N * 4.0 / 43000.0;
     }
 }
@@ -778,6 +863,7 @@ struct moa_batch_plan {
     bool shapes_differ = false;    // some tile of tc_shaped is not 128 x 128
     int n_items = 0, n_jobs = 0;
     int n_grouped = 0, n_cc = 0;  // items in the grouped kernel / the CUDA-core kernels (set by the policy)
+    int n_gv = 0;                 // matrix-vector items (after the CUDA-core items in d_cc_items)
     int cc_off[kCcGroups] = {}, cc_cnt[kCcGroups] = {};  // CUDA-core items of each kernel in d_cc_items
     double work = 0.0;
     std::string signature;
@@ -792,8 +878,9 @@ struct moa_batch_plan {
     void *d_ws = nullptr;
     // graph
     cudaStream_t cap_stream = nullptr;
-    cudaStream_t side = nullptr;  // the split pre-pass runs here, beside the CUDA-core kernels
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t side = nullptr;  // the split pre-pass runs here, beside the CUDA-core kernels, then
+                                  // the matrix-vector kernel, beside the grouped kernel
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_gv = nullptr;
     // under the schedules that run the CUDA-core kernels side by side: their streams and join events
     cudaStream_t cc_streams[kCcGroups] = {};
     cudaEvent_t cc_join[kCcGroups] = {};
@@ -811,7 +898,8 @@ int cc_group(const moa_batch_plan &pl, const BItem &it) {
 }
 
 // The grouped kernel's queue and the CUDA-core kernels' queues for a policy.
-void order_items(const moa_batch_plan &pl, int policy, std::vector<BItem> &grouped, std::vector<BItem> &cc) {
+void order_items(const moa_batch_plan &pl, int policy, std::vector<BItem> &grouped, std::vector<BItem> &cc,
+                 std::vector<BItem> &gv) {
     const bool shaped = (policy & 2) != 0;
     std::vector<BItem> all;
     all.reserve(pl.items.size());
@@ -825,11 +913,17 @@ void order_items(const moa_batch_plan &pl, int policy, std::vector<BItem> &group
     std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost[a] > cost[b]; });
     grouped.clear();
     cc.clear();
+    gv.clear();
     std::vector<int> tc, ccs, other;
-    for (int i : idx) (all[i].type == IT_TC ? tc : all[i].type == IT_CC ? ccs : other).push_back(i);
+    for (int i : idx) {
+        if (all[i].type == IT_GEMV)
+            gv.push_back(all[i]);  // the matrix-vector kernel's queue, longest first
+        else
+            (all[i].type == IT_TC ? tc : all[i].type == IT_CC ? ccs : other).push_back(i);
+    }
     if ((policy & 1) == 0) {
         for (int i : idx)
-            if (all[i].type != IT_CC) grouped.push_back(all[i]);
+            if (all[i].type != IT_CC && all[i].type != IT_GEMV) grouped.push_back(all[i]);
     } else {
         for (int i : tc) grouped.push_back(all[i]);
         for (int i : other) grouped.push_back(all[i]);
@@ -840,13 +934,15 @@ void order_items(const moa_batch_plan &pl, int policy, std::vector<BItem> &group
 }
 
 moa_status upload_order(moa_batch_plan *pl, int policy, cudaStream_t s) {
-    std::vector<BItem> grouped, cc;
-    order_items(*pl, policy, grouped, cc);
+    std::vector<BItem> grouped, cc, gv;
+    order_items(*pl, policy, grouped, cc, gv);
     pl->policy_now = policy;
     pl->n_grouped = (int)grouped.size();
     pl->n_cc = (int)cc.size();
+    pl->n_gv = (int)gv.size();
     for (int g = 0; g < kCcGroups; ++g) pl->cc_cnt[g] = 0;
     for (const BItem &it : cc) ++pl->cc_cnt[cc_group(*pl, it)];
+    cc.insert(cc.end(), gv.begin(), gv.end());  // the matrix-vector items follow the CUDA-core tiles
     for (int g = 0, off = 0; g < kCcGroups; ++g) pl->cc_off[g] = off, off += pl->cc_cnt[g];
     if (!grouped.empty() && cudaMemcpyAsync(pl->d_items, grouped.data(), grouped.size() * sizeof(BItem),
                                             cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -869,15 +965,15 @@ cudaError_t enqueue(moa_batch_plan *pl, cudaStream_t s) {
             attr = true;
         }
     }
-    if (pl->n_grouped > 0 || pl->n_cc > 0) {
-        cudaError_t e = cudaMemsetAsync(pl->d_queue, 0, (1 + kCcGroups) * sizeof(int), s);
+    if (pl->n_grouped > 0 || pl->n_cc > 0 || pl->n_gv > 0) {
+        cudaError_t e = cudaMemsetAsync(pl->d_queue, 0, (2 + kCcGroups) * sizeof(int), s);
         if (e != cudaSuccess) return e;
     }
     // the split pre-pass (memory bound) on the plan's side stream, beside the
     // CUDA-core kernels (ALU bound); the grouped kernel waits for both
     const bool fork = pl->n_jobs > 0 && pl->n_cc > 0;
     const bool cc_side_by_side = (pl->policy_now & 4) != 0;
-    if (fork || cc_side_by_side) {
+    if (fork || cc_side_by_side || pl->n_gv > 0) {
         const cudaError_t e = cudaEventRecord(pl->ev_fork, s);
         if (e != cudaSuccess) return e;
     }
@@ -887,6 +983,17 @@ cudaError_t enqueue(moa_batch_plan *pl, cudaStream_t s) {
         const int blocks = std::min(pl->n_jobs, sm_count_dev() * 8);
         batch_split_kernel<<<blocks, 256, 0, pl->side>>>(pl->d_jobs, pl->n_jobs);
         e = cudaEventRecord(pl->ev_join, pl->side);
+        if (e != cudaSuccess) return e;
+    }
+    // the matrix-vector items need nothing from the other kernels: on the side
+    // stream (after the split pass when it runs there), beside the grouped kernel
+    if (pl->n_gv > 0) {
+        cudaError_t e = fork ? cudaSuccess : cudaStreamWaitEvent(pl->side, pl->ev_fork, 0);
+        if (e != cudaSuccess) return e;
+        const int grid = std::min(sm_count_dev(), pl->n_gv);
+        batch_gemv_kernel<<<grid, 256, 0, pl->side>>>(pl->d_inst, pl->d_cc_items + pl->n_cc, pl->n_gv,
+                                                      pl->d_queue + 1 + kCcGroups);
+        e = cudaEventRecord(pl->ev_gv, pl->side);
         if (e != cudaSuccess) return e;
     }
     // one persistent kernel per (operator, occupied tile halves) present, each with its own queue;
@@ -934,6 +1041,10 @@ cudaError_t enqueue(moa_batch_plan *pl, cudaStream_t s) {
         BatchParams bp{pl->d_inst, pl->d_items, pl->n_grouped, pl->d_queue, pl->d_tmaps};
         const int grid = std::min(sm_count_dev(), std::max(1, pl->n_grouped));
         batch_grouped_kernel<<<grid, kThreads, SMEM, s>>>(bp);
+    }
+    if (pl->n_gv > 0) {
+        const cudaError_t e = cudaStreamWaitEvent(s, pl->ev_gv, 0);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
@@ -1031,6 +1142,7 @@ void plan_free(moa_batch_plan *pl) {
     }
     if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
     if (pl->ev_join) cudaEventDestroy(pl->ev_join);
+    if (pl->ev_gv) cudaEventDestroy(pl->ev_gv);
     cudaFree(pl->d_inst);
     cudaFree(pl->d_items);
     cudaFree(pl->d_cc_items);
@@ -1062,6 +1174,10 @@ moa_status moa_batch_plan_create(int count, const moa_problem *problems, moa_bat
             delete pl;
             return st;
         }
+        // a split-BF16x3 matrix-vector product: a tensor-core tile would be at most 1/64 full, so the
+        // CUDA cores take it directly from the FP32 operands (no split planes)
+        Problem &q = pl->probs[i];
+        if (q.type == IT_TC && (q.M == 1 || q.N == 1)) q.type = IT_GEMV;
     }
     // every problem well formed: then its operands and result must be memory of this device
     for (int i = 0; i < count; ++i) {
@@ -1141,6 +1257,17 @@ moa_status moa_batch_plan_create(int count, const moa_problem *problems, moa_bat
                 }
             pl->work += 2.0 * p.M * p.N * p.K;
             sig_tc += (uint64_t)p.M * p.N * p.K;
+        } else if (p.type == IT_GEMV) {  // about 64K products per item
+            if (p.N == 1) {
+                const int64_t rows = std::max<int64_t>(1, 65536 / p.K);
+                for (int64_t r = 0; r < p.M; r += rows)
+                    pl->items.push_back(BItem{i, IT_GEMV, (int)r, (int)std::min(rows, p.M - r), GV_ROWS});
+            } else {
+                for (int64_t c = 0; c < p.N; c += 1024)  // four columns per thread of the matrix-vector kernel
+                    pl->items.push_back(BItem{i, IT_GEMV, (int)c, (int)std::min<int64_t>(1024, p.N - c), GV_COLS});
+            }
+            pl->work += 2.0 * p.M * p.N * p.K;
+            sig_tc += (uint64_t)p.M * p.N * p.K;
         } else if (p.type == IT_CC) {
             for (int tm = 0; tm < (p.M + 127) / 128; ++tm)
                 for (int tn = 0; tn < (p.N + 127) / 128; ++tn) pl->items.push_back(BItem{i, IT_CC, tm, tn});
@@ -1171,7 +1298,7 @@ moa_status moa_batch_plan_create(int count, const moa_problem *problems, moa_bat
               cudaMalloc(&pl->d_cc_items, std::max<size_t>(1, pl->items.size()) * sizeof(BItem)) == cudaSuccess &&
               cudaMalloc(&pl->d_tmaps, std::max<size_t>(1, tmaps.size()) * sizeof(CUtensorMap)) == cudaSuccess &&
               cudaMalloc(&pl->d_jobs, std::max<size_t>(1, jobs.size()) * sizeof(SplitJob)) == cudaSuccess &&
-              cudaMalloc(&pl->d_queue, (1 + kCcGroups) * sizeof(int)) == cudaSuccess;
+              cudaMalloc(&pl->d_queue, (2 + kCcGroups) * sizeof(int)) == cudaSuccess;  // grouped, CUDA-core, matrix-vector
     if (!ok) {
         cudaGetLastError();
         plan_free(pl);
@@ -1183,7 +1310,8 @@ moa_status moa_batch_plan_create(int count, const moa_problem *problems, moa_bat
     if (!ok || cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&pl->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming) != cudaSuccess || !make_cc_streams(pl)) {
+        cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pl->ev_gv, cudaEventDisableTiming) != cudaSuccess || !make_cc_streams(pl)) {
         plan_free(pl);
         return MOA_ERR_CUDA;
     }
@@ -1231,15 +1359,15 @@ moa_status moa_batch_plan_info(const moa_batch_plan *plan, int64_t *n_problems, 
     if (!plan) return MOA_ERR_NULL;
     if (n_problems) *n_problems = plan->count;
     if (n_launches) {  // before the first execute: the default schedule (CUDA-core items in their own kernel)
-        int64_t cc = 0;
-        for (const BItem &it : plan->items) cc += it.type == IT_CC;
-        const int64_t grouped = plan->n_items - cc;
+        int64_t cc = 0, gv = 0;
+        for (const BItem &it : plan->items) cc += it.type == IT_CC, gv += it.type == IT_GEMV;
+        const int64_t grouped = plan->n_items - cc - gv;
         bool used[kCcGroups] = {};  // one CUDA-core kernel per (operator, tile halves) present
         for (const BItem &it : plan->items)
             if (it.type == IT_CC) used[cc_group(*plan, it)] = true;
         int ops = 0;
         for (bool u : used) ops += u;
-        *n_launches = (plan->n_jobs > 0 ? 1 : 0) + (grouped > 0 ? 1 : 0) + ops;
+        *n_launches = (plan->n_jobs > 0 ? 1 : 0) + (grouped > 0 ? 1 : 0) + (gv > 0 ? 1 : 0) + ops;
     }
     if (n_tiles) *n_tiles = plan->n_items;
     if (work_flops) *work_flops = plan->work;
