@@ -584,7 +584,15 @@ __global__ void __launch_bounds__(256, 8)
             for (int r = it.a + warp; r < it.a + it.b; r += 8) {
                 float sum = 0.0f, cmp = 0.0f;
                 const float *arow = in.A + (int64_t)r * K;
-                for (int64_t k = lane; k < K; k += 32) dot2_step(sum, cmp, __ldg(arow + k), __ldg(in.B + k));
+                int64_t k = lane;
+                for (; k + 96 < K; k += 128) {  // four steps (eight loads) in flight
+                    float a[4], b[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) a[u] = __ldg(arow + k + 32 * u), b[u] = __ldg(in.B + k + 32 * u);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) dot2_step(sum, cmp, a[u], b[u]);
+                }
+                for (; k < K; k += 32) dot2_step(sum, cmp, __ldg(arow + k), __ldg(in.B + k));
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1)
                     dot2_merge(sum, cmp, __shfl_xor_sync(0xffffffffu, sum, o), __shfl_xor_sync(0xffffffffu, cmp, o));
@@ -594,17 +602,31 @@ __global__ void __launch_bounds__(256, 8)
             // columns n0 + threadIdx.x + 256 j, j < 4 (those below the item's end)
             const int n0 = it.a, n1 = it.a + it.b;
             float sum[4] = {0.0f, 0.0f, 0.0f, 0.0f}, cmp[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-            for (int64_t k = 0; k < K; ++k) {
-                const float a = __ldg(in.A + k);
+            auto row_of_b = [&](int64_t k, float (&b)[4]) {
                 const float *brow = in.B + k * N;
-                float b[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const int n = n0 + (int)threadIdx.x + 256 * j;
                     b[j] = n < n1 ? __ldg(brow + n) : 0.0f;
                 }
+            };
+            int64_t k = 0;
+            for (; k + 2 <= K; k += 2) {  // two rows of B (eight loads) in flight
+                float b0[4], b1[4];
+                row_of_b(k, b0);
+                row_of_b(k + 1, b1);
+                const float a0 = __ldg(in.A + k), a1 = __ldg(in.A + k + 1);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) dot2_step(sum[j], cmp[j], a, b[j]);
+                for (int j = 0; j < 4; ++j) dot2_step(sum[j], cmp[j], a0, b0[j]);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) dot2_step(sum[j], cmp[j], a1, b1[j]);
+            }
+            if (k < K) {
+                float b0[4];
+                row_of_b(k, b0);
+                const float a0 = __ldg(in.A + k);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) dot2_step(sum[j], cmp[j], a0, b0[j]);
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
