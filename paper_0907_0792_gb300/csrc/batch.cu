@@ -59,7 +59,7 @@ __device__ uint32_t g_batch_status;
 namespace {
 
 enum ItemType { IT_TC = 0, IT_CC = 1, IT_OUT = 2, IT_FILL = 3, IT_GEMV = 4 };
-// IT_GEMV: a split-BF16x3 (+,*) problem with M = 1 or N = 1, on the CUDA cores
+// IT_GEMV: a split-BF16x3 (+,*) or CUDA-core semiring problem with M = 1 or N = 1, on the CUDA cores
 // (shape GV_ROWS: rows [a, a + b) of an N = 1 product, one warp per row;
 // GV_COLS: columns [a, a + b) of an M = 1 product, one thread per column)
 constexpr int GV_ROWS = 1, GV_COLS = 2;
@@ -561,6 +561,44 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+// A semiring matrix-vector item (a CUDA-core problem with M = 1 or N = 1):
+// one warp per row, the lanes' partial reductions combined across the warp
+// (min / max are exact in any order; the (+,*) form stays within its FP32
+// bound), or four columns per thread for M = 1.
+template <class Op>
+__device__ __forceinline__ void gemv_semiring(const BInst &in, const BItem &it, int lane, int warp) {
+    const int64_t K = in.K, N = in.N;
+    if (it.shape == GV_ROWS) {
+        for (int r = it.a + warp; r < it.a + it.b; r += 8) {
+            float acc = Op::identity();
+            const float *arow = in.A + (int64_t)r * K;
+            for (int64_t k = lane; k < K; k += 32) acc = Op::step(acc, __ldg(arow + k), __ldg(in.B + k));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc = Op::red(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+            if (lane == 0) in.D[r] = acc;
+        }
+    } else {
+        const int n0 = it.a, n1 = it.a + it.b;
+        float acc[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[j] = Op::identity();
+        for (int64_t k = 0; k < K; ++k) {
+            const float a = __ldg(in.A + k);
+            const float *brow = in.B + k * N;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int n = n0 + (int)threadIdx.x + 256 * j;
+                if (n < n1) acc[j] = Op::step(acc[j], a, __ldg(brow + n));
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + (int)threadIdx.x + 256 * j;
+            if (n < n1) in.D[n] = acc[j];
+        }
+    }
+}
+
 // Matrix-vector items (split-BF16x3 problems with M = 1 or N = 1) on their
 // own: a persistent kernel of 256 threads and at most 32 registers per SM, so
 // that it fits beside the grouped kernel and runs while the tensor cores do.
@@ -580,7 +618,15 @@ __global__ void __launch_bounds__(256, 8)
         const BItem it = items[i];
         const BInst in = inst[it.inst];
         const int64_t K = in.K, N = in.N;
-        if (it.shape == GV_ROWS) {
+        if (in.op >= 0) {  // a CUDA-core semiring problem
+            switch (in.op) {
+            case CC_MIN_PLUS: gemv_semiring<sr::F32MinPlus>(in, it, lane, warp); break;
+            case CC_MAX_PLUS: gemv_semiring<sr::F32MaxPlus>(in, it, lane, warp); break;
+            case CC_MIN_TIMES: gemv_semiring<sr::F32MinTimes>(in, it, lane, warp); break;
+            case CC_MAX_TIMES: gemv_semiring<sr::F32MaxTimes>(in, it, lane, warp); break;
+            default: gemv_semiring<sr::F32PlusTimes>(in, it, lane, warp); break;
+            }
+        } else if (it.shape == GV_ROWS) {
             for (int r = it.a + warp; r < it.a + it.b; r += 8) {
                 float sum = 0.0f, cmp = 0.0f;
                 const float *arow = in.A + (int64_t)r * K;
@@ -1196,10 +1242,14 @@ moa_status moa_batch_plan_create(int count, const moa_problem *problems, moa_bat
             delete pl;
             return st;
         }
-        // a split-BF16x3 matrix-vector product: a tensor-core tile would be at most 1/64 full, so the
-        // CUDA cores take it directly from the FP32 operands (no split planes)
+        // a matrix-vector product: a tile would be at most 1/64 (tensor cores) or 1/128 (CUDA cores)
+        // full, so the thin-item kernel takes it straight from the FP32 operands (no split planes);
+        // op -1 marks the split-BF16x3 (+,*) form, otherwise the CUDA-core operator
         Problem &q = pl->probs[i];
-        if (q.type == IT_TC && (q.M == 1 || q.N == 1)) q.type = IT_GEMV;
+        if ((q.type == IT_TC || q.type == IT_CC) && (q.M == 1 || q.N == 1)) {
+            if (q.type == IT_TC) q.op = -1;
+            q.type = IT_GEMV;
+        }
     }
     // every problem well formed: then its operands and result must be memory of this device
     for (int i = 0; i < count; ++i) {

@@ -43,6 +43,7 @@ MOA_DEV void fma2(float x, float y0, float y1, float &c0, float &c1) {
 struct F32PlusTimes {
     using T = float;
     static MOA_DEV float identity() { return 0.0f; }
+    static MOA_DEV float red(float x, float y) { return __fadd_rn(x, y); }
     static MOA_DEV float step(float acc, float a, float b) { return fmaf(a, b, acc); }
     static MOA_DEV float step2(float acc, float a0, float b0, float a1, float b1) {
         return fmaf(a1, b1, fmaf(a0, b0, acc));
