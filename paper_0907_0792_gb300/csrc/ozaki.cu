@@ -188,20 +188,21 @@ int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
 
 }  // namespace
 
-// k-blocks of 64 per chunk of the contraction: 8 (MOA_OZAKI_CHUNK
-// overrides, 1..16); an accumulator takes 16 / chunk slice pairs of a chunk,
-// so it holds at most 1024 products of 2^14.  Measured at 8192^3 on one box,
-// two runs each: chunk 16 (one pair per accumulator) 51.5-52.0 effective
-// TFLOP/s at a 1702 MHz median clock, chunk 8 (two pairs) 54.3-54.5 at
-// 1826-1905 MHz (less DRAM traffic, so more of the power budget for the
-// SMs), chunk 4 (four pairs) 52.0-52.4.
-int ozaki_chunk() {
+// k-blocks of 64 per chunk of the contraction: 16 up to K = 6144, 8 above
+// (MOA_OZAKI_CHUNK overrides, 1..16); an accumulator takes 16 / chunk slice
+// pairs of a chunk, so it holds at most 1024 products of 2^14.  Measured on
+// one box, effective FP64 TFLOP/s, chunk 8 / 16: n = 2048 35.7 / 37.1, 3072
+// 46.1 / 47.9, 4096 59.6 / 61.6, 6144 69.0 / 70.3; at 8192 (power capped)
+// chunk 8 72.3 against 69.7 for 16, since the shorter chunk's smaller working
+// set cuts DRAM traffic and leaves more of the power budget to the SMs
+// (earlier, with 7 slices: 16 51.5-52.0, 8 54.3-54.5, 4 52.0-52.4).
+int ozaki_chunk(int64_t K) {
     static const int forced = [] {
         const char *e = std::getenv("MOA_OZAKI_CHUNK");
         const int v = e ? std::atoi(e) : 0;
         return (v < 1 || v > kChunkKBlocks) ? 0 : v;
     }();
-    return forced ? forced : 8;
+    return forced ? forced : (K <= 6144 ? 16 : 8);
 }
 
 // Slices per operand for a contraction of length K (MOA_OZAKI_SLICES overrides, 4..10).
@@ -252,7 +253,7 @@ moa_status tc_inner_ozaki(const double *A, const double *B, double *D, int64_t M
     if (cudaGetLastError() != cudaSuccess) return MOA_ERR_CUDA;
     // accumulator units 2^-lsb with lsb = (S + 1) beta: every kept pair weight 2^(lsb - (s+u+2) beta) >= 1
     const int lsb = (S + 1) * kBeta;
-    const int chunk = ozaki_chunk();
+    const int chunk = ozaki_chunk(K);
     return tc_gemm_ozaki(a, Kp, b, Np, S, kBeta, lsb, chunk, kChunkKBlocks / chunk, rmax, cmax, D, N, M, N, K, rs, s);
 }
 
@@ -296,7 +297,7 @@ moa_status ozaki_rows(const double *A, int64_t M, const OzakiB &ob, double *D, v
     if (!run_slices<true>(A, M, K, Kp, rmax, S, a, s)) return MOA_ERR_INTERNAL;
     if (cudaGetLastError() != cudaSuccess) return MOA_ERR_CUDA;
     const int lsb = (S + 1) * kBeta;
-    const int chunk = ozaki_chunk();
+    const int chunk = ozaki_chunk(K);
     return tc_gemm_ozaki(a, Kp, ob.planes, round8(N), S, kBeta, lsb, chunk, kChunkKBlocks / chunk, rmax, ob.cmax, D, N,
                          M, N, K, rs, s);
 }
