@@ -351,6 +351,15 @@ moa_status moa_selftest_wait_timeout(uint32_t limit_us, moa_stream stream);
 moa_status moa_kernel_timing(int enable);
 moa_status moa_kernel_timing_read(int64_t *launches, double *total_ms);
 
+/*
+ * moa_ozaki_slices — the number of digit slices per operand the OZAKI form
+ * takes for a contraction of length K (its slice-pair GEMM does
+ * S (S + 1) / 2 products), after any MOA_OZAKI_SLICES override; 0 for
+ * K < 0.  Host-side query, no device work.  Diagnostic only (no counterpart
+ * in the paper).
+ */
+int moa_ozaki_slices(int64_t K);
+
 /* Free the scratch workspace held for every stream of the current device (synchronises). */
 moa_status moa_release_workspace(void);
 

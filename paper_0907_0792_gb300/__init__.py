@@ -22,7 +22,7 @@ __all__ = [
     "moa_device_status", "moa_release_workspace", "moa_version", "inner", "outer", "OPS", "DTYPES", "FORMS",
     "moa_batch_plan_create", "moa_batch_execute", "moa_batch_plan_destroy", "moa_batch_plan_info", "MoaProblem",
     "moa_inner_bf16x3_noalloc", "NOALLOC_SCRATCH_BYTES", "make_problems", "moa_selftest_wait_timeout",
-    "moa_inner_host", "moa_kernel_timing", "moa_kernel_timing_read", "moa_inner_e4m3_scaled",
+    "moa_inner_host", "moa_kernel_timing", "moa_kernel_timing_read", "moa_inner_e4m3_scaled", "moa_ozaki_slices",
 ]
 
 # size of the fixed device buffer behind moa_inner_bf16x3_noalloc (MOA_NOALLOC_SCRATCH_BYTES)
@@ -73,6 +73,8 @@ def lib():
         L.moa_inner_e4m3_scaled.argtypes = [I, _I64P, P, P, I, _I64P, P, P, P, V]
         L.moa_kernel_timing.argtypes = [I]
         L.moa_kernel_timing_read.argtypes = [C.POINTER(I64), C.POINTER(C.c_double)]
+        L.moa_ozaki_slices.argtypes = [I64]
+        L.moa_ozaki_slices.restype = C.c_int
         L.moa_transpose.argtypes = [I, I, _I64P, C.POINTER(C.c_int), P, P, V]
         L.moa_inner_shape.argtypes = [I, _I64P, I, _I64P, C.POINTER(C.c_int), _I64P]
         L.moa_outer_shape.argtypes = [I, _I64P, I, _I64P, C.POINTER(C.c_int), _I64P]
@@ -178,6 +180,11 @@ def moa_inner_e4m3_scaled(shapeA, A, scale_a, shapeB, B, scale_b, out, stream=No
 def moa_kernel_timing(enable: bool):
     """Start (True) or stop (False) CUDA-event timing of the library's GEMM launches."""
     _check(lib().moa_kernel_timing(1 if enable else 0), "moa_kernel_timing")
+
+
+def moa_ozaki_slices(K: int) -> int:
+    """Digit slices per operand the Ozaki form takes for a contraction of length K."""
+    return int(lib().moa_ozaki_slices(int(K)))
 
 
 def moa_kernel_timing_read():

@@ -216,6 +216,8 @@ int ozaki_slices(int64_t K) {
     return K <= 64 ? 10 : (K <= 256 ? 8 : (K < 4096 ? 7 : 6));
 }
 
+extern "C" int moa_ozaki_slices(int64_t K) { return K < 0 ? 0 : ozaki_slices(K); }
+
 size_t ozaki_workspace_bytes(int64_t M, int64_t N, int64_t K) {
     return (size_t)ozaki_slices(K) * (size_t)(M * round8(K) + K * round8(N)) * 2 + (size_t)(M + N) * 8 +
            pair_ozaki_scratch_bytes() + 256;

@@ -223,6 +223,23 @@ def test_host_entry_and_timing_validation(L):
     assert e4((0, 5), (5, 7), A=0, out=0) == 0
 
 
+def test_ozaki_slice_count_matches_the_bench(L, monkeypatch):
+    """The slice count the library's Ozaki form takes (a host-side query) is
+    the one bench.py's roofline counts slice products with, at every
+    threshold of the rule; and the int32 class-sum bound S K 2^14 < 2^31 holds
+    up to the longest contraction the form accepts."""
+    monkeypatch.delenv("MOA_OZAKI_SLICES", raising=False)
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_for_abi", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    for K in (1, 2, 63, 64, 65, 255, 256, 257, 1024, 4095, 4096, 4097, 8192, 16384, 21845):
+        assert moa.moa_ozaki_slices(K) == bench.ozaki_slices(K), K
+        S = moa.moa_ozaki_slices(K)
+        assert S * K * 16384 < 2 ** 31 or K > 21845
+    assert moa.moa_ozaki_slices(-1) == 0
+
+
 def test_status_strings(L):
     assert moa.moa_status_string(0) == "ok"
     assert "shape" in moa.moa_status_string(3)
