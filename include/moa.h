@@ -302,7 +302,7 @@ moa_status moa_batch_plan_create(int count, const moa_problem *problems, moa_bat
  * execute times the plan's schedules on `stream` (the choice is cached per
  * GPU and plan signature in $MOA_TUNE_CACHE, default
  * ~/.cache/moa_autotune.txt; MOA_AUTOTUNE=off|cached|force,
- * MOA_BATCH_SCHEDULE=0..7 fixes one) and records the chosen launch
+ * MOA_BATCH_SCHEDULE=0..15 fixes one) and records the chosen launch
  * sequence into a CUDA graph; every execute then launches that graph on
  * `stream`.  Problems write disjoint outputs.
  */

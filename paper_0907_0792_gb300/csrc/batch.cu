@@ -618,7 +618,17 @@ __global__ void __launch_bounds__(256, 8)
         const BItem it = items[i];
         const BInst in = inst[it.inst];
         const int64_t K = in.K, N = in.N;
-        if (in.op >= 0) {  // a CUDA-core semiring problem
+        if (it.type == IT_OUT) {  // rows [a, a + b) of an outer product
+            const int64_t e0 = (int64_t)it.a * N, e1 = (int64_t)(it.a + it.b) * N;
+            for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+                const int64_t r = e / N;
+                in.D[e] = op_apply(in.op, __ldg(in.A + r), __ldg(in.B + (e - r * N)));
+            }
+        } else if (it.type == IT_FILL) {  // rows [a, a + b) of an empty contraction
+            const int64_t e0 = (int64_t)it.a * N, e1 = (int64_t)(it.a + it.b) * N;
+            const float v = __int_as_float(in.op);
+            for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) in.D[e] = v;
+        } else if (in.op >= 0) {  // a CUDA-core semiring problem
             switch (in.op) {
             case CC_MIN_PLUS: gemv_semiring<sr::F32MinPlus>(in, it, lane, warp); break;
             case CC_MAX_PLUS: gemv_semiring<sr::F32MaxPlus>(in, it, lane, warp); break;
@@ -912,10 +922,13 @@ int tune_mode() {  // 0 off, 1 cached, 2 force
 // box for problems with M <= 64 and a 128 x 64 last column tile where at most
 // 64 columns remain); bit 2 the CUDA-core kernels one after another on the
 // caller's stream (0) or side by side on streams of their own, the largest
-// first, so one kernel's tail overlaps the next (1).  Schedules with bit 1
-// exist only for plans where a tile changes shape, with bit 2 only for plans
-// with more than one CUDA-core kernel.
-constexpr int kPolicies = 8;
+// first, so one kernel's tail overlaps the next (1); bit 3 the outer-product
+// and fill items on the grouped kernel's epilogue warps (0) or in the
+// thin-item kernel beside it (1), away from the tensor-core tile epilogues.
+// Schedules with bit 1 exist only for plans where a tile changes shape, with
+// bit 2 only for plans with more than one CUDA-core kernel, with bit 3 only
+// for plans with outer-product or fill items.
+constexpr int kPolicies = 16;
 
 }  // namespace
 }  // namespace moa
@@ -983,15 +996,19 @@ void order_items(const moa_batch_plan &pl, int policy, std::vector<BItem> &group
     cc.clear();
     gv.clear();
     std::vector<int> tc, ccs, other;
+    const bool thin_out = (policy & 8) != 0;  // outer-product and fill items in the thin-item kernel
+    auto to_thin = [&](const BItem &it) {
+        return it.type == IT_GEMV || (thin_out && (it.type == IT_OUT || it.type == IT_FILL));
+    };
     for (int i : idx) {
-        if (all[i].type == IT_GEMV)
-            gv.push_back(all[i]);  // the matrix-vector kernel's queue, longest first
+        if (to_thin(all[i]))
+            gv.push_back(all[i]);  // the thin-item kernel's queue, longest first
         else
             (all[i].type == IT_TC ? tc : all[i].type == IT_CC ? ccs : other).push_back(i);
     }
     if ((policy & 1) == 0) {
         for (int i : idx)
-            if (all[i].type != IT_CC && all[i].type != IT_GEMV) grouped.push_back(all[i]);
+            if (all[i].type != IT_CC && !to_thin(all[i])) grouped.push_back(all[i]);
     } else {
         for (int i : tc) grouped.push_back(all[i]);
         for (int i : other) grouped.push_back(all[i]);
@@ -1119,12 +1136,13 @@ cudaError_t enqueue(moa_batch_plan *pl, cudaStream_t s) {
 
 moa_status autotune(moa_batch_plan *pl, cudaStream_t s) {
     const char *force = std::getenv("MOA_BATCH_SCHEDULE");  // a fixed schedule (0..kPolicies-1), no timing
-    if (force && force[0] >= '0' && force[0] < '0' + kPolicies && !force[1]) {
-        pl->policy = force[0] - '0';
+    const int forced = force && force[0] >= '0' && force[0] <= '9' ? std::atoi(force) : -1;
+    if (forced >= 0 && forced < kPolicies) {
+        pl->policy = forced;
         return upload_order(pl, pl->policy, s);
     }
     const int mode = tune_mode();
-    const std::string key = gpu_signature() + "|s6|" + pl->signature;  // s6: the schedules listed at kPolicies
+    const std::string key = gpu_signature() + "|s7|" + pl->signature;  // s7: the schedules listed at kPolicies
     if (mode == 0) {
         pl->policy = 0;
         return upload_order(pl, 0, s);
@@ -1145,6 +1163,8 @@ moa_status autotune(moa_batch_plan *pl, cudaStream_t s) {
     double best = 1e30;
     int best_pol = 0;
     int n_cc_kernels = 0;
+    bool has_out = false;
+    for (const BItem &it : pl->items) has_out |= it.type == IT_OUT || it.type == IT_FILL;
     {
         bool used[kCcGroups] = {};
         for (const BItem &it : pl->items)
@@ -1154,6 +1174,7 @@ moa_status autotune(moa_batch_plan *pl, cudaStream_t s) {
     for (int pol = 0; pol < kPolicies; ++pol) {
         if ((pol & 2) && !pl->shapes_differ) continue;  // the same tiles as pol & ~2
         if ((pol & 4) && n_cc_kernels < 2) continue;     // nothing to run side by side
+        if ((pol & 8) && !has_out) continue;             // no outer-product or fill item to move
         moa_status st = upload_order(pl, pol, s);
         if (st != MOA_OK) return st;
         float best_ms = 1e30f;

@@ -97,6 +97,37 @@ def test_batch_full_10000_sampled():
     check_status()
 
 
+@pytest.mark.parametrize("schedule", ["0", "8", "13"])
+def test_batch_outer_and_fill_items_every_schedule(schedule, monkeypatch):
+    """Outer products and empty contractions (identity fills) beside tensor-core
+    and CUDA-core problems, with those items on the grouped kernel's epilogue
+    warps (schedules without bit 3) or in the thin-item kernel (with it);
+    every output checked."""
+    import torch
+    monkeypatch.setenv("MOA_BATCH_SCHEDULE", schedule)
+    probs = [p for p in synth.batched_problems(200, seed=13, mn_octaves=8)][:120]
+    pool, oa, ob, od, dpool, dout, specs = _build(probs, seed=13)
+    # two empty contractions: (+,*) fills 0, (min,+) fills +inf
+    n_out = dout.numel()
+    dfill = torch.full((2 * 35,), float("nan"), dtype=torch.float32, device="cuda")
+    specs.append(dict(kind="inner", form="bf16x3", shapeA=(5, 0), shapeB=(0, 7), A=dpool.data_ptr(),
+                      B=dpool.data_ptr(), out=dfill.data_ptr()))
+    specs.append(dict(kind="inner", reduce="min", combine="add", shapeA=(5, 0), shapeB=(0, 7), A=dpool.data_ptr(),
+                      B=dpool.data_ptr(), out=dfill.data_ptr() + 4 * 35))
+    arr, keep = moa.make_problems(specs)
+    plan = moa.moa_batch_plan_create(arr)
+    try:
+        moa.moa_batch_execute(plan)
+        torch.cuda.synchronize()
+        _check(probs, pool, oa, ob, od, dout.cpu().numpy(), range(len(probs)), max_out=1 << 30)
+        fills = dfill.cpu().numpy()
+        assert np.all(fills[:35] == 0.0) and np.all(fills[35:] == np.inf)
+    finally:
+        moa.moa_batch_plan_destroy(plan)
+    assert n_out > 0
+    check_status()
+
+
 @pytest.mark.parametrize("schedule", ["0", "1", "2", "3", "4", "7"])
 def test_batch_tensor_core_tiles_every_schedule(schedule, monkeypatch):
     """Split-BF16x3 tiles under each schedule: ragged M, N and K (K % 32 != 0,
