@@ -38,6 +38,12 @@ moa_status tc_inner_f32(moa_form form, const float *A, const float *B, float *D,
                         cudaStream_t stream);
 // FP32 operands, FP32 out, e4m3 with per-128 power-of-two block scales.
 moa_status tc_inner_fp8(const float *A, const float *B, float *D, int64_t M, int64_t N, int64_t K, cudaStream_t stream);
+// ozaki_plan.cu — the Ozaki form's slices per operand for a contraction of
+// length K, k-blocks of 64 per exact chunk, and slice pairs per accumulator.
+int ozaki_slices(int64_t K);
+int ozaki_chunk(int64_t K);
+int ozaki_acc_pairs(int chunk);
+
 // FP64 operands, FP64 out, Ozaki-sliced on bf16 tensor cores.
 moa_status tc_inner_ozaki(const double *A, const double *B, double *D, int64_t M, int64_t N, int64_t K,
                           cudaStream_t stream);

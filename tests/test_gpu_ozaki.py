@@ -38,9 +38,13 @@ def test_ozaki_small(shA, shB, dist):
     check_status()
 
 
-def test_ozaki_zero_rows_columns_and_wide_range():
-    A = synth.uniform(42, 0, (70, 90), -1, 1)
-    B = synth.uniform(42, 1, (90, 50), -1, 1)
+@pytest.mark.parametrize("K", [90, 300, 4100])
+def test_ozaki_zero_rows_columns_and_wide_range(K):
+    """Zero rows and columns, scales 1e+-200, a subnormal, and digits that
+    carry into the top one, at 8 slices (K = 90), 7 (K = 300) and 6
+    (K = 4100; A's rows then take the single-pass row kernel)."""
+    A = synth.uniform(42, 0, (70, K), -1, 1)
+    B = synth.uniform(42, 1, (K, 50), -1, 1)
     A[3] = 0.0
     B[:, 7] = 0.0
     A[5] *= 1e200
@@ -48,7 +52,7 @@ def test_ozaki_zero_rows_columns_and_wide_range():
     A[6, 4] = 5e-310  # subnormal entry
     # entries just below a power of two: every lower digit of the scaled value is all ones, so the
     # balanced digits carry into the top one (which becomes 2^(beta-1))
-    A[8] = np.nextafter(1.0, 0.0) * np.where(np.arange(90) % 2, 1.0, -1.0)
+    A[8] = np.nextafter(1.0, 0.0) * np.where(np.arange(K) % 2, 1.0, -1.0)
     B[:, 11] = np.nextafter(0.5, 0.0)
     A[9, :] = np.nextafter(np.ldexp(1.0, -3), 0.0)
     D = _ozaki(A, B).cpu().numpy()
