@@ -80,6 +80,16 @@ __global__ void col_max_kernel(const double *__restrict__ B, int64_t K, int64_t 
     if (m) atomicMax((unsigned long long *)(out + j), (unsigned long long)m);
 }
 
+// B's column maxima into out (zeroed before): about eight blocks per SM
+void launch_col_max(const double *B, int64_t K, int64_t N, uint64_t *out, cudaStream_t s) {
+    const int64_t gx = (N + 255) / 256;
+    int64_t gy = (152 * 8 + gx - 1) / gx;
+    if (gy > K) gy = K;
+    const int64_t rpb = (K + gy - 1) / gy;
+    gy = (K + rpb - 1) / rpb;
+    col_max_kernel<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, s>>>(B, K, N, rpb, out);
+}
+
 // The S balanced digits of one element, signed like it: |x| = mant 2^ex,
 // scaled by 2^-e (|x| < 2^(e-1)).  The unsigned base-2^beta digits u_s of
 // the truncated |x| 2^-e (u_s = floor(|x| 2^(-e + (s+1) beta)) mod 2^beta,
@@ -369,14 +379,7 @@ moa_status tc_inner_ozaki(const double *A, const double *B, double *D, int64_t M
         row_max_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(A, M, K, rmax, cmax, N);
     }
     // B's column maxima
-    {
-        const int64_t gx = (N + 255) / 256;
-        int64_t gy = (152 * 8 + gx - 1) / gx;
-        if (gy > K) gy = K;
-        const int64_t rpb = (K + gy - 1) / gy;
-        gy = (K + rpb - 1) / rpb;
-        col_max_kernel<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, s>>>(B, K, N, rpb, cmax);
-    }
+    launch_col_max(B, K, N, cmax, s);
     // digit planes
     if ((!fused && !run_slices<true>(A, M, K, Kp, rmax, S, a, s)) || !run_slices<false>(B, K, N, Np, cmax, S, b, s))
         return MOA_ERR_INTERNAL;
@@ -404,12 +407,7 @@ moa_status ozaki_prepare_b(const double *B, int64_t K, int64_t N, void *ws, Ozak
     __nv_bfloat16 *b = (__nv_bfloat16 *)ws;
     uint64_t *cmax = (uint64_t *)(((uintptr_t)(b + (int64_t)S * K * Np) + 15) & ~(uintptr_t)15);
     if (launch_fill64(cmax, 0ull, N, s) != cudaSuccess) return MOA_ERR_CUDA;
-    const int64_t gx = (N + 255) / 256;
-    int64_t gy = (152 * 8 + gx - 1) / gx;
-    if (gy > K) gy = K;
-    const int64_t rpb = (K + gy - 1) / gy;
-    gy = (K + rpb - 1) / rpb;
-    col_max_kernel<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, s>>>(B, K, N, rpb, cmax);
+    launch_col_max(B, K, N, cmax, s);
     if (!run_slices<false>(B, K, N, Np, cmax, S, b, s)) return MOA_ERR_INTERNAL;
     if (cudaGetLastError() != cudaSuccess) return MOA_ERR_CUDA;
     *ob = OzakiB{b, cmax, S, K, N};
