@@ -167,6 +167,26 @@ MOA_DEV void dot2_merge(float &sum, float &cmp, float sum2, float cmp2) {
     cmp = __fadd_rn(__fadd_rn(cmp, cmp2), err);
 }
 
+// Rows [a, a + b) of an outer product's row-major result, D[r, c] = A[r] op
+// B[c], walked as one flat range by `nthreads` threads from `tid`; each
+// thread divides once and then steps its row and column by the stride, so no
+// element pays an integer division.  An item holds fewer than 2^31 elements
+// (rows of about 128K elements, or a single row).
+MOA_DEV void outer_rows(const BInst &in, const BItem &it, int tid, int nthreads) {
+    const int N = in.N, count = it.b * N;
+    if (tid >= count) return;
+    float *D = in.D + (int64_t)it.a * N;
+    const float *A = in.A + it.a;
+    int r = tid / N, c = tid - r * N;
+    const int dr = nthreads / N, dc = nthreads - dr * N;
+    for (int t = tid; t < count; t += nthreads) {
+        D[t] = op_apply(in.op, __ldg(A + r), __ldg(in.B + c));
+        r += dr;
+        c += dc;
+        if (c >= N) c -= N, ++r;
+    }
+}
+
 // One 128 x 128 CUDA-core tile of D = reduce_p(A combine B), 256 threads.
 // The panels of A (transposed to [k][m]) and B ([k][n]) stream through four
 // shared-memory stages by 4-byte cp.async copies, three panels ahead of the
@@ -539,11 +559,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 }
             } else if (it.type == IT_OUT) {
-                const int64_t N = in.N, e0 = (int64_t)it.a * N, e1 = (int64_t)(it.a + it.b) * N;
-                for (int64_t e = e0 + etid; e < e1; e += kEpiThreads) {
-                    const int64_t i = e / N;
-                    in.D[e] = op_apply(in.op, __ldg(in.A + i), __ldg(in.B + (e - i * N)));
-                }
+                outer_rows(in, it, etid, kEpiThreads);
             } else {  // IT_FILL
                 const int64_t e0 = (int64_t)it.a * in.N, e1 = (int64_t)(it.a + it.b) * in.N;
                 const float v = __int_as_float(in.op);
@@ -561,54 +577,133 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-// A semiring matrix-vector item (a CUDA-core problem with M = 1 or N = 1):
-// one warp per row, the lanes' partial reductions combined across the warp
-// (min / max are exact in any order; the (+,*) form stays within its FP32
-// bound), or four columns per thread for M = 1.
-template <class Op>
-__device__ __forceinline__ void gemv_semiring(const BInst &in, const BItem &it, int lane, int warp) {
-    const int64_t K = in.K, N = in.N;
-    if (it.shape == GV_ROWS) {
-        for (int r = it.a + warp; r < it.a + it.b; r += 8) {
-            float acc = Op::identity();
+// Accumulators of the matrix-vector items: a compensated FP32 dot product
+// (Dot2) for split-BF16x3 problems, a semiring reduction for CUDA-core ones.
+// Partial accumulators of one output are merged in a fixed order, so a graph
+// replay gives the same bits.
+struct Dot2Acc {
+    float s = 0.0f, c = 0.0f;
+    MOA_DEV void step(float a, float b) { dot2_step(s, c, a, b); }
+    MOA_DEV void merge(const Dot2Acc &o) { dot2_merge(s, c, o.s, o.c); }
+    MOA_DEV Dot2Acc shfl_xor(int o) const {
+        Dot2Acc r;
+        r.s = __shfl_xor_sync(0xffffffffu, s, o);
+        r.c = __shfl_xor_sync(0xffffffffu, c, o);
+        return r;
+    }
+    MOA_DEV float result() const { return __fadd_rn(s, c); }
+    MOA_DEV void put(float2 *slot) const { *slot = make_float2(s, c); }
+    MOA_DEV static Dot2Acc get(const float2 *slot) {
+        Dot2Acc r;
+        r.s = slot->x, r.c = slot->y;
+        return r;
+    }
+};
+template <class Op> struct SemiringAcc {
+    float v = Op::identity();
+    MOA_DEV void step(float a, float b) { v = Op::step(v, a, b); }
+    MOA_DEV void merge(const SemiringAcc &o) { v = Op::red(v, o.v); }
+    MOA_DEV SemiringAcc shfl_xor(int o) const {
+        SemiringAcc r;
+        r.v = __shfl_xor_sync(0xffffffffu, v, o);
+        return r;
+    }
+    MOA_DEV float result() const { return v; }
+    MOA_DEV void put(float2 *slot) const { slot->x = v; }
+    MOA_DEV static SemiringAcc get(const float2 *slot) {
+        SemiringAcc r;
+        r.v = slot->x;
+        return r;
+    }
+};
+
+// Columns of one matrix-vector item at most (M = 1 items); the CTA's other
+// threads split the contraction.
+constexpr int kGvCols = 128;
+
+// Rows [a, a + b) of an N = 1 product, D[r] = A[r, :] . B[:, 0]: W lanes per
+// row (a power of two, about K / 8, at most 32) striding along the
+// contraction, four loads of each in flight, so a warp takes 32 / W rows at
+// once and short contractions still keep every lane busy; the W partial
+// accumulators of a row are merged by shuffles.
+template <class Acc>
+MOA_DEV void gemv_rows(const BInst &in, const BItem &it) {
+    const int64_t K = in.K;
+    int W = 1;
+    while (W < 32 && 8 * (int64_t)(2 * W) <= K) W *= 2;
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, li = lane % W, G = 32 / W;
+    const int r_end = it.a + it.b;
+    for (int r0 = it.a + warp * G; r0 < r_end; r0 += 8 * G) {  // uniform over the warp
+        const int r = r0 + lane / W;
+        Acc acc;
+        if (r < r_end) {
             const float *arow = in.A + (int64_t)r * K;
-            for (int64_t k = lane; k < K; k += 32) acc = Op::step(acc, __ldg(arow + k), __ldg(in.B + k));
+            int64_t k = li;
+            for (; k + 3 * W < K; k += 4 * W) {
+                float a[4], b[4];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc = Op::red(acc, __shfl_xor_sync(0xffffffffu, acc, o));
-            if (lane == 0) in.D[r] = acc;
-        }
-    } else {
-        const int n0 = it.a, n1 = it.a + it.b;
-        float acc[4];
+                for (int u = 0; u < 4; ++u) a[u] = __ldg(arow + k + u * W), b[u] = __ldg(in.B + k + u * W);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[j] = Op::identity();
-        for (int64_t k = 0; k < K; ++k) {
-            const float a = __ldg(in.A + k);
-            const float *brow = in.B + k * N;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int n = n0 + (int)threadIdx.x + 256 * j;
-                if (n < n1) acc[j] = Op::step(acc[j], a, __ldg(brow + n));
+                for (int u = 0; u < 4; ++u) acc.step(a[u], b[u]);
             }
+            for (; k < K; k += W) acc.step(__ldg(arow + k), __ldg(in.B + k));
         }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int n = n0 + (int)threadIdx.x + 256 * j;
-            if (n < n1) in.D[n] = acc[j];
-        }
+        for (int o = W / 2; o > 0; o >>= 1) acc.merge(acc.shfl_xor(o));
+        if (r < r_end && li == 0) in.D[r] = acc.result();
     }
 }
 
-// Matrix-vector items (split-BF16x3 problems with M = 1 or N = 1) on their
-// own: a persistent kernel of 256 threads and at most 32 registers per SM, so
+// Columns [a, a + b) (b <= kGvCols) of an M = 1 product, D[n] = A[0, :] .
+// B[:, n]: Cw threads across the columns (a power of two >= b) and 256 / Cw
+// slices of the contraction, four loads in flight each; the slices' partial
+// accumulators are merged by shuffles within a warp and then, in warp order,
+// through shared memory.
+template <class Acc>
+MOA_DEV void gemv_cols(const BInst &in, const BItem &it, float2 *stash) {
+    const int64_t K = in.K, N = in.N;
+    int Cw = 1;
+    while (Cw < it.b) Cw *= 2;
+    const int KS = 256 / Cw, cc = threadIdx.x % Cw, kk = threadIdx.x / Cw;
+    const int64_t n = it.a + cc;
+    Acc acc;
+    if (cc < it.b) {
+        int64_t k = kk;
+        for (; k + 3 * KS < K; k += 4 * KS) {
+            float a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[u] = __ldg(in.A + k + u * KS), b[u] = __ldg(in.B + (k + u * KS) * N + n);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc.step(a[u], b[u]);
+        }
+        for (; k < K; k += KS) acc.step(__ldg(in.A + k), __ldg(in.B + k * N + n));
+    }
+    for (int o = 16; o >= Cw; o >>= 1) acc.merge(acc.shfl_xor(o));  // the warp's slices of column cc
+    acc.put(stash + threadIdx.x);
+    __syncthreads();
+    if ((int)threadIdx.x < Cw && cc < it.b) {  // kk == 0
+        const int parts = Cw < 32 ? 8 : KS, stride = Cw < 32 ? 32 : Cw;
+        for (int q = 1; q < parts; ++q) acc.merge(Acc::get(stash + q * stride + cc));
+        in.D[n] = acc.result();
+    }
+    __syncthreads();
+}
+
+template <class Acc>
+MOA_DEV void gemv_item(const BInst &in, const BItem &it, float2 *stash) {
+    if (it.shape == GV_ROWS) gemv_rows<Acc>(in, it);
+    else gemv_cols<Acc>(in, it, stash);
+}
+
+// The thin items on their own: matrix-vector items (split-BF16x3 or CUDA-core
+// semiring problems with M = 1 or N = 1) and, under schedule bit 3,
+// outer-product rows and fills.  A persistent kernel of one CTA per SM: 256
+// threads of at most 40 registers (with the grouped kernel's 576 threads of
+// 96 they fill the 64K-register file exactly) and 2 KB of shared memory, so
 // that it fits beside the grouped kernel and runs while the tensor cores do.
-// N = 1 items: one warp per row, the lanes striding along the contraction,
-// the warp's partial sums merged by TwoSum.  M = 1 items: four columns per
-// thread (four loads of B in flight each step), A's element read by all.
-__global__ void __launch_bounds__(256, 8)
+__global__ void __launch_bounds__(256, 6)
     batch_gemv_kernel(const BInst *__restrict__ inst, const BItem *__restrict__ items, int n_items, int *queue) {
     __shared__ int s_next;
-    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+    __shared__ float2 stash[256];
     for (;;) {
         if (threadIdx.x == 0) s_next = atomicAdd(queue, 1);
         __syncthreads();
@@ -617,77 +712,20 @@ __global__ void __launch_bounds__(256, 8)
         if (i >= n_items) break;
         const BItem it = items[i];
         const BInst in = inst[it.inst];
-        const int64_t K = in.K, N = in.N;
-        if (it.type == IT_OUT) {  // rows [a, a + b) of an outer product
-            const int64_t e0 = (int64_t)it.a * N, e1 = (int64_t)(it.a + it.b) * N;
-            for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-                const int64_t r = e / N;
-                in.D[e] = op_apply(in.op, __ldg(in.A + r), __ldg(in.B + (e - r * N)));
-            }
+        if (it.type == IT_OUT) {
+            outer_rows(in, it, threadIdx.x, blockDim.x);
         } else if (it.type == IT_FILL) {  // rows [a, a + b) of an empty contraction
-            const int64_t e0 = (int64_t)it.a * N, e1 = (int64_t)(it.a + it.b) * N;
+            const int64_t e0 = (int64_t)it.a * in.N, e1 = (int64_t)(it.a + it.b) * in.N;
             const float v = __int_as_float(in.op);
             for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) in.D[e] = v;
-        } else if (in.op >= 0) {  // a CUDA-core semiring problem
-            switch (in.op) {
-            case CC_MIN_PLUS: gemv_semiring<sr::F32MinPlus>(in, it, lane, warp); break;
-            case CC_MAX_PLUS: gemv_semiring<sr::F32MaxPlus>(in, it, lane, warp); break;
-            case CC_MIN_TIMES: gemv_semiring<sr::F32MinTimes>(in, it, lane, warp); break;
-            case CC_MAX_TIMES: gemv_semiring<sr::F32MaxTimes>(in, it, lane, warp); break;
-            default: gemv_semiring<sr::F32PlusTimes>(in, it, lane, warp); break;
-            }
-        } else if (it.shape == GV_ROWS) {
-            for (int r = it.a + warp; r < it.a + it.b; r += 8) {
-                float sum = 0.0f, cmp = 0.0f;
-                const float *arow = in.A + (int64_t)r * K;
-                int64_t k = lane;
-                for (; k + 96 < K; k += 128) {  // four steps (eight loads) in flight
-                    float a[4], b[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) a[u] = __ldg(arow + k + 32 * u), b[u] = __ldg(in.B + k + 32 * u);
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) dot2_step(sum, cmp, a[u], b[u]);
-                }
-                for (; k < K; k += 32) dot2_step(sum, cmp, __ldg(arow + k), __ldg(in.B + k));
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1)
-                    dot2_merge(sum, cmp, __shfl_xor_sync(0xffffffffu, sum, o), __shfl_xor_sync(0xffffffffu, cmp, o));
-                if (lane == 0) in.D[r] = __fadd_rn(sum, cmp);
-            }
         } else {
-            // columns n0 + threadIdx.x + 256 j, j < 4 (those below the item's end)
-            const int n0 = it.a, n1 = it.a + it.b;
-            float sum[4] = {0.0f, 0.0f, 0.0f, 0.0f}, cmp[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-            auto row_of_b = [&](int64_t k, float (&b)[4]) {
-                const float *brow = in.B + k * N;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int n = n0 + (int)threadIdx.x + 256 * j;
-                    b[j] = n < n1 ? __ldg(brow + n) : 0.0f;
-                }
-            };
-            int64_t k = 0;
-            for (; k + 2 <= K; k += 2) {  // two rows of B (eight loads) in flight
-                float b0[4], b1[4];
-                row_of_b(k, b0);
-                row_of_b(k + 1, b1);
-                const float a0 = __ldg(in.A + k), a1 = __ldg(in.A + k + 1);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) dot2_step(sum[j], cmp[j], a0, b0[j]);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) dot2_step(sum[j], cmp[j], a1, b1[j]);
-            }
-            if (k < K) {
-                float b0[4];
-                row_of_b(k, b0);
-                const float a0 = __ldg(in.A + k);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) dot2_step(sum[j], cmp[j], a0, b0[j]);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int n = n0 + (int)threadIdx.x + 256 * j;
-                if (n < n1) in.D[n] = __fadd_rn(sum[j], cmp[j]);
+            switch (in.op) {
+            case -1: gemv_item<Dot2Acc>(in, it, stash); break;  // split-BF16x3 (+,*)
+            case CC_MIN_PLUS: gemv_item<SemiringAcc<sr::F32MinPlus>>(in, it, stash); break;
+            case CC_MAX_PLUS: gemv_item<SemiringAcc<sr::F32MaxPlus>>(in, it, stash); break;
+            case CC_MIN_TIMES: gemv_item<SemiringAcc<sr::F32MinTimes>>(in, it, stash); break;
+            case CC_MAX_TIMES: gemv_item<SemiringAcc<sr::F32MaxTimes>>(in, it, stash); break;
+            default: gemv_item<SemiringAcc<sr::F32PlusTimes>>(in, it, stash); break;
             }
         }
     }
@@ -1356,8 +1394,8 @@ moa_status moa_batch_plan_create(int count, const moa_problem *problems, moa_bat
                 for (int64_t r = 0; r < p.M; r += rows)
                     pl->items.push_back(BItem{i, IT_GEMV, (int)r, (int)std::min(rows, p.M - r), GV_ROWS});
             } else {
-                for (int64_t c = 0; c < p.N; c += 1024)  // four columns per thread of the matrix-vector kernel
-                    pl->items.push_back(BItem{i, IT_GEMV, (int)c, (int)std::min<int64_t>(1024, p.N - c), GV_COLS});
+                for (int64_t c = 0; c < p.N; c += kGvCols)
+                    pl->items.push_back(BItem{i, IT_GEMV, (int)c, (int)std::min<int64_t>(kGvCols, p.N - c), GV_COLS});
             }
             pl->work += 2.0 * p.M * p.N * p.K;
             sig_tc += (uint64_t)p.M * p.N * p.K;

@@ -131,12 +131,15 @@ def test_batch_outer_and_fill_items_every_schedule(schedule, monkeypatch):
 @pytest.mark.parametrize("schedule", ["0", "1", "2", "3", "4", "7"])
 def test_batch_tensor_core_tiles_every_schedule(schedule, monkeypatch):
     """Split-BF16x3 tiles under each schedule: ragged M, N and K (K % 32 != 0,
-    K < 32, K = 1), M = 1 and N = 1 problems, narrow last column tiles, K past
-    one promotion block; every output checked."""
+    K < 32, K = 1), M = 1 and N = 1 problems (matrix-vector items with one to
+    32 lanes per row and one to 128 columns per item), narrow last column
+    tiles, K past one promotion block; every output checked."""
     import torch
     monkeypatch.setenv("MOA_BATCH_SCHEDULE", schedule)
     shapes = [(1, 1, 1), (1, 37, 200), (130, 8, 1), (129, 45, 64), (257, 300, 190), (64, 129, 65), (200, 97, 33),
-              (3, 513, 7), (140, 31, 250), (128, 128, 128)]
+              (3, 513, 7), (140, 31, 250), (128, 128, 128),
+              # matrix-vector items: many column blocks, one-lane and eight-lane rows, a one-column last block
+              (1, 512, 2048), (2048, 8, 1), (500, 100, 1), (1, 3, 129), (1, 1000, 33)]
     probs = []
     for M, K, N in shapes:
         probs.append({"kind": "bf16x3", "shapeA": (M, K), "shapeB": (K, N), "M": M, "K": K, "N": N})
@@ -156,13 +159,14 @@ def test_batch_tensor_core_tiles_every_schedule(schedule, monkeypatch):
 @pytest.mark.parametrize("schedule", ["0", "1", "2", "3", "4", "7"])
 def test_batch_every_cuda_core_operator_and_schedule(schedule, monkeypatch):
     """Every CUDA-core (reduce, combine) of the batch, tiles with one, two or
-    four occupied halves and several tiles per problem, under each schedule."""
+    four occupied halves and several tiles per problem, and M = 1 / N = 1
+    problems (matrix-vector items), under each schedule."""
     import torch
     monkeypatch.setenv("MOA_BATCH_SCHEDULE", schedule)
     ops = [("min", "add", "tropical"), ("max", "add", "tropical"), ("min", "mul", "maxmul"), ("max", "mul", "maxmul"),
            ("add", "mul", "maxmul")]
     shapes = [((40, 33), (33, 50)), ((100, 70), (70, 30)), ((20, 90), (90, 200)), ((300, 17), (17, 140)),
-              ((1, 5), (5, 1))]
+              ((1, 5), (5, 1)), ((1, 300), (300, 70)), ((90, 40), (40, 1))]
     cases, chunks, off = [], [], 0
     for t, (red, comb, kind) in enumerate(ops):
         for u, (sa, sb) in enumerate(shapes):
