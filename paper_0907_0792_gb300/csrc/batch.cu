@@ -732,46 +732,49 @@ __global__ void __launch_bounds__(256, 6)
 }
 
 // Grouped split pre-pass: each job is a block of rows of one operand; the
-// threads of a CTA walk the job's rows as one flat range of 4-column groups
+// threads of a CTA walk the job's rows as one flat range of 8-column groups
 // (padded rows are a multiple of 8 columns), so short rows still keep every
-// thread busy; each group is one 16-byte load where the source row allows it
-// and one 8-byte store per plane.
+// thread busy.  A group is two 16-byte loads where the source row allows it
+// (cols % 4 == 0: each 4-column half lies wholly inside the row or wholly in
+// its padding) and one 16-byte store per plane (plane rows start on 16-byte
+// boundaries); each thread has two groups' loads in flight before it stores.
 __global__ void __launch_bounds__(256) batch_split_kernel(const SplitJob *__restrict__ jobs, int n_jobs) {
     for (int j = blockIdx.x; j < n_jobs; j += gridDim.x) {
         const SplitJob jb = jobs[j];
-        const int gpr = (int)(jb.colsp / 4);  // colsp < 2^31 (checked at plan creation)
-        const int count = (int)((jb.r1 - jb.r0) * gpr);  // <= ~16K + one row
+        const int gpr = (int)(jb.colsp / 8);  // colsp < 2^31 (checked at plan creation)
+        const int count = (int)((jb.r1 - jb.r0) * gpr);  // <= ~8K + one row
         const bool vec = (jb.cols & 3) == 0 && ((uintptr_t)jb.src & 15) == 0;
-        auto load = [&](int e, float (&x)[4]) {
-            const int rr = e / gpr, c = (e - rr * gpr) * 4;
+        auto load = [&](int e, float (&x)[8]) {
+            const int rr = e / gpr, c = (e - rr * gpr) * 8;
             const float *src = jb.src + (jb.r0 + rr) * jb.cols + c;
             if (vec) {
-                const float4 v = c < jb.cols ? __ldg(reinterpret_cast<const float4 *>(src)) : make_float4(0, 0, 0, 0);
-                x[0] = v.x, x[1] = v.y, x[2] = v.z, x[3] = v.w;
+                const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                const float4 v0 = c < jb.cols ? __ldg(reinterpret_cast<const float4 *>(src)) : z;
+                const float4 v1 = c + 4 < jb.cols ? __ldg(reinterpret_cast<const float4 *>(src + 4)) : z;
+                x[0] = v0.x, x[1] = v0.y, x[2] = v0.z, x[3] = v0.w, x[4] = v1.x, x[5] = v1.y, x[6] = v1.z, x[7] = v1.w;
             } else {
 #pragma unroll
-                for (int t = 0; t < 4; ++t) x[t] = c + t < jb.cols ? __ldg(src + t) : 0.0f;
+                for (int t = 0; t < 8; ++t) x[t] = c + t < jb.cols ? __ldg(src + t) : 0.0f;
             }
         };
-        auto split_store = [&](int e, const float (&x)[4]) {
-            const int rr = e / gpr, c = (e - rr * gpr) * 4;
-            __align__(8) __nv_bfloat16 hi[4], mid[4], lo[4];
+        auto split_store = [&](int e, const float (&x)[8]) {
+            const int rr = e / gpr, c = (e - rr * gpr) * 8;
+            __align__(16) __nv_bfloat16 hi[8], mid[8], lo[8];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
+            for (int t = 0; t < 8; ++t) {
                 hi[t] = __float2bfloat16_rn(x[t]);
                 const float r1 = __fsub_rn(x[t], __bfloat162float(hi[t]));
                 mid[t] = __float2bfloat16_rn(r1);
                 lo[t] = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(mid[t])));
             }
             __nv_bfloat16 *dst = jb.dst + (jb.r0 + rr) * jb.colsp + c;
-            *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(hi);
-            *reinterpret_cast<uint2 *>(dst + jb.plane) = *reinterpret_cast<const uint2 *>(mid);
-            *reinterpret_cast<uint2 *>(dst + 2 * jb.plane) = *reinterpret_cast<const uint2 *>(lo);
+            *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(hi);
+            *reinterpret_cast<uint4 *>(dst + jb.plane) = *reinterpret_cast<const uint4 *>(mid);
+            *reinterpret_cast<uint4 *>(dst + 2 * jb.plane) = *reinterpret_cast<const uint4 *>(lo);
         };
-        // two groups per pass, both loads in flight before the stores
         for (int e = threadIdx.x; e < count; e += 2 * blockDim.x) {
             const int e1 = e + blockDim.x;
-            float x0[4], x1[4];
+            float x0[8], x1[8];
             load(e, x0);
             if (e1 < count) load(e1, x1);
             split_store(e, x0);
