@@ -40,29 +40,33 @@ template <typename Tin> MOA_DEV float to_f32(Tin x) { return (float)x; }
 template <> MOA_DEV float to_f32<__nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
 
 // X: rows x cols (row stride cols); out: NPL planes of rows x colsp, plane
-// stride plane_elems; columns cols..colsp-1 are zero.  Four consecutive
-// columns per thread (colsp is a multiple of 8): one 16-byte load when the
-// rows allow it (VEC) and one 8-byte store per plane.
+// stride plane_elems; columns cols..colsp-1 are zero.  Eight consecutive
+// columns per thread (colsp is a multiple of 8, so every plane row starts on
+// a 16-byte boundary): two 16-byte loads when the rows allow it (VEC: float
+// rows, cols % 4 == 0, 16-byte aligned; each 4-column half is then wholly
+// inside the row or wholly in its padding) and one 16-byte store per plane.
 template <typename Tin, int NPL, bool VEC>
 __global__ void __launch_bounds__(256) split_planes(const Tin *__restrict__ X, int64_t rows, int64_t cols, int64_t colsp,
                                                      __nv_bfloat16 *__restrict__ out, int64_t plane_elems) {
-    const int64_t groups = colsp / 4;
+    const int64_t groups = colsp / 8;
     for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
         const Tin *src = X + r * cols;
         __nv_bfloat16 *dst = out + r * colsp;
         for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += (int64_t)gridDim.x * blockDim.x) {
-            const int64_t c = 4 * g;
-            float x[4];
-            if constexpr (VEC) {  // float rows, cols % 4 == 0, 16-byte aligned: the group is all in or all out
-                const float4 v = c < cols ? __ldg(reinterpret_cast<const float4 *>(src + c)) : make_float4(0, 0, 0, 0);
-                x[0] = v.x, x[1] = v.y, x[2] = v.z, x[3] = v.w;
+            const int64_t c = 8 * g;
+            float x[8];
+            if constexpr (VEC) {
+                const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                const float4 v0 = c < cols ? __ldg(reinterpret_cast<const float4 *>(src + c)) : z;
+                const float4 v1 = c + 4 < cols ? __ldg(reinterpret_cast<const float4 *>(src + c + 4)) : z;
+                x[0] = v0.x, x[1] = v0.y, x[2] = v0.z, x[3] = v0.w, x[4] = v1.x, x[5] = v1.y, x[6] = v1.z, x[7] = v1.w;
             } else {
 #pragma unroll
-                for (int t = 0; t < 4; ++t) x[t] = c + t < cols ? to_f32(src[c + t]) : 0.0f;
+                for (int t = 0; t < 8; ++t) x[t] = c + t < cols ? to_f32(src[c + t]) : 0.0f;
             }
-            __align__(8) __nv_bfloat16 pl[NPL][4];
+            __align__(16) __nv_bfloat16 pl[NPL][8];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
+            for (int t = 0; t < 8; ++t) {
                 const __nv_bfloat16 hi = __float2bfloat16_rn(x[t]);
                 pl[0][t] = hi;
                 if constexpr (NPL > 1) {
@@ -74,7 +78,7 @@ __global__ void __launch_bounds__(256) split_planes(const Tin *__restrict__ X, i
             }
 #pragma unroll
             for (int q = 0; q < NPL; ++q)
-                *reinterpret_cast<uint2 *>(dst + q * plane_elems + c) = *reinterpret_cast<const uint2 *>(pl[q]);
+                *reinterpret_cast<uint4 *>(dst + q * plane_elems + c) = *reinterpret_cast<const uint4 *>(pl[q]);
         }
     }
 }
@@ -128,7 +132,7 @@ cudaError_t run_i8range(const int32_t *X, int64_t rows, int64_t cols, int64_t co
 template <typename Tin, int NPL>
 cudaError_t run_split(const Tin *X, int64_t rows, int64_t cols, int64_t colsp, __nv_bfloat16 *out, cudaStream_t s) {
     if (rows == 0 || colsp == 0) return cudaSuccess;
-    const int64_t groups = colsp / 4;
+    const int64_t groups = colsp / 8;
     const int64_t gx = groups >= 256 * 4 ? 4 : (groups + 255) / 256;
     int64_t gy = rows < 2048 ? rows : 2048;
     const dim3 grid((unsigned)gx, (unsigned)gy);
@@ -143,25 +147,28 @@ cudaError_t run_split(const Tin *X, int64_t rows, int64_t cols, int64_t colsp, _
 
 // X (rows x cols, float or fp16) -> fp16 rows x colsp (zero columns past
 // cols): RNE rounding of FP32 values with the magnitude held at 65504, or a
-// copy of fp16 values.  Four consecutive columns per thread, one 16-byte
-// load when the float rows allow it (VEC: cols % 4 == 0, 16-byte aligned X).
+// copy of fp16 values.  Eight consecutive columns per thread and one 16-byte
+// store (colsp is a multiple of 8); two 16-byte loads when the float rows
+// allow it (VEC: cols % 4 == 0, 16-byte aligned X).
 template <typename Tin, bool VEC>
 __global__ void __launch_bounds__(256) to_f16_rows(const Tin *__restrict__ X, int64_t rows, int64_t cols, int64_t colsp,
                                                     __half *__restrict__ out) {
-    const int64_t groups = colsp / 4;
+    const int64_t groups = colsp / 8;
     for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
         const Tin *src = X + r * cols;
         for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += (int64_t)gridDim.x * blockDim.x) {
-            const int64_t c = 4 * g;
-            __align__(8) __half y[4];
-            if constexpr (VEC) {  // the group is all in or all out
-                const float4 v = c < cols ? __ldg(reinterpret_cast<const float4 *>(src + c)) : make_float4(0, 0, 0, 0);
-                const float x[4] = {v.x, v.y, v.z, v.w};
+            const int64_t c = 8 * g;
+            __align__(16) __half y[8];
+            if constexpr (VEC) {  // each 4-column half is all in or all out
+                const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                const float4 v0 = c < cols ? __ldg(reinterpret_cast<const float4 *>(src + c)) : z;
+                const float4 v1 = c + 4 < cols ? __ldg(reinterpret_cast<const float4 *>(src + c + 4)) : z;
+                const float x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
 #pragma unroll
-                for (int t = 0; t < 4; ++t) y[t] = __float2half_rn(fminf(fmaxf(x[t], -65504.0f), 65504.0f));
+                for (int t = 0; t < 8; ++t) y[t] = __float2half_rn(fminf(fmaxf(x[t], -65504.0f), 65504.0f));
             } else {
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
+                for (int t = 0; t < 8; ++t) {
                     if constexpr (std::is_same<Tin, float>::value) {
                         const float x = c + t < cols ? src[c + t] : 0.0f;
                         y[t] = __float2half_rn(fminf(fmaxf(x, -65504.0f), 65504.0f));
@@ -170,7 +177,7 @@ __global__ void __launch_bounds__(256) to_f16_rows(const Tin *__restrict__ X, in
                     }
                 }
             }
-            *reinterpret_cast<uint2 *>(out + r * colsp + c) = *reinterpret_cast<const uint2 *>(y);
+            *reinterpret_cast<uint4 *>(out + r * colsp + c) = *reinterpret_cast<const uint4 *>(y);
         }
     }
 }
@@ -178,7 +185,7 @@ __global__ void __launch_bounds__(256) to_f16_rows(const Tin *__restrict__ X, in
 template <typename Tin>
 cudaError_t run_to_f16(const Tin *X, int64_t rows, int64_t cols, int64_t colsp, __half *out, cudaStream_t s) {
     if (rows == 0 || colsp == 0) return cudaSuccess;
-    const int64_t groups = colsp / 4;
+    const int64_t groups = colsp / 8;
     const int64_t gx = groups >= 256 * 4 ? 4 : (groups + 255) / 256;
     const dim3 grid((unsigned)gx, (unsigned)(rows < 2048 ? rows : 2048));
     if (std::is_same<Tin, float>::value && cols % 4 == 0 && (uintptr_t)X % 16 == 0)
