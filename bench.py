@@ -58,16 +58,17 @@ def kernel_source_hash() -> str:
     return h.hexdigest()
 
 
-def _ncu_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
-    None when there is none or the kernel's sources changed since it was taken."""
-    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+def _ncu_traffic(kernel: str, n: int, path=None):
+    """DRAM bytes per launch of `kernel` on the n x n x n product from the
+    committed ncu summary, or None when there is none for that size or the
+    kernel's sources changed since it was taken."""
+    p = path or os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(p) as f:
             rec = json.load(f).get(kernel)
     except (OSError, ValueError):
         return None
-    if not rec or rec.get("source_sha256") != kernel_source_hash():
+    if not rec or rec.get("n") != n or rec.get("source_sha256") != kernel_source_hash():
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -772,7 +773,7 @@ def main():
     achieved = slice_flops / (gemm_ms * 1e-3) / 1e12
     kname = "tc_gemm_pair<3>"
     roofline = {"bound": "tensor", "achieved": round(achieved, 1), "peak": peak_tc, "unit": "TFLOP/s",
-                "frac": round(achieved / peak_tc, 3), "traffic": _ncu_traffic(kname),
+                "frac": round(achieved / peak_tc, 3), "traffic": _ncu_traffic(kname, n),
                 "kernel": kname, "kernel_ms": round(gemm_ms, 4), "kernel_launches": gemm_launches,
                 "work": f"{S * (S + 1) // 2} bf16 slice products of 2 n^3 flop (S = {S} slices per operand)",
                 "algorithmic_bytes": 2 * S * n * n * 2 + n * n * 8,

@@ -74,3 +74,21 @@ def test_reference_arm_nonzero_ranks_do_nothing():
     rank, n = q.get(timeout=120)
     p.join(timeout=60)
     assert p.exitcode == 0 and n == 0
+
+
+def test_recorded_traffic_only_for_its_size_and_sources(tmp_path):
+    """The roofline's DRAM traffic comes from the committed ncu record only for
+    the product size it was captured on and while the kernel's sources hash
+    to the recorded value; anything else reports null."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    rec = {"tc_gemm_pair<3>": {"n": 8192, "source_sha256": bench.kernel_source_hash(), "dram_bytes_per_launch": 123}}
+    p = tmp_path / "traffic.json"
+    p.write_text(json.dumps(rec))
+    assert bench._ncu_traffic("tc_gemm_pair<3>", 8192, path=str(p)) == 123
+    assert bench._ncu_traffic("tc_gemm_pair<3>", 1024, path=str(p)) is None
+    assert bench._ncu_traffic("tc_gemm_pair<0>", 8192, path=str(p)) is None
+    rec["tc_gemm_pair<3>"]["source_sha256"] = "0" * 64
+    p.write_text(json.dumps(rec))
+    assert bench._ncu_traffic("tc_gemm_pair<3>", 8192, path=str(p)) is None
