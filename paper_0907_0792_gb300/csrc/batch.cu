@@ -696,10 +696,12 @@ MOA_DEV void gemv_item(const BInst &in, const BItem &it, float2 *stash) {
 
 // The thin items on their own: matrix-vector items (split-BF16x3 or CUDA-core
 // semiring problems with M = 1 or N = 1) and, under schedule bit 3,
-// outer-product rows and fills.  A persistent kernel of one CTA per SM: 256
-// threads of at most 40 registers (with the grouped kernel's 576 threads of
-// 96 they fill the 64K-register file exactly) and 2 KB of shared memory, so
-// that it fits beside the grouped kernel and runs while the tensor cores do.
+// outer-product rows and fills.  A persistent kernel of one CTA per SM (256
+// threads, at most 40 registers, 2 KB of shared memory) on the side stream:
+// it needs nothing from the split planes, so its CTAs take SMs while the
+// CUDA-core kernels and the split pass run and as the grouped kernel's CTAs
+// leave (a grouped CTA, 608 threads of 96 registers, leaves too few registers
+// for one of these beside it), all of them pulling work from queues.
 __global__ void __launch_bounds__(256, 6)
     batch_gemv_kernel(const BInst *__restrict__ inst, const BItem *__restrict__ items, int n_items, int *queue) {
     __shared__ int s_next;
@@ -1001,7 +1003,7 @@ struct moa_batch_plan {
     // graph
     cudaStream_t cap_stream = nullptr;
     cudaStream_t side = nullptr;  // the split pre-pass runs here, beside the CUDA-core kernels, then
-                                  // the matrix-vector kernel, beside the grouped kernel
+                                  // the thin-item kernel, sharing the SMs with the others
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_gv = nullptr;
     // under the schedules that run the CUDA-core kernels side by side: their streams and join events
     cudaStream_t cc_streams[kCcGroups] = {};
@@ -1111,8 +1113,8 @@ cudaError_t enqueue(moa_batch_plan *pl, cudaStream_t s) {
         e = cudaEventRecord(pl->ev_join, pl->side);
         if (e != cudaSuccess) return e;
     }
-    // the matrix-vector items need nothing from the other kernels: on the side
-    // stream (after the split pass when it runs there), beside the grouped kernel
+    // the thin items need nothing from the other kernels: on the side stream
+    // (after the split pass when it runs there), beside the others
     if (pl->n_gv > 0) {
         cudaError_t e = fork ? cudaSuccess : cudaStreamWaitEvent(pl->side, pl->ev_fork, 0);
         if (e != cudaSuccess) return e;
