@@ -696,7 +696,7 @@ MOA_DEV void gemv_item(const BInst &in, const BItem &it, float2 *stash) {
 
 // The thin items on their own: matrix-vector items (split-BF16x3 or CUDA-core
 // semiring problems with M = 1 or N = 1) and, under schedule bit 3,
-// outer-product rows and fills.  A persistent kernel of one CTA per SM (256
+// outer-product rows and fills.  A persistent kernel of two CTAs per SM (256
 // threads, at most 40 registers, 2 KB of shared memory) on the side stream:
 // it needs nothing from the split planes, so its CTAs take SMs while the
 // CUDA-core kernels and the split pass run and as the grouped kernel's CTAs
@@ -1118,7 +1118,7 @@ cudaError_t enqueue(moa_batch_plan *pl, cudaStream_t s) {
     if (pl->n_gv > 0) {
         cudaError_t e = fork ? cudaSuccess : cudaStreamWaitEvent(pl->side, pl->ev_fork, 0);
         if (e != cudaSuccess) return e;
-        const int grid = std::min(sm_count_dev(), pl->n_gv);
+        const int grid = std::min(2 * sm_count_dev(), pl->n_gv);
         batch_gemv_kernel<<<grid, 256, 0, pl->side>>>(pl->d_inst, pl->d_cc_items + pl->n_cc, pl->n_gv,
                                                       pl->d_queue + 1 + kCcGroups);
         e = cudaEventRecord(pl->ev_gv, pl->side);
